@@ -1,0 +1,152 @@
+/*
+ * nlse.h -- C ABI of libnlse, a GB300 (sm_103a) CUDA library that integrates
+ * the nonlinear Schroedinger / Gross-Pitaevskii equation
+ *
+ *     i Psi_t + a Lap(Psi) - V Psi + s |Psi|^2 Psi = 0,      a > 0   (Eq. NLSE, Sec. 1)
+ *
+ * on 1D/2D/3D grids with the explicit classic RK4 integrator (Eq. RK4, Sec. 3.1)
+ * and the two-step high-order compact (2SHOC) Laplacian of Caplan and
+ * Carretero-Gonzalez, arXiv 1109.1027 (Secs. 2.1-2.3, single-storage form).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: n[0] (x, fastest), n[1] (y), n[2] (z) points per axis, boundary
+ *    points included, one spacing h for every axis (Secs. 2.1-2.3); the first
+ *    and last index on every active axis are boundary points.  Storage is
+ *    row-major with x contiguous: p = x + n[0] * (y + n[1] * z).
+ *  - Psi is interleaved complex: complex64 (float re, float im) when
+ *    prec == NLSE_FP32, complex128 when prec == NLSE_FP64.  V is real, float
+ *    or double to match.  All pointers named *_dev are device pointers; the
+ *    caller owns them.  Device pointers must be 16-byte aligned.
+ *  - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on the stream and return without synchronising, except
+ *    where stated (nlse_invariants, nlse_check, and the stability check of
+ *    nlse_run).
+ *  - Every call returns an nlse_status.  Nothing aborts, throws or traps on
+ *    the device.  nlse_last_error() describes the last failure of the calling
+ *    thread.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef NLSE_H
+#define NLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NLSE_OK = 0,
+    NLSE_EINVAL = 1,        /* invalid argument or parameter                         */
+    NLSE_ENOMEM = 2,        /* device or host allocation failed                      */
+    NLSE_ECUDA = 3,         /* a CUDA runtime call failed (message in nlse_last_error) */
+    NLSE_EUNSTABLE = 4,     /* dt exceeds the stability bound of Eq. (kdfull)        */
+    NLSE_ENONFINITE = 5,    /* a NaN or Inf appeared in the state                    */
+    NLSE_ETIMEOUT = 6,      /* a bounded device-side wait gave up                    */
+    NLSE_EUNSUPPORTED = 7   /* valid request that this build does not implement      */
+} nlse_status;
+
+/* Boundary conditions of Sec. 3.2. */
+typedef enum {
+    NLSE_BC_DIRICHLET = 0,  /* Eqs. (dbc_lap), (dbc_ut): Psi_t = 0 on the boundary   */
+    NLSE_BC_MSD = 1         /* Eqs. (msdbc_ut), (msdbc_lap): |Psi|^2 held constant   */
+} nlse_bc;
+
+/* Arithmetic of the state and the stencil. */
+typedef enum {
+    NLSE_FP32 = 0,          /* complex64 state with a compensated (Kahan) low part;
+                               mass, energy and the stability bound in FP64           */
+    NLSE_FP64 = 1           /* complex128 throughout                                  */
+} nlse_prec;
+
+/* Laplacian inside F (Sec. 3.1 names both). */
+typedef enum {
+    NLSE_LAP_2SHOC = 0,     /* fourth-order 2SHOC, Secs. 2.1-2.3 (single storage)    */
+    NLSE_LAP_CD = 1         /* second-order central difference, Eq. (dx2)            */
+} nlse_lap;
+
+/* nlse_params.flags */
+#define NLSE_FLAG_NO_STABILITY_CHECK 1u  /* nlse_run skips the entry check of dt  */
+
+typedef struct {
+    int dim;                /* 1, 2 or 3                                              */
+    int64_t n[3];           /* points per axis incl. boundary; n[d] >= 3 for d < dim  */
+    double h;               /* grid spacing, > 0                                      */
+    double dt;              /* RK4 time step k, > 0                                   */
+    double a;               /* dispersion coefficient, > 0                            */
+    double s;               /* nonlinearity coefficient (any sign)                    */
+    int bc;                 /* nlse_bc                                                */
+    int prec;               /* nlse_prec                                              */
+    int lap;                /* nlse_lap                                               */
+    unsigned flags;         /* NLSE_FLAG_*                                            */
+} nlse_params;
+
+typedef struct nlse_ctx nlse_ctx;
+
+/* Creates a solver context for one grid on the current CUDA device.
+ * V_dev: the potential V (float for FP32, double for FP64), borrowed: it must
+ * stay valid and unchanged while the context is used.  The context allocates
+ * its own device work space: two stage buffers, the RK4 accumulator, the
+ * compensated low part of the FP32 state (zeroed here) and the reduction
+ * buffers.  Returns NLSE_EINVAL for dim outside 1..3, n < 3 on an active axis,
+ * h, dt or a not positive and finite, or an unknown bc / prec / lap. */
+int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out);
+
+/* Releases the context and its device memory (synchronises the device). */
+void nlse_destroy(nlse_ctx* ctx);
+
+/* 2SHOC Laplacian (or CD, per params.lap) of psi into lap_dev (same layout).
+ * Step 1 is the second-order D (Eqs. 2shoc1d, 2d2shocs1, 3d2shocs), step 2
+ * re-differences it (Eqs. 2shoc1d2, 2d2shocs2, 3d2shocs2).  Boundary points
+ * receive the step-1 boundary value D_b of Sec. 3.2 (Eq. dbc_lap, or Eq.
+ * msdbc_lap for MSD), which the paper states also serves as the boundary of
+ * the whole Laplacian.  psi_dev and lap_dev must not overlap. */
+int nlse_lap2shoc(nlse_ctx* ctx, const void* psi_dev, void* lap_dev, void* stream);
+
+/* One classic RK4 step of size params.dt (Eq. RK4), in place on psi_dev, with
+ * F(Psi) = i[a Lap Psi + (s|Psi|^2 - V) Psi] (Sec. 3.1) and the boundary rule
+ * of Sec. 3.2 for F at boundary points.  Four fused stage kernels.  In FP32
+ * the state is psi_dev plus the context's compensated low part, which is reset
+ * to zero whenever psi_dev differs from the previous call's pointer or
+ * nlse_reset_compensation() is called. */
+int nlse_rk4_step(nlse_ctx* ctx, void* psi_dev, void* stream);
+
+/* nsteps RK4 steps in place (same arithmetic as nsteps calls of
+ * nlse_rk4_step), replayed from a CUDA graph captured on first use for this
+ * psi_dev.  Unless NLSE_FLAG_NO_STABILITY_CHECK is set, first evaluates the
+ * bound of Eq. (kdfull) on the current state (synchronising the stream) and
+ * returns NLSE_EUNSTABLE without stepping when dt exceeds it. */
+int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
+
+/* Mass M = h^d sum |Psi|^2, energy
+ * E = h^d sum_interior [ -a Re(conj(Psi) Lap Psi) + V |Psi|^2 - (s/2)|Psi|^4 ]
+ * (the paper defines neither; this is the discrete Hamiltonian of Eq. NLSE)
+ * and the time-step bound of Eq. (kdfull),
+ *   dt_max = sqrt(8) h^2 / (a max{ ||B||_inf, max_{i, g in G} |L_i - g| }),
+ *   L_i = (h^2/a)(s|Psi_i|^2 - V_i), G from the Table of Sec. 3.3 (t:sumresults),
+ *   B from Table t:bc2 (0 for Dirichlet),
+ * all accumulated in FP64 on the device from the state (plus the FP32
+ * compensated part when psi_dev is the context's current state).  Synchronises
+ * the stream and writes the three host doubles (any may be NULL).  Returns
+ * NLSE_ENONFINITE when the state holds a NaN or Inf. */
+int nlse_invariants(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy,
+                    double* dt_max, void* stream);
+
+/* Zeroes the FP32 compensated low part (call after writing psi externally). */
+int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
+
+/* Synchronises the stream and reports NLSE_ENONFINITE if any RK4 step since
+ * the last check produced a NaN or Inf (a device flag set by the last stage
+ * kernel); clears the flag. */
+int nlse_check(nlse_ctx* ctx, void* stream);
+
+/* Human-readable description of the calling thread's last error ("" if none). */
+const char* nlse_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLSE_H */

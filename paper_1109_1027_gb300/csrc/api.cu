@@ -1,0 +1,356 @@
+// api.cu -- the C ABI of libnlse (include/nlse.h): parameter validation,
+// context and work-space ownership, the RK4 stage schedule, CUDA-graph replay
+// of the time loop and the host side of the invariants.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "nlse.h"
+#include "nlse_internal.h"
+
+using nlse::StageLaunch;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? NLSE_ENOMEM : NLSE_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define NLSE_CUDA(call, what)                                  \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);     \
+    } while (0)
+
+// Steps captured per CUDA graph; nlse_run replays the graph and launches the
+// remainder directly.
+constexpr int64_t kGraphSteps = 32;
+
+}  // namespace
+
+struct nlse_ctx {
+    nlse_params p;
+    const void* V;
+    int device;
+    int64_t npts;
+    size_t cbytes;            // bytes of one complex field
+    void* Y[2];               // stage inputs (ping-pong)
+    void* acc;                // accumulated RK4 increment
+    void* lo;                 // FP32 compensated low part (FP32 only)
+    int* flag;                // non-finite flag set by stage 4
+    double* partials;         // reduction scratch, nblocks x kPartialWidth
+    int nblocks;
+    double* red_out;          // reduced values on the device
+    double* host_out;         // pinned copy of red_out
+    const void* state_psi;    // psi whose compensated part lo currently holds
+    cudaGraphExec_t graph;
+    const void* graph_psi;
+};
+
+namespace {
+
+int validate(const nlse_params* p) {
+    if (!p) return fail(NLSE_EINVAL, "params is NULL");
+    if (p->dim < 1 || p->dim > 3) return fail(NLSE_EINVAL, "dim must be 1, 2 or 3 (got %d)", p->dim);
+    for (int ax = 0; ax < p->dim; ++ax) {
+        if (p->n[ax] < 3) return fail(NLSE_EINVAL, "n[%d] = %lld: need at least 3 points", ax, (long long)p->n[ax]);
+        if (p->n[ax] > (int64_t)1 << 30) return fail(NLSE_EINVAL, "n[%d] too large", ax);
+    }
+    int64_t npts = 1;
+    for (int ax = 0; ax < p->dim; ++ax) npts *= p->n[ax];
+    if (npts > ((int64_t)1 << 34)) return fail(NLSE_EINVAL, "grid too large (%lld points)", (long long)npts);
+    if (!(std::isfinite(p->h) && p->h > 0)) return fail(NLSE_EINVAL, "h must be positive and finite");
+    if (!(std::isfinite(p->dt) && p->dt > 0)) return fail(NLSE_EINVAL, "dt must be positive and finite");
+    if (!(std::isfinite(p->a) && p->a > 0)) return fail(NLSE_EINVAL, "a must be positive and finite (Eq. NLSE)");
+    if (!std::isfinite(p->s)) return fail(NLSE_EINVAL, "s must be finite");
+    if (p->bc != NLSE_BC_DIRICHLET && p->bc != NLSE_BC_MSD) return fail(NLSE_EINVAL, "unknown bc %d", p->bc);
+    if (p->prec != NLSE_FP32 && p->prec != NLSE_FP64) return fail(NLSE_EINVAL, "unknown prec %d", p->prec);
+    if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD) return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
+    if (p->bc == NLSE_BC_MSD && p->dim > 1)
+        return fail(NLSE_EUNSUPPORTED, "MSD boundaries are implemented for dim = 1 only");
+    return NLSE_OK;
+}
+
+StageLaunch base_launch(const nlse_ctx* c) {
+    StageLaunch L;
+    std::memset(&L, 0, sizeof L);
+    L.dim = c->p.dim;
+    for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+    L.prec = c->p.prec;
+    L.lap = c->p.lap;
+    L.bc = c->p.bc;
+    L.h = c->p.h; L.a = c->p.a; L.s = c->p.s; L.dt = c->p.dt;
+    L.V = c->V;
+    L.flag = c->flag;
+    return L;
+}
+
+cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
+    switch (L.dim) {
+        case 1: return nlse::launch_stage_1d(L, st);
+        case 2: return nlse::launch_stage_2d(L, st);
+        default: return nlse::launch_stage_3d(L, st);
+    }
+}
+
+// The four fused stages of one RK4 step (Eq. RK4) on psi, in place.
+int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
+    StageLaunch L = base_launch(c);
+    L.psi = psi;
+    L.psi_out = psi;
+    L.acc = c->acc;
+    L.lo = c->lo;
+    const void* in[5] = {nullptr, psi, c->Y[0], c->Y[1], c->Y[0]};
+    void* out[5] = {nullptr, c->Y[0], c->Y[1], c->Y[0], nullptr};
+    for (int s = 1; s <= 4; ++s) {
+        L.stage = s;
+        L.yin = in[s];
+        L.yout = out[s];
+        cudaError_t e = launch_stage(L, st);
+        if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
+    }
+    return NLSE_OK;
+}
+
+// Zeroes the compensated part when the state pointer changes.
+int bind_state(nlse_ctx* c, const void* psi, cudaStream_t st) {
+    if (c->state_psi == psi) return NLSE_OK;
+    if (c->lo) NLSE_CUDA(cudaMemsetAsync(c->lo, 0, c->cbytes, st), "zeroing the compensated part");
+    c->state_psi = psi;
+    return NLSE_OK;
+}
+
+// Largest |G| entries of the Table of Sec. 3.3 (t:sumresults), in units of
+// 1/12.  |L - g| is convex in L, so the maximum over G and over all points
+// is reached at an extreme of G and an extreme of L.
+void g_extremes(int dim, double* gmin, double* gmax) {
+    static const double mx[4] = {0, 64, 128, 192}, mn[4] = {0, -4, -8, -12};
+    *gmin = mn[dim] / 12.0;
+    *gmax = mx[dim] / 12.0;
+}
+
+int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
+                    cudaStream_t st) {
+    nlse::InvLaunch L;
+    L.dim = c->p.dim;
+    for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+    L.prec = c->p.prec; L.lap = c->p.lap; L.bc = c->p.bc;
+    L.h = c->p.h; L.a = c->p.a; L.s = c->p.s;
+    L.psi = psi;
+    L.lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
+    L.V = c->V;
+    NLSE_CUDA(nlse::launch_invariants(L, c->partials, c->nblocks, c->red_out, st), "invariants launch");
+    NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth,
+                              cudaMemcpyDeviceToHost, st), "invariants copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "invariants synchronise");
+    const double* r = c->host_out;
+    const double h = c->p.h, hd = std::pow(h, (double)c->p.dim);
+    if (mass) *mass = hd * r[0];
+    if (energy) *energy = hd * r[1];
+    if (dt_max) {
+        double gmin, gmax;
+        g_extremes(c->p.dim, &gmin, &gmax);
+        double worst = std::fmax(std::fabs(r[3] - gmin), std::fabs(r[2] - gmax));
+        worst = std::fmax(worst, std::fmax(std::fabs(r[2] - gmin), std::fabs(r[3] - gmax)));
+        worst = std::fmax(worst, r[4]);
+        *dt_max = std::sqrt(8.0) * h * h / (c->p.a * worst);
+    }
+    if (r[5] != 0.0 || !std::isfinite(r[0]))
+        return fail(NLSE_ENONFINITE, "state holds %g non-finite values", r[5]);
+    return NLSE_OK;
+}
+
+void release(nlse_ctx* c) {
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    cudaFree(c->Y[0]);
+    cudaFree(c->Y[1]);
+    cudaFree(c->acc);
+    cudaFree(c->lo);
+    cudaFree(c->flag);
+    cudaFree(c->partials);
+    cudaFree(c->red_out);
+    cudaFreeHost(c->host_out);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nlse_last_error(void) { return g_err; }
+
+int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
+    g_err[0] = 0;
+    if (!out) return fail(NLSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!V_dev) return fail(NLSE_EINVAL, "V_dev is NULL");
+    if ((uintptr_t)V_dev % 16) return fail(NLSE_EINVAL, "V_dev must be 16-byte aligned");
+
+    nlse_ctx* c = new (std::nothrow) nlse_ctx();
+    if (!c) return fail(NLSE_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->V = V_dev;
+    c->npts = 1;
+    for (int ax = 0; ax < p->dim; ++ax) c->npts *= p->n[ax];
+    c->cbytes = (size_t)c->npts * (p->prec == NLSE_FP32 ? 8 : 16);
+
+    cudaError_t e;
+    int nsm = 0;
+#define TRY(call, what) do { e = (call); if (e != cudaSuccess) { rc = cuda_fail(e, what); release(c); return rc; } } while (0)
+    TRY(cudaGetDevice(&c->device), "cudaGetDevice");
+    TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device query");
+    TRY(cudaMalloc(&c->Y[0], c->cbytes), "allocating stage buffer");
+    TRY(cudaMalloc(&c->Y[1], c->cbytes), "allocating stage buffer");
+    TRY(cudaMalloc(&c->acc, c->cbytes), "allocating accumulator");
+    if (p->prec == NLSE_FP32) {
+        TRY(cudaMalloc(&c->lo, c->cbytes), "allocating compensated part");
+        TRY(cudaMemset(c->lo, 0, c->cbytes), "zeroing compensated part");
+    }
+    TRY(cudaMalloc((void**)&c->flag, sizeof(int)), "allocating flag");
+    TRY(cudaMemset(c->flag, 0, sizeof(int)), "zeroing flag");
+    {
+        nlse::InvLaunch L;
+        L.dim = p->dim;
+        for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < p->dim ? p->n[ax] : 1;
+        c->nblocks = nlse::inv_num_blocks(L, nsm);
+    }
+    TRY(cudaMalloc((void**)&c->partials, sizeof(double) * nlse::kPartialWidth * c->nblocks), "allocating partials");
+    TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth), "allocating result");
+    TRY(cudaMallocHost((void**)&c->host_out, sizeof(double) * nlse::kPartialWidth), "allocating pinned result");
+#undef TRY
+    *out = c;
+    return NLSE_OK;
+}
+
+void nlse_destroy(nlse_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    release(c);
+}
+
+int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi || !lap) return fail(NLSE_EINVAL, "NULL argument");
+    if (((uintptr_t)psi | (uintptr_t)lap) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
+    const char *a0 = (const char*)psi, *b0 = (const char*)lap;
+    if (a0 < b0 + c->cbytes && b0 < a0 + c->cbytes) return fail(NLSE_EINVAL, "psi and lap overlap");
+    StageLaunch L = base_launch(c);
+    L.stage = 0;
+    L.yin = psi;
+    L.lap_out = lap;
+    cudaError_t e = launch_stage(L, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Laplacian launch");
+    return NLSE_OK;
+}
+
+int nlse_rk4_step(nlse_ctx* c, void* psi, void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
+    if ((uintptr_t)psi % 16) return fail(NLSE_EINVAL, "psi must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = bind_state(c, psi, st);
+    if (rc) return rc;
+    return enqueue_step(c, psi, st);
+}
+
+int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps must be >= 0");
+    if ((uintptr_t)psi % 16) return fail(NLSE_EINVAL, "psi must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = bind_state(c, psi, st);
+    if (rc) return rc;
+    if (nsteps == 0) return NLSE_OK;
+    if (!(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK)) {
+        double dtmax = 0;
+        rc = invariants_impl(c, psi, nullptr, nullptr, &dtmax, st);
+        if (rc) return rc;
+        if (c->p.dt > dtmax)
+            return fail(NLSE_EUNSTABLE, "dt = %g exceeds the bound %g of Eq. (kdfull)", c->p.dt, dtmax);
+    }
+    if (nsteps >= kGraphSteps && (!c->graph || c->graph_psi != psi)) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaStream_t cs;
+        NLSE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(e, "begin capture");
+        }
+        for (int64_t i = 0; i < kGraphSteps && rc == NLSE_OK; ++i) rc = enqueue_step(c, psi, cs);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return cuda_fail(e, "graph instantiate");
+        }
+        c->graph_psi = psi;
+    }
+    int64_t done = 0;
+    if (c->graph && c->graph_psi == psi)
+        for (; done + kGraphSteps <= nsteps; done += kGraphSteps)
+            NLSE_CUDA(cudaGraphLaunch(c->graph, st), "graph launch");
+    for (; done < nsteps; ++done) {
+        rc = enqueue_step(c, psi, st);
+        if (rc) return rc;
+    }
+    return NLSE_OK;
+}
+
+int nlse_invariants(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
+                    void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
+    return invariants_impl(c, psi, mass, energy, dt_max, (cudaStream_t)stream);
+}
+
+int nlse_reset_compensation(nlse_ctx* c, void* stream) {
+    g_err[0] = 0;
+    if (!c) return fail(NLSE_EINVAL, "NULL argument");
+    if (c->lo) NLSE_CUDA(cudaMemsetAsync(c->lo, 0, c->cbytes, (cudaStream_t)stream), "zeroing the compensated part");
+    return NLSE_OK;
+}
+
+int nlse_check(nlse_ctx* c, void* stream) {
+    g_err[0] = 0;
+    if (!c) return fail(NLSE_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    NLSE_CUDA(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "flag synchronise");
+    if (h) {
+        NLSE_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), st), "flag reset");
+        return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
+    }
+    return NLSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// invariants.cu -- FP64 reductions behind nlse_invariants: mass, energy, the
+// extremes of L_i = (h^2/a)(s|Psi_i|^2 - V_i) and of the MSD boundary term
+// |B_b| of Table t:bc2, which together give the time-step bound of
+// Eq. (kdfull), and a count of non-finite values.
+//
+// Pointwise evaluation straight from global memory (this runs every few
+// hundred steps, not every stage): each thread takes grid points in a
+// grid-stride loop, forms the 2SHOC Laplacian in FP64 where the energy needs
+// it, and the block reduces with warp shuffles.  Every block writes one row
+// of partials to scratch; a single-block kernel then reduces the rows in a
+// fixed order, so the result is deterministic for a given launch shape.
+#include <cfloat>
+
+#include "nlse_device.cuh"
+
+namespace nlse {
+namespace {
+
+template <typename R>
+struct InvView {
+    const cplx<R>* psi;
+    const cplx<R>* lo;
+    const R* V;
+    int dim;
+    int n[3];
+    int64_t stride[3];
+    double h2a;        // h^2 / a
+    double inv_h2, inv_6h2, a, s, inv_a;
+    int bc, lap;
+};
+
+template <typename R>
+__device__ __forceinline__ double2 psi_at(const InvView<R>& v, int64_t p) {
+    cplx<R> z = v.psi[p];
+    double2 r = make_double2((double)z.x, (double)z.y);
+    if (v.lo) {
+        cplx<R> l = v.lo[p];
+        r.x += (double)l.x;
+        r.y += (double)l.y;
+    }
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ bool on_boundary(const InvView<R>& v, const int* c) {
+    for (int ax = 0; ax < v.dim; ++ax)
+        if (c[ax] == 0 || c[ax] == v.n[ax] - 1) return true;
+    return false;
+}
+
+template <typename R>
+__device__ __forceinline__ int64_t index_of(const InvView<R>& v, const int* c) {
+    return c[0] * v.stride[0] + c[1] * v.stride[1] + c[2] * v.stride[2];
+}
+
+// Step-1 D at an interior point: sum of axial neighbours minus 2d centre, / h^2.
+template <typename R>
+__device__ double2 d_interior(const InvView<R>& v, const int* c) {
+    int64_t p = index_of(v, c);
+    double2 ctr = psi_at(v, p);
+    double2 sum = make_double2(0.0, 0.0);
+    for (int ax = 0; ax < v.dim; ++ax) {
+        double2 u = psi_at(v, p + v.stride[ax]);
+        double2 w = psi_at(v, p - v.stride[ax]);
+        sum.x += u.x + w.x;
+        sum.y += u.y + w.y;
+    }
+    double k = 2.0 * v.dim;
+    return make_double2((sum.x - k * ctr.x) * v.inv_h2, (sum.y - k * ctr.y) * v.inv_h2);
+}
+
+// The closest interior point of a boundary point: every coordinate clamped into [1, n-2].
+template <typename R>
+__device__ __forceinline__ void inward(const InvView<R>& v, const int* c, int* q) {
+    for (int ax = 0; ax < 3; ++ax) q[ax] = c[ax];
+    for (int ax = 0; ax < v.dim; ++ax) q[ax] = min(max(c[ax], 1), v.n[ax] - 2);
+}
+
+// Step-1 D at any point, with the boundary rule of Sec. 3.2.
+template <typename R>
+__device__ double2 d_any(const InvView<R>& v, const int* c) {
+    if (!on_boundary(v, c)) return d_interior(v, c);
+    int64_t b = index_of(v, c);
+    double2 pb = psi_at(v, b);
+    double Nb = v.s * (pb.x * pb.x + pb.y * pb.y) - (double)v.V[b];
+    if (v.bc == 0) return make_double2(-Nb * v.inv_a * pb.x, -Nb * v.inv_a * pb.y);
+    int q[3];
+    inward(v, c, q);
+    int64_t qi = index_of(v, q);
+    double2 pq = psi_at(v, qi);
+    double2 dq = d_interior(v, q);
+    double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - (double)v.V[qi];
+    double re_ratio = (dq.x * pq.x + dq.y * pq.y) / (pq.x * pq.x + pq.y * pq.y);
+    double f = re_ratio + (Nq - Nb) * v.inv_a;
+    return make_double2(f * pb.x, f * pb.y);
+}
+
+// Laplacian at an interior point: CD (D itself) or 2SHOC step 2 in the form
+// common to Eqs. (2shoc1d2), (2d2shocs2), (3d2shocs2):
+//   ((16 - 2d)/12) D_c - (1/12) sum_axial D + (1/(6h^2)) (sum_edges Psi - 2d(d-1) Psi_c).
+template <typename R>
+__device__ double2 lap_interior(const InvView<R>& v, const int* c) {
+    double2 dc = d_interior(v, c);
+    if (v.lap == 1) return dc;
+    const int d = v.dim;
+    double2 dsum = make_double2(0.0, 0.0);
+    for (int ax = 0; ax < d; ++ax)
+        for (int sg = -1; sg <= 1; sg += 2) {
+            int q[3] = {c[0], c[1], c[2]};
+            q[ax] += sg;
+            double2 t = d_any(v, q);
+            dsum.x += t.x;
+            dsum.y += t.y;
+        }
+    double2 edges = make_double2(0.0, 0.0);
+    int64_t p = index_of(v, c);
+    for (int a1 = 0; a1 < d; ++a1)
+        for (int a2 = a1 + 1; a2 < d; ++a2)
+            for (int s1 = -1; s1 <= 1; s1 += 2)
+                for (int s2 = -1; s2 <= 1; s2 += 2) {
+                    double2 t = psi_at(v, p + s1 * v.stride[a1] + s2 * v.stride[a2]);
+                    edges.x += t.x;
+                    edges.y += t.y;
+                }
+    double2 pc = psi_at(v, p);
+    double wc = (16.0 - 2.0 * d) / 12.0, we = 2.0 * d * (d - 1);
+    return make_double2(wc * dc.x - dsum.x / 12.0 + (edges.x - we * pc.x) * v.inv_6h2,
+                        wc * dc.y - dsum.y / 12.0 + (edges.y - we * pc.y) * v.inv_6h2);
+}
+
+struct Acc {
+    double mass, energy, lmin, lmax, bmax, nonfinite;
+};
+
+__device__ __forceinline__ void acc_combine(Acc& a, const Acc& b) {
+    a.mass += b.mass;
+    a.energy += b.energy;
+    a.lmin = fmin(a.lmin, b.lmin);
+    a.lmax = fmax(a.lmax, b.lmax);
+    a.bmax = fmax(a.bmax, b.bmax);
+    a.nonfinite += b.nonfinite;
+}
+
+__device__ __forceinline__ Acc acc_shfl_down(const Acc& a, int off) {
+    Acc b;
+    b.mass = __shfl_down_sync(0xffffffffu, a.mass, off);
+    b.energy = __shfl_down_sync(0xffffffffu, a.energy, off);
+    b.lmin = __shfl_down_sync(0xffffffffu, a.lmin, off);
+    b.lmax = __shfl_down_sync(0xffffffffu, a.lmax, off);
+    b.bmax = __shfl_down_sync(0xffffffffu, a.bmax, off);
+    b.nonfinite = __shfl_down_sync(0xffffffffu, a.nonfinite, off);
+    return b;
+}
+
+__device__ __forceinline__ Acc acc_identity() {
+    Acc a;
+    a.mass = a.energy = a.nonfinite = 0.0;
+    a.lmin = DBL_MAX;
+    a.lmax = -DBL_MAX;
+    a.bmax = 0.0;
+    return a;
+}
+
+// Block reduction; thread 0 returns the block total.
+__device__ Acc block_reduce(Acc a) {
+    __shared__ Acc warp_tot[kInvThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) acc_combine(a, acc_shfl_down(a, off));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = lane < kInvThreads / 32 ? warp_tot[lane] : acc_identity();
+        for (int off = 16; off > 0; off >>= 1) acc_combine(a, acc_shfl_down(a, off));
+    }
+    return a;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, int64_t npts,
+                                                                  double* partials) {
+    Acc a = acc_identity();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int c[3];
+        int64_t r = p;
+        c[0] = (int)(r % v.n[0]); r /= v.n[0];
+        c[1] = (int)(r % v.n[1]); r /= v.n[1];
+        c[2] = (int)r;
+        double2 ps = psi_at(v, p);
+        double rho = ps.x * ps.x + ps.y * ps.y;
+        double Vp = (double)v.V[p];
+        if (!isfinite(rho)) { a.nonfinite += 1.0; continue; }
+        a.mass += rho;
+        double L = v.h2a * (v.s * rho - Vp);
+        a.lmin = fmin(a.lmin, L);
+        a.lmax = fmax(a.lmax, L);
+        if (!on_boundary(v, c)) {
+            double2 lp = lap_interior(v, c);
+            a.energy += -v.a * (ps.x * lp.x + ps.y * lp.y) + Vp * rho - 0.5 * v.s * rho * rho;
+        } else if (v.bc == 1) {
+            // B_b = (h^2/(i a)) F_q / Psi_q (Table t:bc2); |1/i| = 1.
+            int q[3];
+            inward(v, c, q);
+            int64_t qi = index_of(v, q);
+            double2 pq = psi_at(v, qi);
+            double2 lq = lap_interior(v, q);
+            double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - (double)v.V[qi];
+            // F_q / i = a Lap + N Psi; |F_q / Psi_q| = |a Lap + N Psi| / |Psi|.
+            double fx = v.a * lq.x + Nq * pq.x, fy = v.a * lq.y + Nq * pq.y;
+            double B = v.h2a * sqrt((fx * fx + fy * fy) / (pq.x * pq.x + pq.y * pq.y));
+            a.bmax = fmax(a.bmax, B);
+        }
+    }
+    a = block_reduce(a);
+    if (threadIdx.x == 0) {
+        double* row = partials + (int64_t)blockIdx.x * kPartialWidth;
+        row[0] = a.mass; row[1] = a.energy; row[2] = a.lmin;
+        row[3] = a.lmax; row[4] = a.bmax; row[5] = a.nonfinite;
+    }
+}
+
+__global__ void __launch_bounds__(kInvThreads) invariants_final(const double* partials, int nrows,
+                                                                double* out) {
+    Acc a = acc_identity();
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        const double* row = partials + (int64_t)i * kPartialWidth;
+        Acc b;
+        b.mass = row[0]; b.energy = row[1]; b.lmin = row[2];
+        b.lmax = row[3]; b.bmax = row[4]; b.nonfinite = row[5];
+        acc_combine(a, b);
+    }
+    a = block_reduce(a);
+    if (threadIdx.x == 0) {
+        out[0] = a.mass; out[1] = a.energy; out[2] = a.lmin;
+        out[3] = a.lmax; out[4] = a.bmax; out[5] = a.nonfinite;
+    }
+}
+
+template <typename R>
+cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* out,
+                     cudaStream_t st) {
+    InvView<R> v;
+    v.psi = (const cplx<R>*)L.psi;
+    v.lo = (const cplx<R>*)L.lo;
+    v.V = (const R*)L.V;
+    v.dim = L.dim;
+    for (int ax = 0; ax < 3; ++ax) v.n[ax] = ax < L.dim ? (int)L.n[ax] : 1;
+    v.stride[0] = 1;
+    v.stride[1] = v.n[0];
+    v.stride[2] = (int64_t)v.n[0] * v.n[1];
+    v.h2a = L.h * L.h / L.a;
+    v.inv_h2 = 1.0 / (L.h * L.h);
+    v.inv_6h2 = 1.0 / (6.0 * L.h * L.h);
+    v.a = L.a; v.s = L.s; v.inv_a = 1.0 / L.a;
+    v.bc = L.bc; v.lap = L.lap;
+    int64_t npts = (int64_t)v.n[0] * v.n[1] * v.n[2];
+    invariants_partial<R><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    invariants_final<<<1, kInvThreads, 0, st>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int inv_num_blocks(const InvLaunch& L, int num_sms) {
+    int64_t npts = 1;
+    for (int ax = 0; ax < L.dim; ++ax) npts *= L.n[ax];
+    int64_t want = (npts + kInvThreads - 1) / kInvThreads;
+    int64_t cap = (int64_t)num_sms * 4;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks, double* out,
+                              cudaStream_t st) {
+    return L.prec == 0 ? launch_r<float>(L, partials, nblocks, out, st)
+                       : launch_r<double>(L, partials, nblocks, out, st);
+}
+
+}  // namespace nlse

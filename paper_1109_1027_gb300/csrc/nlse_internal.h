@@ -1,0 +1,55 @@
+// nlse_internal.h -- host-side interface between the C ABI (api.cu) and the
+// per-dimension kernel files (stage1d.cu, stage2d.cu, stage3d.cu,
+// invariants.cu).  No CUDA device code here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nlse {
+
+// One launch of a fused RK4 stage (stage 1..4) or of the standalone
+// Laplacian (stage 0).  Pointers are device pointers; their element types
+// follow prec (complex64 / float or complex128 / double).
+struct StageLaunch {
+    int dim;
+    int64_t n[3];
+    int prec, lap, bc;
+    double h, a, s, dt;
+    int stage;              // 0: Laplacian only; 1..4: RK4 stage of Eq. (RK4)
+    const void* yin;        // stage input Psi_s (read with a 2-point halo)
+    const void* psi;        // Psi^n (stages 2..4)
+    void* psi_out;          // stage 4: Psi^{n+1} (may equal psi)
+    void* lo;               // FP32 compensated low part (stage 4), else nullptr
+    void* acc;              // accumulated RK4 increment
+    void* yout;             // next stage input
+    void* lap_out;          // stage 0 output
+    const void* V;
+    int* flag;              // stage 4 sets *flag = 1 on a non-finite result
+};
+
+cudaError_t launch_stage_1d(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st);
+
+// FP64 reductions for nlse_invariants.  Each of the nblocks blocks of the
+// partial kernel writes kPartialWidth doubles to partials; the final kernel
+// reduces them in a fixed order into out[0..kPartialWidth).
+constexpr int kPartialWidth = 6;   // mass, energy, min L, max L, max |B|, non-finite count
+constexpr int kInvThreads = 256;
+
+struct InvLaunch {
+    int dim;
+    int64_t n[3];
+    int prec, lap, bc;
+    double h, a, s;
+    const void* psi;        // state (hi part in FP32)
+    const void* lo;         // FP32 compensated part or nullptr
+    const void* V;
+};
+
+int inv_num_blocks(const InvLaunch& L, int num_sms);
+cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks, double* out,
+                              cudaStream_t st);
+
+}  // namespace nlse

@@ -1,0 +1,132 @@
+// stage2d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 2D grid.
+//
+// One CTA owns a TX x TY tile of output points.  It stages the stage input
+// with a 2-point halo in shared memory, computes step 1 of the 2SHOC scheme,
+// the second-order D of Eq. (2d2shocs1), on the tile plus a 1-point ring
+// (boundary points take D_b of Eq. (dbc_lap)), and then step 2,
+// Eq. (2d2shocs2):
+//     Lap = -(1/12)[D_E + D_W + D_N + D_S - 12 D_c]
+//           + (1/(6h^2))[Psi_NE + Psi_NW + Psi_SE + Psi_SW - 4 Psi_c],
+// followed by F (Sec. 3.1), the Dirichlet rule F_b = 0 (Eq. dbc_ut) and the
+// stage epilogue.  D lives only in shared memory.
+#include "nlse_device.cuh"
+
+namespace nlse {
+namespace {
+
+constexpr int TX = 64;       // tile width (x, contiguous)
+constexpr int TY = 16;       // tile height
+constexpr int NT = 256;      // threads per CTA
+constexpr int PX = TX + 4, PY = TY + 4;   // stage input with a 2-point halo
+constexpr int DX = TX + 2, DY = TY + 2;   // D with a 1-point halo
+
+// STAGE 0 writes the Laplacian (boundary = D_b); STAGE 1..4 are RK4 stages.
+template <typename R, bool CD, int STAGE>
+__global__ void __launch_bounds__(NT)
+stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sP = reinterpret_cast<C*>(smem_raw);          // [PY][PX]
+    C* sD = sP + PX * PY;                            // [DY][DX]
+
+    const int x0 = blockIdx.x * TX;
+    const int y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x;
+
+    // Stage input tile with halo; points outside the grid read as zero (never used).
+    for (int i = tid; i < PX * PY; i += NT) {
+        int ly = i / PX, lx = i - ly * PX;
+        int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+        C v = czero<C>();
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) v = io.yin[(int64_t)gy * nx + gx];
+        sP[i] = v;
+    }
+    __syncthreads();
+
+    // Step 1: D on the tile plus a 1-point ring.
+    for (int i = tid; i < DX * DY; i += NT) {
+        int ly = i / DX, lx = i - ly * DX;
+        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        const C* q = sP + (ly + 1) * PX + (lx + 1);
+        C d = czero<C>();
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+            C pc = q[0];
+            if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
+                d = dirichlet_D(c, pc, io.V[(int64_t)gy * nx + gx]);
+            } else {
+                C sum = cadd(cadd(q[1], q[-1]), cadd(q[PX], q[-PX]));
+                d = cscale(c.inv_h2, csub(sum, cscale((R)4, pc)));
+            }
+        }
+        sD[i] = d;
+    }
+    __syncthreads();
+
+    // Step 2, F and the stage epilogue on the tile.
+    bool bad = false;
+    for (int i = tid; i < TX * TY; i += NT) {
+        int ly = i / TX, lx = i - ly * TX;
+        int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const int64_t p = (int64_t)gy * nx + gx;
+        const C* q = sP + (ly + 2) * PX + (lx + 2);
+        const C* e = sD + (ly + 1) * DX + (lx + 1);
+        const C y = q[0];
+        const bool bnd = (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1);
+        C lap;
+        if (bnd || CD) {
+            lap = e[0];
+        } else {
+            C dsum = cadd(cadd(e[1], e[-1]), cadd(e[DX], e[-DX]));
+            C corners = cadd(cadd(q[PX + 1], q[PX - 1]), cadd(q[-PX + 1], q[-PX - 1]));
+            C dpart = cscale((R)(-1.0 / 12.0), csub(dsum, cscale((R)12, e[0])));
+            C ppart = cscale(c.inv_6h2, csub(corners, cscale((R)4, y)));
+            lap = cadd(dpart, ppart);
+        }
+        if constexpr (STAGE == 0) {
+            io.lap[p] = lap;
+        } else {
+            C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[p]);
+            bad |= stage_epilogue<STAGE>(io, p, y, F);
+        }
+    }
+    if constexpr (STAGE == 4) {
+        if (__syncthreads_or(bad) && tid == 0) atomicExch(io.flag, 1);
+    }
+}
+
+template <typename R, bool CD, int STAGE>
+cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
+    const int nx = (int)L.n[0], ny = (int)L.n[1];
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
+    size_t smem = sizeof(cplx<R>) * (PX * PY + DX * DY);
+    auto kern = stage2d_kernel<R, CD, STAGE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, NT, smem, st>>>(make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny);
+    return cudaGetLastError();
+}
+
+template <typename R, bool CD>
+cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
+    switch (L.stage) {
+        case 0: return launch_t<R, CD, 0>(L, st);
+        case 1: return launch_t<R, CD, 1>(L, st);
+        case 2: return launch_t<R, CD, 2>(L, st);
+        case 3: return launch_t<R, CD, 3>(L, st);
+        case 4: return launch_t<R, CD, 4>(L, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st) {
+    const bool cd = L.lap == 1;
+    if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
+    return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);
+}
+
+}  // namespace nlse

@@ -1,0 +1,170 @@
+// stage3d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 3D grid.
+//
+// One CTA owns a TX x TY column of the grid over TZ consecutive z planes and
+// streams through them (2.5D blocking): shared memory holds a ring of four
+// stage-input planes (z-1 .. z+2, each with a 2-point xy halo) and three D
+// planes (z-1 .. z+1, 1-point xy halo).  Per plane it loads input plane z+2,
+// computes step 1, the seven-point D of Eq. (3d2shocs), for plane z+1
+// (boundary points take D_b of Eq. dbc_lap), and evaluates step 2,
+// Eq. (3d2shocs2),
+//     Lap = -(1/12)[sum of the six axial D - 10 D_c]
+//           + (1/(6h^2))[sum of the twelve edge neighbours of Psi - 12 Psi_c],
+// then F, the Dirichlet rule F_b = 0 and the RK4 stage epilogue for plane z.
+// Each input plane is read once per CTA, so the halo overhead is only the xy
+// ring plus four planes per TZ.
+#include "nlse_device.cuh"
+
+namespace nlse {
+namespace {
+
+constexpr int TX = 32, TY = 16, TZ = 32;
+constexpr int NT = 256;
+constexpr int PX = TX + 4, PY = TY + 4, PP = PX * PY;   // input plane with halo 2
+constexpr int DX = TX + 2, DY = TY + 2, DP = DX * DY;   // D plane with halo 1
+
+__device__ __forceinline__ int pslot(int z) { return (z + 4) & 3; }
+__device__ __forceinline__ int dslot(int z) { return (z + 3) % 3; }
+
+template <typename R, bool CD, int STAGE>
+__global__ void __launch_bounds__(NT)
+stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sP = reinterpret_cast<C*>(smem_raw);   // [4][PY][PX]
+    C* sD = sP + 4 * PP;                      // [3][DY][DX]
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int z1 = min(z0 + TZ, nz);
+    const int tid = threadIdx.x;
+    const int64_t plane = (int64_t)nx * ny;
+
+    auto load_plane = [&](int gz) {
+        C* dst = sP + pslot(gz) * PP;
+        const bool zin = gz >= 0 && gz < nz;
+        for (int i = tid; i < PP; i += NT) {
+            int ly = i / PX, lx = i - ly * PX;
+            int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+            C v = czero<C>();
+            if (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                v = io.yin[gz * plane + (int64_t)gy * nx + gx];
+            dst[i] = v;
+        }
+    };
+    auto d_plane = [&](int gz) {
+        C* dst = sD + dslot(gz) * DP;
+        const C* pm = sP + pslot(gz - 1) * PP;
+        const C* pc = sP + pslot(gz) * PP;
+        const C* pp = sP + pslot(gz + 1) * PP;
+        const bool zin = gz >= 0 && gz < nz;
+        const bool zb = gz == 0 || gz == nz - 1;
+        for (int i = tid; i < DP; i += NT) {
+            int ly = i / DX, lx = i - ly * DX;
+            int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            int k = (ly + 1) * PX + (lx + 1);
+            C d = czero<C>();
+            if (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                C ctr = pc[k];
+                if (zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
+                    d = dirichlet_D(c, ctr, io.V[gz * plane + (int64_t)gy * nx + gx]);
+                } else {
+                    C sum = cadd(cadd(cadd(pc[k + 1], pc[k - 1]), cadd(pc[k + PX], pc[k - PX])),
+                                 cadd(pp[k], pm[k]));
+                    d = cscale(c.inv_h2, csub(sum, cscale((R)6, ctr)));
+                }
+            }
+            dst[i] = d;
+        }
+    };
+
+    for (int gz = z0 - 2; gz <= z0 + 1; ++gz) load_plane(gz);
+    __syncthreads();
+    d_plane(z0 - 1);
+    d_plane(z0);
+    __syncthreads();
+
+    bool bad = false;
+    for (int gz = z0; gz < z1; ++gz) {
+        load_plane(gz + 2);
+        __syncthreads();
+        d_plane(gz + 1);
+        __syncthreads();
+
+        const C* pm = sP + pslot(gz - 1) * PP;
+        const C* pc = sP + pslot(gz) * PP;
+        const C* pp = sP + pslot(gz + 1) * PP;
+        const C* dm = sD + dslot(gz - 1) * DP;
+        const C* dc = sD + dslot(gz) * DP;
+        const C* dp = sD + dslot(gz + 1) * DP;
+        const bool zb = gz == 0 || gz == nz - 1;
+        for (int i = tid; i < TX * TY; i += NT) {
+            int ly = i / TX, lx = i - ly * TX;
+            int gx = x0 + lx, gy = y0 + ly;
+            if (gx >= nx || gy >= ny) continue;
+            const int64_t p = gz * plane + (int64_t)gy * nx + gx;
+            const int k = (ly + 2) * PX + (lx + 2);
+            const int kd = (ly + 1) * DX + (lx + 1);
+            const C y = pc[k];
+            const bool bnd = zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1;
+            C lap;
+            if (bnd || CD) {
+                lap = dc[kd];
+            } else {
+                C dsum = cadd(cadd(cadd(dc[kd + 1], dc[kd - 1]), cadd(dc[kd + DX], dc[kd - DX])),
+                              cadd(dp[kd], dm[kd]));
+                C exy = cadd(cadd(pc[k + PX + 1], pc[k + PX - 1]), cadd(pc[k - PX + 1], pc[k - PX - 1]));
+                C exz = cadd(cadd(pp[k + 1], pp[k - 1]), cadd(pm[k + 1], pm[k - 1]));
+                C eyz = cadd(cadd(pp[k + PX], pp[k - PX]), cadd(pm[k + PX], pm[k - PX]));
+                C edges = cadd(cadd(exy, exz), eyz);
+                C dpart = cscale((R)(-1.0 / 12.0), csub(dsum, cscale((R)10, dc[kd])));
+                C ppart = cscale(c.inv_6h2, csub(edges, cscale((R)12, y)));
+                lap = cadd(dpart, ppart);
+            }
+            if constexpr (STAGE == 0) {
+                io.lap[p] = lap;
+            } else {
+                C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[p]);
+                bad |= stage_epilogue<STAGE>(io, p, y, F);
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (STAGE == 4) {
+        if (__syncthreads_or(bad) && tid == 0) atomicExch(io.flag, 1);
+    }
+}
+
+template <typename R, bool CD, int STAGE>
+cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
+    const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ);
+    size_t smem = sizeof(cplx<R>) * (4 * PP + 3 * DP);
+    auto kern = stage3d_kernel<R, CD, STAGE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, NT, smem, st>>>(make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny, nz);
+    return cudaGetLastError();
+}
+
+template <typename R, bool CD>
+cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
+    switch (L.stage) {
+        case 0: return launch_t<R, CD, 0>(L, st);
+        case 1: return launch_t<R, CD, 1>(L, st);
+        case 2: return launch_t<R, CD, 2>(L, st);
+        case 3: return launch_t<R, CD, 3>(L, st);
+        case 4: return launch_t<R, CD, 4>(L, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st) {
+    const bool cd = L.lap == 1;
+    if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
+    return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);
+}
+
+}  // namespace nlse

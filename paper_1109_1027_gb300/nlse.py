@@ -1,0 +1,217 @@
+"""Python binding of libnlse (include/nlse.h): argument marshalling only.
+
+Every step of the numerical method runs in the CUDA library; this module
+checks tensors, hands their device pointers and the current torch stream to
+the C ABI and turns status codes into exceptions.  PyTorch is used for device
+memory and streams, nothing else.  There is no CPU fallback: if the library is
+missing or cannot be loaded, every call raises.
+
+The functions ``nlse_create``, ``nlse_lap2shoc``, ``nlse_rk4_step``,
+``nlse_run``, ``nlse_invariants``, ``nlse_reset_compensation``, ``nlse_check``
+and ``nlse_destroy`` mirror the C entry points one to one; :class:`Solver`
+wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(8)
+BC = {"dirichlet": 0, "msd": 1}
+PREC = {"fp32": 0, "fp64": 1}
+LAP = {"2shoc": 0, "cd": 1}
+FLAG_NO_STABILITY_CHECK = 1
+
+_STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
+                 "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
+
+
+class NLSEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        name = _STATUS_NAMES[code] if 0 <= code < len(_STATUS_NAMES) else str(code)
+        super().__init__(f"{name}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double),
+                ("dt", ctypes.c_double), ("a", ctypes.c_double), ("s", ctypes.c_double),
+                ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("lap", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libnlse.so (building it first when it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnlse.so not found at {path}; build it with "
+                           "paper_1109_1027_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "nlse_create": ([ctypes.POINTER(Params), vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "nlse_destroy": ([vp], None),
+        "nlse_lap2shoc": ([vp, vp, vp, vp], ctypes.c_int),
+        "nlse_rk4_step": ([vp, vp, vp], ctypes.c_int),
+        "nlse_run": ([vp, vp, i64, vp], ctypes.c_int),
+        "nlse_invariants": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
+        "nlse_reset_compensation": ([vp, vp], ctypes.c_int),
+        "nlse_check": ([vp, vp], ctypes.c_int),
+        "nlse_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _raise(rc: int):
+    if rc != OK:
+        raise NLSEError(rc, load_library().nlse_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_params(shape, h, dt, a, s, bc="dirichlet", prec="fp32", lap="2shoc",
+                check_stability=True) -> Params:
+    """Params for a grid of ``shape`` = (nx,), (ny, nx) or (nz, ny, nx) (x fastest)."""
+    p = Params()
+    p.dim = len(shape)
+    n = list(reversed([int(v) for v in shape])) + [1] * (3 - len(shape))
+    for i in range(3):
+        p.n[i] = n[i]
+    p.h, p.dt, p.a, p.s = float(h), float(dt), float(a), float(s)
+    p.bc = BC[bc] if isinstance(bc, str) else int(bc)
+    p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    p.lap = LAP[lap] if isinstance(lap, str) else int(lap)
+    p.flags = 0 if check_stability else FLAG_NO_STABILITY_CHECK
+    return p
+
+
+def nlse_create(params: Params, V_ptr: int) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _raise(load_library().nlse_create(ctypes.byref(params), ctypes.c_void_p(V_ptr),
+                                      ctypes.byref(ctx)))
+    return ctx
+
+
+def nlse_destroy(ctx) -> None:
+    load_library().nlse_destroy(ctx)
+
+
+def nlse_lap2shoc(ctx, psi_ptr: int, lap_ptr: int, stream=None) -> None:
+    _raise(load_library().nlse_lap2shoc(ctx, ctypes.c_void_p(psi_ptr), ctypes.c_void_p(lap_ptr),
+                                        _stream(stream)))
+
+
+def nlse_rk4_step(ctx, psi_ptr: int, stream=None) -> None:
+    _raise(load_library().nlse_rk4_step(ctx, ctypes.c_void_p(psi_ptr), _stream(stream)))
+
+
+def nlse_run(ctx, psi_ptr: int, nsteps: int, stream=None) -> None:
+    _raise(load_library().nlse_run(ctx, ctypes.c_void_p(psi_ptr), int(nsteps), _stream(stream)))
+
+
+def nlse_invariants(ctx, psi_ptr: int, stream=None):
+    m, e, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _raise(load_library().nlse_invariants(ctx, ctypes.c_void_p(psi_ptr), ctypes.byref(m),
+                                          ctypes.byref(e), ctypes.byref(d), _stream(stream)))
+    return m.value, e.value, d.value
+
+
+def nlse_reset_compensation(ctx, stream=None) -> None:
+    _raise(load_library().nlse_reset_compensation(ctx, _stream(stream)))
+
+
+def nlse_check(ctx, stream=None) -> None:
+    _raise(load_library().nlse_check(ctx, _stream(stream)))
+
+
+class Solver:
+    """One NLSE problem i psi_t + a Lap psi - V psi + s|psi|^2 psi = 0 on the GPU.
+
+    ``V`` is a CUDA tensor shaped (nx,), (ny, nx) or (nz, ny, nx); float32 for
+    ``prec="fp32"`` (state complex64) or float64 for ``prec="fp64"``
+    (complex128).  The solver keeps a reference to V."""
+
+    def __init__(self, V: torch.Tensor, h: float, dt: float, a: float, s: float,
+                 bc: str = "dirichlet", prec: str = "fp32", lap: str = "2shoc",
+                 check_stability: bool = True):
+        load_library()
+        want = torch.float32 if prec == "fp32" else torch.float64
+        if not V.is_cuda or V.dtype != want or not V.is_contiguous():
+            raise ValueError(f"V must be a contiguous CUDA {want} tensor")
+        self.V = V
+        self.shape = tuple(V.shape)
+        self.prec = prec
+        self.cdtype = torch.complex64 if prec == "fp32" else torch.complex128
+        self.params = make_params(self.shape, h, dt, a, s, bc, prec, lap, check_stability)
+        with torch.cuda.device(V.device):
+            self.ctx = nlse_create(self.params, V.data_ptr())
+
+    def _check_psi(self, psi: torch.Tensor):
+        if (not psi.is_cuda or psi.dtype != self.cdtype or tuple(psi.shape) != self.shape
+                or not psi.is_contiguous() or psi.device != self.V.device):
+            raise ValueError(f"psi must be a contiguous {self.cdtype} tensor of shape {self.shape} "
+                             f"on {self.V.device}")
+
+    def lap2shoc(self, psi: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._check_psi(psi)
+        out = torch.empty_like(psi) if out is None else out
+        self._check_psi(out)
+        nlse_lap2shoc(self.ctx, psi.data_ptr(), out.data_ptr())
+        return out
+
+    def rk4_step(self, psi: torch.Tensor) -> torch.Tensor:
+        self._check_psi(psi)
+        nlse_rk4_step(self.ctx, psi.data_ptr())
+        return psi
+
+    def run(self, psi: torch.Tensor, nsteps: int) -> torch.Tensor:
+        self._check_psi(psi)
+        nlse_run(self.ctx, psi.data_ptr(), nsteps)
+        return psi
+
+    def invariants(self, psi: torch.Tensor):
+        """(mass, energy, dt_max) in FP64."""
+        self._check_psi(psi)
+        return nlse_invariants(self.ctx, psi.data_ptr())
+
+    def reset_compensation(self):
+        nlse_reset_compensation(self.ctx)
+
+    def check(self):
+        nlse_check(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nlse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports
+every entry point that include/nlse.h declares, and rejects invalid
+parameters on the host before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1109_1027_gb300 import build as nbuild
+from paper_1109_1027_gb300 import nlse
+
+HEADER_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def declared_functions():
+    names = []
+    for fname in sorted(os.listdir(HEADER_DIR)):
+        if not fname.endswith(".h"):
+            continue
+        with open(os.path.join(HEADER_DIR, fname)) as f:
+            text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(nlse_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nbuild.build()
+    return nlse.load_library()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("nlse_create", "nlse_lap2shoc", "nlse_rk4_step", "nlse_run",
+                     "nlse_invariants", "nlse_destroy", "nlse_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _params(**kw):
+    base = dict(shape=(16, 16), h=0.1, dt=1e-3, a=1.0, s=1.0)
+    base.update(kw)
+    shape = base.pop("shape")
+    return nlse.make_params(shape, **base)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(shape=(2, 16)), nlse.EINVAL),               # n < 3
+    (dict(h=0.0), nlse.EINVAL),
+    (dict(h=float("nan")), nlse.EINVAL),
+    (dict(dt=-1.0), nlse.EINVAL),
+    (dict(a=0.0), nlse.EINVAL),                       # a > 0 (Eq. NLSE)
+    (dict(s=float("inf")), nlse.EINVAL),
+    (dict(bc=5), nlse.EINVAL),
+    (dict(prec=7), nlse.EINVAL),
+    (dict(lap=3), nlse.EINVAL),
+    (dict(bc="msd"), nlse.EUNSUPPORTED),              # MSD is 1D only
+])
+def test_invalid_parameters_are_rejected_on_the_host(lib, kw, code):
+    ctx = ctypes.c_void_p()
+    rc = lib.nlse_create(ctypes.byref(_params(**kw)), ctypes.c_void_p(4096), ctypes.byref(ctx))
+    assert rc == code
+    assert ctx.value is None
+    assert lib.nlse_last_error().decode()
+
+
+def test_dimension_out_of_range(lib):
+    p = _params()
+    p.dim = 4
+    ctx = ctypes.c_void_p()
+    assert lib.nlse_create(ctypes.byref(p), ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EINVAL
+
+
+def test_null_arguments(lib):
+    ctx = ctypes.c_void_p()
+    assert lib.nlse_create(None, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EINVAL
+    assert lib.nlse_create(ctypes.byref(_params()), None, ctypes.byref(ctx)) == nlse.EINVAL
+    assert lib.nlse_rk4_step(None, ctypes.c_void_p(4096), None) == nlse.EINVAL
+    assert lib.nlse_run(None, ctypes.c_void_p(4096), 1, None) == nlse.EINVAL
+    assert lib.nlse_lap2shoc(None, None, None, None) == nlse.EINVAL
+
+
+def test_misaligned_potential_is_rejected(lib):
+    ctx = ctypes.c_void_p()
+    rc = lib.nlse_create(ctypes.byref(_params()), ctypes.c_void_p(4100), ctypes.byref(ctx))
+    assert rc == nlse.EINVAL

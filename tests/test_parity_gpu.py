@@ -1,0 +1,379 @@
+"""Parity of the CUDA library with the FP64 CPU oracle, through the C ABI.
+
+Every input is seeded and synthetic (paper_1109_1027_gb300.workloads); both
+sides receive identical bytes (for FP32 the oracle is fed the FP32-rounded
+input).  Tolerances:
+
+* FP64: 1e-12 relative to the field's scale.  The two sides differ only in
+  rounding order (and FMA contraction on the GPU), a few ulps per operation.
+* FP32, one evaluation of the Laplacian: 2e-6 x max|psi| x (sum of the
+  stencil's |coefficients|)/h^2.  The stencil cancels terms of size
+  max|psi|/h^2, so the absolute error is a few FP32 ulps (6e-8) of that scale
+  times the ~25 operations.
+* FP32 state after RK4 steps: 1e-5 relative L2 (the tolerance the FP32 path
+  is specified to), and 1e-5 x max|psi| pointwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_experiments as pe
+from paper_1109_1027_gb300 import nlse
+from paper_1109_1027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def to_dev(arr, prec):
+    if np.iscomplexobj(arr):
+        dt = torch.complex64 if prec == "fp32" else torch.complex128
+    else:
+        dt = torch.float32 if prec == "fp32" else torch.float64
+    return torch.from_numpy(np.ascontiguousarray(arr)).to(DEV).to(dt).contiguous()
+
+
+def rounded(arr, prec):
+    """The bytes the GPU sees, as FP64 numpy for the oracle."""
+    if prec == "fp64":
+        return np.asarray(arr)
+    if np.iscomplexobj(arr):
+        return np.asarray(arr).astype(np.complex64).astype(np.complex128)
+    return np.asarray(arr).astype(np.float32).astype(np.float64)
+
+
+def lap_scale(psi, h, dim):
+    return np.abs(psi).max() * (64.0 / 12.0) * dim / h ** 2 * 2
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+SHAPES = {
+    1: [(3,), (5,), (1030,), (3001,)],
+    2: [(3, 3), (17, 70), (40, 131), (67, 200)],
+    3: [(3, 3, 3), (9, 20, 37), (35, 18, 40), (70, 33, 19)],
+}
+CASES = [(shape, prec, lap) for d in (1, 2, 3) for shape in SHAPES[d]
+         for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
+
+
+def _problem(shape, seed):
+    psi = wl.random_field(shape, seed=seed)
+    V = wl.random_potential(shape, seed=seed + 1, scale=2.0)
+    return psi, V
+
+
+@pytest.mark.parametrize("shape,prec,lap", CASES)
+def test_laplacian_matches_oracle(shape, prec, lap):
+    h, a, s = 0.37, 0.8, -1.3
+    psi, V = _problem(shape, 100 + len(shape))
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    ref = oracle.laplacian(oracle.Problem(shape, h, a, s, lap=oracle.LAP_CD if lap == "cd" else 0),
+                           psi_r, V_r)
+    solver = nlse.Solver(to_dev(V, prec), h, 1e-3, a, s, prec=prec, lap=lap)
+    got = solver.lap2shoc(to_dev(psi, prec)).cpu().numpy()
+    tol = (1e-12 if prec == "fp64" else 2e-6) * lap_scale(psi_r, h, len(shape))
+    assert np.abs(got - ref).max() <= tol
+
+
+def test_laplacian_msd_1d_matches_oracle():
+    for n in (3, 4, 1025, 2049):
+        for prec in ("fp64", "fp32"):
+            psi, V = _problem((n,), 7)
+            psi = psi + 3.0           # keep psi away from zero at the boundary neighbours
+            h, a, s = 0.21, 1.1, 0.7
+            psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+            ref = oracle.laplacian(oracle.Problem((n,), h, a, s, bc=oracle.BC_MSD), psi_r, V_r)
+            solver = nlse.Solver(to_dev(V, prec), h, 1e-3, a, s, bc="msd", prec=prec)
+            got = solver.lap2shoc(to_dev(psi, prec)).cpu().numpy()
+            tol = (1e-12 if prec == "fp64" else 4e-6) * lap_scale(psi_r, h, 1)
+            assert np.abs(got - ref).max() <= tol, (n, prec)
+
+
+STEP_CASES = [(shape, prec, lap, "dirichlet") for d in (1, 2, 3) for shape in SHAPES[d][1:]
+              for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
+STEP_CASES += [((n,), prec, "2shoc", "msd") for n in (5, 1030, 3001) for prec in ("fp64", "fp32")]
+
+
+@pytest.mark.parametrize("shape,prec,lap,bc", STEP_CASES)
+def test_rk4_steps_match_oracle(shape, prec, lap, bc):
+    a, s = 0.7, -1.1
+    h = 0.5
+    psi, V = _problem(shape, 300 + sum(shape))
+    if bc == "msd":
+        psi = psi + 2.5
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    prob = oracle.Problem(shape, h, a, s, bc=oracle.BC_MSD if bc == "msd" else 0,
+                          lap=oracle.LAP_CD if lap == "cd" else 0)
+    _, _, dtmax = oracle.invariants(prob, psi_r, V_r)
+    k = 0.5 * dtmax
+    nsteps = 5
+    ref = oracle.run(prob, psi_r, V_r, k, nsteps)
+    solver = nlse.Solver(to_dev(V, prec), h, k, a, s, bc=bc, prec=prec, lap=lap)
+    x = to_dev(psi, prec)
+    for _ in range(nsteps):
+        solver.rk4_step(x)
+    solver.check()
+    got = x.cpu().numpy()
+    scale = np.abs(ref).max()
+    if prec == "fp64":
+        assert np.abs(got - ref).max() <= 1e-12 * scale
+    else:
+        assert np.abs(got - ref).max() <= 1e-5 * scale
+        assert rel_l2(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("shape,prec", [((3001,), "fp64"), ((67, 200), "fp32"), ((67, 200), "fp64"),
+                                        ((35, 18, 40), "fp32")])
+def test_run_replays_the_same_steps(shape, prec):
+    """nlse_run (CUDA graph of 32 steps + direct remainder) is bit-identical to
+    repeated nlse_rk4_step."""
+    psi, V = _problem(shape, 55)
+    h, a, s = 0.5, 0.9, 1.0
+    prob = oracle.Problem(shape, h, a, s)
+    _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
+    Vd = to_dev(V, prec)
+    s1 = nlse.Solver(Vd, h, 0.5 * dtmax, a, s, prec=prec)
+    s2 = nlse.Solver(Vd, h, 0.5 * dtmax, a, s, prec=prec)
+    x1, x2 = to_dev(psi, prec), to_dev(psi, prec)
+    s1.run(x1, 70)
+    for _ in range(70):
+        s2.rk4_step(x2)
+    assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("shape", [(1030,), (67, 200), (35, 18, 40)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_invariants_match_oracle(shape, prec):
+    psi, V = _problem(shape, 77)
+    h, a, s = 0.4, 0.6, -0.9
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    m0, e0, d0 = oracle.invariants(oracle.Problem(shape, h, a, s), psi_r, V_r)
+    solver = nlse.Solver(to_dev(V, prec), h, 1e-4, a, s, prec=prec)
+    m, e, d = solver.invariants(to_dev(psi, prec))
+    assert m == pytest.approx(m0, rel=1e-12)
+    assert e == pytest.approx(e0, rel=1e-11)
+    assert d == pytest.approx(d0, rel=1e-12)
+
+
+def test_invariants_msd_1d_match_oracle():
+    n = 1030
+    psi, V = _problem((n,), 78)
+    psi = psi + 2.0
+    h, a, s = 0.4, 0.6, -0.9
+    m0, e0, d0 = oracle.invariants(oracle.Problem((n,), h, a, s, bc=oracle.BC_MSD), psi, V)
+    solver = nlse.Solver(to_dev(V, "fp64"), h, 1e-4, a, s, bc="msd", prec="fp64")
+    m, e, d = solver.invariants(to_dev(psi, "fp64"))
+    assert (m, e, d) == (pytest.approx(m0, rel=1e-12), pytest.approx(e0, rel=1e-11),
+                         pytest.approx(d0, rel=1e-12))
+
+
+def test_dirichlet_boundary_is_bit_exact_over_a_run():
+    """Eq. (dbc_ut): F_b = 0, so boundary values never change, in either precision."""
+    for prec in ("fp32", "fp64"):
+        inst = wl.dark_vortex_2d(n=130, steps=0)
+        prob = oracle.Problem(inst.shape, inst.h, inst.a, inst.s)
+        _, _, dtmax = oracle.invariants(prob, inst.psi0, inst.V)
+        solver = nlse.Solver(to_dev(inst.V, prec), inst.h, 0.5 * dtmax, inst.a, inst.s, prec=prec)
+        x = to_dev(inst.psi0, prec)
+        x0 = x.clone()
+        solver.run(x, 40)
+        for sl in [(0, slice(None)), (-1, slice(None)), (slice(None), 0), (slice(None), -1)]:
+            assert torch.equal(x[sl], x0[sl])
+
+
+# -- the workloads at reduced size / steps ------------------------------------
+
+def test_bright_soliton_1d_full_config():
+    """1D bright soliton, FP64, n = 2048 on [-40, 40], dt = 0.5 dt_max, 2000
+    steps: GPU = oracle to 1e-12 (relative L2), and both follow the exact
+    travelling sech soliton to the scheme's accuracy."""
+    inst = wl.bright_soliton_1d()
+    prob = oracle.Problem(inst.shape, inst.h, inst.a, inst.s)
+    _, _, dtmax = oracle.invariants(prob, inst.psi0, inst.V)
+    k = 0.5 * dtmax
+    ref = oracle.run(prob, inst.psi0, inst.V, k, inst.steps)
+    solver = nlse.Solver(to_dev(inst.V, "fp64"), inst.h, k, inst.a, inst.s, prec="fp64")
+    x = to_dev(inst.psi0, "fp64")
+    solver.run(x, inst.steps)
+    got = x.cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-12
+    x_axis = wl.axis(inst.shape[0], inst.lo, inst.hi)
+    exact = pe.bright_soliton(x_axis, inst.steps * k, x0=inst.meta["x0"], c=inst.meta["c"])
+    assert rel_l2(got, exact) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_dark_vortex_2d_reduced(prec, tol):
+    """2D dark vortex on a 256^2 crop of the workload's recipe, 200 steps."""
+    inst = wl.dark_vortex_2d(n=256, steps=200)
+    prob = oracle.Problem(inst.shape, inst.h, inst.a, inst.s)
+    _, _, dtmax = oracle.invariants(prob, inst.psi0, inst.V)
+    k = 0.5 * dtmax
+    psi_r, V_r = rounded(inst.psi0, prec), rounded(inst.V, prec)
+    ref = oracle.run(prob, psi_r, V_r, k, inst.steps)
+    solver = nlse.Solver(to_dev(inst.V, prec), inst.h, k, inst.a, inst.s, prec=prec)
+    x = to_dev(inst.psi0, prec)
+    solver.run(x, inst.steps)
+    assert rel_l2(x.cpu().numpy(), ref) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_vortex_ring_3d_reduced(prec, tol):
+    """3D vortex ring on a 48^3 grid of the workload's recipe, 60 steps."""
+    inst = vr = wl.vortex_ring_3d(n=48, steps=60)
+    prob = oracle.Problem(inst.shape, inst.h, inst.a, inst.s)
+    _, _, dtmax = oracle.invariants(prob, inst.psi0, inst.V)
+    k = 0.5 * dtmax
+    psi_r, V_r = rounded(vr.psi0, prec), rounded(vr.V, prec)
+    ref = oracle.run(prob, psi_r, V_r, k, inst.steps)
+    solver = nlse.Solver(to_dev(inst.V, prec), inst.h, k, inst.a, inst.s, prec=prec)
+    x = to_dev(inst.psi0, prec)
+    solver.run(x, inst.steps)
+    assert rel_l2(x.cpu().numpy(), ref) <= tol
+
+
+def _crop_one_step(psi, V, inst, k, y, x, r=10):
+    """Oracle value of one RK4 step at (y, x): the step's result at a point
+    depends only on the state within 8 points (four stages, two points
+    each), so it is computed on a window of half-width r >= 9 that keeps
+    the grid's real boundary where the window reaches it."""
+    ny, nx = psi.shape
+    y0, y1 = max(0, y - r), min(ny, y + r + 1)
+    x0, x1 = max(0, x - r), min(nx, x + r + 1)
+    sub = psi[y0:y1, x0:x1]
+    out = oracle.run(oracle.Problem(sub.shape, inst.h, inst.a, inst.s), sub, V[y0:y1, x0:x1], k, 1)
+    return out[y - y0, x - x0]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_dark_vortex_2d_full_size_sampled(prec):
+    """The 2048^2 workload in the benchmark's launch configuration: one RK4
+    step through nlse_run, checked at sampled points (incl. corners, edges
+    and the vortex core) against the oracle on windows."""
+    inst = wl.dark_vortex_2d()
+    prob_small = oracle.Problem((64, 64), inst.h, inst.a, inst.s)
+    psi_r, V_r = rounded(inst.psi0, prec), rounded(inst.V, prec)
+    # dt from the oracle's bound on the full state
+    _, _, dtmax = oracle.invariants(oracle.Problem(inst.shape, inst.h, inst.a, inst.s), psi_r, V_r)
+    k = 0.5 * dtmax
+    solver = nlse.Solver(to_dev(inst.V, prec), inst.h, k, inst.a, inst.s, prec=prec,
+                         check_stability=False)
+    x = to_dev(inst.psi0, prec)
+    solver.run(x, 1)
+    got = x.cpu().numpy()
+    n = inst.shape[0]
+    rng = np.random.Generator(np.random.PCG64(2024))
+    pts = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (1, 1), (n // 2, n // 2), (n // 2 + 1, n // 2),
+           (2, n // 3), (n - 2, 700), (63, 64), (64, 63), (1000, 1023)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(36)]
+    tol = (1e-12 if prec == "fp64" else 1e-6) * np.abs(psi_r).max()
+    del prob_small
+    for (yy, xx) in pts:
+        ref = _crop_one_step(psi_r, V_r, inst, k, yy, xx)
+        assert abs(got[yy, xx] - ref) <= tol, (yy, xx, got[yy, xx], ref)
+
+
+# -- the paper's accuracy experiments on the GPU -------------------------------
+
+TABLES = pe.read_tables(pe.__file__.replace("paper_experiments.py", "golden/paper_tables.txt"))
+
+
+def _gpu_runner(name, h, lap):
+    st = pe.setup(name, h)
+    solver = nlse.Solver(to_dev(st["V"], "fp64"), h, st["k"], st["a"], st["s"],
+                         bc="msd" if st["bc"] == 1 else "dirichlet", prec="fp64", lap=lap,
+                         check_stability=False)
+
+    def run(p, n):
+        x = to_dev(p, "fp64")
+        solver.run(x, n)
+        return x.cpu().numpy()
+    return run
+
+
+@pytest.mark.parametrize("lap,scheme", [("2shoc", "2SHOC"), ("cd", "CD")])
+def test_paper_table_2d_on_gpu(lap, scheme):
+    """Fig. f:num2d table (Sec. 4.2), FP64 on the GPU, h = 1 .. 1/8."""
+    for i, h in enumerate(pe.E23_H[:4]):
+        er, ei = pe.measure("E2", h, _gpu_runner("E2", h, lap))
+        assert er == pytest.approx(TABLES[("E2", scheme, "real")][i], rel=2e-4)
+        assert ei == pytest.approx(TABLES[("E2", scheme, "imag")][i], rel=2e-4)
+
+
+def test_paper_table_1d_on_gpu():
+    """Fig. f:num1d table (Sec. 4.1), MSD boundaries, FP64 on the GPU: the
+    printed orders of the 2SHOC errors to 0.01."""
+    got = [pe.measure("E1", h, _gpu_runner("E1", h, "2shoc")) for h in pe.E1_H]
+    ref = TABLES[("E1", "2SHOC", "real")]
+    for i in range(4):
+        o = pe.order(got[i][0], got[i + 1][0], pe.E1_H[i], pe.E1_H[i + 1])
+        assert o == pytest.approx(pe.order(ref[i], ref[i + 1], 2, 1), abs=1e-2)
+
+
+def test_paper_table_3d_on_gpu():
+    """Fig. f:num3d table (Sec. 4.3), FP64 on the GPU, h = 1, 1/2, 1/4."""
+    for i, h in enumerate(pe.E23_H[:3]):
+        er, ei = pe.measure("E3", h, _gpu_runner("E3", h, "2shoc"))
+        assert er == pytest.approx(TABLES[("E3", "2SHOC", "real")][i], rel=2e-4)
+        assert ei == pytest.approx(TABLES[("E3", "2SHOC", "imag")][i], rel=2e-4)
+
+
+# -- failure reporting ---------------------------------------------------------
+
+def test_nonfinite_state_is_reported():
+    shape = (40, 70)
+    psi, V = _problem(shape, 5)
+    psi[20, 30] = np.nan
+    solver = nlse.Solver(to_dev(V, "fp32"), 0.5, 1e-3, 1.0, 1.0, prec="fp32", check_stability=False)
+    x = to_dev(psi, "fp32")
+    with pytest.raises(nlse.NLSEError) as ei:
+        solver.invariants(x)
+    assert ei.value.code == nlse.ENONFINITE
+    solver.rk4_step(x)
+    with pytest.raises(nlse.NLSEError) as ei:
+        solver.check()
+    assert ei.value.code == nlse.ENONFINITE
+    solver.check()       # the flag was cleared
+
+
+def test_unstable_time_step_is_refused():
+    shape = (64,)
+    psi, V = _problem(shape, 6)
+    prob = oracle.Problem(shape, 0.25, 1.0, 0.0)
+    _, _, dtmax = oracle.invariants(prob, psi, np.zeros(shape))
+    solver = nlse.Solver(to_dev(np.zeros(shape), "fp64"), 0.25, 1.2 * dtmax, 1.0, 0.0, prec="fp64")
+    x = to_dev(psi, "fp64")
+    x0 = x.clone()
+    with pytest.raises(nlse.NLSEError) as ei:
+        solver.run(x, 10)
+    assert ei.value.code == nlse.EUNSTABLE
+    assert torch.equal(x, x0)
+
+
+def test_bad_tensors_are_rejected():
+    solver = nlse.Solver(to_dev(np.zeros((8, 8)), "fp32"), 0.5, 1e-3, 1.0, 1.0)
+    with pytest.raises(ValueError):
+        solver.rk4_step(torch.zeros((8, 8), dtype=torch.complex128, device=DEV))
+    with pytest.raises(ValueError):
+        solver.rk4_step(torch.zeros((8, 9), dtype=torch.complex64, device=DEV))
+    with pytest.raises(ValueError):
+        solver.rk4_step(torch.zeros((8, 8), dtype=torch.complex64))
+
+
+def test_compensation_resets_when_the_state_changes():
+    """The FP32 low part belongs to one state: switching psi buffers resets it,
+    so two independent runs from the same start agree bit for bit."""
+    inst = wl.dark_vortex_2d(n=96, steps=0)
+    prob = oracle.Problem(inst.shape, inst.h, inst.a, inst.s)
+    _, _, dtmax = oracle.invariants(prob, inst.psi0, inst.V)
+    solver = nlse.Solver(to_dev(inst.V, "fp32"), inst.h, 0.5 * dtmax, inst.a, inst.s)
+    a_ = to_dev(inst.psi0, "fp32")
+    b_ = to_dev(inst.psi0, "fp32")
+    solver.run(a_, 40)
+    solver.run(b_, 40)
+    assert torch.equal(a_, b_)
