@@ -52,6 +52,8 @@ WORKLOAD = ("2D NLSE/GPE dark vortex 2048x2048 on [-60,60]^2, a=0.5, s=-1, V=0.0
 BYTES_PER_UPDATE_FP32 = 168
 # FP64 fused path (complex128 = 16 B, V double = 8 B, no low part): 56 + 88 + 88 + 72.
 BYTES_PER_UPDATE_FP64 = 304
+# The paper's unfused FP64 schedule: 4 x (D: 32 + F: 56) + axpy lines 5 x 48 + 64.
+BYTES_PER_UPDATE_PLAIN = 656
 # DRAM bytes per stage launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean over the four stages) for the stage kernel
 # source with the given hash; null when the kernel has changed since.
@@ -277,6 +279,21 @@ def run_ours(args):
     m64, en64, _ = s64.invariants(x64)
     m0, en0, _ = s64.invariants(psi0.clone())
 
+    # ---- the paper's unfused FP64 schedule on the same GPU (baseline) -------
+    kp = min(args.steps, 1000)
+    sp = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", plain=True)
+    xp = psi0.clone().contiguous()
+    sp.run(xp, args.warmup)
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    sp.run(xp, kp)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    msp = max_over_ranks(g0.elapsed_time(g1))
+    sp.check()
+    sp.close()
+
     # ---- end to end through host buffers ------------------------------------
     ke = min(args.steps, 200)
     host_in = torch.empty((N_SIDE, N_SIDE), dtype=torch.complex64, pin_memory=True)
@@ -338,6 +355,10 @@ def run_ours(args):
             "fp64_fused": {"value": world * npts * args.steps / (ms64 * 1e-3), "unit": UNIT,
                            "ms_per_step": ms64 / args.steps,
                            "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / args.steps * 1e-3) / 1e9},
+            "fp64_plain": {"value": world * npts * kp / (msp * 1e-3), "unit": UNIT, "steps": kp,
+                           "ms_per_step": msp / kp,
+                           "achieved_gbs": BYTES_PER_UPDATE_PLAIN * npts / (msp / kp * 1e-3) / 1e9,
+                           "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"},
             "fp32_vs_fp64_rel_l2": l2,
             "mass_drift": {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1},
             "energy_drift": {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1},

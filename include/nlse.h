@@ -69,6 +69,11 @@ typedef enum {
 
 /* nlse_params.flags */
 #define NLSE_FLAG_NO_STABILITY_CHECK 1u  /* nlse_run skips the entry check of dt  */
+#define NLSE_FLAG_PLAIN_SCHEDULE 2u      /* step with the paper's unfused schedule
+                                            (Sec. 3.1): D, K_tot, K_tmp, Psi_tmp as
+                                            full device arrays, one launch per
+                                            line of Eq. (RK4); no compensation.
+                                            Dirichlet only.  A baseline.        */
 
 typedef struct {
     int dim;                /* 1, 2 or 3                                              */

@@ -50,6 +50,7 @@ struct nlse_ctx {
     void* Y[2];               // stage inputs (ping-pong)
     void* acc;                // accumulated RK4 increment
     void* lo;                 // FP32 compensated low part (FP32 only)
+    void* plain[4];           // unfused schedule: D, K_tot, K_tmp, Psi_tmp
     int* flag;                // non-finite flag set by stage 4
     double* partials;         // reduction scratch, nblocks x kPartialWidth
     int nblocks;
@@ -81,6 +82,8 @@ int validate(const nlse_params* p) {
     if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD) return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
     if (p->bc == NLSE_BC_MSD && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "MSD boundaries are implemented for dim = 1 only");
+    if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->bc != NLSE_BC_DIRICHLET)
+        return fail(NLSE_EUNSUPPORTED, "the unfused schedule supports Dirichlet boundaries only");
     return NLSE_OK;
 }
 
@@ -106,8 +109,24 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     }
 }
 
+// One step of the paper's unfused schedule (plain.cu).
+int enqueue_plain_step(nlse_ctx* c, void* psi, cudaStream_t st) {
+    nlse::PlainLaunch L;
+    L.dim = c->p.dim;
+    for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+    L.prec = c->p.prec; L.lap = c->p.lap;
+    L.h = c->p.h; L.a = c->p.a; L.s = c->p.s; L.dt = c->p.dt;
+    L.psi = psi; L.V = c->V;
+    L.D = c->plain[0]; L.Ktot = c->plain[1]; L.Ktmp = c->plain[2]; L.ptmp = c->plain[3];
+    L.flag = c->flag;
+    cudaError_t e = nlse::launch_plain_step(L, st);
+    if (e != cudaSuccess) return cuda_fail(e, "unfused RK4 step launch");
+    return NLSE_OK;
+}
+
 // The four fused stages of one RK4 step (Eq. RK4) on psi, in place.
 int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
+    if (c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) return enqueue_plain_step(c, psi, st);
     StageLaunch L = base_launch(c);
     L.psi = psi;
     L.psi_out = psi;
@@ -180,6 +199,7 @@ void release(nlse_ctx* c) {
     cudaFree(c->Y[1]);
     cudaFree(c->acc);
     cudaFree(c->lo);
+    for (int i = 0; i < 4; ++i) cudaFree(c->plain[i]);
     cudaFree(c->flag);
     cudaFree(c->partials);
     cudaFree(c->red_out);
@@ -215,10 +235,14 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
 #define TRY(call, what) do { e = (call); if (e != cudaSuccess) { rc = cuda_fail(e, what); release(c); return rc; } } while (0)
     TRY(cudaGetDevice(&c->device), "cudaGetDevice");
     TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device query");
-    TRY(cudaMalloc(&c->Y[0], c->cbytes), "allocating stage buffer");
-    TRY(cudaMalloc(&c->Y[1], c->cbytes), "allocating stage buffer");
-    TRY(cudaMalloc(&c->acc, c->cbytes), "allocating accumulator");
-    if (p->prec == NLSE_FP32) {
+    if (p->flags & NLSE_FLAG_PLAIN_SCHEDULE) {
+        for (int i = 0; i < 4; ++i) TRY(cudaMalloc(&c->plain[i], c->cbytes), "allocating RK4 work array");
+    } else {
+        TRY(cudaMalloc(&c->Y[0], c->cbytes), "allocating stage buffer");
+        TRY(cudaMalloc(&c->Y[1], c->cbytes), "allocating stage buffer");
+        TRY(cudaMalloc(&c->acc, c->cbytes), "allocating accumulator");
+    }
+    if (p->prec == NLSE_FP32 && !(p->flags & NLSE_FLAG_PLAIN_SCHEDULE)) {
         TRY(cudaMalloc(&c->lo, c->cbytes), "allocating compensated part");
         TRY(cudaMemset(c->lo, 0, c->cbytes), "zeroing compensated part");
     }

@@ -32,6 +32,21 @@ cudaError_t launch_stage_1d(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st);
 
+// One RK4 step of the paper's unfused schedule (plain.cu): D, K_tot, K_tmp
+// and Psi_tmp are full device arrays (Sec. 3.1).
+struct PlainLaunch {
+    int dim;
+    int64_t n[3];
+    int prec, lap;
+    double h, a, s, dt;
+    void* psi;
+    const void* V;
+    void *D, *Ktot, *Ktmp, *ptmp;
+    int* flag;
+};
+
+cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st);
+
 // FP64 reductions for nlse_invariants.  Each of the nblocks blocks of the
 // partial kernel writes kPartialWidth doubles to partials; the final kernel
 // reduces them in a fixed order into out[0..kPartialWidth).

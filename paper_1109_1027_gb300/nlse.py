@@ -25,6 +25,7 @@ BC = {"dirichlet": 0, "msd": 1}
 PREC = {"fp32": 0, "fp64": 1}
 LAP = {"2shoc": 0, "cd": 1}
 FLAG_NO_STABILITY_CHECK = 1
+FLAG_PLAIN_SCHEDULE = 2
 
 _STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
                  "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
@@ -95,7 +96,7 @@ def _stream(stream) -> ctypes.c_void_p:
 
 
 def make_params(shape, h, dt, a, s, bc="dirichlet", prec="fp32", lap="2shoc",
-                check_stability=True) -> Params:
+                check_stability=True, plain=False) -> Params:
     """Params for a grid of ``shape`` = (nx,), (ny, nx) or (nz, ny, nx) (x fastest)."""
     p = Params()
     p.dim = len(shape)
@@ -106,7 +107,7 @@ def make_params(shape, h, dt, a, s, bc="dirichlet", prec="fp32", lap="2shoc",
     p.bc = BC[bc] if isinstance(bc, str) else int(bc)
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     p.lap = LAP[lap] if isinstance(lap, str) else int(lap)
-    p.flags = 0 if check_stability else FLAG_NO_STABILITY_CHECK
+    p.flags = (0 if check_stability else FLAG_NO_STABILITY_CHECK) | (FLAG_PLAIN_SCHEDULE if plain else 0)
     return p
 
 
@@ -154,11 +155,12 @@ class Solver:
 
     ``V`` is a CUDA tensor shaped (nx,), (ny, nx) or (nz, ny, nx); float32 for
     ``prec="fp32"`` (state complex64) or float64 for ``prec="fp64"``
-    (complex128).  The solver keeps a reference to V."""
+    (complex128).  The solver keeps a reference to V.  ``plain=True`` selects
+    the paper's unfused schedule (a baseline, Dirichlet only)."""
 
     def __init__(self, V: torch.Tensor, h: float, dt: float, a: float, s: float,
                  bc: str = "dirichlet", prec: str = "fp32", lap: str = "2shoc",
-                 check_stability: bool = True):
+                 check_stability: bool = True, plain: bool = False):
         load_library()
         want = torch.float32 if prec == "fp32" else torch.float64
         if not V.is_cuda or V.dtype != want or not V.is_contiguous():
@@ -167,7 +169,7 @@ class Solver:
         self.shape = tuple(V.shape)
         self.prec = prec
         self.cdtype = torch.complex64 if prec == "fp32" else torch.complex128
-        self.params = make_params(self.shape, h, dt, a, s, bc, prec, lap, check_stability)
+        self.params = make_params(self.shape, h, dt, a, s, bc, prec, lap, check_stability, plain)
         with torch.cuda.device(V.device):
             self.ctx = nlse_create(self.params, V.data_ptr())
 

@@ -127,6 +127,23 @@ def test_rk4_steps_match_oracle(shape, prec, lap, bc):
         assert rel_l2(got, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("shape", [(1030,), (67, 200), (35, 18, 40)])
+@pytest.mark.parametrize("lap", ["2shoc", "cd"])
+def test_unfused_schedule_matches_oracle(shape, lap):
+    """The paper's own unfused schedule (NLSE_FLAG_PLAIN_SCHEDULE), FP64."""
+    a, s, h = 0.7, -1.1, 0.5
+    psi, V = _problem(shape, 400 + sum(shape))
+    prob = oracle.Problem(shape, h, a, s, lap=oracle.LAP_CD if lap == "cd" else 0)
+    _, _, dtmax = oracle.invariants(prob, psi, V)
+    k = 0.5 * dtmax
+    ref = oracle.run(prob, psi, V, k, 40)
+    solver = nlse.Solver(to_dev(V, "fp64"), h, k, a, s, prec="fp64", lap=lap, plain=True)
+    x = to_dev(psi, "fp64")
+    solver.run(x, 40)
+    solver.check()
+    assert np.abs(x.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("shape,prec", [((3001,), "fp64"), ((67, 200), "fp32"), ((67, 200), "fp64"),
                                         ((35, 18, 40), "fp32")])
 def test_run_replays_the_same_steps(shape, prec):
