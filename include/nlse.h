@@ -147,6 +147,24 @@ int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
  * kernel); clears the flag. */
 int nlse_check(nlse_ctx* ctx, void* stream);
 
+/* nlse_invariants without a context and without allocating anything.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device memory -- code inside a framework that owns all device memory
+ * through its own pool or budget, or a latency-critical path that cannot
+ * take the device synchronisation a cudaMalloc may cause -- and so cannot
+ * create an nlse_ctx.  Same reductions as nlse_invariants (p->dt and flags
+ * are ignored; an FP32 state is taken as psi_dev alone, without a
+ * compensated part), with the block partials in a static device array of
+ * 786,480 bytes that the library holds on every GPU that loads it, for the
+ * life of the process.  Grids above 67,108,864 points are rejected with
+ * NLSE_EINVAL.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (unordered streams) race and must not be issued.  Synchronises
+ * the stream; writes the three host doubles (any may be NULL). */
+int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const void* V_dev,
+                            double* mass, double* energy, double* dt_max, void* stream);
+
 /* Human-readable description of the calling thread's last error ("" if none). */
 const char* nlse_last_error(void);
 

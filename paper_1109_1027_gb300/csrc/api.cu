@@ -209,6 +209,10 @@ void release(nlse_ctx* c) {
 
 }  // namespace
 
+namespace nlse {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace nlse
+
 extern "C" {
 
 const char* nlse_last_error(void) { return g_err; }

@@ -64,6 +64,9 @@ struct InvLaunch {
 };
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);
+
+// Records msg as the calling thread's nlse_last_error() and returns code.
+int report_error(int code, const char* msg);
 cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks, double* out,
                               cudaStream_t st);
 

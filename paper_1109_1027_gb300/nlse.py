@@ -73,6 +73,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_reset_compensation": ([vp, vp], ctypes.c_int),
         "nlse_check": ([vp, vp], ctypes.c_int),
         "nlse_last_error": ([], ctypes.c_char_p),
+        "nlse_invariants_noalloc": ([ctypes.POINTER(Params), vp, vp, dp, dp, dp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -139,6 +140,16 @@ def nlse_invariants(ctx, psi_ptr: int, stream=None):
     m, e, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _raise(load_library().nlse_invariants(ctx, ctypes.c_void_p(psi_ptr), ctypes.byref(m),
                                           ctypes.byref(e), ctypes.byref(d), _stream(stream)))
+    return m.value, e.value, d.value
+
+
+def nlse_invariants_noalloc(params: Params, psi_ptr: int, V_ptr: int, stream=None):
+    """(mass, energy, dt_max) without a context: for callers that cannot
+    allocate device memory; the library's static scratch is used instead."""
+    m, e, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _raise(load_library().nlse_invariants_noalloc(ctypes.byref(params), ctypes.c_void_p(psi_ptr),
+                                                  ctypes.c_void_p(V_ptr), ctypes.byref(m),
+                                                  ctypes.byref(e), ctypes.byref(d), _stream(stream)))
     return m.value, e.value, d.value
 
 
