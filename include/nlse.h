@@ -144,7 +144,8 @@ int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
 
 /* Synchronises the stream and reports NLSE_ENONFINITE if any RK4 step since
  * the last check produced a NaN or Inf (a device flag set by the last stage
- * kernel); clears the flag. */
+ * kernel), or NLSE_ETIMEOUT if a kernel gave up a bounded wait for its own
+ * data transfers; clears the flag. */
 int nlse_check(nlse_ctx* ctx, void* stream);
 
 /* nlse_invariants without a context and without allocating anything.  The

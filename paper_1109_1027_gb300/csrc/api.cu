@@ -376,6 +376,8 @@ int nlse_check(nlse_ctx* c, void* stream) {
     NLSE_CUDA(cudaStreamSynchronize(st), "flag synchronise");
     if (h) {
         NLSE_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), st), "flag reset");
+        NLSE_CUDA(cudaStreamSynchronize(st), "flag synchronise");
+        if (h & 2) return fail(NLSE_ETIMEOUT, "a bounded device-side wait gave up (a data transfer never completed)");
         return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
     }
     return NLSE_OK;

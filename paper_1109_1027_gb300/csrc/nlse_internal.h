@@ -25,11 +25,15 @@ struct StageLaunch {
     void* yout;             // next stage input
     void* lap_out;          // stage 0 output
     const void* V;
-    int* flag;              // stage 4 sets *flag = 1 on a non-finite result
+    int* flag;              // status bits: 1 = non-finite result (stage 4),
+                            // 2 = a bounded device-side wait timed out
 };
 
 cudaError_t launch_stage_1d(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
+// The TMA-fed y-streaming 2D kernel (stage2d_tma.cu) and when it applies.
+bool stage_2d_tma_eligible(const StageLaunch& L);
+cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st);
 
 // One RK4 step of the paper's unfused schedule (plain.cu): D, K_tot, K_tmp

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, R w, const cplx<
     if (p >= n) return;
     cplx<R> v = caxpy(psi[p], w, cadd(a[p], b[p]));
     psi[p] = v;
-    if (!(isfinite(v.x) && isfinite(v.y))) atomicExch(flag, 1);
+    if (!(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
 }
 
 template <typename R>

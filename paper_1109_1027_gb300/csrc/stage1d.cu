@@ -96,7 +96,7 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
         }
     }
     if constexpr (STAGE == 4) {
-        if (__syncthreads_or(bad) && tid == 0) atomicExch(io.flag, 1);
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(io.flag, 1);
     }
 }
 

@@ -1,4 +1,6 @@
-// stage2d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 2D grid.
+// stage2d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 2D grid,
+// generic tile kernel for grids whose rows TMA cannot address (row pitch not
+// a multiple of 16 bytes); the TMA-fed kernel in stage2d_tma.cu serves the rest.
 //
 // One CTA owns a TX x TY tile of output points.  It stages the stage input
 // with a 2-point halo in shared memory, computes step 1 of the 2SHOC scheme,
@@ -91,7 +93,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         }
     }
     if constexpr (STAGE == 4) {
-        if (__syncthreads_or(bad) && tid == 0) atomicExch(io.flag, 1);
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(io.flag, 1);
     }
 }
 
@@ -124,6 +126,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st) {
+    if (stage_2d_tma_eligible(L)) return launch_stage_2d_tma(L, st);
     const bool cd = L.lap == 1;
     if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
     return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);

@@ -129,7 +129,7 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
         __syncthreads();
     }
     if constexpr (STAGE == 4) {
-        if (__syncthreads_or(bad) && tid == 0) atomicExch(io.flag, 1);
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(io.flag, 1);
     }
 }
 

@@ -54,7 +54,9 @@ def rel_l2(a, b):
 
 SHAPES = {
     1: [(3,), (5,), (1030,), (3001,)],
-    2: [(3, 3), (17, 70), (40, 131), (67, 200)],
+    # widths divisible by 4 run the TMA-fed streaming kernel (ragged CTA
+    # tails in x and y included); the others the generic tile kernel
+    2: [(3, 3), (17, 70), (40, 131), (67, 200), (45, 260), (100, 388), (33, 4), (70, 128)],
     3: [(3, 3, 3), (9, 20, 37), (35, 18, 40), (70, 33, 19)],
 }
 CASES = [(shape, prec, lap) for d in (1, 2, 3) for shape in SHAPES[d]
@@ -145,7 +147,7 @@ def test_unfused_schedule_matches_oracle(shape, lap):
 
 
 @pytest.mark.parametrize("shape,prec", [((3001,), "fp64"), ((67, 200), "fp32"), ((67, 200), "fp64"),
-                                        ((35, 18, 40), "fp32")])
+                                        ((35, 18, 40), "fp32"), ((40, 131), "fp32")])
 def test_run_replays_the_same_steps(shape, prec):
     """nlse_run (CUDA graph of 32 steps + direct remainder) is bit-identical to
     repeated nlse_rk4_step."""
