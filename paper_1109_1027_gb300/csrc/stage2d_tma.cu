@@ -1,16 +1,19 @@
 // stage2d_tma.cu -- the fused 2D RK4 stage (and standalone 2SHOC Laplacian)
 // as a y-streaming kernel fed by the tensor memory accelerator.
 //
-// One CTA of TX threads owns TX consecutive columns and walks down TY rows.
-// A ring of S row slots in shared memory is filled by TMA tile loads (one
-// mbarrier per slot), S rows ahead of use:
-//   * the stage input row with a 2-point x halo,
-//   * the potential V row (x halo 4, for the boundary rule),
-//   * on output rows: Psi^n, the accumulator and (stage 4, FP32) the
-//     compensated low part.
-// Each thread keeps its column's stage input and D in registers as a sliding
-// window; only the x neighbours of D travel through a two-row shared ring.
-// Per output row y, with D(x, y+1) computed one row ahead:
+// One CTA of NT threads owns TXC = 2 NT consecutive columns (two per thread)
+// and walks down TY rows.  Two rings of shared-memory row slots are filled by
+// TMA tile loads, each slot completing on its own mbarrier:
+//   * the input ring (S slots, up to S rows ahead): the stage input row with
+//     a 2-point x halo (a TXC-point and a 4-point TMA box, so that both land
+//     on 128-byte aligned shared addresses);
+//   * the epilogue ring (2 slots, one output row ahead): V, and for stages
+//     2-4 Psi^n and the RK4 accumulator (stage 4 in FP32: the compensated
+//     part too) on the output row.
+// Each thread keeps its two columns' stage input, their outer x neighbours
+// and D in registers as a sliding window; the x neighbours of D travel
+// through a two-row shared ring.  Per output row y, with D(., y+1) formed one
+// row ahead:
 //   step 1 (Eq. 2d2shocs1): D = (sum of the four axial Psi - 4 Psi_c) / h^2,
 //                           boundary points D_b of Eq. (dbc_lap);
 //   step 2 (Eq. 2d2shocs2): Lap = D_c - (1/12) sum of the four axial D
@@ -19,7 +22,7 @@
 //   the RK4 stage epilogue (Eq. RK4, accumulated-increment form).
 // Complex64 arithmetic uses the packed f32x2 instructions.  Every mbarrier
 // wait is bounded (1 s); on timeout the CTA sets bit 2 of the status flag,
-// drains its own copies in flight and returns.
+// lets its own copies in flight land and returns.
 #include <mutex>
 
 #include "nlse_device.cuh"
@@ -28,34 +31,40 @@
 namespace nlse {
 namespace {
 
-constexpr int TX = 128;              // columns per CTA (= threads)
-constexpr int TY = 32;               // rows per CTA
-constexpr int S = 6;                 // row slots in flight
+constexpr int NT = 128;              // threads per CTA
+constexpr int TXC = 2 * NT;          // columns per CTA
+constexpr int HB = TXC;              // first input TMA box: x0-2 .. x0+TXC-3
+constexpr int HB2 = 4;               // second input TMA box: x0+TXC-2 .. x0+TXC+1
+constexpr int TY = 16;               // rows per CTA
+constexpr int S = 6;                 // input ring slots
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint64_t kDrainNs = 50000000ull;
 
 constexpr int al128(int v) { return (v + 127) / 128 * 128; }
 
+// Shared-memory layout.  Input rows and D rows are indexed by column
+// x - (x0 - 2), so a thread's column pair (xa, xa+1) sits at the 16-byte
+// aligned index 2t + 2.  Every TMA destination is 128-byte aligned.
 template <typename R>
 struct Lay {
     static constexpr int CB = (int)sizeof(cplx<R>);
-    static constexpr int P_BYTES = (TX + 4) * CB;            // stage input row, x0-2 .. x0+TX+1
-    static constexpr int V_BYTES = (TX + 8) * (int)sizeof(R);  // V row, x0-4 .. x0+TX+3
-    static constexpr int T_BYTES = TX * CB;                  // Psi^n / acc / lo rows, x0 .. x0+TX-1
-    static constexpr int P_OFF = 0;
-    static constexpr int V_OFF = al128(P_BYTES);
-    static constexpr int PSI_OFF = V_OFF + al128(V_BYTES);
-    static constexpr int ACC_OFF = PSI_OFF + T_BYTES;
-    static constexpr int LO_OFF = ACC_OFF + T_BYTES;
-    static constexpr int SLOT = LO_OFF + (sizeof(R) == 4 ? T_BYTES : 0);
-    static constexpr int D_ROW = TX + 2;                     // D row, x0-1 .. x0+TX
-    static constexpr int D_OFF = S * SLOT;
-    static constexpr int BAR_OFF = al128(D_OFF + 2 * D_ROW * CB);
-    static constexpr int TOTAL = BAR_OFF + 8 * S + 128;      // +128: base alignment slack
+    static constexpr int ROW = TXC + 4;                       // x0-2 .. x0+TXC+1
+    static constexpr int IN_BYTES = ROW * CB;
+    static constexpr int IN_SLOT = al128(IN_BYTES);
+    static constexpr int T_BYTES = TXC * CB;                  // one complex output row
+    static constexpr int V_BYTES = TXC * (int)sizeof(R);
+    static constexpr int E_PSI = 0, E_ACC = T_BYTES, E_LO = 2 * T_BYTES;
+    static constexpr int E_V = E_LO + (sizeof(R) == 4 ? T_BYTES : 0);
+    static constexpr int E_SLOT = al128(E_V + V_BYTES);
+    static constexpr int IN_OFF = 0;
+    static constexpr int E_OFF = S * IN_SLOT;
+    static constexpr int D_OFF = E_OFF + 2 * E_SLOT;
+    static constexpr int BAR_OFF = al128(D_OFF + 2 * ROW * CB);
+    static constexpr int TOTAL = BAR_OFF + 8 * (S + 2) + 128;   // +128: base alignment slack
 };
 
 template <typename R>
-__device__ __forceinline__ void load_cplx_row(uint32_t dst, const CUtensorMap* m, int x, int r, uint32_t bar) {
+__device__ __forceinline__ void load_cplx_box(uint32_t dst, const CUtensorMap* m, int x, int r, uint32_t bar) {
     if constexpr (sizeof(R) == 4) tma_load_2d(dst, m, x, r, bar);       // complex64 as 8-byte elements
     else tma_load_3d(dst, m, 0, x, r, bar);                             // complex128 as (re, im) doubles
 }
@@ -64,64 +73,91 @@ template <typename C> __device__ __forceinline__ C pair(decltype(C::x) a, declty
     C z; z.x = a; z.y = b; return z;
 }
 
+// Two adjacent complex values (columns x, x+1).
+template <typename C> struct Two { C a, b; };
+__device__ __forceinline__ Two<float2> ld2(const float2* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Two<double2> ld2(const double2* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ void st2(float2* p, Two<float2> v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
+__device__ __forceinline__ void st2(double2* p, Two<double2> v) { p[0] = v.a; p[1] = v.b; }
+
 template <typename R, bool CD, int STAGE>
-__global__ void __launch_bounds__(TX)
-stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_V,
+__global__ void __launch_bounds__(NT)
+stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_in2,
+                   const __grid_constant__ CUtensorMap m_V,
                    const __grid_constant__ CUtensorMap m_psi, const __grid_constant__ CUtensorMap m_acc,
                    const __grid_constant__ CUtensorMap m_lo, const StageIO<R> io, const Coef<R> c,
                    const int nx, const int ny) {
     using C = cplx<R>;
     using L = Lay<R>;
+    using T2 = Two<C>;
+    constexpr bool NEED_E = STAGE >= 1;          // V on the output row
     constexpr bool NEED_PA = STAGE >= 2;
     constexpr bool NEED_LO = STAGE == 4 && sizeof(R) == 4;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
 
-    const int tx = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TY;
     const int nrows = min(TY, ny - y0);
-    const int jmax = nrows + 4;                 // rows j = 0 .. jmax-1 are y0-2 .. y0+nrows+1
+    const int jmax = nrows + 4;                  // input rows j = 0 .. jmax-1 are y0-2 .. y0+nrows+1
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + L::BAR_OFF;
+    const uint32_t ibar0 = sbase + L::BAR_OFF;   // S input barriers, then 2 epilogue barriers
+    const uint32_t ebar0 = ibar0 + 8 * S;
 
-    if (tx == 0) {
+    if (t == 0) {
         tma_prefetch_desc(&m_in);
-        tma_prefetch_desc(&m_V);
-        for (int s = 0; s < S; ++s) mbar_init(bar0 + 8 * s, 1);
+        tma_prefetch_desc(&m_in2);
+        for (int s = 0; s < S + 2; ++s) mbar_init(ibar0 + 8 * s, 1);
         mbar_init_fence();
     }
     __syncthreads();
 
-    auto issue = [&](int j) {
+    // Producer side (thread 0): input row j, epilogue row e (= grid row y0 + e).
+    auto issue_in = [&](int j) {
         const int s = j % S;
-        const uint32_t slot = sbase + s * L::SLOT;
-        const uint32_t bar = bar0 + 8 * s;
+        const uint32_t dst = sbase + L::IN_OFF + s * L::IN_SLOT;
+        const uint32_t bar = ibar0 + 8 * s;
         const int r = y0 - 2 + j;
-        const bool outrow = j >= 2 && j < nrows + 2;
-        uint32_t bytes = L::P_BYTES + L::V_BYTES;
-        if (NEED_PA && outrow) bytes += 2 * L::T_BYTES;
-        if (NEED_LO && outrow) bytes += L::T_BYTES;
-        mbar_expect_tx(bar, bytes);
-        load_cplx_row<R>(slot + L::P_OFF, &m_in, x0 - 2, r, bar);
-        tma_load_2d(slot + L::V_OFF, &m_V, x0 - 4, r, bar);
-        if (NEED_PA && outrow) {
-            load_cplx_row<R>(slot + L::PSI_OFF, &m_psi, x0, r, bar);
-            load_cplx_row<R>(slot + L::ACC_OFF, &m_acc, x0, r, bar);
-        }
-        if (NEED_LO && outrow) load_cplx_row<R>(slot + L::LO_OFF, &m_lo, x0, r, bar);
+        mbar_expect_tx(bar, L::IN_BYTES);
+        load_cplx_box<R>(dst, &m_in, x0 - 2, r, bar);
+        load_cplx_box<R>(dst + HB * L::CB, &m_in2, x0 - 2 + HB, r, bar);
     };
-    int next = 0;                                // rows issued so far (thread 0)
-    if (tx == 0)
-        for (; next < S && next < jmax; ++next) issue(next);
+    auto issue_e = [&](int e) {
+        const uint32_t dst = sbase + L::E_OFF + (e & 1) * L::E_SLOT;
+        const uint32_t bar = ebar0 + 8 * (e & 1);
+        const int r = y0 + e;
+        uint32_t bytes = L::V_BYTES;
+        if (NEED_PA) bytes += 2 * L::T_BYTES;
+        if (NEED_LO) bytes += L::T_BYTES;
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(dst + L::E_V, &m_V, x0, r, bar);
+        if (NEED_PA) {
+            load_cplx_box<R>(dst + L::E_PSI, &m_psi, x0, r, bar);
+            load_cplx_box<R>(dst + L::E_ACC, &m_acc, x0, r, bar);
+        }
+        if (NEED_LO) load_cplx_box<R>(dst + L::E_LO, &m_lo, x0, r, bar);
+    };
+    int next = 0, enext = 0;                     // rows issued so far (thread 0)
+    if (t == 0) {
+        for (; next < S && next < jmax; ++next) issue_in(next);
+        if (NEED_E) issue_e(enext++);
+    }
 
-    auto prow = [&](int j) { return reinterpret_cast<const C*>(smem + (j % S) * L::SLOT + L::P_OFF); };
-    auto vrow = [&](int j) { return reinterpret_cast<const R*>(smem + (j % S) * L::SLOT + L::V_OFF); };
-    auto trow = [&](int j, int off) { return reinterpret_cast<const C*>(smem + (j % S) * L::SLOT + off); };
+    auto irow = [&](int j) { return reinterpret_cast<const C*>(smem + L::IN_OFF + (j % S) * L::IN_SLOT); };
+    auto erow = [&](int e) { return smem + L::E_OFF + (e & 1) * L::E_SLOT; };
     C* dring = reinterpret_cast<C*>(smem + L::D_OFF);
 
     bool ok = true;
-    auto wait_row = [&](int j) {
-        if (ok) ok = mbar_wait(bar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kWaitNs);
+    auto wait_in = [&](int j) {
+        if (ok) ok = mbar_wait(ibar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kWaitNs);
+    };
+    auto wait_e = [&](int e) {
+        if (ok) ok = mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kWaitNs);
     };
 
     const C m4 = pair<C>(-4, -4), m12 = pair<C>(R(-1.0 / 12.0), R(-1.0 / 12.0));
@@ -129,124 +165,142 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     const C a2 = pair<C>(c.a, c.a);
     const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
 
-    // D at an arbitrary grid point (x, r) from its five stencil values; used
-    // for the two halo columns x0-1 and x0+TX.
-    auto halo_d = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> C {
+    // D at grid point (x, r) from its five stencil values (boundary: Eq. dbc_lap,
+    // V read from global memory; outside the grid: 0, never used).
+    auto dpoint = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> C {
         if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
         if (x == 0 || x == nx - 1 || r == 0 || r == ny - 1)
             return dirichlet_D(c, ctr, io.V[(int64_t)r * nx + x]);
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
 
-    const int gx = x0 + tx;
-    const int k = tx + 2;                        // this column in the row buffers
-    const bool xin = gx < nx;
-    const bool xb = gx == 0 || gx == nx - 1;
-    // D at (gx, r) from the register window (cm, cc, cp: rows r-1, r, r+1; cl, cr: x neighbours).
-    auto d_reg = [&](int r, int j, C cm, C cc, C cp, C cl, C cr) -> C {
-        if (!xin || r < 0 || r >= ny) return czero<C>();
-        if (xb || r == 0 || r == ny - 1) return dirichlet_D(c, cc, vrow(j)[tx + 4]);
-        return mul2(fma2(m4, cc, add2(add2(cl, cr), add2(cm, cp))), ih2);
-    };
+    const int xa = x0 + 2 * t;                   // this thread's columns xa, xa + 1
+    const int k = 2 * t + 2;                     // xa in the row buffers
+    const bool xin = xa < nx;                    // nx is even: then xa + 1 < nx too
 
-    // Prologue: rows y0-2 .. y0+1 give D(y0-1) (registers) and D(y0) (registers + ring).
-    wait_row(0); wait_row(1); wait_row(2); wait_row(3);
+    // Prologue: input rows y0-2 .. y0+1 give D(., y0-1) and D(., y0).
+    wait_in(0); wait_in(1); wait_in(2); wait_in(3);
     bool alive = __syncthreads_and(ok);
-    C lm, rm, l0, r0, c0, c1, dm, d0;
+    T2 cm, c0, c1, dm, d0;
+    C lm, rm, l0, r0;
     if (alive) {
-        lm = prow(1)[k - 1]; rm = prow(1)[k + 1];
-        l0 = prow(2)[k - 1]; r0 = prow(2)[k + 1];
-        const C cm = prow(1)[k];
-        c0 = prow(2)[k];
-        c1 = prow(3)[k];
-        dm = d_reg(y0 - 1, 1, prow(0)[k], cm, c0, lm, rm);
-        d0 = d_reg(y0, 2, cm, c0, c1, l0, r0);
-        dring[tx + 1] = d0;                                  // row j = 2 -> ring row 0
-        if (tx == 0) dring[0] = halo_d(x0 - 1, y0, l0, lm, prow(3)[1], prow(2)[0], c0);
-        if (tx == TX - 1) dring[TX + 1] = halo_d(x0 + TX, y0, r0, rm, prow(3)[TX + 2], c0, prow(2)[TX + 3]);
+        const C* q0 = irow(0); const C* q1 = irow(1); const C* q2 = irow(2); const C* q3 = irow(3);
+        const T2 cmm = ld2(q0 + k);
+        cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
+        lm = q1[k - 1]; rm = q1[k + 2];
+        l0 = q2[k - 1]; r0 = q2[k + 2];
+        dm.a = dpoint(xa, y0 - 1, cm.a, cmm.a, c0.a, lm, cm.b);
+        dm.b = dpoint(xa + 1, y0 - 1, cm.b, cmm.b, c0.b, cm.a, rm);
+        d0.a = dpoint(xa, y0, c0.a, cm.a, c1.a, l0, c0.b);
+        d0.b = dpoint(xa + 1, y0, c0.b, cm.b, c1.b, c0.a, r0);
+        C* drow = dring;                                   // input row 2 -> D ring row 0
+        st2(drow + k, d0);
+        if (t == 0) drow[1] = dpoint(x0 - 1, y0, l0, q1[1], q3[1], q2[0], c0.a);
+        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, y0, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
     }
     __syncthreads();
 
     bool bad = false;
     for (int i = 0; alive && i < nrows; ++i) {
-        const int j = i + 2;                                 // buffer row of y
+        const int j = i + 2;                     // input row of y
         const int y = y0 + i;
-        wait_row(j + 2);
+        wait_in(j + 2);
         if (!__syncthreads_and(ok)) { alive = false; break; }
-        if (tx == 0 && next < jmax) { issue(next); ++next; }
+        if (t == 0) {
+            if (next < jmax) issue_in(next++);
+            if (NEED_E && enext < nrows) issue_e(enext++);
+        }
 
-        // D(gx, y+1), one row ahead.
-        const C* p1 = prow(j + 1);
-        const C l1 = p1[k - 1], r1 = p1[k + 1];
-        const C c2 = prow(j + 2)[k];
-        const C d1 = d_reg(y + 1, j + 1, c0, c1, c2, l1, r1);
-        C* dnext = dring + ((j + 1) & 1) * L::D_ROW;
-        dnext[tx + 1] = d1;
-        if (tx == 0) dnext[0] = halo_d(x0 - 1, y + 1, l1, l0, prow(j + 2)[1], p1[0], c1);
-        if (tx == TX - 1) dnext[TX + 1] = halo_d(x0 + TX, y + 1, r1, r0, prow(j + 2)[TX + 2], c1, p1[TX + 3]);
-        __syncthreads();
+        // D(., y+1), one row ahead.
+        const C* q1 = irow(j + 1);
+        const C* q2 = irow(j + 2);
+        const T2 c2 = ld2(q2 + k);
+        const C l1 = q1[k - 1], r1 = q1[k + 2];
+        T2 d1;
+        d1.a = dpoint(xa, y + 1, c1.a, c0.a, c2.a, l1, c1.b);
+        d1.b = dpoint(xa + 1, y + 1, c1.b, c0.b, c2.b, c1.a, r1);
+        C* dn = dring + ((j + 1) & 1) * L::ROW;
+        st2(dn + k, d1);
+        if (t == 0) dn[1] = dpoint(x0 - 1, y + 1, l1, l0, q2[1], q1[0], c1.a);
+        if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, y + 1, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+        if (NEED_E) wait_e(i);
+        if (!__syncthreads_and(ok)) { alive = false; break; }
 
         if (xin) {
-            const C* dr = dring + (j & 1) * L::D_ROW + tx;   // dr[0] = D(gx-1, y), dr[2] = D(gx+1, y)
-            const bool bnd = xb || y == 0 || y == ny - 1;
-            C lap = d0;
-            if (!CD && !bnd) {
-                const C dsum = add2(add2(dr[0], dr[2]), add2(dm, d1));
-                const C corners = add2(add2(lm, rm), add2(l1, r1));
-                lap = fma2(i6h2, fma2(m4, c0, corners), fma2(m12, dsum, d0));
+            const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
+            const bool rowb = y == 0 || y == ny - 1;
+            const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
+            T2 lap = d0;
+            if (!CD) {
+                const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));
+                const C dsb = add2(add2(d0.a, dr[k + 2]), add2(dm.b, d1.b));
+                const C cna = add2(add2(lm, cm.b), add2(l1, c1.b));
+                const C cnb = add2(add2(cm.a, rm), add2(c1.a, r1));
+                if (!ba) lap.a = fma2(i6h2, fma2(m4, c0.a, cna), fma2(m12, dsa, d0.a));
+                if (!bb) lap.b = fma2(i6h2, fma2(m4, c0.b, cnb), fma2(m12, dsb, d0.b));
             }
-            const int64_t p = (int64_t)y * nx + gx;
+            const int64_t p = (int64_t)y * nx + xa;
             if constexpr (STAGE == 0) {
-                io.lap[p] = lap;
+                st2(io.lap + p, lap);
             } else {
-                // w = a Lap + (s|Psi|^2 - V) Psi, F = i w; F_b = 0.
-                C sw = czero<C>();
-                if (!bnd) {
-                    const R v = vrow(j)[tx + 4];
-                    const R N = c.s * (c0.x * c0.x + c0.y * c0.y) - v;
-                    const C w = fma2(pair<C>(N, N), c0, mul2(a2, lap));
-                    sw = pair<C>(w.y, w.x);                  // c * F = (-c w.y, c w.x) = (-c, c) * swap(w)
-                }
+                const unsigned char* es = erow(i);
+                const R* vv = reinterpret_cast<const R*>(es + L::E_V) + 2 * t;
+                // w = a Lap + (s|Psi|^2 - V) Psi; c F = (-c, c) * swap(w); F_b = 0.
+                auto swapped_w = [&](C y_, C lap_, R v_, bool b_) -> C {
+                    if (b_) return czero<C>();
+                    const R N = c.s * (y_.x * y_.x + y_.y * y_.y) - v_;
+                    const C w = fma2(pair<C>(N, N), y_, mul2(a2, lap_));
+                    return pair<C>(w.y, w.x);
+                };
+                const C swa = swapped_w(c0.a, lap.a, vv[0], ba);
+                const C swb = swapped_w(c0.b, lap.b, vv[1], bb);
                 if constexpr (STAGE == 1) {
-                    io.acc[p] = mul2(ca2, sw);
-                    io.yout[p] = fma2(cy2, sw, c0);
-                } else if constexpr (STAGE == 2 || STAGE == 3) {
-                    const C pn = trow(j, L::PSI_OFF)[tx];
-                    const C ac = trow(j, L::ACC_OFF)[tx];
-                    io.acc[p] = fma2(ca2, sw, ac);
-                    io.yout[p] = fma2(cy2, sw, pn);
+                    st2(io.acc + p, T2{mul2(ca2, swa), mul2(ca2, swb)});
+                    st2(io.yout + p, T2{fma2(cy2, swa, c0.a), fma2(cy2, swb, c0.b)});
                 } else {
-                    C pn = trow(j, L::PSI_OFF)[tx];
-                    const C d = fma2(ca2, sw, trow(j, L::ACC_OFF)[tx]);
-                    if constexpr (sizeof(R) == 4) {
-                        C lo = trow(j, L::LO_OFF)[tx];
-                        kahan_add(pn.x, lo.x, d.x);
-                        kahan_add(pn.y, lo.y, d.y);
-                        io.lo[p] = lo;
+                    const T2 pn = ld2(reinterpret_cast<const C*>(es + L::E_PSI) + 2 * t);
+                    const T2 ac = ld2(reinterpret_cast<const C*>(es + L::E_ACC) + 2 * t);
+                    if constexpr (STAGE == 2 || STAGE == 3) {
+                        st2(io.acc + p, T2{fma2(ca2, swa, ac.a), fma2(ca2, swb, ac.b)});
+                        st2(io.yout + p, T2{fma2(cy2, swa, pn.a), fma2(cy2, swb, pn.b)});
                     } else {
-                        pn = add2(pn, d);
+                        const C da = fma2(ca2, swa, ac.a), db = fma2(ca2, swb, ac.b);
+                        T2 out = pn;
+                        if constexpr (sizeof(R) == 4) {
+                            T2 lo = ld2(reinterpret_cast<const C*>(es + L::E_LO) + 2 * t);
+                            kahan_add(out.a.x, lo.a.x, da.x);
+                            kahan_add(out.a.y, lo.a.y, da.y);
+                            kahan_add(out.b.x, lo.b.x, db.x);
+                            kahan_add(out.b.y, lo.b.y, db.y);
+                            st2(io.lo + p, lo);
+                        } else {
+                            out.a = add2(out.a, da);
+                            out.b = add2(out.b, db);
+                        }
+                        st2(io.psi_out + p, out);
+                        bad |= !(isfinite(out.a.x) && isfinite(out.a.y) && isfinite(out.b.x) && isfinite(out.b.y));
                     }
-                    io.psi_out[p] = pn;
-                    bad |= !(isfinite(pn.x) && isfinite(pn.y));
                 }
             }
         }
         lm = l0; rm = r0; l0 = l1; r0 = r1;
-        c0 = c1; c1 = c2;
+        cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
     }
 
     if (!alive) {
-        // A row never arrived: report, let this CTA's copies in flight land, leave.
-        if (tx == 0) {
+        // A transfer never arrived: report, let this CTA's copies in flight land, leave.
+        if (t == 0) {
             atomicOr(io.flag, 2);
             for (int j = next > S ? next - S : 0; j < next; ++j)
-                mbar_wait(bar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kDrainNs);
+                mbar_wait(ibar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kDrainNs);
+            for (int e = enext > 2 ? enext - 2 : 0; e < enext; ++e)
+                mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kDrainNs);
         }
         return;
     }
     if constexpr (STAGE == 4) {
-        if (__syncthreads_or(bad) && tx == 0) atomicOr(io.flag, 1);
+        if (__syncthreads_or(bad) && t == 0) atomicOr(io.flag, 1);
     }
 }
 
@@ -270,17 +324,17 @@ EncodeTiled encoder() {
     return fn;
 }
 
-bool encode(CUtensorMap* m, CUtensorMapDataType t, int rank, const void* base, const cuuint64_t* dims,
+bool encode(CUtensorMap* m, CUtensorMapDataType type, int rank, const void* base, const cuuint64_t* dims,
             const cuuint64_t* strides, const cuuint32_t* box) {
     EncodeTiled fn = encoder();
     if (!fn || !base) return false;
     const cuuint32_t ones[3] = {1, 1, 1};
-    return fn(m, t, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, ones,
+    return fn(m, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, ones,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// A complex row map over an nx x ny grid with boxes `width` points wide.
+// Row boxes `width` points wide over an nx x ny complex grid.
 template <typename R>
 bool complex_map(CUtensorMap* m, const void* base, int nx, int ny, int width) {
     if constexpr (sizeof(R) == 4) {
@@ -308,23 +362,24 @@ bool real_map(CUtensorMap* m, const void* base, int nx, int ny, int width) {
 template <typename R, bool CD, int STAGE>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     const int nx = (int)L.n[0], ny = (int)L.n[1];
-    CUtensorMap m_in, m_V, m_psi, m_acc, m_lo;
-    if (!complex_map<R>(&m_in, L.yin, nx, ny, TX + 4) || !real_map<R>(&m_V, L.V, nx, ny, TX + 8))
+    CUtensorMap m_in, m_in2, m_V, m_psi, m_acc, m_lo;
+    if (!complex_map<R>(&m_in, L.yin, nx, ny, HB) || !complex_map<R>(&m_in2, L.yin, nx, ny, HB2))
         return cudaErrorInvalidValue;
-    m_psi = m_acc = m_lo = m_in;
+    m_V = m_psi = m_acc = m_lo = m_in;
+    if (STAGE >= 1 && !real_map<R>(&m_V, L.V, nx, ny, TXC)) return cudaErrorInvalidValue;
     if (STAGE >= 2) {
-        if (!complex_map<R>(&m_psi, L.psi, nx, ny, TX) || !complex_map<R>(&m_acc, L.acc, nx, ny, TX))
+        if (!complex_map<R>(&m_psi, L.psi, nx, ny, TXC) || !complex_map<R>(&m_acc, L.acc, nx, ny, TXC))
             return cudaErrorInvalidValue;
     }
-    if (STAGE == 4 && sizeof(R) == 4 && !complex_map<R>(&m_lo, L.lo, nx, ny, TX)) return cudaErrorInvalidValue;
+    if (STAGE == 4 && sizeof(R) == 4 && !complex_map<R>(&m_lo, L.lo, nx, ny, TXC)) return cudaErrorInvalidValue;
     auto kern = stage2d_tma_kernel<R, CD, STAGE>;
     const int smem = Lay<R>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
-    kern<<<grid, TX, smem, st>>>(m_in, m_V, m_psi, m_acc, m_lo, make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny);
+    dim3 grid((nx + TXC - 1) / TXC, (ny + TY - 1) / TY);
+    kern<<<grid, NT, smem, st>>>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny);
     return cudaGetLastError();
 }
 
@@ -344,11 +399,12 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 
 // TMA needs 16-byte aligned bases and row pitches: nx a multiple of 4
 // (complex64 rows and float V rows) or of 2 (complex128 rows, double V).
+// The column pairs also need nx even.
 bool stage_2d_tma_eligible(const StageLaunch& L) {
     if (L.bc != 0) return false;
     const int64_t nx = L.n[0];
     if (nx % (L.prec == 0 ? 4 : 2) != 0) return false;
-    const void* ptrs[6] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout};
+    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
     for (const void* p : ptrs)
         if ((uintptr_t)p % 16) return false;
     return encoder() != nullptr;
