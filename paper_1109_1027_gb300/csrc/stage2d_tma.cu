@@ -35,7 +35,7 @@ constexpr int NT = 128;              // threads per CTA
 constexpr int TXC = 2 * NT;          // columns per CTA
 constexpr int HB = TXC;              // first input TMA box: x0-2 .. x0+TXC-3
 constexpr int HB2 = 4;               // second input TMA box: x0+TXC-2 .. x0+TXC+1
-constexpr int TY = 16;               // rows per CTA
+constexpr int TY = 16;               // rows per CTA: 2048^2 fits one wave of CTAs
 constexpr int S = 6;                 // input ring slots
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint64_t kDrainNs = 50000000ull;
@@ -201,7 +201,11 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     __syncthreads();
 
     bool bad = false;
-    for (int i = 0; alive && i < nrows; ++i) {
+    // Unrolled by 3, the period of the three-row register windows, so that
+    // sliding them is register renaming rather than moves.
+#pragma unroll 3
+    for (int i = 0; i < TY; ++i) {
+        if (!alive || i >= nrows) break;
         const int j = i + 2;                     // input row of y
         const int y = y0 + i;
         wait_in(j + 2);
