@@ -62,7 +62,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash() -> str:
     h = hashlib.sha1()
-    for f in ("stage2d.cu", "nlse_device.cuh"):
+    for f in ("stage2d_tma.cu", "tma.cuh", "nlse_device.cuh"):
         with open(os.path.join(ROOT, "paper_1109_1027_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -323,7 +323,7 @@ def run_ours(args):
     achieved = BYTES_PER_UPDATE_FP32 * npts / (ms_step * 1e-3) / 1e9
     kh = kernel_hash()
     traffic = NCU_TRAFFIC.get(kh)
-    roofline = {"bound": "hbm", "kernel": "stage2d_kernel<float> (RK4 stages 1-4, mean per launch)",
+    roofline = {"bound": "hbm", "kernel": "stage2d_tma_kernel<float> (RK4 stages 1-4, mean per launch)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": BYTES_PER_UPDATE_FP32 / 4 * npts,

@@ -12,8 +12,9 @@
 //     part too) on the output row.
 // Each thread keeps its two columns' stage input, their outer x neighbours
 // and D in registers as a sliding window; the x neighbours of D travel
-// through a two-row shared ring.  Per output row y, with D(., y+1) formed one
-// row ahead:
+// through a two-row shared ring.  The walk runs down the grid on odd stages
+// and up on even ones, so each stage starts on the rows the previous stage
+// wrote last (still in L2).  Per output row y, with D formed one row ahead:
 //   step 1 (Eq. 2d2shocs1): D = (sum of the four axial Psi - 4 Psi_c) / h^2,
 //                           boundary points D_b of Eq. (dbc_lap);
 //   step 2 (Eq. 2d2shocs2): Lap = D_c - (1/12) sum of the four axial D
@@ -91,7 +92,7 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                    const __grid_constant__ CUtensorMap m_V,
                    const __grid_constant__ CUtensorMap m_psi, const __grid_constant__ CUtensorMap m_acc,
                    const __grid_constant__ CUtensorMap m_lo, const StageIO<R> io, const Coef<R> c,
-                   const int nx, const int ny) {
+                   const int nx, const int ny, const int dir) {
     using C = cplx<R>;
     using L = Lay<R>;
     using T2 = Two<C>;
@@ -104,7 +105,10 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TY;
     const int nrows = min(TY, ny - y0);
-    const int jmax = nrows + 4;                  // input rows j = 0 .. jmax-1 are y0-2 .. y0+nrows+1
+    const int jmax = nrows + 4;                  // input rows j = 0 .. jmax-1
+    // The CTA walks its rows downwards (dir = +1) or upwards (dir = -1):
+    // output row e is grid row ybase + dir * e, input row j is ybase + dir * (j - 2).
+    const int ybase = dir > 0 ? y0 : y0 + nrows - 1;
     const uint32_t sbase = smem_u32(smem);
     const uint32_t ibar0 = sbase + L::BAR_OFF;   // S input barriers, then 2 epilogue barriers
     const uint32_t ebar0 = ibar0 + 8 * S;
@@ -117,12 +121,12 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     }
     __syncthreads();
 
-    // Producer side (thread 0): input row j, epilogue row e (= grid row y0 + e).
+    // Producer side (thread 0): input row j, epilogue row e.
     auto issue_in = [&](int j) {
         const int s = j % S;
         const uint32_t dst = sbase + L::IN_OFF + s * L::IN_SLOT;
         const uint32_t bar = ibar0 + 8 * s;
-        const int r = y0 - 2 + j;
+        const int r = ybase + dir * (j - 2);
         mbar_expect_tx(bar, L::IN_BYTES);
         load_cplx_box<R>(dst, &m_in, x0 - 2, r, bar);
         load_cplx_box<R>(dst + HB * L::CB, &m_in2, x0 - 2 + HB, r, bar);
@@ -130,7 +134,7 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     auto issue_e = [&](int e) {
         const uint32_t dst = sbase + L::E_OFF + (e & 1) * L::E_SLOT;
         const uint32_t bar = ebar0 + 8 * (e & 1);
-        const int r = y0 + e;
+        const int r = ybase + dir * e;
         uint32_t bytes = L::V_BYTES;
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
@@ -189,14 +193,15 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
         lm = q1[k - 1]; rm = q1[k + 2];
         l0 = q2[k - 1]; r0 = q2[k + 2];
-        dm.a = dpoint(xa, y0 - 1, cm.a, cmm.a, c0.a, lm, cm.b);
-        dm.b = dpoint(xa + 1, y0 - 1, cm.b, cmm.b, c0.b, cm.a, rm);
-        d0.a = dpoint(xa, y0, c0.a, cm.a, c1.a, l0, c0.b);
-        d0.b = dpoint(xa + 1, y0, c0.b, cm.b, c1.b, c0.a, r0);
+        const int yb = ybase - dir;              // the row before the first output row
+        dm.a = dpoint(xa, yb, cm.a, cmm.a, c0.a, lm, cm.b);
+        dm.b = dpoint(xa + 1, yb, cm.b, cmm.b, c0.b, cm.a, rm);
+        d0.a = dpoint(xa, ybase, c0.a, cm.a, c1.a, l0, c0.b);
+        d0.b = dpoint(xa + 1, ybase, c0.b, cm.b, c1.b, c0.a, r0);
         C* drow = dring;                                   // input row 2 -> D ring row 0
         st2(drow + k, d0);
-        if (t == 0) drow[1] = dpoint(x0 - 1, y0, l0, q1[1], q3[1], q2[0], c0.a);
-        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, y0, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
+        if (t == 0) drow[1] = dpoint(x0 - 1, ybase, l0, q1[1], q3[1], q2[0], c0.a);
+        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, ybase, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
     }
     __syncthreads();
 
@@ -207,7 +212,8 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     for (int i = 0; i < TY; ++i) {
         if (!alive || i >= nrows) break;
         const int j = i + 2;                     // input row of y
-        const int y = y0 + i;
+        const int y = ybase + dir * i;
+        const int ya = y + dir;                  // the row after y in walk order
         wait_in(j + 2);
         if (!__syncthreads_and(ok)) { alive = false; break; }
         if (t == 0) {
@@ -215,18 +221,18 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
             if (NEED_E && enext < nrows) issue_e(enext++);
         }
 
-        // D(., y+1), one row ahead.
+        // D(., ya), one row ahead.
         const C* q1 = irow(j + 1);
         const C* q2 = irow(j + 2);
         const T2 c2 = ld2(q2 + k);
         const C l1 = q1[k - 1], r1 = q1[k + 2];
         T2 d1;
-        d1.a = dpoint(xa, y + 1, c1.a, c0.a, c2.a, l1, c1.b);
-        d1.b = dpoint(xa + 1, y + 1, c1.b, c0.b, c2.b, c1.a, r1);
+        d1.a = dpoint(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
+        d1.b = dpoint(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
         C* dn = dring + ((j + 1) & 1) * L::ROW;
         st2(dn + k, d1);
-        if (t == 0) dn[1] = dpoint(x0 - 1, y + 1, l1, l0, q2[1], q1[0], c1.a);
-        if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, y + 1, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+        if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
+        if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
         if (NEED_E) wait_e(i);
         if (!__syncthreads_and(ok)) { alive = false; break; }
 
@@ -383,7 +389,11 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((nx + TXC - 1) / TXC, (ny + TY - 1) / TY);
-    kern<<<grid, NT, smem, st>>>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny);
+    // Consecutive stages walk the rows in opposite directions, so that each
+    // stage starts on the rows the previous one wrote last (still in L2).
+    const int dir = (STAGE % 2 == 0 && STAGE != 0) ? -1 : 1;
+    kern<<<grid, NT, smem, st>>>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx,
+                                 ny, dir);
     return cudaGetLastError();
 }
 
