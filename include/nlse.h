@@ -99,6 +99,28 @@ typedef struct nlse_ctx nlse_ctx;
  * h, dt or a not positive and finite, or an unknown bc / prec / lap. */
 int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out);
 
+/* Creates one context for `count` independent 2D instances of uneven sizes
+ * and parameters, advanced together (one launch per RK4 stage covers every
+ * instance).  p[i] gives instance i's grid, h, dt, a and s; prec, lap, bc
+ * and flags must be the same for all, bc Dirichlet, and n[0] a multiple of 4
+ * (FP32) or 2 (FP64).  Psi, V and every work array are single flat device
+ * buffers: instance i occupies n[0](i) * n[1](i) points starting at element
+ * offset sum_{j<i} n[0](j) * n[1](j).  V_dev is that flat potential
+ * (borrowed).  nlse_rk4_step, nlse_run, nlse_lap2shoc, nlse_check and
+ * nlse_reset_compensation then take the flat Psi; nlse_run's stability check
+ * refuses when any instance's dt exceeds its own bound. */
+int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_ctx** out);
+
+/* Number of instances of a batch context (0 for a single-grid context). */
+int nlse_batch_count(const nlse_ctx* ctx);
+
+/* Per-instance mass, energy and dt_max (arrays of nlse_batch_count entries,
+ * any may be NULL) of a batch context, as nlse_invariants computes them for
+ * one grid.  Synchronises the stream.  Returns NLSE_ENONFINITE if any
+ * instance holds a NaN or Inf. */
+int nlse_invariants_batch(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy, double* dt_max,
+                          void* stream);
+
 /* Releases the context and its device memory (synchronises the device). */
 void nlse_destroy(nlse_ctx* ctx);
 
@@ -137,7 +159,7 @@ int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
  * the stream and writes the three host doubles (any may be NULL).  Returns
  * NLSE_ENONFINITE when the state holds a NaN or Inf. */
 int nlse_invariants(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy,
-                    double* dt_max, void* stream);
+                    double* dt_max, void* stream);   /* single-grid contexts only */
 
 /* Zeroes the FP32 compensated low part (call after writing psi externally). */
 int nlse_reset_compensation(nlse_ctx* ctx, void* stream);

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "nlse.h"
 #include "nlse_internal.h"
@@ -59,6 +60,13 @@ struct nlse_ctx {
     const void* state_psi;    // psi whose compensated part lo currently holds
     cudaGraphExec_t graph;
     const void* graph_psi;
+    // Batched instances (nlse_create_batch): count > 0.
+    int count;
+    nlse::BatchPlan* batch;
+    nlse_params* bparams;     // per-instance parameters
+    int64_t* boff;            // per-instance element offsets
+    int* brow;                // per-instance first row of partials (count + 1 entries)
+    const void* maps_psi;     // Psi buffer the batch tensor maps currently point at
 };
 
 namespace {
@@ -138,14 +146,29 @@ int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
         L.stage = s;
         L.yin = in[s];
         L.yout = out[s];
-        cudaError_t e = launch_stage(L, st);
+        cudaError_t e = c->batch ? nlse::batch2d_launch(c->batch, L, st) : launch_stage(L, st);
         if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
     }
     return NLSE_OK;
 }
 
+// Points the batch's tensor maps at psi (re-encoding and uploading the
+// descriptor table on the stream) when they point elsewhere.
+int bind_maps(nlse_ctx* c, const void* psi, cudaStream_t st) {
+    if (!c->batch || c->maps_psi == psi) return NLSE_OK;
+    cudaError_t e = nlse::batch2d_bind(c->batch, psi, st);
+    if (e != cudaSuccess) {
+        c->maps_psi = nullptr;
+        return cuda_fail(e, "encoding the batch tensor maps");
+    }
+    c->maps_psi = psi;
+    return NLSE_OK;
+}
+
 // Zeroes the compensated part when the state pointer changes.
 int bind_state(nlse_ctx* c, const void* psi, cudaStream_t st) {
+    int rc = bind_maps(c, psi, st);
+    if (rc) return rc;
     if (c->state_psi == psi) return NLSE_OK;
     if (c->lo) NLSE_CUDA(cudaMemsetAsync(c->lo, 0, c->cbytes, st), "zeroing the compensated part");
     c->state_psi = psi;
@@ -161,8 +184,22 @@ void g_extremes(int dim, double* gmin, double* gmax) {
     *gmax = mx[dim] / 12.0;
 }
 
+// dt_max of Eq. (kdfull) from the reduced extremes (see g_extremes).
+double dt_bound(int dim, double h, double a, const double* r) {
+    double gmin, gmax;
+    g_extremes(dim, &gmin, &gmax);
+    double worst = std::fmax(std::fabs(r[3] - gmin), std::fabs(r[2] - gmax));
+    worst = std::fmax(worst, std::fmax(std::fabs(r[2] - gmin), std::fabs(r[3] - gmax)));
+    worst = std::fmax(worst, r[4]);
+    return std::sqrt(8.0) * h * h / (a * worst);
+}
+
+int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
+                          cudaStream_t st);
+
 int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
                     cudaStream_t st) {
+    if (c->batch) return fail(NLSE_EINVAL, "a batch context takes nlse_invariants_batch");
     nlse::InvLaunch L;
     L.dim = c->p.dim;
     for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
@@ -179,22 +216,57 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     const double h = c->p.h, hd = std::pow(h, (double)c->p.dim);
     if (mass) *mass = hd * r[0];
     if (energy) *energy = hd * r[1];
-    if (dt_max) {
-        double gmin, gmax;
-        g_extremes(c->p.dim, &gmin, &gmax);
-        double worst = std::fmax(std::fabs(r[3] - gmin), std::fabs(r[2] - gmax));
-        worst = std::fmax(worst, std::fmax(std::fabs(r[2] - gmin), std::fabs(r[3] - gmax)));
-        worst = std::fmax(worst, r[4]);
-        *dt_max = std::sqrt(8.0) * h * h / (c->p.a * worst);
-    }
+    if (dt_max) *dt_max = dt_bound(c->p.dim, h, c->p.a, r);
     if (r[5] != 0.0 || !std::isfinite(r[0]))
         return fail(NLSE_ENONFINITE, "state holds %g non-finite values", r[5]);
+    return NLSE_OK;
+}
+
+// Per-instance invariants of a batch: the reductions of each instance into
+// its own rows of partials and its own result row, one copy, one sync.
+int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
+                          cudaStream_t st) {
+    const size_t cb = c->p.prec == NLSE_FP32 ? 8 : 16, rb = c->p.prec == NLSE_FP32 ? 4 : 8;
+    const bool with_lo = c->lo && psi == c->state_psi;
+    for (int i = 0; i < c->count; ++i) {
+        const nlse_params& q = c->bparams[i];
+        nlse::InvLaunch L;
+        L.dim = 2;
+        L.n[0] = q.n[0]; L.n[1] = q.n[1]; L.n[2] = 1;
+        L.prec = q.prec; L.lap = q.lap; L.bc = q.bc;
+        L.h = q.h; L.a = q.a; L.s = q.s;
+        L.psi = static_cast<const char*>(psi) + c->boff[i] * cb;
+        L.lo = with_lo ? static_cast<const char*>(c->lo) + c->boff[i] * cb : nullptr;
+        L.V = static_cast<const char*>(c->V) + c->boff[i] * rb;
+        NLSE_CUDA(nlse::launch_invariants(L, c->partials + (size_t)c->brow[i] * nlse::kPartialWidth,
+                                          c->brow[i + 1] - c->brow[i],
+                                          c->red_out + (size_t)i * nlse::kPartialWidth, st),
+                  "invariants launch");
+    }
+    NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth * c->count,
+                              cudaMemcpyDeviceToHost, st), "invariants copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "invariants synchronise");
+    int bad = -1;
+    for (int i = 0; i < c->count; ++i) {
+        const double* r = c->host_out + (size_t)i * nlse::kPartialWidth;
+        const nlse_params& q = c->bparams[i];
+        const double h2 = q.h * q.h;
+        if (mass) mass[i] = h2 * r[0];
+        if (energy) energy[i] = h2 * r[1];
+        if (dt_max) dt_max[i] = dt_bound(2, q.h, q.a, r);
+        if ((r[5] != 0.0 || !std::isfinite(r[0])) && bad < 0) bad = i;
+    }
+    if (bad >= 0) return fail(NLSE_ENONFINITE, "instance %d holds non-finite values", bad);
     return NLSE_OK;
 }
 
 void release(nlse_ctx* c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    nlse::batch2d_destroy(c->batch);
+    delete[] c->bparams;
+    delete[] c->boff;
+    delete[] c->brow;
     cudaFree(c->Y[0]);
     cudaFree(c->Y[1]);
     cudaFree(c->acc);
@@ -272,6 +344,81 @@ void nlse_destroy(nlse_ctx* c) {
     release(c);
 }
 
+int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_ctx** out) {
+    g_err[0] = 0;
+    if (!out) return fail(NLSE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !p) return fail(NLSE_EINVAL, "need count >= 1 and a params array");
+    if (!V_dev || (uintptr_t)V_dev % 16) return fail(NLSE_EINVAL, "V_dev must be a 16-byte aligned device pointer");
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        int rc = validate(&p[i]);
+        if (rc) return fail(rc, "instance %d: %s", i, std::string(g_err).c_str());
+        if (p[i].prec != p[0].prec || p[i].lap != p[0].lap || p[i].bc != p[0].bc || p[i].flags != p[0].flags)
+            return fail(NLSE_EINVAL, "instance %d: prec, lap, bc and flags must match instance 0", i);
+        if (p[i].flags & NLSE_FLAG_PLAIN_SCHEDULE)
+            return fail(NLSE_EUNSUPPORTED, "batches run the fused schedule only");
+        if (!nlse::batch2d_instance_ok(p[i]))
+            return fail(NLSE_EUNSUPPORTED, "instance %d: batches need 2D Dirichlet grids with n[0] a multiple of "
+                        "%d", i, p[0].prec == NLSE_FP32 ? 4 : 2);
+        total += p[i].n[0] * p[i].n[1];
+    }
+    nlse_ctx* c = new (std::nothrow) nlse_ctx();
+    if (!c) return fail(NLSE_ENOMEM, "host allocation failed");
+    c->p = p[0];
+    c->V = V_dev;
+    c->count = count;
+    c->npts = total;
+    c->cbytes = (size_t)total * (p[0].prec == NLSE_FP32 ? 8 : 16);
+    c->bparams = new (std::nothrow) nlse_params[count];
+    c->boff = new (std::nothrow) int64_t[count];
+    c->brow = new (std::nothrow) int[count + 1];
+    if (!c->bparams || !c->boff || !c->brow) { release(c); return fail(NLSE_ENOMEM, "host allocation failed"); }
+    cudaError_t e;
+    int rc, nsm = 0;
+#define TRY(call, what) do { e = (call); if (e != cudaSuccess) { rc = cuda_fail(e, what); release(c); return rc; } } while (0)
+    TRY(cudaGetDevice(&c->device), "cudaGetDevice");
+    TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device query");
+    int64_t off = 0;
+    c->brow[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        c->bparams[i] = p[i];
+        c->boff[i] = off;
+        off += p[i].n[0] * p[i].n[1];
+        nlse::InvLaunch L;
+        L.dim = 2; L.n[0] = p[i].n[0]; L.n[1] = p[i].n[1]; L.n[2] = 1;
+        c->brow[i + 1] = c->brow[i] + nlse::inv_num_blocks(L, nsm);
+    }
+    TRY(cudaMalloc(&c->Y[0], c->cbytes), "allocating stage buffer");
+    TRY(cudaMalloc(&c->Y[1], c->cbytes), "allocating stage buffer");
+    TRY(cudaMalloc(&c->acc, c->cbytes), "allocating accumulator");
+    if (p[0].prec == NLSE_FP32) {
+        TRY(cudaMalloc(&c->lo, c->cbytes), "allocating compensated part");
+        TRY(cudaMemset(c->lo, 0, c->cbytes), "zeroing compensated part");
+    }
+    TRY(cudaMalloc((void**)&c->flag, sizeof(int)), "allocating flag");
+    TRY(cudaMemset(c->flag, 0, sizeof(int)), "zeroing flag");
+    c->nblocks = c->brow[count];
+    TRY(cudaMalloc((void**)&c->partials, sizeof(double) * nlse::kPartialWidth * c->nblocks), "allocating partials");
+    TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth * count), "allocating results");
+    TRY(cudaMallocHost((void**)&c->host_out, sizeof(double) * nlse::kPartialWidth * count),
+        "allocating pinned results");
+    TRY(nlse::batch2d_create(count, p, V_dev, c->Y[0], c->Y[1], c->acc, c->lo, &c->batch), "building the batch plan");
+#undef TRY
+    *out = c;
+    return NLSE_OK;
+}
+
+int nlse_invariants_batch(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
+                          void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
+    if (!c->batch) return fail(NLSE_EINVAL, "not a batch context: use nlse_invariants");
+    return invariants_batch_impl(c, psi, mass, energy, dt_max, (cudaStream_t)stream);
+}
+
+int nlse_batch_count(const nlse_ctx* c) { return c ? c->count : 0; }
+
 int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     g_err[0] = 0;
     if (!c || !psi || !lap) return fail(NLSE_EINVAL, "NULL argument");
@@ -282,7 +429,12 @@ int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     L.stage = 0;
     L.yin = psi;
     L.lap_out = lap;
-    cudaError_t e = launch_stage(L, (cudaStream_t)stream);
+    if (c->batch) {
+        int rc = bind_maps(c, psi, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    cudaError_t e = c->batch ? nlse::batch2d_launch(c->batch, L, (cudaStream_t)stream)
+                             : launch_stage(L, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "Laplacian launch");
     return NLSE_OK;
 }
@@ -307,11 +459,26 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
     if (rc) return rc;
     if (nsteps == 0) return NLSE_OK;
     if (!(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK)) {
-        double dtmax = 0;
-        rc = invariants_impl(c, psi, nullptr, nullptr, &dtmax, st);
-        if (rc) return rc;
-        if (c->p.dt > dtmax)
-            return fail(NLSE_EUNSTABLE, "dt = %g exceeds the bound %g of Eq. (kdfull)", c->p.dt, dtmax);
+        if (c->batch) {
+            double* dtmax = new (std::nothrow) double[c->count];
+            if (!dtmax) return fail(NLSE_ENOMEM, "host allocation failed");
+            rc = invariants_batch_impl(c, psi, nullptr, nullptr, dtmax, st);
+            int worst = -1;
+            for (int i = 0; rc == NLSE_OK && i < c->count; ++i)
+                if (c->bparams[i].dt > dtmax[i]) { worst = i; break; }
+            double b = worst >= 0 ? dtmax[worst] : 0.0;
+            delete[] dtmax;
+            if (rc) return rc;
+            if (worst >= 0)
+                return fail(NLSE_EUNSTABLE, "instance %d: dt = %g exceeds the bound %g of Eq. (kdfull)", worst,
+                            c->bparams[worst].dt, b);
+        } else {
+            double dtmax = 0;
+            rc = invariants_impl(c, psi, nullptr, nullptr, &dtmax, st);
+            if (rc) return rc;
+            if (c->p.dt > dtmax)
+                return fail(NLSE_EUNSTABLE, "dt = %g exceeds the bound %g of Eq. (kdfull)", c->p.dt, dtmax);
+        }
     }
     if (nsteps >= kGraphSteps && (!c->graph || c->graph_psi != psi)) {
         if (c->graph) {

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "nlse.h"
+
 namespace nlse {
 
 // One launch of a fused RK4 stage (stage 1..4) or of the standalone
@@ -50,6 +52,16 @@ struct PlainLaunch {
 };
 
 cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st);
+
+// Batched uneven 2D instances (batch2d.cu).  The plan owns the per-instance
+// tensor-map descriptors and the tile work lists.
+struct BatchPlan;
+bool batch2d_instance_ok(const nlse_params& p);
+cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
+                           void* lo, BatchPlan** out);
+cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st);
+cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st);
+void batch2d_destroy(BatchPlan* b);
 
 // FP64 reductions for nlse_invariants.  Each of the nblocks blocks of the
 // partial kernel writes kPartialWidth doubles to partials; the final kernel

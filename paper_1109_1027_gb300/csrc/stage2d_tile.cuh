@@ -1,0 +1,316 @@
+// stage2d_tile.cuh -- one CTA's work of the fused 2D RK4 stage (and of the
+// standalone 2SHOC Laplacian): a y-streaming walk fed by the tensor memory
+// accelerator.  Used by the single-grid kernel (stage2d_tma.cu) and by the
+// batched kernel over many grids (batch2d.cu).
+//
+// One CTA of NT threads owns TXC = 2 NT consecutive columns (two per thread)
+// and walks down TY rows.  Two rings of shared-memory row slots are filled by
+// TMA tile loads, each slot completing on its own mbarrier:
+//   * the input ring (S slots, up to S rows ahead): the stage input row with
+//     a 2-point x halo (a TXC-point and a 4-point TMA box, so that both land
+//     on 128-byte aligned shared addresses);
+//   * the epilogue ring (2 slots, one output row ahead): V, and for stages
+//     2-4 Psi^n and the RK4 accumulator (stage 4 in FP32: the compensated
+//     part too) on the output row.
+// Each thread keeps its two columns' stage input, their outer x neighbours
+// and D in registers as a sliding window; the x neighbours of D travel
+// through a two-row shared ring.  The walk runs down the grid on odd stages
+// and up on even ones, so each stage starts on the rows the previous stage
+// wrote last (still in L2).  Per output row y, with D formed one row ahead:
+//   step 1 (Eq. 2d2shocs1): D = (sum of the four axial Psi - 4 Psi_c) / h^2,
+//                           boundary points D_b of Eq. (dbc_lap);
+//   step 2 (Eq. 2d2shocs2): Lap = D_c - (1/12) sum of the four axial D
+//                           + (1/(6h^2)) (four corner Psi - 4 Psi_c);
+//   F = i[a Lap + (s|Psi|^2 - V) Psi] (Sec. 3.1), F_b = 0 (Eq. dbc_ut);
+//   the RK4 stage epilogue (Eq. RK4, accumulated-increment form).
+// Complex64 arithmetic uses the packed f32x2 instructions.  Every mbarrier
+// wait is bounded (1 s); on timeout the CTA sets bit 2 of the status flag,
+// lets its own copies in flight land and returns.
+#pragma once
+
+#include "nlse_device.cuh"
+#include "tma.cuh"
+
+namespace nlse {
+namespace tile2d {
+
+constexpr int S = 6;                 // input ring slots
+constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint64_t kDrainNs = 50000000ull;
+
+constexpr int al128(int v) { return (v + 127) / 128 * 128; }
+
+// Shared-memory layout.  Input rows and D rows are indexed by column
+// x - (x0 - 2), so a thread's column pair (xa, xa+1) sits at the 16-byte
+// aligned index 2t + 2.  Every TMA destination is 128-byte aligned.
+template <typename R, int NT>
+struct Lay {
+    static constexpr int TXC = 2 * NT;
+    static constexpr int CB = (int)sizeof(cplx<R>);
+    static constexpr int ROW = TXC + 4;                       // x0-2 .. x0+TXC+1
+    static constexpr int IN_BYTES = ROW * CB;
+    static constexpr int IN_SLOT = al128(IN_BYTES);
+    static constexpr int T_BYTES = TXC * CB;                  // one complex output row
+    static constexpr int V_BYTES = TXC * (int)sizeof(R);
+    static constexpr int E_PSI = 0, E_ACC = T_BYTES, E_LO = 2 * T_BYTES;
+    static constexpr int E_V = E_LO + (sizeof(R) == 4 ? T_BYTES : 0);
+    static constexpr int E_SLOT = al128(E_V + V_BYTES);
+    static constexpr int IN_OFF = 0;
+    static constexpr int E_OFF = S * IN_SLOT;
+    static constexpr int D_OFF = E_OFF + 2 * E_SLOT;
+    static constexpr int BAR_OFF = al128(D_OFF + 2 * ROW * CB);
+    static constexpr int TOTAL = BAR_OFF + 8 * (S + 2) + 128;   // +128: base alignment slack
+};
+
+template <typename R>
+__device__ __forceinline__ void load_cplx_box(uint32_t dst, const CUtensorMap* m, int x, int r, uint32_t bar) {
+    if constexpr (sizeof(R) == 4) tma_load_2d(dst, m, x, r, bar);       // complex64 as 8-byte elements
+    else tma_load_3d(dst, m, 0, x, r, bar);                             // complex128 as (re, im) doubles
+}
+
+template <typename C> __device__ __forceinline__ C pair(decltype(C::x) a, decltype(C::x) b) {
+    C z; z.x = a; z.y = b; return z;
+}
+
+// Two adjacent complex values (columns x, x+1).
+template <typename C> struct Two { C a, b; };
+__device__ __forceinline__ Two<float2> ld2(const float2* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ Two<double2> ld2(const double2* p) { return {p[0], p[1]}; }
+__device__ __forceinline__ void st2(float2* p, Two<float2> v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
+__device__ __forceinline__ void st2(double2* p, Two<double2> v) { p[0] = v.a; p[1] = v.b; }
+
+template <typename R, bool CD, int STAGE, int NT, int TY>
+__device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUtensorMap* m_in2,
+                                             const CUtensorMap* m_V, const CUtensorMap* m_psi,
+                                             const CUtensorMap* m_acc, const CUtensorMap* m_lo,
+                                             const StageIO<R>& io, const Coef<R>& c, const int nx, const int ny,
+                                             const int x0, const int y0, const int dir) {
+    constexpr int TXC = 2 * NT;          // columns per CTA
+    constexpr int HB = TXC;              // first input TMA box: x0-2 .. x0+TXC-3; the second: 4 points
+    using C = cplx<R>;
+    using L = Lay<R, NT>;
+    using T2 = Two<C>;
+    constexpr bool NEED_E = STAGE >= 1;          // V on the output row
+    constexpr bool NEED_PA = STAGE >= 2;
+    constexpr bool NEED_LO = STAGE == 4 && sizeof(R) == 4;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+
+    const int t = threadIdx.x;
+    const int nrows = min(TY, ny - y0);
+    const int jmax = nrows + 4;                  // input rows j = 0 .. jmax-1
+    // The CTA walks its rows downwards (dir = +1) or upwards (dir = -1):
+    // output row e is grid row ybase + dir * e, input row j is ybase + dir * (j - 2).
+    const int ybase = dir > 0 ? y0 : y0 + nrows - 1;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t ibar0 = sbase + L::BAR_OFF;   // S input barriers, then 2 epilogue barriers
+    const uint32_t ebar0 = ibar0 + 8 * S;
+
+    if (t == 0) {
+        tma_prefetch_desc(m_in);
+        tma_prefetch_desc(m_in2);
+        for (int s = 0; s < S + 2; ++s) mbar_init(ibar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // Producer side (thread 0): input row j, epilogue row e.
+    auto issue_in = [&](int j) {
+        const int s = j % S;
+        const uint32_t dst = sbase + L::IN_OFF + s * L::IN_SLOT;
+        const uint32_t bar = ibar0 + 8 * s;
+        const int r = ybase + dir * (j - 2);
+        mbar_expect_tx(bar, L::IN_BYTES);
+        load_cplx_box<R>(dst, m_in, x0 - 2, r, bar);
+        load_cplx_box<R>(dst + HB * L::CB, m_in2, x0 - 2 + HB, r, bar);
+    };
+    auto issue_e = [&](int e) {
+        const uint32_t dst = sbase + L::E_OFF + (e & 1) * L::E_SLOT;
+        const uint32_t bar = ebar0 + 8 * (e & 1);
+        const int r = ybase + dir * e;
+        uint32_t bytes = L::V_BYTES;
+        if (NEED_PA) bytes += 2 * L::T_BYTES;
+        if (NEED_LO) bytes += L::T_BYTES;
+        mbar_expect_tx(bar, bytes);
+        tma_load_2d(dst + L::E_V, m_V, x0, r, bar);
+        if (NEED_PA) {
+            load_cplx_box<R>(dst + L::E_PSI, m_psi, x0, r, bar);
+            load_cplx_box<R>(dst + L::E_ACC, m_acc, x0, r, bar);
+        }
+        if (NEED_LO) load_cplx_box<R>(dst + L::E_LO, m_lo, x0, r, bar);
+    };
+    int next = 0, enext = 0;                     // rows issued so far (thread 0)
+    if (t == 0) {
+        for (; next < S && next < jmax; ++next) issue_in(next);
+        if (NEED_E) issue_e(enext++);
+    }
+
+    auto irow = [&](int j) { return reinterpret_cast<const C*>(smem + L::IN_OFF + (j % S) * L::IN_SLOT); };
+    auto erow = [&](int e) { return smem + L::E_OFF + (e & 1) * L::E_SLOT; };
+    C* dring = reinterpret_cast<C*>(smem + L::D_OFF);
+
+    bool ok = true;
+    auto wait_in = [&](int j) {
+        if (ok) ok = mbar_wait(ibar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kWaitNs);
+    };
+    auto wait_e = [&](int e) {
+        if (ok) ok = mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kWaitNs);
+    };
+
+    const C m4 = pair<C>(-4, -4), m12 = pair<C>(R(-1.0 / 12.0), R(-1.0 / 12.0));
+    const C ih2 = pair<C>(c.inv_h2, c.inv_h2), i6h2 = pair<C>(c.inv_6h2, c.inv_6h2);
+    const C a2 = pair<C>(c.a, c.a);
+    const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
+
+    // D at grid point (x, r) from its five stencil values (boundary: Eq. dbc_lap,
+    // V read from global memory; outside the grid: 0, never used).
+    auto dpoint = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> C {
+        if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
+        if (x == 0 || x == nx - 1 || r == 0 || r == ny - 1)
+            return dirichlet_D(c, ctr, io.V[(int64_t)r * nx + x]);
+        return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
+    };
+
+    const int xa = x0 + 2 * t;                   // this thread's columns xa, xa + 1
+    const int k = 2 * t + 2;                     // xa in the row buffers
+    const bool xin = xa < nx;                    // nx is even: then xa + 1 < nx too
+
+    // Prologue: input rows y0-2 .. y0+1 give D(., y0-1) and D(., y0).
+    wait_in(0); wait_in(1); wait_in(2); wait_in(3);
+    bool alive = __syncthreads_and(ok);
+    T2 cm, c0, c1, dm, d0;
+    C lm, rm, l0, r0;
+    if (alive) {
+        const C* q0 = irow(0); const C* q1 = irow(1); const C* q2 = irow(2); const C* q3 = irow(3);
+        const T2 cmm = ld2(q0 + k);
+        cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
+        lm = q1[k - 1]; rm = q1[k + 2];
+        l0 = q2[k - 1]; r0 = q2[k + 2];
+        const int yb = ybase - dir;              // the row before the first output row
+        dm.a = dpoint(xa, yb, cm.a, cmm.a, c0.a, lm, cm.b);
+        dm.b = dpoint(xa + 1, yb, cm.b, cmm.b, c0.b, cm.a, rm);
+        d0.a = dpoint(xa, ybase, c0.a, cm.a, c1.a, l0, c0.b);
+        d0.b = dpoint(xa + 1, ybase, c0.b, cm.b, c1.b, c0.a, r0);
+        C* drow = dring;                                   // input row 2 -> D ring row 0
+        st2(drow + k, d0);
+        if (t == 0) drow[1] = dpoint(x0 - 1, ybase, l0, q1[1], q3[1], q2[0], c0.a);
+        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, ybase, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
+    }
+    __syncthreads();
+
+    bool bad = false;
+    // Unrolled by 3, the period of the three-row register windows, so that
+    // sliding them is register renaming rather than moves.
+#pragma unroll 3
+    for (int i = 0; i < TY; ++i) {
+        if (!alive || i >= nrows) break;
+        const int j = i + 2;                     // input row of y
+        const int y = ybase + dir * i;
+        const int ya = y + dir;                  // the row after y in walk order
+        wait_in(j + 2);
+        if (!__syncthreads_and(ok)) { alive = false; break; }
+        if (t == 0) {
+            if (next < jmax) issue_in(next++);
+            if (NEED_E && enext < nrows) issue_e(enext++);
+        }
+
+        // D(., ya), one row ahead.
+        const C* q1 = irow(j + 1);
+        const C* q2 = irow(j + 2);
+        const T2 c2 = ld2(q2 + k);
+        const C l1 = q1[k - 1], r1 = q1[k + 2];
+        T2 d1;
+        d1.a = dpoint(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
+        d1.b = dpoint(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+        C* dn = dring + ((j + 1) & 1) * L::ROW;
+        st2(dn + k, d1);
+        if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
+        if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+        if (NEED_E) wait_e(i);
+        if (!__syncthreads_and(ok)) { alive = false; break; }
+
+        if (xin) {
+            const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
+            const bool rowb = y == 0 || y == ny - 1;
+            const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
+            T2 lap = d0;
+            if (!CD) {
+                const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));
+                const C dsb = add2(add2(d0.a, dr[k + 2]), add2(dm.b, d1.b));
+                const C cna = add2(add2(lm, cm.b), add2(l1, c1.b));
+                const C cnb = add2(add2(cm.a, rm), add2(c1.a, r1));
+                if (!ba) lap.a = fma2(i6h2, fma2(m4, c0.a, cna), fma2(m12, dsa, d0.a));
+                if (!bb) lap.b = fma2(i6h2, fma2(m4, c0.b, cnb), fma2(m12, dsb, d0.b));
+            }
+            const int64_t p = (int64_t)y * nx + xa;
+            if constexpr (STAGE == 0) {
+                st2(io.lap + p, lap);
+            } else {
+                const unsigned char* es = erow(i);
+                const R* vv = reinterpret_cast<const R*>(es + L::E_V) + 2 * t;
+                // w = a Lap + (s|Psi|^2 - V) Psi; c F = (-c, c) * swap(w); F_b = 0.
+                auto swapped_w = [&](C y_, C lap_, R v_, bool b_) -> C {
+                    if (b_) return czero<C>();
+                    const R N = c.s * (y_.x * y_.x + y_.y * y_.y) - v_;
+                    const C w = fma2(pair<C>(N, N), y_, mul2(a2, lap_));
+                    return pair<C>(w.y, w.x);
+                };
+                const C swa = swapped_w(c0.a, lap.a, vv[0], ba);
+                const C swb = swapped_w(c0.b, lap.b, vv[1], bb);
+                if constexpr (STAGE == 1) {
+                    st2(io.acc + p, T2{mul2(ca2, swa), mul2(ca2, swb)});
+                    st2(io.yout + p, T2{fma2(cy2, swa, c0.a), fma2(cy2, swb, c0.b)});
+                } else {
+                    const T2 pn = ld2(reinterpret_cast<const C*>(es + L::E_PSI) + 2 * t);
+                    const T2 ac = ld2(reinterpret_cast<const C*>(es + L::E_ACC) + 2 * t);
+                    if constexpr (STAGE == 2 || STAGE == 3) {
+                        st2(io.acc + p, T2{fma2(ca2, swa, ac.a), fma2(ca2, swb, ac.b)});
+                        st2(io.yout + p, T2{fma2(cy2, swa, pn.a), fma2(cy2, swb, pn.b)});
+                    } else {
+                        const C da = fma2(ca2, swa, ac.a), db = fma2(ca2, swb, ac.b);
+                        T2 out = pn;
+                        if constexpr (sizeof(R) == 4) {
+                            T2 lo = ld2(reinterpret_cast<const C*>(es + L::E_LO) + 2 * t);
+                            kahan_add(out.a.x, lo.a.x, da.x);
+                            kahan_add(out.a.y, lo.a.y, da.y);
+                            kahan_add(out.b.x, lo.b.x, db.x);
+                            kahan_add(out.b.y, lo.b.y, db.y);
+                            st2(io.lo + p, lo);
+                        } else {
+                            out.a = add2(out.a, da);
+                            out.b = add2(out.b, db);
+                        }
+                        st2(io.psi_out + p, out);
+                        bad |= !(isfinite(out.a.x) && isfinite(out.a.y) && isfinite(out.b.x) && isfinite(out.b.y));
+                    }
+                }
+            }
+        }
+        lm = l0; rm = r0; l0 = l1; r0 = r1;
+        cm = c0; c0 = c1; c1 = c2;
+        dm = d0; d0 = d1;
+    }
+
+    if (!alive) {
+        // A transfer never arrived: report, let this CTA's copies in flight land, leave.
+        if (t == 0) {
+            atomicOr(io.flag, 2);
+            for (int j = next > S ? next - S : 0; j < next; ++j)
+                mbar_wait(ibar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kDrainNs);
+            for (int e = enext > 2 ? enext - 2 : 0; e < enext; ++e)
+                mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kDrainNs);
+        }
+        return;
+    }
+    if constexpr (STAGE == 4) {
+        if (__syncthreads_or(bad) && t == 0) atomicOr(io.flag, 1);
+    }
+}
+
+}  // namespace tile2d
+}  // namespace nlse

@@ -74,6 +74,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_check": ([vp, vp], ctypes.c_int),
         "nlse_last_error": ([], ctypes.c_char_p),
         "nlse_invariants_noalloc": ([ctypes.POINTER(Params), vp, vp, dp, dp, dp, vp], ctypes.c_int),
+        "nlse_create_batch": ([ctypes.c_int, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "nlse_invariants_batch": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
+        "nlse_batch_count": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -117,6 +120,23 @@ def nlse_create(params: Params, V_ptr: int) -> ctypes.c_void_p:
     _raise(load_library().nlse_create(ctypes.byref(params), ctypes.c_void_p(V_ptr),
                                       ctypes.byref(ctx)))
     return ctx
+
+
+def nlse_create_batch(params_list, V_ptr: int) -> ctypes.c_void_p:
+    arr = (Params * len(params_list))(*params_list)
+    ctx = ctypes.c_void_p()
+    _raise(load_library().nlse_create_batch(len(params_list), arr, ctypes.c_void_p(V_ptr), ctypes.byref(ctx)))
+    return ctx
+
+
+def nlse_invariants_batch(ctx, psi_ptr: int, count: int, stream=None):
+    m, e, d = (ctypes.c_double * count)(), (ctypes.c_double * count)(), (ctypes.c_double * count)()
+    _raise(load_library().nlse_invariants_batch(ctx, ctypes.c_void_p(psi_ptr), m, e, d, _stream(stream)))
+    return list(m), list(e), list(d)
+
+
+def nlse_batch_count(ctx) -> int:
+    return load_library().nlse_batch_count(ctx)
 
 
 def nlse_destroy(ctx) -> None:
@@ -214,6 +234,87 @@ class Solver:
 
     def reset_compensation(self):
         nlse_reset_compensation(self.ctx)
+
+    def check(self):
+        nlse_check(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nlse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """Many independent 2D instances advanced together (nlse_create_batch).
+
+    ``shapes`` lists each instance's (ny, nx); ``h``, ``dt``, ``a``, ``s`` are
+    scalars or per-instance sequences.  ``V`` is the flat potential: the
+    instances' arrays raveled and concatenated in order (see :meth:`pack`).
+    Psi is the same kind of flat complex tensor."""
+
+    def __init__(self, V: torch.Tensor, shapes, h, dt, a, s, prec: str = "fp32", lap: str = "2shoc",
+                 check_stability: bool = True):
+        load_library()
+        want = torch.float32 if prec == "fp32" else torch.float64
+        if not V.is_cuda or V.dtype != want or not V.is_contiguous() or V.dim() != 1:
+            raise ValueError(f"V must be a flat contiguous CUDA {want} tensor")
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        n = len(self.shapes)
+        self.sizes = [sh[0] * sh[1] for sh in self.shapes]
+        self.offsets = [sum(self.sizes[:i]) for i in range(n)]
+        if V.numel() != sum(self.sizes):
+            raise ValueError("V has the wrong number of points for these shapes")
+        per = lambda v: [float(x) for x in v] if hasattr(v, "__len__") else [float(v)] * n
+        hs, dts, as_, ss = per(h), per(dt), per(a), per(s)
+        self.params = [make_params(self.shapes[i], hs[i], dts[i], as_[i], ss[i], "dirichlet", prec, lap,
+                                   check_stability) for i in range(n)]
+        self.V = V
+        self.count = n
+        self.cdtype = torch.complex64 if prec == "fp32" else torch.complex128
+        with torch.cuda.device(V.device):
+            self.ctx = nlse_create_batch(self.params, V.data_ptr())
+
+    @staticmethod
+    def pack(arrays, dtype, device):
+        """Flat tensor of the arrays raveled and concatenated in order."""
+        return torch.cat([torch.as_tensor(a).reshape(-1) for a in arrays]).to(device=device, dtype=dtype).contiguous()
+
+    def unpack(self, flat: torch.Tensor):
+        """Views of a flat tensor as the instances' (ny, nx) grids."""
+        return [flat[o:o + z].view(sh) for o, z, sh in zip(self.offsets, self.sizes, self.shapes)]
+
+    def _check_psi(self, psi):
+        if (not psi.is_cuda or psi.dtype != self.cdtype or psi.dim() != 1 or psi.numel() != sum(self.sizes)
+                or not psi.is_contiguous() or psi.device != self.V.device):
+            raise ValueError(f"psi must be a flat contiguous {self.cdtype} tensor on {self.V.device}")
+
+    def run(self, psi, nsteps):
+        self._check_psi(psi)
+        nlse_run(self.ctx, psi.data_ptr(), nsteps)
+        return psi
+
+    def rk4_step(self, psi):
+        self._check_psi(psi)
+        nlse_rk4_step(self.ctx, psi.data_ptr())
+        return psi
+
+    def lap2shoc(self, psi, out=None):
+        self._check_psi(psi)
+        out = torch.empty_like(psi) if out is None else out
+        self._check_psi(out)
+        nlse_lap2shoc(self.ctx, psi.data_ptr(), out.data_ptr())
+        return out
+
+    def invariants(self, psi):
+        """Per-instance (mass, energy, dt_max) lists, FP64."""
+        self._check_psi(psi)
+        return nlse_invariants_batch(self.ctx, psi.data_ptr(), self.count)
 
     def check(self):
         nlse_check(self.ctx)

@@ -89,3 +89,18 @@ def test_misaligned_potential_is_rejected(lib):
     ctx = ctypes.c_void_p()
     rc = lib.nlse_create(ctypes.byref(_params()), ctypes.c_void_p(4100), ctypes.byref(ctx))
     assert rc == nlse.EINVAL
+
+
+def test_batch_validation_on_the_host(lib):
+    ctx = ctypes.c_void_p()
+    bad = [_params(shape=(16, 16)), _params(shape=(8, 10))]        # width not a multiple of 4
+    arr = (nlse.Params * 2)(*bad)
+    assert lib.nlse_create_batch(2, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EUNSUPPORTED
+    mixed = [_params(shape=(16, 16)), _params(shape=(8, 12), prec="fp64")]
+    arr = (nlse.Params * 2)(*mixed)
+    assert lib.nlse_create_batch(2, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EINVAL
+    three_d = [_params(shape=(4, 16, 16))]
+    arr = (nlse.Params * 1)(*three_d)
+    assert lib.nlse_create_batch(1, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EUNSUPPORTED
+    assert lib.nlse_create_batch(0, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EINVAL
+    assert ctx.value is None

@@ -1,0 +1,152 @@
+"""The batched path (nlse_create_batch): many uneven 2D instances advanced by
+one launch per RK4 stage must give, for every instance, what the single-grid
+path gives for it alone (which the parity suite pins to the oracle), and the
+oracle directly on small instances.
+
+Tolerance: FP64 1e-12 and FP32 1e-6 relative to max|psi| after 40 steps.  The
+batched and single-grid kernels run the same per-point arithmetic, so the
+difference is at most a few rounding steps."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1109_1027_gb300 import nlse
+from paper_1109_1027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _batch(sides, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i, (ny, nx) in enumerate(sides):
+        x, y = wl.mesh((ny, nx), -8.0, 8.0)
+        w = rng.uniform(0.02, 0.1)
+        V = w * w * (x * x + y * y)
+        width = rng.uniform(1.0, 3.0)
+        psi = np.exp(-(x * x + y * y) / (2 * width ** 2)) * np.exp(1j * (rng.uniform(-1, 1) * x + rng.uniform(-1, 1) * y))
+        psi = psi + 0.05 * wl.random_field((ny, nx), seed=seed + i)
+        h = wl.spacing(nx, -8.0, 8.0)
+        a = float(rng.uniform(0.3, 1.0))
+        s = float(rng.choice([-1.0, 1.0]))
+        out.append(dict(shape=(ny, nx), V=V, psi=psi, h=h, a=a, s=s))
+    return out
+
+
+SIDES = [(64, 64), (40, 68), (128, 128), (96, 192), (70, 260), (33, 64), (200, 320), (17, 132), (256, 256), (3, 4)]
+
+
+def _dts(insts, prec):
+    dts = []
+    for q in insts:
+        prob = oracle.Problem(q["shape"], q["h"], q["a"], q["s"])
+        psi = q["psi"].astype(np.complex64).astype(np.complex128) if prec == "fp32" else q["psi"]
+        V = q["V"].astype(np.float32).astype(np.float64) if prec == "fp32" else q["V"]
+        dts.append(0.5 * oracle.invariants(prob, psi, V)[2])
+    return dts
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_equals_single_grid_runs(prec):
+    insts = _batch(SIDES)
+    cdt, rdt = (torch.complex64, torch.float32) if prec == "fp32" else (torch.complex128, torch.float64)
+    dts = _dts(insts, prec)
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec)
+    psi = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
+    bs.run(psi, 40)
+    bs.check()
+    got = [g.cpu().numpy() for g in bs.unpack(psi)]
+    for i, q in enumerate(insts):
+        Vi = torch.from_numpy(q["V"]).to(DEV).to(rdt).contiguous()
+        sv = nlse.Solver(Vi, q["h"], dts[i], q["a"], q["s"], prec=prec)
+        x = torch.from_numpy(q["psi"]).to(DEV).to(cdt).contiguous()
+        sv.run(x, 40)
+        ref = x.cpu().numpy()
+        tol = (1e-12 if prec == "fp64" else 1e-6) * np.abs(ref).max()
+        assert np.abs(got[i] - ref).max() <= tol, (i, q["shape"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_matches_oracle_on_small_instances(prec):
+    insts = _batch([(64, 64), (40, 68), (33, 64), (17, 132)], seed=11)
+    cdt, rdt = (torch.complex64, torch.float32) if prec == "fp32" else (torch.complex128, torch.float64)
+    dts = _dts(insts, prec)
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec)
+    psi = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
+    bs.run(psi, 10)
+    for i, (g, q) in enumerate(zip(bs.unpack(psi), insts)):
+        r = lambda a_, dt_: a_.astype(dt_).astype(np.complex128 if np.iscomplexobj(a_) else np.float64)
+        p0 = r(q["psi"], np.complex64) if prec == "fp32" else q["psi"]
+        V0 = r(q["V"], np.float32) if prec == "fp32" else q["V"]
+        ref = oracle.run(oracle.Problem(q["shape"], q["h"], q["a"], q["s"]), p0, V0, dts[i], 10)
+        tol = (1e-12 if prec == "fp64" else 1e-5) * np.abs(ref).max()
+        assert np.abs(g.cpu().numpy() - ref).max() <= tol, i
+
+
+def test_batch_laplacian_and_invariants():
+    insts = _batch(SIDES, seed=3)
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], torch.float64, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], 1e-4,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec="fp64")
+    psi = nlse.BatchSolver.pack([q["psi"] for q in insts], torch.complex128, DEV)
+    lap = [l.cpu().numpy() for l in bs.unpack(bs.lap2shoc(psi))]
+    m, e, d = bs.invariants(psi)
+    for i, q in enumerate(insts):
+        prob = oracle.Problem(q["shape"], q["h"], q["a"], q["s"])
+        ref = oracle.laplacian(prob, q["psi"], q["V"])
+        assert np.abs(lap[i] - ref).max() <= 1e-12 * np.abs(ref).max() * 16, i
+        m0, e0, d0 = oracle.invariants(prob, q["psi"], q["V"])
+        assert m[i] == pytest.approx(m0, rel=1e-12)
+        assert e[i] == pytest.approx(e0, rel=1e-11, abs=1e-12)
+        assert d[i] == pytest.approx(d0, rel=1e-12)
+
+
+def test_batch_refuses_an_unstable_instance():
+    insts = _batch([(64, 64), (128, 128), (40, 68)], seed=5)
+    dts = _dts(insts, "fp64")
+    dts[1] *= 3.0                                   # 1.5x its bound
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], torch.float64, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec="fp64")
+    psi = nlse.BatchSolver.pack([q["psi"] for q in insts], torch.complex128, DEV)
+    with pytest.raises(nlse.NLSEError) as ei:
+        bs.run(psi, 5)
+    assert ei.value.code == nlse.EUNSTABLE and "instance 1" in str(ei.value)
+
+
+def test_batch_workload_sample_equals_single_grid():
+    """The 512-instance batch workload (sides 64..1024): 3 steps of the whole
+    batch, sampled instances compared with their single-grid runs."""
+    insts = wl.gaussian_batch_2d(count=512, steps=0)
+    dts = []
+    Vs, psis = [], []
+    for q in insts:
+        Vs.append(q.V)
+        psis.append(q.psi0)
+    # dt from the library's own FP64 bound, instance by instance (no oracle on 2e8 points)
+    Vf = nlse.BatchSolver.pack(Vs, torch.float32, DEV)
+    probe = nlse.BatchSolver(Vf, [q.shape for q in insts], [q.h for q in insts], 1e-9,
+                             [q.a for q in insts], [q.s for q in insts], prec="fp32", check_stability=False)
+    psi = nlse.BatchSolver.pack(psis, torch.complex64, DEV)
+    _, _, dtmax = probe.invariants(psi)
+    probe.close()
+    dts = [0.5 * d for d in dtmax]
+    bs = nlse.BatchSolver(Vf, [q.shape for q in insts], [q.h for q in insts], dts,
+                          [q.a for q in insts], [q.s for q in insts], prec="fp32")
+    bs.run(psi, 3)
+    bs.check()
+    out = bs.unpack(psi)
+    for i in [0, 1, 17, 100, 255, 256, 400, 511]:
+        q = insts[i]
+        sv = nlse.Solver(torch.from_numpy(q.V).to(DEV).float().contiguous(), q.h, dts[i], q.a, q.s)
+        x = torch.from_numpy(q.psi0).to(DEV).to(torch.complex64).contiguous()
+        sv.run(x, 3)
+        diff = (out[i] - x).abs().max().item()
+        assert diff <= 1e-6 * x.abs().max().item(), (i, q.shape, diff)
