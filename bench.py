@@ -294,6 +294,11 @@ def run_ours(args):
     sp.check()
     sp.close()
 
+    # ---- batched uneven instances, FP32 vs FP64 ------------------------------
+    batch = None
+    if not args.no_batch:
+        batch = run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks)
+
     # ---- end to end through host buffers ------------------------------------
     ke = min(args.steps, 200)
     host_in = torch.empty((N_SIDE, N_SIDE), dtype=torch.complex64, pin_memory=True)
@@ -360,11 +365,82 @@ def run_ours(args):
                            "achieved_gbs": BYTES_PER_UPDATE_PLAIN * npts / (msp / kp * 1e-3) / 1e9,
                            "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"},
             "fp32_vs_fp64_rel_l2": l2,
+            "batched": batch,
             "mass_drift": {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1},
             "energy_drift": {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1},
         }))
     if pg is not None:
         pg.destroy_process_group()
+
+
+def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
+    """512 independent 2D instances (sides 64..1024 step 64, seeded per rank),
+    one launch per RK4 stage for the whole batch: FP32 and FP64 over the same
+    steps, per-instance relative L2 difference of the final states."""
+    import torch
+
+    from paper_1109_1027_gb300 import nlse
+
+    insts = wl.gaussian_batch_2d(count=512, seed=4 + rank, steps=0)
+    shapes = [q.shape for q in insts]
+    npts = sum(q.shape[0] * q.shape[1] for q in insts)
+    Vs = [q.V for q in insts]
+    psis = [q.psi0 for q in insts]
+    V64 = nlse.BatchSolver.pack(Vs, torch.float64, dev)
+    psi64 = nlse.BatchSolver.pack(psis, torch.complex128, dev)
+    del Vs, psis
+    probe = nlse.BatchSolver(V64, shapes, [q.h for q in insts], 1.0, [q.a for q in insts], [q.s for q in insts],
+                             prec="fp64", check_stability=False)
+    _, _, dtmax = probe.invariants(psi64)
+    probe.close()
+    dts = [0.5 * d for d in dtmax]
+    hs, as_, ss = [q.h for q in insts], [q.a for q in insts], [q.s for q in insts]
+    steps = args.batch_steps
+    out = {"workload": "512 2D instances, sides U{64..1024 step 64}, a~U[0.3,1], s=+-1, V=w^2 r^2, Gaussian "
+                       "psi0 with phase gradient, per-instance dt = 0.5 dt_max (seeded)",
+           "points": npts, "steps": steps, "warmup": 3}
+    res = {}
+    for prec, rdt, cdt in (("fp32", torch.float32, torch.complex64), ("fp64", torch.float64, torch.complex128)):
+        V = V64.to(rdt).contiguous()
+        x = psi64.to(cdt).contiguous()
+        bs = nlse.BatchSolver(V, shapes, hs, dts, as_, ss, prec=prec)
+        bs.run(x, 3)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bs.run(x, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        try:
+            bs.check()          # focusing instances above the critical mass may collapse (reported below)
+        except nlse.NLSEError as err:
+            if err.code != nlse.ENONFINITE:
+                raise
+        res[prec] = x
+        out[prec] = {"value": world * npts * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
+        bs.close()
+    out["fp32"]["achieved_gbs"] = BYTES_PER_UPDATE_FP32 * npts / (out["fp32"]["ms_per_step"] * 1e-3) / 1e9
+    errs, collapsed = [], 0
+    a64 = res["fp64"]
+    a32 = res["fp32"].to(torch.complex128)
+    off = 0
+    for q in insts:
+        n = q.shape[0] * q.shape[1]
+        s64, s32 = a64[off:off + n], a32[off:off + n]
+        off += n
+        if not (bool(torch.isfinite(s64).all()) and bool(torch.isfinite(s32).all())):
+            collapsed += 1
+            continue
+        errs.append(float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64)))
+    errs.sort()
+    out["fp32_vs_fp64_rel_l2"] = {"max": errs[-1], "median": errs[len(errs) // 2], "instances": len(errs),
+                                  "within_1e-5": sum(e <= 1e-5 for e in errs)} if errs else None
+    out["collapsed_instances"] = collapsed
+    out["collapsed_note"] = ("focusing (s=+1) instances whose mass exceeds the 2D critical mass collapse; "
+                             "with dt fixed at 0.5 dt_max(psi0) the explicit scheme then overflows (the bound "
+                             "of Eq. kdfull shrinks as |psi| grows); they are excluded from the error statistics")
+    return out
 
 
 def main():
@@ -374,6 +450,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--batch-steps", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
