@@ -188,6 +188,22 @@ int nlse_check(nlse_ctx* ctx, void* stream);
 int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const void* V_dev,
                             double* mass, double* energy, double* dt_max, void* stream);
 
+/* Gradient of the final-time loss L = sum_points |Psi_T - target|^2, where
+ * Psi_T is the state after nsteps RK4 steps from psi0 (as nlse_run computes
+ * it), with respect to psi0 and V: the discrete adjoint of Eq. (RK4) with F
+ * of Sec. 3.1, the 2SHOC Laplacian (Secs. 2.2) and the Dirichlet rule
+ * (Eqs. dbc_lap, dbc_ut), checkpointed every ckpt_every steps (the reverse
+ * sweep recomputes each segment from its checkpoint).  Single-grid 2D
+ * Dirichlet contexts.  psi0_dev and target_dev are complex fields of the
+ * context's precision (not modified); dpsi0_dev (same type) receives
+ * dL/dRe(psi0) + i dL/dIm(psi0); dV_dev receives dL/dV as FP64 (double,
+ * accumulated in FP64); *loss the FP64 loss.  The context allocates its work
+ * space on first use (state + (nsteps/ckpt_every) checkpoints + ckpt_every
+ * states + 7 fields).  Uses the context's compensated part, which then no
+ * longer belongs to any caller state.  Synchronises the stream. */
+int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
+                 int64_t ckpt_every, void* dpsi0_dev, void* dV_dev, double* loss, void* stream);
+
 /* Human-readable description of the calling thread's last error ("" if none). */
 const char* nlse_last_error(void);
 

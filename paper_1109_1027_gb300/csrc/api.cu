@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -67,6 +68,9 @@ struct nlse_ctx {
     int64_t* boff;            // per-instance element offsets
     int* brow;                // per-instance first row of partials (count + 1 entries)
     const void* maps_psi;     // Psi buffer the batch tensor maps currently point at
+    // Adjoint work space (nlse_adjoint), allocated on first use.
+    void* adj_buf;
+    size_t adj_bytes;
 };
 
 namespace {
@@ -262,6 +266,7 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
 
 void release(nlse_ctx* c) {
     if (!c) return;
+    cudaFree(c->adj_buf);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     nlse::batch2d_destroy(c->batch);
     delete[] c->bparams;
@@ -406,6 +411,123 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
     TRY(nlse::batch2d_create(count, p, V_dev, c->Y[0], c->Y[1], c->acc, c->lo, &c->batch), "building the batch plan");
 #undef TRY
     *out = c;
+    return NLSE_OK;
+}
+
+int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nsteps, int64_t ckpt_every,
+                 void* dpsi0, void* dV, double* loss, void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi0 || !target || !dpsi0 || !dV) return fail(NLSE_EINVAL, "NULL argument");
+    if (c->batch || c->p.dim != 2 || c->p.bc != NLSE_BC_DIRICHLET || (c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE))
+        return fail(NLSE_EUNSUPPORTED, "the adjoint is implemented for single 2D Dirichlet grids (fused schedule)");
+    if (nsteps < 0 || ckpt_every < 1) return fail(NLSE_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
+    if (((uintptr_t)psi0 | (uintptr_t)target | (uintptr_t)dpsi0 | (uintptr_t)dV) % 16)
+        return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cb = c->cbytes;
+    const bool has_lo = c->lo != nullptr;
+    const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    const int64_t seglen = nsteps < ckpt_every ? nsteps : ckpt_every;
+    const int nb = nlse::loss_num_blocks(c->npts);
+    // Work space: state S, checkpoints (state + compensated part), one
+    // segment of states, Y2 Y3 Y4, two cotangents, two adjoint states, loss partials.
+    const size_t ck_bytes = (size_t)nseg * cb * (has_lo ? 2 : 1);
+    const size_t need = cb + ck_bytes + (size_t)seglen * cb + 7 * cb + sizeof(double) * (nb + 1);
+    if (need > c->adj_bytes) {
+        cudaFree(c->adj_buf);
+        c->adj_buf = nullptr;
+        c->adj_bytes = 0;
+        NLSE_CUDA(cudaMalloc(&c->adj_buf, need), "allocating adjoint work space");
+        c->adj_bytes = need;
+    }
+    char* base = static_cast<char*>(c->adj_buf);
+    char* S = base;
+    char* ck = S + cb;
+    char* seg = ck + ck_bytes;
+    char* Y2 = seg + (size_t)seglen * cb;
+    char* Y3 = Y2 + cb;
+    char* Y4 = Y3 + cb;
+    char* W = Y4 + cb;
+    char* WN = W + cb;
+    char* LA = WN + cb;
+    char* LB = LA + cb;
+    double* part = reinterpret_cast<double*>(LB + cb);
+    double* lossd = part + nb;
+    auto ckp = [&](int64_t i) { return ck + (size_t)i * cb * (has_lo ? 2 : 1); };
+
+    // Forward pass with checkpoints.  S is the state; the context's
+    // compensated part belongs to S for the duration of the call.
+    NLSE_CUDA(cudaMemcpyAsync(S, psi0, cb, cudaMemcpyDeviceToDevice, st), "copying psi0");
+    if (has_lo) NLSE_CUDA(cudaMemsetAsync(c->lo, 0, cb, st), "zeroing the compensated part");
+    c->state_psi = nullptr;
+    int rc;
+    for (int64_t g = 0; g < nseg; ++g) {
+        NLSE_CUDA(cudaMemcpyAsync(ckp(g), S, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+        if (has_lo) NLSE_CUDA(cudaMemcpyAsync(ckp(g) + cb, c->lo, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+        const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
+        for (int64_t m = 0; m < steps; ++m)
+            if ((rc = enqueue_step(c, S, st))) return rc;
+    }
+    NLSE_CUDA(nlse::launch_loss(c->p.prec, S, target, LA, c->npts, part, nb, lossd, st), "loss launch");
+
+    // Reverse sweep, segment by segment from the last.
+    char* lamp = LA;
+    char* lam = LB;
+    StageLaunch F = base_launch(c);
+    F.acc = c->acc;
+    nlse::AdjLaunch A;
+    A.prec = c->p.prec; A.lap = c->p.lap;
+    A.nx = c->p.n[0]; A.ny = c->p.n[1];
+    A.h = c->p.h; A.a = c->p.a; A.s = c->p.s;
+    A.V = c->V;
+    A.gV = static_cast<double*>(dV);
+    NLSE_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * c->npts, st), "zeroing dV");
+    const double k = c->p.dt;
+    for (int64_t g = nseg - 1; g >= 0; --g) {
+        const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
+        NLSE_CUDA(cudaMemcpyAsync(S, ckp(g), cb, cudaMemcpyDeviceToDevice, st), "restore");
+        if (has_lo) NLSE_CUDA(cudaMemcpyAsync(c->lo, ckp(g) + cb, cb, cudaMemcpyDeviceToDevice, st), "restore");
+        for (int64_t m = 0; m < steps; ++m) {
+            NLSE_CUDA(cudaMemcpyAsync(seg + (size_t)m * cb, S, cb, cudaMemcpyDeviceToDevice, st), "segment state");
+            if (m + 1 < steps && (rc = enqueue_step(c, S, st))) return rc;
+        }
+        for (int64_t m = steps - 1; m >= 0; --m) {
+            const void* psi_n = seg + (size_t)m * cb;
+            // Stage inputs Y2, Y3, Y4 of this step, recomputed by the forward stage kernels.
+            const void* fin[4] = {nullptr, psi_n, Y2, Y3};
+            void* fout[4] = {nullptr, Y2, Y3, Y4};
+            for (int sg = 1; sg <= 3; ++sg) {
+                F.stage = sg;
+                F.psi = psi_n;
+                F.yin = fin[sg];
+                F.yout = fout[sg];
+                cudaError_t e = launch_stage(F, st);
+                if (e != cudaSuccess) return cuda_fail(e, "stage recompute");
+            }
+            // Stages 4 .. 1 reversed.
+            const void* w[5] = {nullptr, W, WN, W, lamp};
+            const double sw[5] = {0, 1, 1, 1, k / 6.0};
+            const void* Ys[5] = {nullptr, psi_n, Y2, Y3, Y4};
+            void* wn[5] = {nullptr, nullptr, W, WN, W};
+            const double cw[5] = {0, 0, k / 6.0, k / 3.0, k / 3.0};
+            const double cy[5] = {0, 0, k / 2.0, k / 2.0, k};
+            for (int j = 4; j >= 1; --j) {
+                A.j = j;
+                A.w = w[j]; A.scale_w = sw[j]; A.Y = Ys[j];
+                A.lamp = lamp; A.lam = lam; A.w_next = wn[j];
+                A.cw = cw[j]; A.cy = cy[j];
+                cudaError_t e = nlse::launch_adjoint_stage_2d(A, st);
+                if (e != cudaSuccess) return cuda_fail(e, "adjoint stage launch");
+            }
+            std::swap(lamp, lam);
+        }
+    }
+    NLSE_CUDA(cudaMemcpyAsync(dpsi0, lamp, cb, cudaMemcpyDeviceToDevice, st), "gradient copy");
+    double h_loss = 0.0;
+    NLSE_CUDA(cudaMemcpyAsync(&h_loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, st), "loss copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "adjoint synchronise");
+    c->state_psi = nullptr;          // the compensated part no longer belongs to any caller state
+    if (loss) *loss = h_loss;
     return NLSE_OK;
 }
 

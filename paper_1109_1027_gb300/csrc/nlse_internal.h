@@ -63,6 +63,26 @@ cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st);
 cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st);
 void batch2d_destroy(BatchPlan* b);
 
+// Adjoint of one RK4 stage on a 2D grid (adjoint2d.cu).
+struct AdjLaunch {
+    int prec, lap, j;       // j = 4, 3, 2, 1: the stage being reversed
+    int64_t nx, ny;
+    double h, a, s;
+    const void* w;          // cotangent of K_j (times scale_w)
+    double scale_w;
+    const void* Y;          // stage input Y_j
+    const void* V;
+    const void* lamp;       // dL/dPsi_{n+1}
+    void* lam;              // dL/dPsi_n being accumulated
+    void* w_next;           // cotangent of K_{j-1} = cw lam' + cy Ybar_j
+    double* gV;             // dL/dV (FP64, accumulated)
+    double cw, cy;
+};
+cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st);
+int loss_num_blocks(int64_t n);
+cudaError_t launch_loss(int prec, const void* psi, const void* target, void* lam, int64_t n, double* partials,
+                        int nblocks, double* out, cudaStream_t st);
+
 // FP64 reductions for nlse_invariants.  Each of the nblocks blocks of the
 // partial kernel writes kPartialWidth doubles to partials; the final kernel
 // reduces them in a fixed order into out[0..kPartialWidth).

@@ -77,6 +77,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_create_batch": ([ctypes.c_int, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)], ctypes.c_int),
         "nlse_invariants_batch": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
         "nlse_batch_count": ([vp], ctypes.c_int),
+        "nlse_adjoint": ([vp, vp, vp, i64, i64, vp, vp, dp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -173,6 +174,15 @@ def nlse_invariants_noalloc(params: Params, psi_ptr: int, V_ptr: int, stream=Non
     return m.value, e.value, d.value
 
 
+def nlse_adjoint(ctx, psi0_ptr: int, target_ptr: int, nsteps: int, ckpt_every: int, dpsi0_ptr: int,
+                 dV_ptr: int, stream=None) -> float:
+    loss = ctypes.c_double()
+    _raise(load_library().nlse_adjoint(ctx, ctypes.c_void_p(psi0_ptr), ctypes.c_void_p(target_ptr), int(nsteps),
+                                       int(ckpt_every), ctypes.c_void_p(dpsi0_ptr), ctypes.c_void_p(dV_ptr),
+                                       ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
 def nlse_reset_compensation(ctx, stream=None) -> None:
     _raise(load_library().nlse_reset_compensation(ctx, _stream(stream)))
 
@@ -231,6 +241,18 @@ class Solver:
         """(mass, energy, dt_max) in FP64."""
         self._check_psi(psi)
         return nlse_invariants(self.ctx, psi.data_ptr())
+
+    def adjoint(self, psi0: torch.Tensor, target: torch.Tensor, nsteps: int, ckpt_every: int = 100):
+        """(loss, dL/dpsi0, dL/dV) of L = sum |Psi_T - target|^2 after nsteps
+        steps from psi0; dL/dpsi0 has psi0's dtype (d/dRe + i d/dIm), dL/dV is
+        float64."""
+        self._check_psi(psi0)
+        self._check_psi(target)
+        g_psi = torch.empty_like(psi0)
+        g_V = torch.empty(self.shape, dtype=torch.float64, device=psi0.device)
+        loss = nlse_adjoint(self.ctx, psi0.data_ptr(), target.data_ptr(), nsteps, ckpt_every,
+                            g_psi.data_ptr(), g_V.data_ptr())
+        return loss, g_psi, g_V
 
     def reset_compensation(self):
         nlse_reset_compensation(self.ctx)
@@ -329,3 +351,34 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+class _FinalLoss(torch.autograd.Function):
+    """L = sum |Psi_T(psi0, V) - target|^2 through the CUDA library; the
+    forward call runs the adjoint too (checkpointed), so backward only scales
+    the stored gradients by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, psi0, V, target, h, dt, a, s, nsteps, ckpt_every, lap):
+        prec = "fp32" if psi0.dtype == torch.complex64 else "fp64"
+        solver = Solver(V.detach().contiguous(), h, dt, a, s, prec=prec, lap=lap, check_stability=False)
+        loss, g_psi, g_V = solver.adjoint(psi0.detach().contiguous(), target.detach().contiguous(), nsteps,
+                                          ckpt_every)
+        solver.close()
+        ctx.save_for_backward(g_psi, g_V)
+        ctx.v_dtype = V.dtype
+        return torch.tensor(loss, dtype=torch.float64, device=psi0.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g_psi, g_V = ctx.saved_tensors
+        go = grad_out.to(torch.float64)
+        return (g_psi * go.to(g_psi.real.dtype), (g_V * go).to(ctx.v_dtype), None, None, None, None, None, None,
+                None, None)
+
+
+def final_loss(psi0, V, target, h, dt, a, s, nsteps, ckpt_every=100, lap="2shoc"):
+    """Differentiable L = sum |Psi_T - target|^2 (FP64 scalar) of an RK4+2SHOC
+    run on a 2D Dirichlet grid; gradients w.r.t. psi0 and V come from the
+    library's adjoint (torch.autograd.Function)."""
+    return _FinalLoss.apply(psi0, V, target, h, dt, a, s, nsteps, ckpt_every, lap)

@@ -133,3 +133,33 @@ def gaussian_batch_2d(count: int = 512, seed: int = 4, sides=range(64, 1025, 64)
         out.append(Instance(f"gauss_{i}", (n, n), lo, hi, a, s, V, psi0, 0, steps,
                             {"w": w, "width": width, "k": (float(kx), float(ky))}))
     return out
+
+
+def gradient_problem_2d(n: int = 512, lo: float = -16.0, hi: float = 16.0, seed: int = 5, batch: int = 16,
+                        modes: int = 8, steps: int = 3000):
+    """Inputs of the final-time-loss gradient problem: a = 0.5, s = -1,
+    V = 0.01 r^2 + a smooth seeded perturbation (modes x modes Fourier modes,
+    coefficients N(0, 0.02^2) / (1 + |m|^2)), a batch of Gaussian initial
+    states (width U[2, 4], centre U(-2, 2)^2, phase gradient U[-1, 1]^2) and
+    a batch of Gaussian targets drawn the same way from a second stream.
+    Returns (V, [psi0], [target], h, a, s)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x, y = mesh((n, n), lo, hi)
+    L = hi - lo
+    V = 0.01 * (x * x + y * y)
+    for mx in range(modes):
+        for my in range(modes):
+            c1, c2 = rng.standard_normal(2) * 0.02 / (1.0 + mx * mx + my * my)
+            arg = 2 * np.pi * (mx * (x - lo) + my * (y - lo)) / L
+            V = V + c1 * np.cos(arg) + c2 * np.sin(arg)
+
+    def gauss(r):
+        w = r.uniform(2.0, 4.0)
+        cx, cy = r.uniform(-2.0, 2.0, 2)
+        kx, ky = r.uniform(-1.0, 1.0, 2)
+        return np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * w * w)) * np.exp(1j * (kx * x + ky * y))
+
+    psi0 = [gauss(rng) for _ in range(batch)]
+    rng2 = np.random.Generator(np.random.PCG64(seed + 1000))
+    targets = [gauss(rng2) for _ in range(batch)]
+    return V, psi0, targets, spacing(n, lo, hi), 0.5, -1.0

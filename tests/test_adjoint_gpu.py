@@ -1,0 +1,125 @@
+"""The CUDA adjoint (nlse_adjoint) against the FP64 reference adjoint of
+oracle/adjoint.py (itself pinned by finite differences), against central
+finite differences of the GPU forward, and through torch.autograd.
+
+Tolerances: FP64 1e-10 relative to the largest gradient entry (the reverse
+sweep sums thousands of rounded terms per entry); FP32 state and cotangents
+with FP64 loss and dL/dV accumulation: 2e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import adjoint as oadj
+from paper_1109_1027_gb300 import nlse
+from paper_1109_1027_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _problem(shape, seed):
+    x, y = wl.mesh(shape, -3.0, 3.0)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    V = 0.3 * (x * x + y * y) + 0.1 * rng.standard_normal(shape)
+    psi0 = np.exp(-(x * x + y * y) / 2.0) * np.exp(1j * (0.7 * x - 0.3 * y)) + 0.05 * wl.random_field(shape, seed)
+    target = np.exp(-((x - 0.5) ** 2 + y * y) / 1.5) + 0.05 * wl.random_field(shape, seed + 1)
+    h = wl.spacing(shape[1], -3.0, 3.0)
+    return psi0, V, target, h
+
+
+def _close(a, b, tol):
+    return np.abs(a - b).max() <= tol * np.abs(b).max()
+
+
+@pytest.mark.parametrize("shape,lap", [((16, 20), "2shoc"), ((40, 70), "2shoc"), ((33, 130), "2shoc"),
+                                       ((24, 36), "cd")])
+def test_adjoint_fp64_matches_reference(shape, lap):
+    psi0, V, target, h = _problem(shape, 3)
+    a, s = 0.6, -1.0
+    prob = oracle.Problem(shape, h, a, s, lap=oracle.LAP_CD if lap == "cd" else 0)
+    k = 0.5 * oracle.invariants(prob, psi0, V)[2]
+    n = 7
+    L0, g0, gV0 = oadj.loss_and_gradient(prob, psi0, V, target, k, n)
+    solver = nlse.Solver(torch.from_numpy(V).to(DEV), h, k, a, s, prec="fp64", lap=lap, check_stability=False)
+    t = lambda z: torch.from_numpy(z).to(DEV).to(torch.complex128).contiguous()
+    L, g, gV = solver.adjoint(t(psi0), t(target), n, ckpt_every=3)
+    assert L == pytest.approx(L0, rel=1e-12)
+    assert _close(g.cpu().numpy(), g0, 1e-10)
+    assert _close(gV.cpu().numpy(), gV0, 1e-10)
+
+
+def test_adjoint_fp32_matches_reference():
+    shape = (40, 68)
+    psi0, V, target, h = _problem(shape, 9)
+    a, s = 0.5, -1.0
+    r32 = lambda z: z.astype(np.complex64).astype(np.complex128)
+    psi0, target = r32(psi0), r32(target)
+    V = V.astype(np.float32).astype(np.float64)
+    prob = oracle.Problem(shape, h, a, s)
+    k = 0.5 * oracle.invariants(prob, psi0, V)[2]
+    n = 12
+    L0, g0, gV0 = oadj.loss_and_gradient(prob, psi0, V, target, k, n)
+    solver = nlse.Solver(torch.from_numpy(V).to(DEV).float(), h, k, a, s, prec="fp32", check_stability=False)
+    t = lambda z: torch.from_numpy(z).to(DEV).to(torch.complex64).contiguous()
+    L, g, gV = solver.adjoint(t(psi0), t(target), n, ckpt_every=5)
+    assert L == pytest.approx(L0, rel=2e-5)
+    assert _close(g.cpu().numpy(), g0, 2e-4)
+    assert _close(gV.cpu().numpy(), gV0, 2e-4)
+
+
+def test_gradient_workload_crop_reference_and_finite_differences():
+    """The gradient workload's recipe on a 64 x 64 grid (domain [-16, 16]^2):
+    the FP64 GPU gradient equals the FP64 CPU reference gradient, and central
+    differences (eps = 1e-4) of the GPU forward along random directions of
+    psi0 and V match it."""
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=1)
+    psi0, target = psis[0], targets[0]
+    prob = oracle.Problem((64, 64), h, a, s)
+    k = 0.5 * oracle.invariants(prob, psi0, V)[2]
+    n = 30
+    L0, g0, gV0 = oadj.loss_and_gradient(prob, psi0, V, target, k, n)
+    Vd = torch.from_numpy(V).to(DEV)
+    solver = nlse.Solver(Vd, h, k, a, s, prec="fp64", check_stability=False)
+    t = lambda z: torch.from_numpy(z).to(DEV).to(torch.complex128).contiguous()
+    L, g, gV = solver.adjoint(t(psi0), t(target), n, ckpt_every=10)
+    assert L == pytest.approx(L0, rel=1e-12)
+    assert _close(g.cpu().numpy(), g0, 1e-10)
+    assert _close(gV.cpu().numpy(), gV0, 1e-10)
+
+    def loss_of(p, v):
+        sv = nlse.Solver(v, h, k, a, s, prec="fp64", check_stability=False)
+        x = p.clone()
+        sv.run(x, n)
+        return float(((x - t(target)).abs() ** 2).sum())
+
+    eps = 1e-4
+    d = t(wl.random_field((64, 64), seed=77))
+    fd = (loss_of(t(psi0) + eps * d, Vd) - loss_of(t(psi0) - eps * d, Vd)) / (2 * eps)
+    ad = float(torch.real(torch.sum(torch.conj(g) * d)))
+    assert ad == pytest.approx(fd, rel=1e-6)
+    dv = torch.from_numpy(wl.random_potential((64, 64), seed=78) - 0.5).to(DEV)
+    fd = (loss_of(t(psi0), Vd + eps * dv) - loss_of(t(psi0), Vd - eps * dv)) / (2 * eps)
+    assert float((gV * dv).sum()) == pytest.approx(fd, rel=1e-6)
+
+
+def test_autograd_function_gives_the_adjoint_gradients():
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=2)
+    prob = oracle.Problem((64, 64), h, a, s)
+    k = 0.5 * oracle.invariants(prob, psis[0], V)[2]
+    Vt = torch.from_numpy(V).to(DEV).float().requires_grad_(True)
+    total = 0.0
+    refs = []
+    for p, tg in zip(psis, targets):
+        p_t = torch.from_numpy(p).to(DEV).to(torch.complex64).requires_grad_(True)
+        tg_t = torch.from_numpy(tg).to(DEV).to(torch.complex64)
+        loss = nlse.final_loss(p_t, Vt, tg_t, h, k, a, s, nsteps=20, ckpt_every=7)
+        loss.backward()
+        sv = nlse.Solver(Vt.detach().contiguous(), h, k, a, s, prec="fp32", check_stability=False)
+        L, g, gV = sv.adjoint(p_t.detach().contiguous(), tg_t, 20, 7)
+        assert float(loss) == pytest.approx(L, rel=1e-12)
+        assert torch.allclose(p_t.grad, g)
+        refs.append(gV)
+        total += L
+    assert torch.allclose(Vt.grad.double(), (refs[0] + refs[1]), rtol=1e-5, atol=1e-6 * float(refs[0].abs().max()))
