@@ -299,6 +299,11 @@ def run_ours(args):
     if not args.no_batch:
         batch = run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks)
 
+    # ---- gradient of a final-time loss (checkpointed adjoint) ----------------
+    grad = None
+    if not args.no_batch:
+        grad = run_gradient_leg(args, dev, barrier, max_over_ranks)
+
     # ---- end to end through host buffers ------------------------------------
     ke = min(args.steps, 200)
     host_in = torch.empty((N_SIDE, N_SIDE), dtype=torch.complex64, pin_memory=True)
@@ -366,6 +371,7 @@ def run_ours(args):
                            "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"},
             "fp32_vs_fp64_rel_l2": l2,
             "batched": batch,
+            "gradient": grad,
             "mass_drift": {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1},
             "energy_drift": {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1},
         }))
@@ -443,6 +449,42 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
     return out
 
 
+def run_gradient_leg(args, dev, barrier, max_over_ranks):
+    """dL/dpsi0 and dL/dV of L = sum |Psi_T - target|^2 for the gradient
+    workload: 16 initial states on a 512 x 512 grid, a = 0.5, s = -1,
+    V = harmonic + seeded 8x8 Fourier-mode perturbation, complex64 state with
+    FP64 loss and dL/dV accumulation, checkpoints every 100 steps."""
+    import torch
+
+    from paper_1109_1027_gb300 import nlse
+
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=512, batch=16)
+    Vd = torch.from_numpy(V).to(dev).float().contiguous()
+    probe = nlse.Solver(torch.from_numpy(V).to(dev), h, 1.0, a, s, prec="fp64", check_stability=False)
+    dt = 0.5 * min(probe.invariants(torch.from_numpy(p).to(dev).contiguous())[2] for p in psis)
+    probe.close()
+    solver = nlse.Solver(Vd, h, dt, a, s, prec="fp32", check_stability=False)
+    steps = args.grad_steps
+    xs = [torch.from_numpy(p).to(dev).to(torch.complex64).contiguous() for p in psis]
+    ts = [torch.from_numpy(t).to(dev).to(torch.complex64).contiguous() for t in targets]
+    solver.adjoint(xs[0], ts[0], 10, 5)          # warm-up (allocates the work space)
+    barrier()
+    t0 = time.perf_counter()
+    gV = torch.zeros_like(Vd, dtype=torch.float64)
+    losses = []
+    for x, t in zip(xs, ts):
+        loss, g_psi, g_V = solver.adjoint(x, t, steps, 100)
+        gV += g_V
+        losses.append(loss)
+    torch.cuda.synchronize()
+    el = max_over_ranks(time.perf_counter() - t0)
+    solver.close()
+    return {"workload": "16 x 512^2, a=0.5, s=-1, V = 0.01 r^2 + 8x8 Fourier modes (seed 5), Gaussian psi0/targets",
+            "steps": steps, "checkpoint_every": 100, "batch": 16, "seconds_per_batch_gradient": el,
+            "forward_equivalent_updates_per_s": 16 * 512 * 512 * steps / el,
+            "loss_sum": float(sum(losses)), "dV_norm": float(torch.linalg.vector_norm(gV))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,8 +492,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances and gradient legs")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--grad-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

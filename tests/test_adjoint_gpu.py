@@ -118,7 +118,7 @@ def test_autograd_function_gives_the_adjoint_gradients():
         loss.backward()
         sv = nlse.Solver(Vt.detach().contiguous(), h, k, a, s, prec="fp32", check_stability=False)
         L, g, gV = sv.adjoint(p_t.detach().contiguous(), tg_t, 20, 7)
-        assert float(loss) == pytest.approx(L, rel=1e-12)
+        assert loss.item() == pytest.approx(L, rel=1e-12)
         assert torch.allclose(p_t.grad, g)
         refs.append(gV)
         total += L
