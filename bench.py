@@ -139,6 +139,30 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_barrier(pg, cuda: bool):
+    """All ranks reach this point (and, on a GPU, have finished their work)."""
+    if pg is not None:
+        pg.barrier()
+    if cuda:
+        import torch
+        torch.cuda.synchronize()
+
+
+def ranks_max(pg, x: float, device="cpu") -> float:
+    """The maximum of x over all ranks (x itself on one rank)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 # -- CPU oracle (the cpu_baseline leg and the reference arm) -------------------
 
 def oracle_rate(seconds: float, side: int | None = None, steps: int | None = None):
@@ -229,18 +253,8 @@ def run_ours(args):
     k = 0.5 * dtmax
 
     stream = torch.cuda.current_stream()
-
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if pg is None:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    barrier = lambda: rank_barrier(pg, cuda=True)
+    max_over_ranks = lambda x: ranks_max(pg, x, dev)
 
     # ---- FP32 compensated fused path: the headline --------------------------
     s32 = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
@@ -257,7 +271,7 @@ def run_ours(args):
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     s32.check()
     ms_step = ms / args.steps
-    value = world * npts * args.steps / (ms * 1e-3)
+    value = job_rate(world, npts * args.steps, ms * 1e-3)
     clocks = clk.summary()
     launches = 4 * args.steps + 2
 
@@ -303,6 +317,11 @@ def run_ours(args):
     grad = None
     if not args.no_batch:
         grad = run_gradient_leg(args, dev, barrier, max_over_ranks)
+
+    # ---- the 3D and 1D workloads (context; the headline is the 2D grid) -------
+    other = None
+    if not args.no_batch:
+        other = run_other_grids(dev, barrier, max_over_ranks)
 
     # ---- end to end through host buffers ------------------------------------
     ke = min(args.steps, 200)
@@ -372,6 +391,7 @@ def run_ours(args):
             "fp32_vs_fp64_rel_l2": l2,
             "batched": batch,
             "gradient": grad,
+            "other_grids": other,
             "mass_drift": {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1},
             "energy_drift": {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1},
         }))
@@ -446,6 +466,44 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
     out["collapsed_note"] = ("focusing (s=+1) instances whose mass exceeds the 2D critical mass collapse; "
                              "with dt fixed at 0.5 dt_max(psi0) the explicit scheme then overflows (the bound "
                              "of Eq. kdfull shrinks as |psi| grows); they are excluded from the error statistics")
+    return out
+
+
+def run_other_grids(dev, barrier, max_over_ranks):
+    """Step rates of the 3D vortex ring (512^3) and the 1D bright soliton
+    (2048 points, the whole 2000-step run) in FP32 and FP64."""
+    import torch
+
+    from paper_1109_1027_gb300 import nlse
+
+    out = {}
+
+    def rate(inst, prec, steps):
+        rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+        V = torch.from_numpy(inst.V).to(dev).to(rdt).contiguous()
+        x = torch.from_numpy(inst.psi0).to(dev).to(cdt).contiguous()
+        probe = nlse.Solver(V, inst.h, 1.0, inst.a, inst.s, prec=prec, check_stability=False)
+        dtm = probe.invariants(x)[2]
+        probe.close()
+        sv = nlse.Solver(V, inst.h, 0.5 * dtm, inst.a, inst.s, prec=prec, check_stability=False)
+        sv.run(x, 3)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sv.run(x, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+        sv.close()
+        npts = int(np.prod(inst.shape))
+        bpu = BYTES_PER_UPDATE_FP32 if prec == "fp32" else BYTES_PER_UPDATE_FP64
+        return {"ms_per_step": ms, "updates_per_s": npts / (ms * 1e-3), "achieved_gbs": bpu * npts / (ms * 1e-3) / 1e9}
+
+    ring = wl.vortex_ring_3d(n=512, steps=0)
+    out["vortex_ring_3d_512"] = {"fp32": rate(ring, "fp32", 40), "fp64": rate(ring, "fp64", 8)}
+    del ring
+    sol = wl.bright_soliton_1d()
+    out["bright_soliton_1d_2048"] = {"fp32": rate(sol, "fp32", 2000), "fp64": rate(sol, "fp64", 2000)}
     return out
 
 
