@@ -37,6 +37,9 @@ cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
 bool stage_2d_tma_eligible(const StageLaunch& L);
 cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st);
+// The TMA-fed z-streaming FP32 3D kernel (stage3d_tma.cu) and when it applies.
+bool stage_3d_tma_eligible(const StageLaunch& L);
+cudaError_t launch_stage_3d_tma(const StageLaunch& L, cudaStream_t st);
 
 // One RK4 step of the paper's unfused schedule (plain.cu): D, K_tot, K_tmp
 // and Psi_tmp are full device arrays (Sec. 3.1).

@@ -1,4 +1,6 @@
-// stage3d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 3D grid.
+// stage3d.cu -- fused RK4 stage and standalone 2SHOC Laplacian on a 3D grid:
+// the generic kernel (FP64, and FP32 grids whose rows TMA cannot address);
+// the TMA-fed FP32 kernel is in stage3d_tma.cu.
 //
 // One CTA owns a TX x TY column of the grid over TZ consecutive z planes and
 // streams through them (2.5D blocking): shared memory holds a ring of four
@@ -162,6 +164,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 }  // namespace
 
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st) {
+    if (stage_3d_tma_eligible(L)) return launch_stage_3d_tma(L, st);
     const bool cd = L.lap == 1;
     if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
     return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);

@@ -57,7 +57,9 @@ SHAPES = {
     # widths divisible by 4 run the TMA-fed streaming kernel (ragged CTA
     # tails in x and y included); the others the generic tile kernel
     2: [(3, 3), (17, 70), (40, 131), (67, 200), (45, 260), (100, 388), (33, 4), (70, 128)],
-    3: [(3, 3, 3), (9, 20, 37), (35, 18, 40), (70, 33, 19)],
+    # widths divisible by 4 run the TMA-fed FP32 kernel (ragged tiles in x, y
+    # and z, z spanning two 64-plane chunks); the others the generic kernel
+    3: [(3, 3, 3), (9, 20, 37), (35, 18, 40), (70, 33, 19), (70, 40, 100), (5, 17, 64)],
 }
 CASES = [(shape, prec, lap) for d in (1, 2, 3) for shape in SHAPES[d]
          for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
