@@ -183,12 +183,17 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                           add2(iplane(j - 1)[hk], iplane(j + 1)[hk]));
         return dval(o, b, ((int64_t)z * ny + hy) * nx + hx, pc[hk], s6);
     };
-    // D of this thread's pair at input plane j (grid plane z), centre values
-    // cc, vertical neighbours cm / cp.
-    auto pair_d = [&](int j, int z, Two cm, Two cc, Two cp) -> Two {
+    // In-plane axial neighbours of this thread's pair in input plane j.
+    struct Nbr { Two up, dn; C l, r; };
+    auto nbrs = [&](int j) -> Nbr {
         const C* pc = iplane(j);
-        const Two up = ld2(pc + k - PW), dn = ld2(pc + k + PW);
-        const C l = pc[k - 1], r = pc[k + 2];
+        return {ld2(pc + k - PW), ld2(pc + k + PW), pc[k - 1], pc[k + 2]};
+    };
+    // D of this thread's pair at input plane j (grid plane z), centre values
+    // cc, vertical neighbours cm / cp, in-plane neighbours nb.
+    auto pair_d = [&](const Nbr& nb, int z, Two cm, Two cc, Two cp) -> Two {
+        const Two up = nb.up, dn = nb.dn;
+        const C l = nb.l, r = nb.r;
         const bool zo = zout(z), zb = zbnd(z);
         const int64_t gp = ((int64_t)z * ny + y) * nx + xa;
         Two d;
@@ -206,8 +211,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     if (alive) {
         const Two cmm = ld2(iplane(0) + k);
         cm = ld2(iplane(1) + k); c0 = ld2(iplane(2) + k); c1 = ld2(iplane(3) + k);
-        dm = pair_d(1, zbase - dir, cmm, cm, c0);
-        d0 = pair_d(2, zbase, cm, c0, c1);
+        dm = pair_d(nbrs(1), zbase - dir, cmm, cm, c0);
+        d0 = pair_d(nbrs(2), zbase, cm, c0, c1);
         st2(dring + k, d0);                       // input plane 2 -> D ring plane 0
         if (hk >= 0) dring[hk] = halo_d(2, zbase);
     }
@@ -227,7 +232,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         }
         // D of the plane ahead (za).
         const Two c2 = ld2(iplane(j + 2) + k);
-        const Two d1 = pair_d(j + 1, za, c0, c1, c2);
+        const Nbr np = nbrs(j + 1);              // also the z+1 edge terms of Lap(z)
+        const Two d1 = pair_d(np, za, c0, c1, c2);
         C* dn = dring + ((j + 1) & 1) * (PW * PH);
         st2(dn + k, d1);
         if (hk >= 0) dn[hk] = halo_d(j + 1, za);
@@ -237,7 +243,6 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         if (pin) {
             const C* pz = iplane(j);
             const C* pzm = iplane(j - 1);
-            const C* pzp = iplane(j + 1);
             const C* dz = dring + (j & 1) * (PW * PH);
             const bool zb = zbnd(z);
             const bool bA = ba || zb, bB = bb || zb;
@@ -251,8 +256,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                 const Two pu = ld2(pz + k - PW), pd = ld2(pz + k + PW);
                 const C pul = pz[k - PW - 1], pur = pz[k - PW + 2], pdl = pz[k + PW - 1], pdr = pz[k + PW + 2];
                 const Two upm = ld2(pzm + k - PW), dnm = ld2(pzm + k + PW);
-                const Two upp = ld2(pzp + k - PW), dnp = ld2(pzp + k + PW);
-                const C lm = pzm[k - 1], rm = pzm[k + 2], lp = pzp[k - 1], rp = pzp[k + 2];
+                const Two upp = np.up, dnp = np.dn;
+                const C lm = pzm[k - 1], rm = pzm[k + 2], lp = np.l, rp = np.r;
                 const C ea = add2(add2(add2(pul, pu.b), add2(pdl, pd.b)),
                                   add2(add2(add2(lm, cm.b), add2(lp, c1.b)), add2(add2(upm.a, dnm.a), add2(upp.a, dnp.a))));
                 const C eb = add2(add2(add2(pu.a, pur), add2(pd.a, pdr)),

@@ -1,0 +1,61 @@
+"""A small, fixed run of one workload for profilers (ncu): builds the inputs,
+takes a few warm-up steps, then a few more, and exits.
+
+    python -m paper_1109_1027_gb300.profile_case --workload vortex2d --n 2048 --steps 3
+    python -m paper_1109_1027_gb300.profile_case --workload ring3d --n 256 --steps 3
+
+Workloads: vortex2d (2D dark vortex), ring3d (3D vortex ring), soliton1d
+(1D bright soliton), batch2d (512 uneven 2D instances).  FP32 unless --fp64.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import nlse
+from . import workloads as wl
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="vortex2d", choices=["vortex2d", "ring3d", "soliton1d", "batch2d"])
+    ap.add_argument("--n", type=int, default=0, help="points per axis (default: the workload's)")
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64", action="store_true")
+    args = ap.parse_args()
+    prec = "fp64" if args.fp64 else "fp32"
+    rdt, cdt = (torch.float64, torch.complex128) if args.fp64 else (torch.float32, torch.complex64)
+    dev = "cuda:0"
+    if args.workload == "batch2d":
+        insts = wl.gaussian_batch_2d(count=512, steps=0)
+        V = nlse.BatchSolver.pack([q.V for q in insts], rdt, dev)
+        x = nlse.BatchSolver.pack([q.psi0 for q in insts], cdt, dev)
+        shapes = [q.shape for q in insts]
+        probe = nlse.BatchSolver(V, shapes, [q.h for q in insts], 1.0, [q.a for q in insts],
+                                 [q.s for q in insts], prec=prec, check_stability=False)
+        dts = [0.5 * d for d in probe.invariants(x)[2]]
+        probe.close()
+        solver = nlse.BatchSolver(V, shapes, [q.h for q in insts], dts, [q.a for q in insts],
+                                  [q.s for q in insts], prec=prec, check_stability=False)
+    else:
+        make = {"vortex2d": wl.dark_vortex_2d, "ring3d": wl.vortex_ring_3d, "soliton1d": wl.bright_soliton_1d}
+        inst = make[args.workload](n=args.n, steps=0) if args.n else make[args.workload](steps=0)
+        V = torch.from_numpy(inst.V).to(dev).to(rdt).contiguous()
+        x = torch.from_numpy(inst.psi0).to(dev).to(cdt).contiguous()
+        probe = nlse.Solver(V, inst.h, 1.0, inst.a, inst.s, prec=prec, check_stability=False)
+        dt = 0.5 * probe.invariants(x)[2]
+        probe.close()
+        solver = nlse.Solver(V, inst.h, dt, inst.a, inst.s, prec=prec, check_stability=False)
+    for _ in range(args.warmup):
+        solver.rk4_step(x)
+    for _ in range(args.steps):
+        solver.rk4_step(x)
+    torch.cuda.synchronize()
+    solver.check()
+    print("profile_case: ok")
+
+
+if __name__ == "__main__":
+    main()
