@@ -299,6 +299,46 @@ def test_dark_vortex_2d_full_size_sampled(prec):
         assert abs(got[yy, xx] - ref) <= tol, (yy, xx, got[yy, xx], ref)
 
 
+def _crop_one_step_3d(psi, V, inst, k, z, y, x, r=10):
+    """Oracle value of one RK4 step at (z, y, x) from a window of half-width
+    r >= 9 (the step's result depends on the state within 8 points)."""
+    nz, ny, nx = psi.shape
+    sl = tuple(slice(max(0, c - r), min(n, c + r + 1)) for c, n in ((z, nz), (y, ny), (x, nx)))
+    sub = psi[sl]
+    out = oracle.run(oracle.Problem(sub.shape, inst.h, inst.a, inst.s), sub, V[sl], k, 1)
+    return out[z - sl[0].start, y - sl[1].start, x - sl[2].start]
+
+
+def test_vortex_ring_3d_full_size_sampled():
+    """The 512^3 vortex ring in FP32 (the TMA-fed kernel, the benchmark's
+    launch configuration): one RK4 step through nlse_run, checked at sampled
+    points (corners, faces, the ring core, random points) against the oracle
+    on windows."""
+    inst = wl.vortex_ring_3d()
+    psi_r = inst.psi0.astype(np.complex64).astype(np.complex128)
+    V_r = inst.V.astype(np.float32).astype(np.float64)
+    Vd = torch.from_numpy(inst.V).to(DEV).float().contiguous()
+    x = torch.from_numpy(inst.psi0).to(DEV).to(torch.complex64).contiguous()
+    probe = nlse.Solver(Vd, inst.h, 1.0, inst.a, inst.s, prec="fp32", check_stability=False)
+    k = 0.5 * probe.invariants(x)[2]
+    probe.close()
+    solver = nlse.Solver(Vd, inst.h, k, inst.a, inst.s, prec="fp32", check_stability=False)
+    solver.run(x, 1)
+    n = inst.shape[0]
+    cx, cy = inst.meta["centre"]
+    ring = int(round((cx + 8.0 + 30.0) / inst.h)), int(round((cy + 30.0) / inst.h))
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n // 2, 5), (n // 2, 0, n // 2), (n // 2, n // 2, n - 1),
+           (1, 1, 1), (n // 2, ring[1], ring[0]), (n // 2 + 1, ring[1], ring[0] + 1), (63, 64, 31), (64, 63, 32),
+           (255, 256, 257)]
+    rng = np.random.Generator(np.random.PCG64(303))
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(20)]
+    got = {p: complex(x[p].item()) for p in pts}
+    tol = 1e-6 * np.abs(psi_r).max()
+    for p in pts:
+        ref = _crop_one_step_3d(psi_r, V_r, inst, k, *p)
+        assert abs(got[p] - ref) <= tol, (p, got[p], ref)
+
+
 # -- the paper's accuracy experiments on the GPU -------------------------------
 
 TABLES = pe.read_tables(pe.__file__.replace("paper_experiments.py", "golden/paper_tables.txt"))
