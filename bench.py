@@ -257,8 +257,10 @@ def run_ours(args):
     max_over_ranks = lambda x: ranks_max(pg, x, dev)
 
     # ---- FP32 compensated fused path: the headline --------------------------
+    from paper_1109_1027_gb300 import autotune
     s32 = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
     x32 = psi0.to(torch.complex64).contiguous()
+    tuning = autotune.tune(s32, x32, use_cache=False)
     s32.run(x32, args.warmup)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -270,6 +272,7 @@ def run_ours(args):
     barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     s32.check()
+    s32_rows = s32.get_tiling(nlse.TILE_ROWS)
     ms_step = ms / args.steps
     value = job_rate(world, npts * args.steps, ms * 1e-3)
     clocks = clk.summary()
@@ -373,7 +376,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": [N_SIDE, N_SIDE], "dt": k, "precision":
                        "complex64 state + compensated low part, FP64 invariants",
                        "l2_cache": "working set 176 MiB (Psi, lo, 2 stage buffers, acc, V) > 126 MiB L2; no flush",
-                       "parallelism": f"{world} independent replica(s)"},
+                       "parallelism": f"{world} independent replica(s)",
+                       "tiling": {"rows_per_cta": s32_rows, "chosen_by": "autotune (timed on this problem)",
+                                  "ms_per_step": {str(k_): v["ms_per_step"] for k_, v in tuning.items()}}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
@@ -430,6 +435,11 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
         V = V64.to(rdt).contiguous()
         x = psi64.to(cdt).contiguous()
         bs = nlse.BatchSolver(V, shapes, hs, dts, as_, ss, prec=prec)
+        if prec == "fp32":
+            from paper_1109_1027_gb300 import autotune
+            out["tiling"] = {"narrow_tile_width_bound": None,
+                             "ms_per_step": autotune.tune(bs, x, steps=3, use_cache=False)}
+            out["tiling"]["narrow_tile_width_bound"] = bs.get_tiling(nlse.TILE_BATCH_NARROW)
         bs.run(x, 3)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -486,6 +496,8 @@ def run_other_grids(dev, barrier, max_over_ranks):
         dtm = probe.invariants(x)[2]
         probe.close()
         sv = nlse.Solver(V, inst.h, 0.5 * dtm, inst.a, inst.s, prec=prec, check_stability=False)
+        from paper_1109_1027_gb300 import autotune
+        autotune.tune(sv, x, steps=4, use_cache=False)
         sv.run(x, 3)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -204,6 +204,19 @@ int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const voi
 int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
                  int64_t ckpt_every, void* dpsi0_dev, void* dV_dev, double* loss, void* stream);
 
+/* Tiling of the streaming kernels (the paper has no counterpart: these are
+ * launch-shape choices that leave the arithmetic unchanged; results are bit
+ * for bit the same).  Set per context, typically by an autotuner that times
+ * the candidates on the actual problem.  Setting a key drops the context's
+ * captured time-loop graph; NLSE_TILE_BATCH_NARROW also rebuilds the batch
+ * work list (synchronising the device). */
+#define NLSE_TILE_ROWS 1          /* 2D: rows per CTA, 8, 16 (default) or 32            */
+#define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32, 64 (default) or 128 */
+#define NLSE_TILE_BATCH_NARROW 3  /* batch: instances with n[0] <= value get 64-column
+                                     tiles, the others 256-column tiles (default 64)    */
+int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
+int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
+
 /* Human-readable description of the calling thread's last error ("" if none). */
 const char* nlse_last_error(void);
 

@@ -71,6 +71,8 @@ struct nlse_ctx {
     // Adjoint work space (nlse_adjoint), allocated on first use.
     void* adj_buf;
     size_t adj_bytes;
+    // Tiling choices (nlse_set_tiling); 0 = the default.
+    int tile_rows, tile_planes;
 };
 
 namespace {
@@ -110,7 +112,16 @@ StageLaunch base_launch(const nlse_ctx* c) {
     L.h = c->p.h; L.a = c->p.a; L.s = c->p.s; L.dt = c->p.dt;
     L.V = c->V;
     L.flag = c->flag;
+    L.tile_rows = c->tile_rows ? c->tile_rows : 16;
+    L.tile_planes = c->tile_planes ? c->tile_planes : 64;
     return L;
+}
+
+// Drops the captured time-loop graph (its launches bake in the tiling).
+void drop_graph(nlse_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_psi = nullptr;
 }
 
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
@@ -540,6 +551,47 @@ int nlse_invariants_batch(nlse_ctx* c, const void* psi, double* mass, double* en
 }
 
 int nlse_batch_count(const nlse_ctx* c) { return c ? c->count : 0; }
+
+int nlse_set_tiling(nlse_ctx* c, int key, int value) {
+    g_err[0] = 0;
+    if (!c) return fail(NLSE_EINVAL, "NULL context");
+    switch (key) {
+        case NLSE_TILE_ROWS:
+            if (value != 8 && value != 16 && value != 32) return fail(NLSE_EINVAL, "rows per CTA: 8, 16 or 32");
+            c->tile_rows = value;
+            break;
+        case NLSE_TILE_PLANES:
+            if (value != 32 && value != 64 && value != 128) return fail(NLSE_EINVAL, "planes per CTA: 32, 64 or 128");
+            c->tile_planes = value;
+            break;
+        case NLSE_TILE_BATCH_NARROW: {
+            if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
+            if (value < 0) return fail(NLSE_EINVAL, "the narrow-tile width bound must be >= 0");
+            cudaError_t e = nlse::batch2d_retile(c->batch, value);
+            if (e != cudaSuccess) return cuda_fail(e, "rebuilding the batch tiles");
+            c->maps_psi = nullptr;                       // re-encode the maps for the new box widths
+            break;
+        }
+        default:
+            return fail(NLSE_EINVAL, "unknown tiling key %d", key);
+    }
+    drop_graph(c);
+    return NLSE_OK;
+}
+
+int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
+    g_err[0] = 0;
+    if (!c || !value) return fail(NLSE_EINVAL, "NULL argument");
+    switch (key) {
+        case NLSE_TILE_ROWS: *value = c->tile_rows ? c->tile_rows : 16; return NLSE_OK;
+        case NLSE_TILE_PLANES: *value = c->tile_planes ? c->tile_planes : 64; return NLSE_OK;
+        case NLSE_TILE_BATCH_NARROW:
+            if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
+            *value = nlse::batch2d_narrow(c->batch);
+            return NLSE_OK;
+    }
+    return fail(NLSE_EINVAL, "unknown tiling key %d", key);
+}
 
 int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     g_err[0] = 0;

@@ -125,6 +125,7 @@ struct BatchPlan {
     int4* tiles = nullptr;                    // device work lists, group 0 then group 1
     int ntiles[2] = {0, 0};
     int nt[2] = {32, 128};
+    int narrow = 64;
     const void* bases[6] = {};                // psi, Y0, Y1, acc, lo, V
 };
 
@@ -133,6 +134,48 @@ bool batch2d_instance_ok(const nlse_params& p) {
 }
 
 int64_t batch2d_points(const nlse_params& p) { return p.n[0] * p.n[1]; }
+
+// Tile lists: instances with n[0] <= narrow get 64-column tiles (one warp),
+// the rest 256-column tiles; largest instances first.
+cudaError_t build_tiles(BatchPlan* b, int narrow) {
+    std::vector<int> order(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        order[i] = i;
+        b->host[i].nt = b->host[i].nx <= narrow ? 32 : 128;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (int64_t)b->host[x].nx * b->host[x].ny > (int64_t)b->host[y].nx * b->host[y].ny;
+    });
+    std::vector<int4> lists[2];
+    for (int i : order) {
+        const BatchDesc& d = b->host[i];
+        const int g = d.nt == 32 ? 0 : 1;
+        const int txc = 2 * d.nt;
+        for (int y0 = 0; y0 < d.ny; y0 += TYB)
+            for (int x0 = 0; x0 < d.nx; x0 += txc) lists[g].push_back(make_int4(i, x0, y0, 0));
+    }
+    const size_t total = lists[0].size() + lists[1].size();
+    cudaFree(b->tiles);
+    b->tiles = nullptr;
+    cudaError_t e = cudaMalloc((void**)&b->tiles, sizeof(int4) * (total ? total : 1));
+    if (e != cudaSuccess) return e;
+    for (int g = 0; g < 2; ++g) b->ntiles[g] = (int)lists[g].size();
+    if (!lists[0].empty())
+        e = cudaMemcpy(b->tiles, lists[0].data(), sizeof(int4) * lists[0].size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !lists[1].empty())
+        e = cudaMemcpy(b->tiles + lists[0].size(), lists[1].data(), sizeof(int4) * lists[1].size(),
+                       cudaMemcpyHostToDevice);
+    b->narrow = narrow;
+    return e;
+}
+
+cudaError_t batch2d_retile(BatchPlan* b, int narrow) {
+    cudaError_t e = cudaDeviceSynchronize();          // no launch may still read the old lists
+    if (e != cudaSuccess) return e;
+    return build_tiles(b, narrow);                     // the maps are re-encoded at the next bind
+}
+
+int batch2d_narrow(const BatchPlan* b) { return b->narrow; }
 
 cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
                            void* lo, BatchPlan** out) {
@@ -149,8 +192,7 @@ cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void*
     if (e != cudaSuccess) { batch2d_destroy(b); return e; }
     std::memset(b->host, 0, sizeof(BatchDesc) * count);
 
-    // Offsets, scalars and tile groups.  Grids up to 64 columns wide get
-    // 64-column tiles (one warp), the rest 256-column tiles.
+    // Offsets and scalars.
     std::vector<int64_t> off(count);
     int64_t acc_off = 0;
     for (int i = 0; i < count; ++i) {
@@ -160,7 +202,6 @@ cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void*
         d.off = off[i];
         d.nx = (int)p[i].n[0];
         d.ny = (int)p[i].n[1];
-        d.nt = d.nx <= 64 ? 32 : 128;
         const double h = p[i].h, k = p[i].dt;
         d.inv_h2 = 1.0 / (h * h);
         d.inv_6h2 = 1.0 / (6.0 * h * h);
@@ -169,28 +210,7 @@ cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void*
         const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};
         for (int s = 0; s < 5; ++s) { d.c_acc[s] = wa[s]; d.c_y[s] = wy[s]; }
     }
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return batch2d_points(p[x]) > batch2d_points(p[y]);
-    });
-    std::vector<int4> lists[2];
-    for (int i : order) {
-        const BatchDesc& d = b->host[i];
-        const int g = d.nt == 32 ? 0 : 1;
-        const int txc = 2 * d.nt;
-        for (int y0 = 0; y0 < d.ny; y0 += TYB)
-            for (int x0 = 0; x0 < d.nx; x0 += txc) lists[g].push_back(make_int4(i, x0, y0, 0));
-    }
-    const size_t total = lists[0].size() + lists[1].size();
-    e = cudaMalloc((void**)&b->tiles, sizeof(int4) * (total ? total : 1));
-    if (e != cudaSuccess) { batch2d_destroy(b); return e; }
-    for (int g = 0; g < 2; ++g) b->ntiles[g] = (int)lists[g].size();
-    if (!lists[0].empty())
-        e = cudaMemcpy(b->tiles, lists[0].data(), sizeof(int4) * lists[0].size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !lists[1].empty())
-        e = cudaMemcpy(b->tiles + lists[0].size(), lists[1].data(), sizeof(int4) * lists[1].size(),
-                       cudaMemcpyHostToDevice);
+    e = build_tiles(b, 64);
     if (e != cudaSuccess) { batch2d_destroy(b); return e; }
     *out = b;
     return cudaSuccess;
@@ -204,7 +224,7 @@ cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     b->bases[0] = psi;
-    for (int i = 0; i < b->count; ++i) {
+    for (int i = 0; i < b->count; ++i) {   // box widths follow the instance's tile group
         BatchDesc& d = b->host[i];
         const bool ok = b->prec == 0 ? encode_instance<float>(d, b->bases, d.off, d.nx, d.ny, d.nt)
                                      : encode_instance<double>(d, b->bases, d.off, d.nx, d.ny, d.nt);

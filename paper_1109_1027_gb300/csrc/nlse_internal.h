@@ -29,17 +29,27 @@ struct StageLaunch {
     const void* V;
     int* flag;              // status bits: 1 = non-finite result (stage 4),
                             // 2 = a bounded device-side wait timed out
+    int tile_rows;          // 2D TMA kernel: rows per CTA (8, 16, 32)
+    int tile_planes;        // 3D TMA kernel: z planes per CTA (32, 64, 128)
 };
 
 cudaError_t launch_stage_1d(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
-// The TMA-fed y-streaming 2D kernel (stage2d_tma.cu) and when it applies.
+// The TMA-fed y-streaming 2D kernel (stage2d_tma.cuh) and when it applies;
+// one entry per compiled rows-per-CTA variant.
 bool stage_2d_tma_eligible(const StageLaunch& L);
 cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_2d_tma_rows8(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_2d_tma_rows16(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_2d_tma_rows32(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st);
-// The TMA-fed z-streaming FP32 3D kernel (stage3d_tma.cu) and when it applies.
+// The TMA-fed z-streaming FP32 3D kernel (stage3d_tma.cuh) and when it
+// applies; one entry per compiled planes-per-CTA variant.
 bool stage_3d_tma_eligible(const StageLaunch& L);
 cudaError_t launch_stage_3d_tma(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_3d_tma_planes32(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_3d_tma_planes64(const StageLaunch& L, cudaStream_t st);
+cudaError_t launch_stage_3d_tma_planes128(const StageLaunch& L, cudaStream_t st);
 
 // One RK4 step of the paper's unfused schedule (plain.cu): D, K_tot, K_tmp
 // and Psi_tmp are full device arrays (Sec. 3.1).
@@ -63,6 +73,8 @@ bool batch2d_instance_ok(const nlse_params& p);
 cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
                            void* lo, BatchPlan** out);
 cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st);
+cudaError_t batch2d_retile(BatchPlan* b, int narrow);   // synchronises the device
+int batch2d_narrow(const BatchPlan* b);
 cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st);
 void batch2d_destroy(BatchPlan* b);
 

@@ -12,6 +12,7 @@
 // followed by F (Sec. 3.1), the Dirichlet rule F_b = 0 (Eq. dbc_ut) and the
 // stage epilogue.  D lives only in shared memory.
 #include "nlse_device.cuh"
+#include "tmap.cuh"
 
 namespace nlse {
 namespace {
@@ -124,6 +125,27 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace
+
+// TMA needs 16-byte aligned bases and row pitches: nx a multiple of 4
+// (complex64 rows and float V rows) or of 2 (complex128 rows, double V).
+// The column pairs also need nx even.
+bool stage_2d_tma_eligible(const StageLaunch& L) {
+    if (L.bc != 0) return false;
+    const int64_t nx = L.n[0];
+    if (nx % (L.prec == 0 ? 4 : 2) != 0) return false;
+    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
+    for (const void* p : ptrs)
+        if ((uintptr_t)p % 16) return false;
+    return encoder() != nullptr;
+}
+
+cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st) {
+    switch (L.tile_rows) {
+        case 8: return launch_stage_2d_tma_rows8(L, st);
+        case 32: return launch_stage_2d_tma_rows32(L, st);
+        default: return launch_stage_2d_tma_rows16(L, st);
+    }
+}
 
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st) {
     if (stage_2d_tma_eligible(L)) return launch_stage_2d_tma(L, st);

@@ -1,20 +1,23 @@
-// stage2d_tma.cu -- the fused 2D RK4 stage (and standalone 2SHOC Laplacian)
+// stage2d_tma.cuh -- the fused 2D RK4 stage (and standalone 2SHOC Laplacian)
 // on one grid: a grid of CTAs, each running the TMA-fed y-streaming walk of
-// stage2d_tile.cuh over TXC = 256 columns and TY = 16 rows (a 2048 x 2048
-// grid is then one wave of 1024 CTAs on 152 SMs at 7 CTAs per SM).
+// stage2d_tile.cuh over TXC = 256 columns and TY rows.  TY is a tiling
+// choice (8, 16 or 32; 16 by default: a 2048 x 2048 grid is then one wave of
+// 1024 CTAs on 152 SMs at 7 CTAs per SM); each TY is instantiated in its own
+// translation unit (stage2d_tma_r{8,16,32}.cu).
+#pragma once
+
 #include "stage2d_tile.cuh"
 #include "tmap.cuh"
 
 namespace nlse {
-namespace {
+namespace tma2d {
 
 constexpr int NT = 128;              // threads per CTA
 constexpr int TXC = 2 * NT;          // columns per CTA
 constexpr int HB = TXC;              // first input TMA box; the second is 4 points
 constexpr int HB2 = 4;
-constexpr int TY = 16;               // rows per CTA
 
-template <typename R, bool CD, int STAGE>
+template <typename R, bool CD, int STAGE, int TY>
 __global__ void __launch_bounds__(NT)
 stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_in2,
                    const __grid_constant__ CUtensorMap m_V,
@@ -27,7 +30,7 @@ stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
 
 // ---- host side -------------------------------------------------------------
 
-template <typename R, bool CD, int STAGE>
+template <typename R, bool CD, int STAGE, int TY>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     using tile2d::Lay;
     const int nx = (int)L.n[0], ny = (int)L.n[1];
@@ -41,7 +44,7 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
             return cudaErrorInvalidValue;
     }
     if (STAGE == 4 && sizeof(R) == 4 && !complex_map<R>(&m_lo, L.lo, nx, ny, TXC)) return cudaErrorInvalidValue;
-    auto kern = stage2d_tma_kernel<R, CD, STAGE>;
+    auto kern = stage2d_tma_kernel<R, CD, STAGE, TY>;
     const int smem = Lay<R, NT>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -56,37 +59,24 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename R, bool CD>
+template <typename R, bool CD, int TY>
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     switch (L.stage) {
-        case 0: return launch_t<R, CD, 0>(L, st);
-        case 1: return launch_t<R, CD, 1>(L, st);
-        case 2: return launch_t<R, CD, 2>(L, st);
-        case 3: return launch_t<R, CD, 3>(L, st);
-        case 4: return launch_t<R, CD, 4>(L, st);
+        case 0: return launch_t<R, CD, 0, TY>(L, st);
+        case 1: return launch_t<R, CD, 1, TY>(L, st);
+        case 2: return launch_t<R, CD, 2, TY>(L, st);
+        case 3: return launch_t<R, CD, 3, TY>(L, st);
+        case 4: return launch_t<R, CD, 4, TY>(L, st);
     }
     return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-// TMA needs 16-byte aligned bases and row pitches: nx a multiple of 4
-// (complex64 rows and float V rows) or of 2 (complex128 rows, double V).
-// The column pairs also need nx even.
-bool stage_2d_tma_eligible(const StageLaunch& L) {
-    if (L.bc != 0) return false;
-    const int64_t nx = L.n[0];
-    if (nx % (L.prec == 0 ? 4 : 2) != 0) return false;
-    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
-    for (const void* p : ptrs)
-        if ((uintptr_t)p % 16) return false;
-    return encoder() != nullptr;
-}
-
-cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st) {
+template <int TY>
+cudaError_t launch_rows(const StageLaunch& L, cudaStream_t st) {
     const bool cd = L.lap == 1;
-    if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
-    return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);
+    if (L.prec == 0) return cd ? launch_stage<float, true, TY>(L, st) : launch_stage<float, false, TY>(L, st);
+    return cd ? launch_stage<double, true, TY>(L, st) : launch_stage<double, false, TY>(L, st);
 }
 
+}  // namespace tma2d
 }  // namespace nlse

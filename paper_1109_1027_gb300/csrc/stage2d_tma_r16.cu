@@ -1,0 +1,10 @@
+// stage2d_tma_r16.cu -- the TMA-fed 2D stage kernels with 16 rows per CTA.
+#include "stage2d_tma.cuh"
+
+namespace nlse {
+
+cudaError_t launch_stage_2d_tma_rows16(const StageLaunch& L, cudaStream_t st) {
+    return tma2d::launch_rows<16>(L, st);
+}
+
+}  // namespace nlse

@@ -15,6 +15,7 @@
 // Each input plane is read once per CTA, so the halo overhead is only the xy
 // ring plus four planes per TZ.
 #include "nlse_device.cuh"
+#include "tmap.cuh"
 
 namespace nlse {
 namespace {
@@ -162,6 +163,24 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace
+
+// FP32 Dirichlet grids whose rows TMA can address (nx a multiple of 4) and
+// 16-byte aligned buffers; other 3D grids use the generic kernel.
+bool stage_3d_tma_eligible(const StageLaunch& L) {
+    if (L.prec != 0 || L.bc != 0 || L.n[0] % 4 != 0) return false;
+    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
+    for (const void* p : ptrs)
+        if ((uintptr_t)p % 16) return false;
+    return encoder() != nullptr;
+}
+
+cudaError_t launch_stage_3d_tma(const StageLaunch& L, cudaStream_t st) {
+    switch (L.tile_planes) {
+        case 32: return launch_stage_3d_tma_planes32(L, st);
+        case 128: return launch_stage_3d_tma_planes128(L, st);
+        default: return launch_stage_3d_tma_planes64(L, st);
+    }
+}
 
 cudaError_t launch_stage_3d(const StageLaunch& L, cudaStream_t st) {
     if (stage_3d_tma_eligible(L)) return launch_stage_3d_tma(L, st);

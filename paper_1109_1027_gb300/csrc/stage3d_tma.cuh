@@ -1,8 +1,10 @@
-// stage3d_tma.cu -- the fused 3D RK4 stage (and standalone 2SHOC Laplacian) in
+// stage3d_tma.cuh -- the fused 3D RK4 stage (and standalone 2SHOC Laplacian) in
 // FP32 as a z-streaming kernel fed by the tensor memory accelerator.
 //
 // One CTA of 256 threads owns a TX x TY = 32 x 16 column of the grid (two
-// x-adjacent points per thread) and walks TZ planes along z.  Two rings of
+// x-adjacent points per thread) and walks TZ planes along z (TZ a tiling
+// choice, 32, 64 or 128; each in its own translation unit
+// stage3d_tma_z{32,64,128}.cu).  Two rings of
 // shared-memory plane slots are filled by TMA tile loads, each completing on
 // its own mbarrier:
 //   * the input ring (S slots): the stage-input plane with a 2-point xy halo
@@ -23,14 +25,16 @@
 // planes the previous one wrote last.  Every mbarrier wait is bounded (1 s);
 // on timeout the CTA sets bit 2 of the status flag, lets its copies land and
 // returns.
+#pragma once
+
 #include "nlse_device.cuh"
 #include "tma.cuh"
 #include "tmap.cuh"
 
 namespace nlse {
-namespace {
+namespace tma3d {
 
-constexpr int TX = 32, TY = 16, TZ = 64;
+constexpr int TX = 32, TY = 16;
 constexpr int TXP = TX / 2;                  // thread columns (pairs)
 constexpr int NT = TXP * TY;                 // 256 threads
 constexpr int PW = TX + 4, PH = TY + 4;      // input plane with a 2-point halo (36 x 20)
@@ -67,7 +71,7 @@ __device__ __forceinline__ void st2(float2* p, Two v) {
     *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
 
-template <bool CD, int STAGE>
+template <bool CD, int STAGE, int TZ>
 __global__ void __launch_bounds__(NT, 3)      // three CTAs per SM (shared memory allows three)
 stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_V,
                    const __grid_constant__ CUtensorMap m_psi, const __grid_constant__ CUtensorMap m_acc,
@@ -324,7 +328,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
 }
 
 // 3D boxes over a complex64 (8-byte elements) or float grid.
-bool map3(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const void* base, int nx, int ny, int nz,
+inline bool map3(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const void* base, int nx, int ny, int nz,
           int bx, int by) {
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     cuuint64_t strides[2] = {(cuuint64_t)nx * esize, (cuuint64_t)nx * ny * esize};
@@ -332,7 +336,7 @@ bool map3(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const void* ba
     return encode(m, type, 3, base, dims, strides, box);
 }
 
-template <bool CD, int STAGE>
+template <bool CD, int STAGE, int TZ>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
     const CUtensorMapDataType CX = CU_TENSOR_MAP_DATA_TYPE_UINT64, RF = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -344,7 +348,7 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
                        !map3(&m_acc, CX, 8, L.acc, nx, ny, nz, TX, TY)))
         return cudaErrorInvalidValue;
     if (STAGE == 4 && !map3(&m_lo, CX, 8, L.lo, nx, ny, nz, TX, TY)) return cudaErrorInvalidValue;
-    auto kern = stage3d_tma_kernel<CD, STAGE>;
+    auto kern = stage3d_tma_kernel<CD, STAGE, TZ>;
     const int smem = Lay3::TOTAL;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -356,32 +360,22 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <bool CD>
+template <bool CD, int TZ>
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     switch (L.stage) {
-        case 0: return launch_t<CD, 0>(L, st);
-        case 1: return launch_t<CD, 1>(L, st);
-        case 2: return launch_t<CD, 2>(L, st);
-        case 3: return launch_t<CD, 3>(L, st);
-        case 4: return launch_t<CD, 4>(L, st);
+        case 0: return launch_t<CD, 0, TZ>(L, st);
+        case 1: return launch_t<CD, 1, TZ>(L, st);
+        case 2: return launch_t<CD, 2, TZ>(L, st);
+        case 3: return launch_t<CD, 3, TZ>(L, st);
+        case 4: return launch_t<CD, 4, TZ>(L, st);
     }
     return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-// FP32 Dirichlet grids whose rows TMA can address (nx a multiple of 4) and
-// 16-byte aligned buffers; other 3D grids use the generic kernel.
-bool stage_3d_tma_eligible(const StageLaunch& L) {
-    if (L.prec != 0 || L.bc != 0 || L.n[0] % 4 != 0) return false;
-    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
-    for (const void* p : ptrs)
-        if ((uintptr_t)p % 16) return false;
-    return encoder() != nullptr;
+template <int TZ>
+cudaError_t launch_planes(const StageLaunch& L, cudaStream_t st) {
+    return L.lap == 1 ? launch_stage<true, TZ>(L, st) : launch_stage<false, TZ>(L, st);
 }
 
-cudaError_t launch_stage_3d_tma(const StageLaunch& L, cudaStream_t st) {
-    return L.lap == 1 ? launch_stage<true>(L, st) : launch_stage<false>(L, st);
-}
-
+}  // namespace tma3d
 }  // namespace nlse

@@ -1,0 +1,10 @@
+// stage3d_tma_z64.cu -- the TMA-fed FP32 3D stage kernels with 64 z planes per CTA.
+#include "stage3d_tma.cuh"
+
+namespace nlse {
+
+cudaError_t launch_stage_3d_tma_planes64(const StageLaunch& L, cudaStream_t st) {
+    return tma3d::launch_planes<64>(L, st);
+}
+
+}  // namespace nlse

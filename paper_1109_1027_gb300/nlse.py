@@ -26,6 +26,7 @@ PREC = {"fp32": 0, "fp64": 1}
 LAP = {"2shoc": 0, "cd": 1}
 FLAG_NO_STABILITY_CHECK = 1
 FLAG_PLAIN_SCHEDULE = 2
+TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW = 1, 2, 3
 
 _STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
                  "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
@@ -78,6 +79,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_invariants_batch": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
         "nlse_batch_count": ([vp], ctypes.c_int),
         "nlse_adjoint": ([vp, vp, vp, i64, i64, vp, vp, dp, vp], ctypes.c_int),
+        "nlse_set_tiling": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "nlse_get_tiling": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +186,16 @@ def nlse_adjoint(ctx, psi0_ptr: int, target_ptr: int, nsteps: int, ckpt_every: i
     return loss.value
 
 
+def nlse_set_tiling(ctx, key: int, value: int) -> None:
+    _raise(load_library().nlse_set_tiling(ctx, int(key), int(value)))
+
+
+def nlse_get_tiling(ctx, key: int) -> int:
+    v = ctypes.c_int()
+    _raise(load_library().nlse_get_tiling(ctx, int(key), ctypes.byref(v)))
+    return v.value
+
+
 def nlse_reset_compensation(ctx, stream=None) -> None:
     _raise(load_library().nlse_reset_compensation(ctx, _stream(stream)))
 
@@ -259,6 +272,12 @@ class Solver:
 
     def check(self):
         nlse_check(self.ctx)
+
+    def set_tiling(self, key: int, value: int):
+        nlse_set_tiling(self.ctx, key, value)
+
+    def get_tiling(self, key: int) -> int:
+        return nlse_get_tiling(self.ctx, key)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -337,6 +356,12 @@ class BatchSolver:
         """Per-instance (mass, energy, dt_max) lists, FP64."""
         self._check_psi(psi)
         return nlse_invariants_batch(self.ctx, psi.data_ptr(), self.count)
+
+    def set_tiling(self, key: int, value: int):
+        nlse_set_tiling(self.ctx, key, value)
+
+    def get_tiling(self, key: int) -> int:
+        return nlse_get_tiling(self.ctx, key)
 
     def check(self):
         nlse_check(self.ctx)

@@ -150,3 +150,20 @@ def test_batch_workload_sample_equals_single_grid():
         sv.run(x, 3)
         diff = (out[i] - x).abs().max().item()
         assert diff <= 1e-6 * x.abs().max().item(), (i, q.shape, diff)
+
+
+def test_batch_tiling_variants_give_identical_results():
+    insts = _batch(SIDES, seed=13)
+    dts = _dts(insts, "fp32")
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], torch.float32, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec="fp32")
+    outs = []
+    for narrow in (0, 64, 192, 1024):
+        bs.set_tiling(nlse.TILE_BATCH_NARROW, narrow)
+        assert bs.get_tiling(nlse.TILE_BATCH_NARROW) == narrow
+        psi = nlse.BatchSolver.pack([q["psi"] for q in insts], torch.complex64, DEV)
+        bs.run(psi, 20)
+        outs.append(psi)
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])

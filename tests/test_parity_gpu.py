@@ -438,3 +438,30 @@ def test_compensation_resets_when_the_state_changes():
     solver.run(a_, 40)
     solver.run(b_, 40)
     assert torch.equal(a_, b_)
+
+
+# -- tiling choices (launch shape only: results identical bit for bit) ---------
+
+def test_tiling_variants_give_identical_results():
+    from paper_1109_1027_gb300 import autotune
+    for shape, prec, key, values in [((100, 388), "fp32", nlse.TILE_ROWS, (8, 16, 32)),
+                                     ((45, 260), "fp64", nlse.TILE_ROWS, (8, 16, 32)),
+                                     ((70, 40, 100), "fp32", nlse.TILE_PLANES, (32, 64, 128))]:
+        psi, V = _problem(shape, 600)
+        h, a, s = 0.5, 0.9, -1.0
+        prob = oracle.Problem(shape, h, a, s)
+        _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
+        solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, prec=prec)
+        outs = []
+        for v in values:
+            solver.set_tiling(key, v)
+            assert solver.get_tiling(key) == v
+            x = to_dev(psi, prec)
+            solver.run(x, 40)
+            outs.append(x)
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0]), (shape, prec)
+        with pytest.raises(nlse.NLSEError):
+            solver.set_tiling(key, 7)
+        rep = autotune.tune(solver, to_dev(psi, prec), steps=2, use_cache=False)
+        assert rep[key]["choice"] in values
