@@ -85,6 +85,7 @@ def tune(solver, psi: torch.Tensor, steps: int = 8, use_cache: bool = True) -> d
         work = psi.clone()
         for v in CANDIDATES[tile_key]:
             solver.set_tiling(tile_key, v)
+            work.copy_(psi)                          # every candidate starts from the caller's state
             solver.run(work, 2)                      # captures the graph for this tiling
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()

@@ -85,10 +85,20 @@ StageIO<R> make_io(const StageLaunch& L) {
     return io;
 }
 
+// N = s|y|^2 - V (Eq. nbnb1) with explicitly rounded fused multiply-adds, so
+// that every kernel and every launch shape evaluates it with the same
+// roundings: fma(s, fma(y.x, y.x, y.y * y.y), -V).
+__device__ __forceinline__ float nonlin(float s, float2 y, float v) {
+    return __fmaf_rn(s, __fmaf_rn(y.x, y.x, __fmul_rn(y.y, y.y)), -v);
+}
+__device__ __forceinline__ double nonlin(double s, double2 y, double v) {
+    return __fma_rn(s, __fma_rn(y.x, y.x, __dmul_rn(y.y, y.y)), -v);
+}
+
 // Dirichlet step-1 boundary value, Eq. (dbc_lap): D_b = -(s|psi_b|^2 - V_b) psi_b / a.
 template <typename R>
 __device__ __forceinline__ cplx<R> dirichlet_D(const Coef<R>& c, cplx<R> pb, R Vb) {
-    R Nb = c.s * cabs2(pb) - Vb;
+    R Nb = nonlin(c.s, pb, Vb);
     return cscale(-Nb * c.inv_a, pb);
 }
 
@@ -98,8 +108,8 @@ __device__ __forceinline__ cplx<R> dirichlet_D(const Coef<R>& c, cplx<R> pb, R V
 template <typename R>
 __device__ __forceinline__ cplx<R> msd_D(const Coef<R>& c, cplx<R> pb, R Vb, cplx<R> pq, R Vq,
                                          cplx<R> Dq) {
-    R Nb = c.s * cabs2(pb) - Vb;
-    R Nq = c.s * cabs2(pq) - Vq;
+    R Nb = nonlin(c.s, pb, Vb);
+    R Nq = nonlin(c.s, pq, Vq);
     R re_ratio = (Dq.x * pq.x + Dq.y * pq.y) / cabs2(pq);
     return cscale(re_ratio + (Nq - Nb) * c.inv_a, pb);
 }
@@ -114,7 +124,7 @@ __device__ __forceinline__ C msd_F(C pb, C pq, C Fq) {
 // F = i [ a Lap + (s|y|^2 - V) y ] at an interior point (Sec. 3.1).
 template <typename R>
 __device__ __forceinline__ cplx<R> rhs_point(const Coef<R>& c, cplx<R> y, cplx<R> lap, R v) {
-    R N = c.s * cabs2(y) - v;
+    R N = nonlin(c.s, y, v);
     return ctimesi(cmake<cplx<R>>(c.a * lap.x + N * y.x, c.a * lap.y + N * y.y));
 }
 

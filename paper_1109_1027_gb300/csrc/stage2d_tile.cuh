@@ -256,7 +256,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
                 // w = a Lap + (s|Psi|^2 - V) Psi; c F = (-c, c) * swap(w); F_b = 0.
                 auto swapped_w = [&](C y_, C lap_, R v_, bool b_) -> C {
                     if (b_) return czero<C>();
-                    const R N = c.s * (y_.x * y_.x + y_.y * y_.y) - v_;
+                    const R N = nonlin(c.s, y_, v_);
                     const C w = fma2(pair<C>(N, N), y_, mul2(a2, lap_));
                     return pair<C>(w.y, w.x);
                 };

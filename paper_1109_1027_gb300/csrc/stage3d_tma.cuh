@@ -278,7 +278,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                 const float* vv = reinterpret_cast<const float*>(es + L::E_V) + ke;
                 auto swapped_w = [&](C y_, C lap_, float v_, bool b_) -> C {
                     if (b_) return czero<C>();
-                    const float N = c.s * (y_.x * y_.x + y_.y * y_.y) - v_;
+                    const float N = nonlin(c.s, y_, v_);
                     const C w = fma2(pair<C>(N, N), y_, mul2(a2, lap_));
                     return pair<C>(w.y, w.x);
                 };
