@@ -62,7 +62,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash() -> str:
     h = hashlib.sha1()
-    for f in ("stage2d_tma.cu", "tma.cuh", "nlse_device.cuh"):
+    for f in ("stage2d_tma.cuh", "stage2d_tile.cuh", "tma.cuh", "nlse_device.cuh"):
         with open(os.path.join(ROOT, "paper_1109_1027_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

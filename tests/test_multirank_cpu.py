@@ -44,3 +44,12 @@ def test_two_gloo_ranks_take_the_slowest_time():
 def test_single_rank_needs_no_process_group():
     assert bench.ranks_max(None, 3.5) == 3.5
     assert bench.job_rate(1, 10.0, 2.0) == pytest.approx(5.0)
+
+
+def test_bench_helpers_run_without_a_gpu():
+    """The pieces of bench.py that need no GPU: the kernel-source hash that
+    keys recorded ncu traffic, and the measured-peak lookup."""
+    h = bench.kernel_hash()
+    assert len(h) == 12 and int(h, 16) >= 0
+    peak, kind = bench.load_peaks()
+    assert peak > 0 and kind in ("measured", "fallback")
