@@ -407,3 +407,33 @@ def final_loss(psi0, V, target, h, dt, a, s, nsteps, ckpt_every=100, lap="2shoc"
     run on a 2D Dirichlet grid; gradients w.r.t. psi0 and V come from the
     library's adjoint (torch.autograd.Function)."""
     return _FinalLoss.apply(psi0, V, target, h, dt, a, s, nsteps, ckpt_every, lap)
+
+
+def adjoint_many(psi0s, V: torch.Tensor, targets, h, dt, a, s, nsteps: int, ckpt_every: int = 100,
+                 lap: str = "2shoc", workers: int | None = None):
+    """Gradients of L_b = sum |Psi_T^b - target_b|^2 for a batch of initial
+    states sharing V: one context and one CUDA stream per state, driven from
+    host threads so that the instances' kernels run concurrently.  Returns
+    (losses, [dL_b/dpsi0_b], sum_b dL_b/dV in FP64)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    prec = "fp32" if psi0s[0].dtype == torch.complex64 else "fp64"
+    dev = V.device
+    solvers = [Solver(V, h, dt, a, s, prec=prec, lap=lap, check_stability=False) for _ in psi0s]
+    streams = [torch.cuda.Stream(device=dev) for _ in psi0s]
+    torch.cuda.current_stream(dev).synchronize()
+
+    def one(i):
+        with torch.cuda.device(dev), torch.cuda.stream(streams[i]):
+            return solvers[i].adjoint(psi0s[i], targets[i], nsteps, ckpt_every)
+
+    with ThreadPoolExecutor(max_workers=workers or len(psi0s)) as ex:
+        res = list(ex.map(one, range(len(psi0s))))
+    for st in streams:
+        st.synchronize()
+    for sv in solvers:
+        sv.close()
+    gV = torch.zeros(V.shape, dtype=torch.float64, device=dev)
+    for _, _, g in res:
+        gV += g
+    return [r[0] for r in res], [r[1] for r in res], gV

@@ -123,3 +123,21 @@ def test_autograd_function_gives_the_adjoint_gradients():
         refs.append(gV)
         total += L
     assert torch.allclose(Vt.grad.double(), (refs[0] + refs[1]), rtol=1e-5, atol=1e-6 * float(refs[0].abs().max()))
+
+
+def test_concurrent_adjoints_equal_sequential_ones():
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=4)
+    prob = oracle.Problem((64, 64), h, a, s)
+    k = 0.5 * oracle.invariants(prob, psis[0], V)[2]
+    Vd = torch.from_numpy(V).to(DEV).float().contiguous()
+    xs = [torch.from_numpy(p).to(DEV).to(torch.complex64).contiguous() for p in psis]
+    ts = [torch.from_numpy(t).to(DEV).to(torch.complex64).contiguous() for t in targets]
+    losses, gps, gV = nlse.adjoint_many(xs, Vd, ts, h, k, a, s, 25, 10)
+    sv = nlse.Solver(Vd, h, k, a, s, prec="fp32", check_stability=False)
+    total = torch.zeros_like(gV)
+    for i in range(4):
+        L, g, g_V = sv.adjoint(xs[i], ts[i], 25, 10)
+        assert L == losses[i]
+        assert torch.equal(g, gps[i])
+        total += g_V
+    assert torch.allclose(total, gV, rtol=1e-12, atol=0)
