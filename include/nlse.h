@@ -214,6 +214,10 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
 #define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32, 64 (default) or 128 */
 #define NLSE_TILE_BATCH_NARROW 3  /* batch: instances with n[0] <= value get 64-column
                                      tiles, the others 256-column tiles (default 64)    */
+#define NLSE_TILE_1D_RESIDENT 4   /* 1D grids of up to 4096 points: 1 (default) runs
+                                     nlse_run / nlse_rk4_step as one CTA-resident
+                                     launch for all steps, 0 the four tiled launches
+                                     per step                                          */
 int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 

@@ -21,6 +21,7 @@ CANDIDATES = {
     nlse.TILE_ROWS: (8, 16, 32),
     nlse.TILE_PLANES: (32, 64, 128),
     nlse.TILE_BATCH_NARROW: (0, 64, 128, 192, 256),
+    nlse.TILE_1D_RESIDENT: (0, 1),
 }
 
 
@@ -63,6 +64,8 @@ def _keys_for(solver):
     if isinstance(solver, nlse.BatchSolver):
         return [nlse.TILE_BATCH_NARROW]
     d = len(solver.shape)
+    if d == 1 and solver.shape[0] <= 4096:
+        return [nlse.TILE_1D_RESIDENT]
     if d == 2:
         return [nlse.TILE_ROWS]
     if d == 3 and solver.prec == "fp32":

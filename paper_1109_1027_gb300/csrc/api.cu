@@ -73,6 +73,7 @@ struct nlse_ctx {
     size_t adj_bytes;
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
+    int no_resident;          // 1: 1D grids step through the tiled kernels
 };
 
 namespace {
@@ -177,6 +178,25 @@ int bind_maps(nlse_ctx* c, const void* psi, cudaStream_t st) {
         return cuda_fail(e, "encoding the batch tensor maps");
     }
     c->maps_psi = psi;
+    return NLSE_OK;
+}
+
+// Whether this context's steps run as one CTA-resident launch (small 1D grids).
+bool resident_1d(const nlse_ctx* c) {
+    return !c->batch && c->p.dim == 1 && !c->no_resident && !(c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) &&
+           nlse::rk4_1d_resident_fits(c->p.n[0]);
+}
+
+int enqueue_resident(nlse_ctx* c, void* psi, int64_t nsteps, cudaStream_t st) {
+    nlse::ResidentLaunch R;
+    R.prec = c->p.prec; R.lap = c->p.lap; R.bc = c->p.bc;
+    R.n = c->p.n[0];
+    R.h = c->p.h; R.a = c->p.a; R.s = c->p.s; R.dt = c->p.dt;
+    R.psi = psi; R.lo = c->lo; R.V = c->V;
+    R.nsteps = nsteps;
+    R.flag = c->flag;
+    cudaError_t e = nlse::launch_rk4_1d_resident(R, st);
+    if (e != cudaSuccess) return cuda_fail(e, "1D resident RK4 launch");
     return NLSE_OK;
 }
 
@@ -564,6 +584,10 @@ int nlse_set_tiling(nlse_ctx* c, int key, int value) {
             if (value != 32 && value != 64 && value != 128) return fail(NLSE_EINVAL, "planes per CTA: 32, 64 or 128");
             c->tile_planes = value;
             break;
+        case NLSE_TILE_1D_RESIDENT:
+            if (value != 0 && value != 1) return fail(NLSE_EINVAL, "1D resident loop: 0 or 1");
+            c->no_resident = !value;
+            break;
         case NLSE_TILE_BATCH_NARROW: {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             if (value < 0) return fail(NLSE_EINVAL, "the narrow-tile width bound must be >= 0");
@@ -589,6 +613,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             *value = nlse::batch2d_narrow(c->batch);
             return NLSE_OK;
+        case NLSE_TILE_1D_RESIDENT: *value = !c->no_resident; return NLSE_OK;
     }
     return fail(NLSE_EINVAL, "unknown tiling key %d", key);
 }
@@ -620,6 +645,7 @@ int nlse_rk4_step(nlse_ctx* c, void* psi, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     int rc = bind_state(c, psi, st);
     if (rc) return rc;
+    if (resident_1d(c)) return enqueue_resident(c, psi, 1, st);
     return enqueue_step(c, psi, st);
 }
 
@@ -654,6 +680,7 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
                 return fail(NLSE_EUNSTABLE, "dt = %g exceeds the bound %g of Eq. (kdfull)", c->p.dt, dtmax);
         }
     }
+    if (resident_1d(c)) return enqueue_resident(c, psi, nsteps, st);
     if (nsteps >= kGraphSteps && (!c->graph || c->graph_psi != psi)) {
         if (c->graph) {
             cudaGraphExecDestroy(c->graph);

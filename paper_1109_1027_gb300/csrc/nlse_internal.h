@@ -66,6 +66,20 @@ struct PlainLaunch {
 
 cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st);
 
+// Whole RK4 time loops of a small 1D grid in one CTA (rk4_1d_resident.cu).
+struct ResidentLaunch {
+    int prec, lap, bc;
+    int64_t n;
+    double h, a, s, dt;
+    void* psi;              // state, in place
+    void* lo;               // FP32 compensated part, or nullptr
+    const void* V;
+    int64_t nsteps;
+    int* flag;
+};
+bool rk4_1d_resident_fits(int64_t n);
+cudaError_t launch_rk4_1d_resident(const ResidentLaunch& L, cudaStream_t st);
+
 // Batched uneven 2D instances (batch2d.cu).  The plan owns the per-instance
 // tensor-map descriptors and the tile work lists.
 struct BatchPlan;

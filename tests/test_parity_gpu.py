@@ -465,3 +465,24 @@ def test_tiling_variants_give_identical_results():
             solver.set_tiling(key, 7)
         rep = autotune.tune(solver, to_dev(psi, prec), steps=2, use_cache=False)
         assert rep[key]["choice"] in values
+
+
+@pytest.mark.parametrize("n,prec,bc", [(3, "fp64", "dirichlet"), (1030, "fp32", "dirichlet"), (2048, "fp64", "dirichlet"),
+                                       (4096, "fp32", "dirichlet"), (2049, "fp32", "msd"), (5, "fp64", "msd")])
+def test_1d_resident_loop_equals_tiled_steps(n, prec, bc):
+    """The CTA-resident 1D time loop gives the bits of the tiled kernels."""
+    psi, V = _problem((n,), 700 + n)
+    if bc == "msd":
+        psi = psi + 2.5
+    h, a, s = 0.5, 0.8, -1.0
+    prob = oracle.Problem((n,), h, a, s, bc=oracle.BC_MSD if bc == "msd" else 0)
+    _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
+    solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, bc=bc, prec=prec)
+    outs = []
+    for resident in (1, 0):
+        solver.set_tiling(nlse.TILE_1D_RESIDENT, resident)
+        x = to_dev(psi, prec)
+        solver.run(x, 37)
+        solver.rk4_step(x)
+        outs.append(x)
+    assert torch.equal(outs[0], outs[1])
