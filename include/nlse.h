@@ -214,10 +214,12 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
 #define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32, 64 (default) or 128 */
 #define NLSE_TILE_BATCH_NARROW 3  /* batch: instances with n[0] <= value get 64-column
                                      tiles, the others 256-column tiles (default 64)    */
-#define NLSE_TILE_1D_RESIDENT 4   /* 1D grids of up to 4096 points: 1 (default) runs
-                                     nlse_run / nlse_rk4_step as one CTA-resident
-                                     launch for all steps, 0 the four tiled launches
-                                     per step                                          */
+#define NLSE_TILE_1D_RESIDENT 4   /* 1D grids of up to 4096 points: a power of two
+                                     c <= 16 runs nlse_run / nlse_rk4_step as one
+                                     launch for all steps on a cluster of at most c
+                                     CTAs (fewer where the grid is too short); 0 the
+                                     four tiled launches per step.  Default 1 for
+                                     FP32, 16 for FP64                                 */
 int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 

@@ -21,7 +21,7 @@ CANDIDATES = {
     nlse.TILE_ROWS: (8, 16, 32),
     nlse.TILE_PLANES: (32, 64, 128),
     nlse.TILE_BATCH_NARROW: (0, 64, 128, 192, 256),
-    nlse.TILE_1D_RESIDENT: (0, 1),
+    nlse.TILE_1D_RESIDENT: (0, 1, 2, 4, 8, 16),
 }
 
 

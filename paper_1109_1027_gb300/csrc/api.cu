@@ -73,7 +73,7 @@ struct nlse_ctx {
     size_t adj_bytes;
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
-    int no_resident;          // 1: 1D grids step through the tiled kernels
+    int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
 };
 
 namespace {
@@ -181,15 +181,25 @@ int bind_maps(nlse_ctx* c, const void* psi, cudaStream_t st) {
     return NLSE_OK;
 }
 
-// Whether this context's steps run as one CTA-resident launch (small 1D grids).
+// Largest cluster for the resident 1D loop (0: tiled kernels).  By default
+// FP64 spreads over 16 SMs (its per-SM rate bounds a single CTA) and FP32
+// stays on one CTA (the cluster barriers would cost more than they spread).
+int resident_cluster(const nlse_ctx* c) {
+    if (c->resident < 0) return 0;
+    if (c->resident > 0) return c->resident;
+    return c->p.prec == NLSE_FP64 ? 16 : 1;
+}
+
+// Whether this context's steps run as one resident launch (small 1D grids).
 bool resident_1d(const nlse_ctx* c) {
-    return !c->batch && c->p.dim == 1 && !c->no_resident && !(c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) &&
+    return !c->batch && c->p.dim == 1 && resident_cluster(c) > 0 && !(c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) &&
            nlse::rk4_1d_resident_fits(c->p.n[0]);
 }
 
 int enqueue_resident(nlse_ctx* c, void* psi, int64_t nsteps, cudaStream_t st) {
     nlse::ResidentLaunch R;
     R.prec = c->p.prec; R.lap = c->p.lap; R.bc = c->p.bc;
+    R.max_cluster = resident_cluster(c);
     R.n = c->p.n[0];
     R.h = c->p.h; R.a = c->p.a; R.s = c->p.s; R.dt = c->p.dt;
     R.psi = psi; R.lo = c->lo; R.V = c->V;
@@ -585,8 +595,9 @@ int nlse_set_tiling(nlse_ctx* c, int key, int value) {
             c->tile_planes = value;
             break;
         case NLSE_TILE_1D_RESIDENT:
-            if (value != 0 && value != 1) return fail(NLSE_EINVAL, "1D resident loop: 0 or 1");
-            c->no_resident = !value;
+            if (value < 0 || value > nlse::rk4_1d_max_cluster() || (value & (value - 1)))
+                return fail(NLSE_EINVAL, "1D resident loop: 0 or a power of two up to %d", nlse::rk4_1d_max_cluster());
+            c->resident = value ? value : -1;
             break;
         case NLSE_TILE_BATCH_NARROW: {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
@@ -613,7 +624,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             *value = nlse::batch2d_narrow(c->batch);
             return NLSE_OK;
-        case NLSE_TILE_1D_RESIDENT: *value = !c->no_resident; return NLSE_OK;
+        case NLSE_TILE_1D_RESIDENT: *value = resident_cluster(c); return NLSE_OK;
     }
     return fail(NLSE_EINVAL, "unknown tiling key %d", key);
 }

@@ -66,9 +66,11 @@ struct PlainLaunch {
 
 cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st);
 
-// Whole RK4 time loops of a small 1D grid in one CTA (rk4_1d_resident.cu).
+// Whole RK4 time loops of a small 1D grid in one thread-block cluster
+// (rk4_1d_resident.cu).
 struct ResidentLaunch {
     int prec, lap, bc;
+    int max_cluster;        // largest number of CTAs to spread the grid over (1..16)
     int64_t n;
     double h, a, s, dt;
     void* psi;              // state, in place
@@ -78,6 +80,7 @@ struct ResidentLaunch {
     int* flag;
 };
 bool rk4_1d_resident_fits(int64_t n);
+int rk4_1d_max_cluster();
 cudaError_t launch_rk4_1d_resident(const ResidentLaunch& L, cudaStream_t st);
 
 // Batched uneven 2D instances (batch2d.cu).  The plan owns the per-instance

@@ -1,144 +1,252 @@
 // rk4_1d_resident.cu -- whole RK4 time loops on a small 1D grid inside one
-// CTA.  One-dimensional problems (a few thousand points) are far too small to
-// fill the GPU, so the four launches per step of the tiled path are pure
-// latency.  Here one CTA of 1024 threads keeps the stage input, D and F in
-// shared memory and each point's Psi^n, compensated part, accumulator and V
-// in registers, and runs every stage of every step with CTA barriers between
-// the sweeps: step 1 (Eq. 2shoc1d), the boundary value D_b (Eq. dbc_lap, or
-// Eq. msdbc_lap once interior D is known), step 2 (Eq. 2shoc1d2), F with its
+// thread-block cluster.  One-dimensional problems (a few thousand points) are
+// far too small to fill the GPU, so the four launches per step of the tiled
+// path are pure latency.  Here one launch runs every stage of every step: the
+// grid is cut into CS contiguous chunks, one per CTA of a cluster (CS = 1 is a
+// single CTA).  Each CTA keeps its chunk of the stage input Y (with a 2-point
+// halo), D and F in shared memory and each point's Psi^n, compensated part,
+// accumulator and V in registers.  Per stage: a cluster barrier publishes the
+// new Y, the halo is read from the neighbouring CTAs' shared memory, then
+// step 1 (Eq. 2shoc1d) with the boundary value D_b (Eq. dbc_lap, or Eq.
+// msdbc_lap once interior D is known), step 2 (Eq. 2shoc1d2), F with its
 // boundary rule (Eq. dbc_ut / msdbc_ut) and the RK4 stage update.  The
 // per-point arithmetic is the same device code as the tiled kernel
-// (stage1d.cu), so the two give the same bits.
+// (stage1d.cu), so the two give the same bits for every CS.
+//
+// Spreading the chunk over several SMs matters most in FP64, whose per-SM
+// rate on this part is a few FMAs per clock: one CTA is bound by it.
+//
+// Y is double-buffered when CS > 1: stage g reads buffer g % 2 of the
+// neighbours and writes Y_{g+1} to the other buffer; the barrier before stage
+// g + 1 orders the neighbours' reads of buffer g % 2 before its rewrite at
+// stage g + 2.  A last barrier keeps every CTA's shared memory alive until the
+// neighbours' final halo reads are done.  The cluster barrier is the hardware
+// one, with all CTAs of a cluster co-scheduled by construction.
+#include <cooperative_groups.h>
+
+#include <atomic>
+
 #include "nlse_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nlse {
 namespace {
 
-constexpr int NT = 1024;
-constexpr int PPT = 4;                        // points per thread: n <= 4096
+constexpr int MAX_T = 1024;
+constexpr int PPT = 4;                        // points per thread: chunk <= 4096
+constexpr int MAX_CS = 16;
+constexpr int MIN_CHUNK = 32;                 // smallest chunk worth its own CTA
 
 // Stage weights, rounded from FP64 on the host exactly as for the tiled kernels.
 template <typename R> struct Weights { R acc[5], y[5]; };
 
 template <typename R, bool CD, bool MSD>
-__global__ void __launch_bounds__(NT) rk4_1d_resident_kernel(cplx<R>* psi_g, cplx<R>* lo_g, const R* V_g,
-                                                             Coef<R> c, Weights<R> w, int n, int64_t nsteps,
-                                                             int* flag) {
+__global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, cplx<R>* lo_g, const R* V_g,
+                                                                Coef<R> c, Weights<R> w, int n, int m,
+                                                                int64_t nsteps, int* flag) {
     using C = cplx<R>;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CS = (int)cl.num_blocks();
+    const int r = (int)cl.block_rank();
+    const int nbuf = CS > 1 ? 2 : 1;
+    const int p0 = r * m;                                  // first own point
+    const int mr = min(m, n - p0);                         // own points (>= 2)
+    const bool first = r == 0, last = r == CS - 1;
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sY = reinterpret_cast<C*>(smem_raw);   // stage input
-    C* sD = sY + n;                           // step-1 field
-    C* sF = sD + n;                           // F (MSD boundary rule needs F at b-1)
-    const int tid = threadIdx.x;
+    C* sY = reinterpret_cast<C*>(smem_raw);                // [nbuf][m + 4]: local j <-> point p0 - 2 + j
+    C* sD = sY + nbuf * (m + 4);                           // [m + 2]: local j <-> point p0 - 1 + j
+    C* sF = sD + (m + 2);                                  // [m] (MSD only): local j <-> point p0 + j
+    const int tid = threadIdx.x, T = blockDim.x;
 
     C psi[PPT], lo[PPT], acc[PPT];
     R V[PPT];
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) {
-        const int p = tid + m * NT;
-        if (p < n) {
-            psi[m] = psi_g[p];
-            lo[m] = lo_g ? lo_g[p] : czero<C>();
-            V[m] = V_g[p];
-            sY[p] = psi[m];
+    for (int k = 0; k < PPT; ++k) {
+        const int j = tid + k * T;
+        if (j < mr) {
+            psi[k] = psi_g[p0 + j];
+            lo[k] = lo_g ? lo_g[p0 + j] : czero<C>();
+            V[k] = V_g[p0 + j];
+            sY[j + 2] = psi[k];
         }
     }
     const R* wa = w.acc;
     const R* wy = w.y;
     bool bad = false;
+    int buf = 0;
     for (int64_t step = 0; step < nsteps; ++step) {
         for (int stage = 1; stage <= 4; ++stage) {
-            __syncthreads();
-            // Step 1: interior D; boundary D_b by Dirichlet (provisional for MSD).
+            cl.sync();
+            C* Y = sY + buf * (m + 4);
+            // Halo: the last two points of the left neighbour, the first two of the right one.
+            if (CS > 1) {
+                if (tid < 2 && !first) {
+                    const C* q = cl.map_shared_rank(sY + buf * (m + 4), r - 1);
+                    Y[tid] = q[m + tid];
+                } else if (tid >= 2 && tid < 4 && !last) {
+                    const C* q = cl.map_shared_rank(sY + buf * (m + 4), r + 1);
+                    Y[mr + tid] = q[tid];
+                }
+                __syncthreads();
+            }
+            // Step 1: own D (boundary D_b by Dirichlet, provisional for MSD) and
+            // the interior D one point beyond each chunk edge.
 #pragma unroll
-            for (int m = 0; m < PPT; ++m) {
-                const int p = tid + m * NT;
-                if (p >= n) continue;
-                C d;
-                if (p == 0 || p == n - 1) d = dirichlet_D(c, sY[p], V[m]);
-                else d = cscale(c.inv_h2, csub(cadd(sY[p + 1], sY[p - 1]), cscale((R)2, sY[p])));
-                sD[p] = d;
+            for (int k = 0; k < PPT; ++k) {
+                const int j = tid + k * T;
+                if (j >= mr) continue;
+                const int p = p0 + j;
+                const C* y = Y + j + 2;
+                sD[j + 1] = (p == 0 || p == n - 1) ? dirichlet_D(c, y[0], V[k])
+                                                   : cscale(c.inv_h2, csub(cadd(y[1], y[-1]), cscale((R)2, y[0])));
+            }
+            if (tid == 0 && !first) {
+                const C* y = Y + 1;
+                sD[0] = cscale(c.inv_h2, csub(cadd(y[1], y[-1]), cscale((R)2, y[0])));
+            } else if (tid == 1 && !last) {
+                const C* y = Y + mr + 2;
+                sD[mr + 1] = cscale(c.inv_h2, csub(cadd(y[1], y[-1]), cscale((R)2, y[0])));
             }
             __syncthreads();
             if constexpr (MSD) {
-                if (tid < 2) {
-                    const int b = tid == 0 ? 0 : n - 1, q = tid == 0 ? 1 : n - 2;
-                    sD[b] = msd_D(c, sY[b], V_g[b], sY[q], V_g[q], sD[q]);
-                }
+                if (tid == 0 && first) sD[1] = msd_D(c, Y[2], V_g[0], Y[3], V_g[1], sD[2]);
+                if (tid == 1 && last) sD[mr] = msd_D(c, Y[mr + 1], V_g[n - 1], Y[mr], V_g[n - 2], sD[mr - 1]);
                 __syncthreads();
             }
             // Step 2 and F.
             C F[PPT];
 #pragma unroll
-            for (int m = 0; m < PPT; ++m) {
-                const int p = tid + m * NT;
-                F[m] = czero<C>();
-                if (p >= n || p == 0 || p == n - 1) continue;
-                const C lap = CD ? sD[p] : csub(cscale((R)(7.0 / 6.0), sD[p]),
-                                                cscale((R)(1.0 / 12.0), cadd(sD[p + 1], sD[p - 1])));
-                F[m] = rhs_point(c, sY[p], lap, V[m]);
-                if (MSD) sF[p] = F[m];
+            for (int k = 0; k < PPT; ++k) {
+                const int j = tid + k * T;
+                const int p = p0 + j;
+                F[k] = czero<C>();
+                if (j >= mr || p == 0 || p == n - 1) continue;
+                const C* d = sD + j + 1;
+                const C lap = CD ? d[0] : csub(cscale((R)(7.0 / 6.0), d[0]), cscale((R)(1.0 / 12.0), cadd(d[1], d[-1])));
+                F[k] = rhs_point(c, Y[j + 2], lap, V[k]);
+                if (MSD) sF[j] = F[k];
             }
             if constexpr (MSD) {
                 __syncthreads();
 #pragma unroll
-                for (int m = 0; m < PPT; ++m) {
-                    const int p = tid + m * NT;
-                    if (p == 0) F[m] = msd_F(sY[0], sY[1], sF[1]);
-                    if (p == n - 1) F[m] = msd_F(sY[n - 1], sY[n - 2], sF[n - 2]);
+                for (int k = 0; k < PPT; ++k) {
+                    const int j = tid + k * T;
+                    if (first && j == 0) F[k] = msd_F(Y[2], Y[3], sF[1]);
+                    if (last && j == mr - 1) F[k] = msd_F(Y[mr + 1], Y[mr], sF[mr - 2]);
                 }
                 __syncthreads();
             }
             // RK4 stage update (same algebra as the tiled kernels' epilogue).
+            const int nb = nbuf == 2 ? buf ^ 1 : buf;
+            C* Yn = sY + nb * (m + 4);
 #pragma unroll
-            for (int m = 0; m < PPT; ++m) {
-                const int p = tid + m * NT;
-                if (p >= n) continue;
+            for (int k = 0; k < PPT; ++k) {
+                const int j = tid + k * T;
+                if (j >= mr) continue;
                 if (stage == 1) {
-                    acc[m] = cscale(wa[1], F[m]);
-                    sY[p] = caxpy(psi[m], wy[1], F[m]);
+                    acc[k] = cscale(wa[1], F[k]);
+                    Yn[j + 2] = caxpy(psi[k], wy[1], F[k]);
                 } else if (stage < 4) {
-                    acc[m] = caxpy(acc[m], wa[stage], F[m]);
-                    sY[p] = caxpy(psi[m], wy[stage], F[m]);
+                    acc[k] = caxpy(acc[k], wa[stage], F[k]);
+                    Yn[j + 2] = caxpy(psi[k], wy[stage], F[k]);
                 } else {
-                    const C d = caxpy(acc[m], wa[4], F[m]);
+                    const C d = caxpy(acc[k], wa[4], F[k]);
                     if constexpr (sizeof(R) == 4) {
-                        kahan_add(psi[m].x, lo[m].x, d.x);
-                        kahan_add(psi[m].y, lo[m].y, d.y);
+                        kahan_add(psi[k].x, lo[k].x, d.x);
+                        kahan_add(psi[k].y, lo[k].y, d.y);
                     } else {
-                        psi[m] = cadd(psi[m], d);
+                        psi[k] = cadd(psi[k], d);
                     }
-                    sY[p] = psi[m];
-                    bad |= !(isfinite(psi[m].x) && isfinite(psi[m].y));
+                    Yn[j + 2] = psi[k];
+                    bad |= !(isfinite(psi[k].x) && isfinite(psi[k].y));
                 }
             }
+            buf = nb;
         }
     }
 #pragma unroll
-    for (int m = 0; m < PPT; ++m) {
-        const int p = tid + m * NT;
-        if (p < n) {
-            psi_g[p] = psi[m];
-            if (lo_g) lo_g[p] = lo[m];
+    for (int k = 0; k < PPT; ++k) {
+        const int j = tid + k * T;
+        if (j < mr) {
+            psi_g[p0 + j] = psi[k];
+            if (lo_g) lo_g[p0 + j] = lo[k];
         }
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
+    cl.sync();
+}
+
+// Chunk length for a cluster of cs CTAs, or 0 when cs does not fit n: every
+// chunk needs MIN_CHUNK points (the last one at least 2, so that the MSD
+// boundary neighbours and every halo D point stay interior to one CTA) and at
+// most PPT * MAX_T.
+int chunk_for(int64_t n, int cs) {
+    const int64_t m = (n + cs - 1) / cs;
+    if (m > (int64_t)PPT * MAX_T) return 0;
+    if (cs > 1 && (m < MIN_CHUNK || n - (int64_t)(cs - 1) * m < 2)) return 0;
+    return (int)m;
+}
+
+size_t smem_bytes(int m, int cs, bool msd, size_t elem) {
+    const int nbuf = cs > 1 ? 2 : 1;
+    return elem * ((size_t)nbuf * (m + 4) + (m + 2) + (msd ? m : 0));
 }
 
 template <typename R, bool CD, bool MSD>
 cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t st) {
     auto kern = rk4_1d_resident_kernel<R, CD, MSD>;
-    const size_t smem = sizeof(cplx<R>) * 3 * (size_t)L.n;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    Weights<R> w;
-    const double k = L.dt;
-    const double wa[5] = {0.0, k / 6.0, k / 3.0, k / 3.0, k / 6.0};
-    const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};
-    for (int s = 0; s < 5; ++s) { w.acc[s] = (R)wa[s]; w.y[s] = (R)wy[s]; }
-    kern<<<1, NT, smem, st>>>((cplx<R>*)L.psi, (cplx<R>*)L.lo, (const R*)L.V, make_coef<R>(L.h, L.a, L.s), w,
-                              (int)L.n, L.nsteps, L.flag);
-    return cudaGetLastError();
+    // Whether a cluster of 2^i CTAs can be resident: -1 unknown, 0 no, 1 yes.
+    static std::atomic<int> cluster_ok[5] = {-1, -1, -1, -1, -1};
+    int cs = 1;
+    while (cs * 2 <= L.max_cluster && chunk_for(L.n, cs * 2)) cs *= 2;
+    for (;; cs /= 2) {
+        const int m = chunk_for(L.n, cs);
+        const size_t smem = smem_bytes(m, cs, MSD, sizeof(cplx<R>));
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (cs > 8) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        const int T = (int)std::min<int64_t>(MAX_T, (std::min(m, (int)((L.n + cs - 1) / cs)) + 31) / 32 * 32);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(T);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cs > 1) {
+            int lg = 0;
+            while ((1 << lg) < cs) ++lg;
+            int ok = cluster_ok[lg].load();
+            if (ok < 0) {
+                int clusters = 0;
+                e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+                if (e != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    clusters = 0;
+                }
+                ok = clusters > 0 ? 1 : 0;
+                cluster_ok[lg].store(ok);
+            }
+            if (!ok) continue;
+        }
+        Weights<R> w;
+        const double k = L.dt;
+        const double wa[5] = {0.0, k / 6.0, k / 3.0, k / 3.0, k / 6.0};
+        const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};
+        for (int s = 0; s < 5; ++s) { w.acc[s] = (R)wa[s]; w.y[s] = (R)wy[s]; }
+        return cudaLaunchKernelEx(&cfg, kern, (cplx<R>*)L.psi, (cplx<R>*)L.lo, (const R*)L.V,
+                                  make_coef<R>(L.h, L.a, L.s), w, (int)L.n, m, L.nsteps, L.flag);
+    }
 }
 
 template <typename R>
@@ -150,9 +258,12 @@ cudaError_t launch_r(const ResidentLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
-bool rk4_1d_resident_fits(int64_t n) { return n >= 3 && n <= (int64_t)NT * PPT; }
+bool rk4_1d_resident_fits(int64_t n) { return n >= 3 && chunk_for(n, 1) > 0; }
+
+int rk4_1d_max_cluster() { return MAX_CS; }
 
 cudaError_t launch_rk4_1d_resident(const ResidentLaunch& L, cudaStream_t st) {
+    if (L.max_cluster < 1 || L.max_cluster > MAX_CS || !rk4_1d_resident_fits(L.n)) return cudaErrorInvalidValue;
     return L.prec == 0 ? launch_r<float>(L, st) : launch_r<double>(L, st);
 }
 

@@ -468,9 +468,11 @@ def test_tiling_variants_give_identical_results():
 
 
 @pytest.mark.parametrize("n,prec,bc", [(3, "fp64", "dirichlet"), (1030, "fp32", "dirichlet"), (2048, "fp64", "dirichlet"),
-                                       (4096, "fp32", "dirichlet"), (2049, "fp32", "msd"), (5, "fp64", "msd")])
+                                       (4096, "fp32", "dirichlet"), (2049, "fp32", "msd"), (5, "fp64", "msd"),
+                                       (130, "fp64", "msd"), (4096, "fp64", "msd")])
 def test_1d_resident_loop_equals_tiled_steps(n, prec, bc):
-    """The CTA-resident 1D time loop gives the bits of the tiled kernels."""
+    """The resident 1D time loop, on one CTA or spread over a cluster, gives
+    the bits of the tiled kernels."""
     psi, V = _problem((n,), 700 + n)
     if bc == "msd":
         psi = psi + 2.5
@@ -479,10 +481,16 @@ def test_1d_resident_loop_equals_tiled_steps(n, prec, bc):
     _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
     solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, bc=bc, prec=prec)
     outs = []
-    for resident in (1, 0):
-        solver.set_tiling(nlse.TILE_1D_RESIDENT, resident)
+    for cluster in (0, 1, 2, 4, 8, 16):
+        solver.set_tiling(nlse.TILE_1D_RESIDENT, cluster)
+        assert solver.get_tiling(nlse.TILE_1D_RESIDENT) == cluster
         x = to_dev(psi, prec)
         solver.run(x, 37)
         solver.rk4_step(x)
         outs.append(x)
-    assert torch.equal(outs[0], outs[1])
+    for x in outs[1:]:
+        assert torch.equal(x, outs[0])
+    solver.check()
+    for bad in (3, 32, -1):
+        with pytest.raises(nlse.NLSEError):
+            solver.set_tiling(nlse.TILE_1D_RESIDENT, bad)
