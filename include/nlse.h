@@ -218,8 +218,7 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
                                      c <= 16 runs nlse_run / nlse_rk4_step as one
                                      launch for all steps on a cluster of at most c
                                      CTAs (fewer where the grid is too short); 0 the
-                                     four tiled launches per step.  Default 1 for
-                                     FP32, 16 for FP64                                 */
+                                     four tiled launches per step.  Default 16       */
 int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 

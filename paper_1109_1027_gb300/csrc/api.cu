@@ -181,13 +181,11 @@ int bind_maps(nlse_ctx* c, const void* psi, cudaStream_t st) {
     return NLSE_OK;
 }
 
-// Largest cluster for the resident 1D loop (0: tiled kernels).  By default
-// FP64 spreads over 16 SMs (its per-SM rate bounds a single CTA) and FP32
-// stays on one CTA (the cluster barriers would cost more than they spread).
+// Largest cluster for the resident 1D loop (0: tiled kernels; default 16,
+// the fastest in both precisions for 1024 to 4096 points).
 int resident_cluster(const nlse_ctx* c) {
     if (c->resident < 0) return 0;
-    if (c->resident > 0) return c->resident;
-    return c->p.prec == NLSE_FP64 ? 16 : 1;
+    return c->resident > 0 ? c->resident : 16;
 }
 
 // Whether this context's steps run as one resident launch (small 1D grids).

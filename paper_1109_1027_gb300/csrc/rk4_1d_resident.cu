@@ -5,9 +5,9 @@
 // grid is cut into CS contiguous chunks, one per CTA of a cluster (CS = 1 is a
 // single CTA).  Each CTA keeps its chunk of the stage input Y (with a 2-point
 // halo), D and F in shared memory and each point's Psi^n, compensated part,
-// accumulator and V in registers.  Per stage: a cluster barrier publishes the
-// new Y, the halo is read from the neighbouring CTAs' shared memory, then
-// step 1 (Eq. 2shoc1d) with the boundary value D_b (Eq. dbc_lap, or Eq.
+// accumulator and V in registers.  Per stage: each CTA has written the two
+// points at each edge of its new Y into the halo slots of its neighbours'
+// shared memory, and a cluster barrier publishes them; then step 1 (Eq. 2shoc1d) with the boundary value D_b (Eq. dbc_lap, or Eq.
 // msdbc_lap once interior D is known), step 2 (Eq. 2shoc1d2), F with its
 // boundary rule (Eq. dbc_ut / msdbc_ut) and the RK4 stage update.  The
 // per-point arithmetic is the same device code as the tiled kernel
@@ -16,12 +16,13 @@
 // Spreading the chunk over several SMs matters most in FP64, whose per-SM
 // rate on this part is a few FMAs per clock: one CTA is bound by it.
 //
-// Y is double-buffered when CS > 1: stage g reads buffer g % 2 of the
-// neighbours and writes Y_{g+1} to the other buffer; the barrier before stage
-// g + 1 orders the neighbours' reads of buffer g % 2 before its rewrite at
-// stage g + 2.  A last barrier keeps every CTA's shared memory alive until the
-// neighbours' final halo reads are done.  The cluster barrier is the hardware
-// one, with all CTAs of a cluster co-scheduled by construction.
+// Y is double-buffered when CS > 1: stage g reads buffer g % 2 and writes
+// Y_{g+1}, own points and the neighbours' halo slots, to the other buffer; the
+// barrier before stage g + 1 orders every read of buffer g % 2 before its
+// rewrite at stage g + 1.  A first barrier makes sure every CTA runs before
+// any writes into its shared memory, a last one that none exits while a
+// neighbour may still write into it.  The cluster barrier is the hardware one,
+// with all CTAs of a cluster co-scheduled by construction.
 #include <cooperative_groups.h>
 
 #include <atomic>
@@ -34,14 +35,14 @@ namespace nlse {
 namespace {
 
 constexpr int MAX_T = 1024;
-constexpr int PPT = 4;                        // points per thread: chunk <= 4096
+constexpr int MAX_PPT = 4;                    // points per thread: chunk <= 4096
 constexpr int MAX_CS = 16;
 constexpr int MIN_CHUNK = 32;                 // smallest chunk worth its own CTA
 
 // Stage weights, rounded from FP64 on the host exactly as for the tiled kernels.
 template <typename R> struct Weights { R acc[5], y[5]; };
 
-template <typename R, bool CD, bool MSD>
+template <typename R, bool CD, bool MSD, int PPT>
 __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, cplx<R>* lo_g, const R* V_g,
                                                                 Coef<R> c, Weights<R> w, int n, int m,
                                                                 int64_t nsteps, int* flag) {
@@ -60,6 +61,23 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
     C* sF = sD + (m + 2);                                  // [m] (MSD only): local j <-> point p0 + j
     const int tid = threadIdx.x, T = blockDim.x;
 
+    // Writes own point j of buffer b and, for the two points at each chunk
+    // edge, the matching halo slot of the neighbouring CTA.
+    auto publish = [&](int b, int j, C v) {
+        C* Yb = sY + b * (m + 4);
+        Yb[j + 2] = v;
+        if (CS > 1) {
+            if (j < 2 && !first) cl.map_shared_rank(Yb, r - 1)[m + 2 + j] = v;
+            if (j >= mr - 2 && !last) cl.map_shared_rank(Yb, r + 1)[j - mr + 2] = v;
+        }
+    };
+    auto barrier = [&]() {
+        if (CS > 1) cl.sync();
+        else __syncthreads();
+    };
+
+    // Every CTA of the cluster must be running before any writes its shared memory.
+    if (CS > 1) cl.sync();
     C psi[PPT], lo[PPT], acc[PPT];
     R V[PPT];
 #pragma unroll
@@ -69,28 +87,16 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
             psi[k] = psi_g[p0 + j];
             lo[k] = lo_g ? lo_g[p0 + j] : czero<C>();
             V[k] = V_g[p0 + j];
-            sY[j + 2] = psi[k];
+            publish(0, j, psi[k]);
         }
     }
-    const R* wa = w.acc;
-    const R* wy = w.y;
     bool bad = false;
     int buf = 0;
     for (int64_t step = 0; step < nsteps; ++step) {
+#pragma unroll
         for (int stage = 1; stage <= 4; ++stage) {
-            cl.sync();
-            C* Y = sY + buf * (m + 4);
-            // Halo: the last two points of the left neighbour, the first two of the right one.
-            if (CS > 1) {
-                if (tid < 2 && !first) {
-                    const C* q = cl.map_shared_rank(sY + buf * (m + 4), r - 1);
-                    Y[tid] = q[m + tid];
-                } else if (tid >= 2 && tid < 4 && !last) {
-                    const C* q = cl.map_shared_rank(sY + buf * (m + 4), r + 1);
-                    Y[mr + tid] = q[tid];
-                }
-                __syncthreads();
-            }
+            barrier();
+            const C* Y = sY + buf * (m + 4);
             // Step 1: own D (boundary D_b by Dirichlet, provisional for MSD) and
             // the interior D one point beyond each chunk edge.
 #pragma unroll
@@ -140,26 +146,25 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
             }
             // RK4 stage update (same algebra as the tiled kernels' epilogue).
             const int nb = nbuf == 2 ? buf ^ 1 : buf;
-            C* Yn = sY + nb * (m + 4);
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const int j = tid + k * T;
                 if (j >= mr) continue;
                 if (stage == 1) {
-                    acc[k] = cscale(wa[1], F[k]);
-                    Yn[j + 2] = caxpy(psi[k], wy[1], F[k]);
+                    acc[k] = cscale(w.acc[1], F[k]);
+                    publish(nb, j, caxpy(psi[k], w.y[1], F[k]));
                 } else if (stage < 4) {
-                    acc[k] = caxpy(acc[k], wa[stage], F[k]);
-                    Yn[j + 2] = caxpy(psi[k], wy[stage], F[k]);
+                    acc[k] = caxpy(acc[k], w.acc[stage], F[k]);
+                    publish(nb, j, caxpy(psi[k], w.y[stage], F[k]));
                 } else {
-                    const C d = caxpy(acc[k], wa[4], F[k]);
+                    const C d = caxpy(acc[k], w.acc[4], F[k]);
                     if constexpr (sizeof(R) == 4) {
                         kahan_add(psi[k].x, lo[k].x, d.x);
                         kahan_add(psi[k].y, lo[k].y, d.y);
                     } else {
                         psi[k] = cadd(psi[k], d);
                     }
-                    Yn[j + 2] = psi[k];
+                    publish(nb, j, psi[k]);
                     bad |= !(isfinite(psi[k].x) && isfinite(psi[k].y));
                 }
             }
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
         }
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
-    cl.sync();
+    if (CS > 1) cl.sync();
 }
 
 // Chunk length for a cluster of cs CTAs, or 0 when cs does not fit n: every
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
 // most PPT * MAX_T.
 int chunk_for(int64_t n, int cs) {
     const int64_t m = (n + cs - 1) / cs;
-    if (m > (int64_t)PPT * MAX_T) return 0;
+    if (m > (int64_t)MAX_PPT * MAX_T) return 0;
     if (cs > 1 && (m < MIN_CHUNK || n - (int64_t)(cs - 1) * m < 2)) return 0;
     return (int)m;
 }
@@ -194,13 +199,11 @@ size_t smem_bytes(int m, int cs, bool msd, size_t elem) {
     return elem * ((size_t)nbuf * (m + 4) + (m + 2) + (msd ? m : 0));
 }
 
-template <typename R, bool CD, bool MSD>
-cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t st) {
-    auto kern = rk4_1d_resident_kernel<R, CD, MSD>;
+template <typename R, bool CD, bool MSD, int PPT>
+cudaError_t launch_t(const ResidentLaunch& L, int cs, cudaStream_t st) {
+    auto kern = rk4_1d_resident_kernel<R, CD, MSD, PPT>;
     // Whether a cluster of 2^i CTAs can be resident: -1 unknown, 0 no, 1 yes.
     static std::atomic<int> cluster_ok[5] = {-1, -1, -1, -1, -1};
-    int cs = 1;
-    while (cs * 2 <= L.max_cluster && chunk_for(L.n, cs * 2)) cs *= 2;
     for (;; cs /= 2) {
         const int m = chunk_for(L.n, cs);
         const size_t smem = smem_bytes(m, cs, MSD, sizeof(cplx<R>));
@@ -249,11 +252,20 @@ cudaError_t launch_t(const ResidentLaunch& L, cudaStream_t st) {
     }
 }
 
+// One point per thread where the chunk allows (no register pressure), else up to MAX_PPT.
+template <typename R, bool CD, bool MSD>
+cudaError_t launch_p(const ResidentLaunch& L, cudaStream_t st) {
+    int cs = 1;
+    while (cs * 2 <= L.max_cluster && chunk_for(L.n, cs * 2)) cs *= 2;
+    if (chunk_for(L.n, cs) <= MAX_T) return launch_t<R, CD, MSD, 1>(L, cs, st);
+    return launch_t<R, CD, MSD, MAX_PPT>(L, cs, st);
+}
+
 template <typename R>
 cudaError_t launch_r(const ResidentLaunch& L, cudaStream_t st) {
     const bool cd = L.lap == 1, msd = L.bc == 1;
-    if (cd) return msd ? launch_t<R, true, true>(L, st) : launch_t<R, true, false>(L, st);
-    return msd ? launch_t<R, false, true>(L, st) : launch_t<R, false, false>(L, st);
+    if (cd) return msd ? launch_p<R, true, true>(L, st) : launch_p<R, true, false>(L, st);
+    return msd ? launch_p<R, false, true>(L, st) : launch_p<R, false, false>(L, st);
 }
 
 }  // namespace
