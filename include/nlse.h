@@ -156,7 +156,8 @@ int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
  *   B from Table t:bc2 (0 for Dirichlet),
  * all accumulated in FP64 on the device from the state (plus the FP32
  * compensated part when psi_dev is the context's current state).  Synchronises
- * the stream and writes the three host doubles (any may be NULL).  Returns
+ * the stream and writes the three host doubles (any may be NULL; with energy
+ * NULL the energy sum, the costly FP64 Laplacian, is skipped).  Returns
  * NLSE_ENONFINITE when the state holds a NaN or Inf. */
 int nlse_invariants(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy,
                     double* dt_max, void* stream);   /* single-grid contexts only */

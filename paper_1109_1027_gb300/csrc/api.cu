@@ -251,6 +251,7 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     L.psi = psi;
     L.lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
     L.V = c->V;
+    L.energy = energy != nullptr;
     NLSE_CUDA(nlse::launch_invariants(L, c->partials, c->nblocks, c->red_out, st), "invariants launch");
     NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth,
                               cudaMemcpyDeviceToHost, st), "invariants copy");
@@ -281,6 +282,7 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
         L.psi = static_cast<const char*>(psi) + c->boff[i] * cb;
         L.lo = with_lo ? static_cast<const char*>(c->lo) + c->boff[i] * cb : nullptr;
         L.V = static_cast<const char*>(c->V) + c->boff[i] * rb;
+        L.energy = energy != nullptr;
         NLSE_CUDA(nlse::launch_invariants(L, c->partials + (size_t)c->brow[i] * nlse::kPartialWidth,
                                           c->brow[i + 1] - c->brow[i],
                                           c->red_out + (size_t)i * nlse::kPartialWidth, st),

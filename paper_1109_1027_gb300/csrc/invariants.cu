@@ -1,7 +1,8 @@
 // invariants.cu -- FP64 reductions behind nlse_invariants: mass, energy, the
 // extremes of L_i = (h^2/a)(s|Psi_i|^2 - V_i) and of the MSD boundary term
 // |B_b| of Table t:bc2, which together give the time-step bound of
-// Eq. (kdfull), and a count of non-finite values.
+// Eq. (kdfull), and a count of non-finite values.  The stability check before
+// a run asks for the extremes only and skips the energy.
 //
 // Pointwise evaluation straight from global memory (this runs every few
 // hundred steps, not every stage): each thread takes grid points in a
@@ -175,7 +176,10 @@ __device__ Acc block_reduce(Acc a) {
     return a;
 }
 
-template <typename R>
+// ENERGY = false leaves the energy sum at zero: the time-step bound needs
+// only the pointwise extremes (and, for MSD, the boundary term), which read
+// each point once, while the energy's FP64 Laplacian is the costly part.
+template <typename R, bool ENERGY>
 __global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, int64_t npts,
                                                                   double* partials) {
     Acc a = acc_identity();
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, 
         a.lmin = fmin(a.lmin, L);
         a.lmax = fmax(a.lmax, L);
         if (!on_boundary(v, c)) {
+            if (!ENERGY) continue;
             double2 lp = lap_interior(v, c);
             a.energy += -v.a * (ps.x * lp.x + ps.y * lp.y) + Vp * rho - 0.5 * v.s * rho * rho;
         } else if (v.bc == 1) {
@@ -254,7 +259,8 @@ cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* 
     v.a = L.a; v.s = L.s; v.inv_a = 1.0 / L.a;
     v.bc = L.bc; v.lap = L.lap;
     int64_t npts = (int64_t)v.n[0] * v.n[1] * v.n[2];
-    invariants_partial<R><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
+    if (L.energy) invariants_partial<R, true><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
+    else invariants_partial<R, false><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     invariants_final<<<1, kInvThreads, 0, st>>>(partials, nblocks, out);

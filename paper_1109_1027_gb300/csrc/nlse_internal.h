@@ -129,6 +129,7 @@ struct InvLaunch {
     const void* psi;        // state (hi part in FP32)
     const void* lo;         // FP32 compensated part or nullptr
     const void* V;
+    bool energy = true;     // false: skip the energy sum (mass, extremes and count only)
 };
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);

@@ -113,6 +113,7 @@ extern "C" int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev
     L.psi = psi_dev;
     L.lo = nullptr;
     L.V = V_dev;
+    L.energy = energy != nullptr;
     const int nrows = (int)((npts + kPointsPerBlock - 1) / kPointsPerBlock);
     double* result = scratch + (size_t)kMaxRows * nlse::kPartialWidth;
     cudaStream_t st = (cudaStream_t)stream;

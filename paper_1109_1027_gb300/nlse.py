@@ -133,10 +133,11 @@ def nlse_create_batch(params_list, V_ptr: int) -> ctypes.c_void_p:
     return ctx
 
 
-def nlse_invariants_batch(ctx, psi_ptr: int, count: int, stream=None):
+def nlse_invariants_batch(ctx, psi_ptr: int, count: int, stream=None, energy: bool = True):
     m, e, d = (ctypes.c_double * count)(), (ctypes.c_double * count)(), (ctypes.c_double * count)()
-    _raise(load_library().nlse_invariants_batch(ctx, ctypes.c_void_p(psi_ptr), m, e, d, _stream(stream)))
-    return list(m), list(e), list(d)
+    _raise(load_library().nlse_invariants_batch(ctx, ctypes.c_void_p(psi_ptr), m, e if energy else None, d,
+                                                _stream(stream)))
+    return list(m), (list(e) if energy else None), list(d)
 
 
 def nlse_batch_count(ctx) -> int:
@@ -160,11 +161,12 @@ def nlse_run(ctx, psi_ptr: int, nsteps: int, stream=None) -> None:
     _raise(load_library().nlse_run(ctx, ctypes.c_void_p(psi_ptr), int(nsteps), _stream(stream)))
 
 
-def nlse_invariants(ctx, psi_ptr: int, stream=None):
+def nlse_invariants(ctx, psi_ptr: int, stream=None, energy: bool = True):
+    """(mass, energy, dt_max); energy=False skips the energy sum and returns None for it."""
     m, e, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _raise(load_library().nlse_invariants(ctx, ctypes.c_void_p(psi_ptr), ctypes.byref(m),
-                                          ctypes.byref(e), ctypes.byref(d), _stream(stream)))
-    return m.value, e.value, d.value
+                                          ctypes.byref(e) if energy else None, ctypes.byref(d), _stream(stream)))
+    return m.value, (e.value if energy else None), d.value
 
 
 def nlse_invariants_noalloc(params: Params, psi_ptr: int, V_ptr: int, stream=None):
@@ -250,10 +252,10 @@ class Solver:
         nlse_run(self.ctx, psi.data_ptr(), nsteps)
         return psi
 
-    def invariants(self, psi: torch.Tensor):
-        """(mass, energy, dt_max) in FP64."""
+    def invariants(self, psi: torch.Tensor, energy: bool = True):
+        """(mass, energy, dt_max) in FP64 (energy None when not asked for)."""
         self._check_psi(psi)
-        return nlse_invariants(self.ctx, psi.data_ptr())
+        return nlse_invariants(self.ctx, psi.data_ptr(), energy=energy)
 
     def adjoint(self, psi0: torch.Tensor, target: torch.Tensor, nsteps: int, ckpt_every: int = 100):
         """(loss, dL/dpsi0, dL/dV) of L = sum |Psi_T - target|^2 after nsteps
@@ -352,10 +354,10 @@ class BatchSolver:
         nlse_lap2shoc(self.ctx, psi.data_ptr(), out.data_ptr())
         return out
 
-    def invariants(self, psi):
-        """Per-instance (mass, energy, dt_max) lists, FP64."""
+    def invariants(self, psi, energy: bool = True):
+        """Per-instance (mass, energy, dt_max) lists, FP64 (energy None when not asked for)."""
         self._check_psi(psi)
-        return nlse_invariants_batch(self.ctx, psi.data_ptr(), self.count)
+        return nlse_invariants_batch(self.ctx, psi.data_ptr(), self.count, energy=energy)
 
     def set_tiling(self, key: int, value: int):
         nlse_set_tiling(self.ctx, key, value)

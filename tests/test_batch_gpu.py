@@ -106,6 +106,8 @@ def test_batch_laplacian_and_invariants():
         assert m[i] == pytest.approx(m0, rel=1e-12)
         assert e[i] == pytest.approx(e0, rel=1e-11, abs=1e-12)
         assert d[i] == pytest.approx(d0, rel=1e-12)
+    m2, e2, d2 = bs.invariants(psi, energy=False)
+    assert (m2, d2) == (m, d) and e2 is None
 
 
 def test_batch_refuses_an_unstable_instance():

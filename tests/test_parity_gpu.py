@@ -193,6 +193,18 @@ def test_invariants_msd_1d_match_oracle():
                          pytest.approx(d0, rel=1e-12))
 
 
+def test_invariants_without_energy_give_the_same_mass_and_bound():
+    """Skipping the energy sum (the stability check's mode) leaves mass and
+    dt_max bit for bit as they are with it, Dirichlet and MSD."""
+    for shape, bc, prec in [((130, 77), "dirichlet", "fp32"), ((1030,), "msd", "fp64"), ((20, 18, 33), "dirichlet", "fp64")]:
+        psi, V = _problem(shape, 79)
+        solver = nlse.Solver(to_dev(V, prec), 0.4, 1e-4, 0.6, -0.9, bc=bc, prec=prec)
+        x = to_dev(psi + 2.0, prec)
+        m, e, d = solver.invariants(x)
+        m2, e2, d2 = solver.invariants(x, energy=False)
+        assert (m2, d2) == (m, d) and e2 is None and e != 0.0
+
+
 def test_dirichlet_boundary_is_bit_exact_over_a_run():
     """Eq. (dbc_ut): F_b = 0, so boundary values never change, in either precision."""
     for prec in ("fp32", "fp64"):
