@@ -459,7 +459,7 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
         out[prec] = {"value": world * npts * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
         bs.close()
     out["fp32"]["achieved_gbs"] = BYTES_PER_UPDATE_FP32 * npts / (out["fp32"]["ms_per_step"] * 1e-3) / 1e9
-    errs, collapsed = [], 0
+    errs, collapsed = {-1: [], 1: []}, 0
     a64 = res["fp64"]
     a32 = res["fp32"].to(torch.complex128)
     off = 0
@@ -470,10 +470,16 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
         if not (bool(torch.isfinite(s64).all()) and bool(torch.isfinite(s32).all())):
             collapsed += 1
             continue
-        errs.append(float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64)))
-    errs.sort()
-    out["fp32_vs_fp64_rel_l2"] = {"max": errs[-1], "median": errs[len(errs) // 2], "instances": len(errs),
-                                  "within_1e-5": sum(e <= 1e-5 for e in errs)} if errs else None
+        errs[1 if q.s > 0 else -1].append(float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64)))
+
+    def stats(e):
+        e = sorted(e)
+        return {"max": e[-1], "median": e[len(e) // 2], "instances": len(e),
+                "within_1e-5": sum(v <= 1e-5 for v in e)} if e else None
+
+    # Defocusing (s = -1) instances stay smooth; focusing ones (s = +1) self-focus, and near
+    # collapse the dynamics amplify any rounding difference, so they are reported apart.
+    out["fp32_vs_fp64_rel_l2"] = {"defocusing_s-1": stats(errs[-1]), "focusing_s+1": stats(errs[1])}
     out["collapsed_instances"] = collapsed
     out["collapsed_note"] = ("focusing (s=+1) instances whose mass exceeds the 2D critical mass collapse; "
                              "with dt fixed at 0.5 dt_max(psi0) the explicit scheme then overflows (the bound "
