@@ -212,7 +212,7 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
  * captured time-loop graph; NLSE_TILE_BATCH_NARROW also rebuilds the batch
  * work list (synchronising the device). */
 #define NLSE_TILE_ROWS 1          /* 2D: rows per CTA, 8, 16 (default) or 32            */
-#define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32, 64 (default) or 128 */
+#define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32 (default), 64 or 128 */
 #define NLSE_TILE_BATCH_NARROW 3  /* batch: instances with n[0] <= value get 64-column
                                      tiles, the others 256-column tiles (default 64)    */
 #define NLSE_TILE_1D_RESIDENT 4   /* 1D grids of up to 4096 points: a power of two

@@ -114,7 +114,7 @@ StageLaunch base_launch(const nlse_ctx* c) {
     L.V = c->V;
     L.flag = c->flag;
     L.tile_rows = c->tile_rows ? c->tile_rows : 16;
-    L.tile_planes = c->tile_planes ? c->tile_planes : 64;
+    L.tile_planes = c->tile_planes ? c->tile_planes : 32;
     return L;
 }
 
@@ -619,7 +619,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
     if (!c || !value) return fail(NLSE_EINVAL, "NULL argument");
     switch (key) {
         case NLSE_TILE_ROWS: *value = c->tile_rows ? c->tile_rows : 16; return NLSE_OK;
-        case NLSE_TILE_PLANES: *value = c->tile_planes ? c->tile_planes : 64; return NLSE_OK;
+        case NLSE_TILE_PLANES: *value = c->tile_planes ? c->tile_planes : 32; return NLSE_OK;
         case NLSE_TILE_BATCH_NARROW:
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             *value = nlse::batch2d_narrow(c->batch);

@@ -176,9 +176,9 @@ bool stage_3d_tma_eligible(const StageLaunch& L) {
 
 cudaError_t launch_stage_3d_tma(const StageLaunch& L, cudaStream_t st) {
     switch (L.tile_planes) {
-        case 32: return launch_stage_3d_tma_planes32(L, st);
+        case 64: return launch_stage_3d_tma_planes64(L, st);
         case 128: return launch_stage_3d_tma_planes128(L, st);
-        default: return launch_stage_3d_tma_planes64(L, st);
+        default: return launch_stage_3d_tma_planes32(L, st);
     }
 }
 

@@ -194,29 +194,31 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         return {ld2(pc + k - PW), ld2(pc + k + PW), pc[k - 1], pc[k + 2]};
     };
     // D of this thread's pair at input plane j (grid plane z), centre values
-    // cc, vertical neighbours cm / cp, in-plane neighbours nb.
-    auto pair_d = [&](const Nbr& nb, int z, Two cm, Two cc, Two cp) -> Two {
+    // cc, vertical neighbours cm / cp, in-plane neighbours nb.  Also returns q,
+    // the sum of the four in-plane axial neighbours: the x and y edge terms
+    // that plane z contributes to the Laplacian of planes z -+ 1.
+    auto pair_d = [&](const Nbr& nb, int z, Two cm, Two cc, Two cp, Two& q) -> Two {
         const Two up = nb.up, dn = nb.dn;
         const C l = nb.l, r = nb.r;
         const bool zo = zout(z), zb = zbnd(z);
         const int64_t gp = ((int64_t)z * ny + y) * nx + xa;
+        q.a = add2(add2(l, cc.b), add2(up.a, dn.a));
+        q.b = add2(add2(cc.a, r), add2(up.b, dn.b));
         Two d;
-        d.a = dval(oa || zo, ba || zb, gp, cc.a,
-                   add2(add2(add2(l, cc.b), add2(up.a, dn.a)), add2(cm.a, cp.a)));
-        d.b = dval(ob || zo, bb || zb, gp + 1, cc.b,
-                   add2(add2(add2(cc.a, r), add2(up.b, dn.b)), add2(cm.b, cp.b)));
+        d.a = dval(oa || zo, ba || zb, gp, cc.a, add2(q.a, add2(cm.a, cp.a)));
+        d.b = dval(ob || zo, bb || zb, gp + 1, cc.b, add2(q.b, add2(cm.b, cp.b)));
         return d;
     };
 
     // Prologue: input planes 0 .. 3 (z0-2 .. z0+1 in walk order).
     wait_in(0); wait_in(1); wait_in(2); wait_in(3);
     bool alive = __syncthreads_and(ok);
-    Two cm, c0, c1, dm, d0;
+    Two cm, c0, c1, dm, d0, qm, q0;
     if (alive) {
         const Two cmm = ld2(iplane(0) + k);
         cm = ld2(iplane(1) + k); c0 = ld2(iplane(2) + k); c1 = ld2(iplane(3) + k);
-        dm = pair_d(nbrs(1), zbase - dir, cmm, cm, c0);
-        d0 = pair_d(nbrs(2), zbase, cm, c0, c1);
+        dm = pair_d(nbrs(1), zbase - dir, cmm, cm, c0, qm);
+        d0 = pair_d(nbrs(2), zbase, cm, c0, c1, q0);
         st2(dring + k, d0);                       // input plane 2 -> D ring plane 0
         if (hk >= 0) dring[hk] = halo_d(2, zbase);
     }
@@ -236,8 +238,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         }
         // D of the plane ahead (za).
         const Two c2 = ld2(iplane(j + 2) + k);
-        const Nbr np = nbrs(j + 1);              // also the z+1 edge terms of Lap(z)
-        const Two d1 = pair_d(np, za, c0, c1, c2);
+        Two q1;                                  // also the z+1 edge terms of Lap(z)
+        const Two d1 = pair_d(nbrs(j + 1), za, c0, c1, c2, q1);
         C* dn = dring + ((j + 1) & 1) * (PW * PH);
         st2(dn + k, d1);
         if (hk >= 0) dn[hk] = halo_d(j + 1, za);
@@ -246,7 +248,6 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
 
         if (pin) {
             const C* pz = iplane(j);
-            const C* pzm = iplane(j - 1);
             const C* dz = dring + (j & 1) * (PW * PH);
             const bool zb = zbnd(z);
             const bool bA = ba || zb, bB = bb || zb;
@@ -256,16 +257,12 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                 const Two dup = ld2(dz + k - PW), ddn = ld2(dz + k + PW);
                 const C dsa = add2(add2(add2(dz[k - 1], d0.b), add2(dup.a, ddn.a)), add2(dm.a, d1.a));
                 const C dsb = add2(add2(add2(d0.a, dz[k + 2]), add2(dup.b, ddn.b)), add2(dm.b, d1.b));
-                // twelve edge neighbours of Psi: xy corners in plane z, xz and yz edges in z -+ 1
+                // twelve edge neighbours of Psi: xy corners in plane z, xz and yz edges in
+                // z -+ 1 (the in-plane axial sums q of those planes)
                 const Two pu = ld2(pz + k - PW), pd = ld2(pz + k + PW);
                 const C pul = pz[k - PW - 1], pur = pz[k - PW + 2], pdl = pz[k + PW - 1], pdr = pz[k + PW + 2];
-                const Two upm = ld2(pzm + k - PW), dnm = ld2(pzm + k + PW);
-                const Two upp = np.up, dnp = np.dn;
-                const C lm = pzm[k - 1], rm = pzm[k + 2], lp = np.l, rp = np.r;
-                const C ea = add2(add2(add2(pul, pu.b), add2(pdl, pd.b)),
-                                  add2(add2(add2(lm, cm.b), add2(lp, c1.b)), add2(add2(upm.a, dnm.a), add2(upp.a, dnp.a))));
-                const C eb = add2(add2(add2(pu.a, pur), add2(pd.a, pdr)),
-                                  add2(add2(add2(cm.a, rm), add2(c1.a, rp)), add2(add2(upm.b, dnm.b), add2(upp.b, dnp.b))));
+                const C ea = add2(add2(add2(pul, pu.b), add2(pdl, pd.b)), add2(qm.a, q1.a));
+                const C eb = add2(add2(add2(pu.a, pur), add2(pd.a, pdr)), add2(qm.b, q1.b));
                 if (!bA) lap.a = fma2(i6h2, fma2(m12c, c0.a, ea), fma2(m12, dsa, mul2(c10, d0.a)));
                 if (!bB) lap.b = fma2(i6h2, fma2(m12c, c0.b, eb), fma2(m12, dsb, mul2(c10, d0.b)));
             }
@@ -310,6 +307,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         }
         cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
+        qm = q0; q0 = q1;
     }
 
     if (!alive) {
