@@ -69,7 +69,8 @@ cudaError_t launch_group(const BatchDesc* descs, const int4* tiles, int ntiles, 
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    return launch_programmatic(kern, dim3(ntiles), dim3(NT), smem, st, descs, tiles, io, dir);
+    kern<<<ntiles, NT, smem, st>>>(descs, tiles, io, dir);
+    return cudaGetLastError();
 }
 
 template <typename R, bool CD, int NT>

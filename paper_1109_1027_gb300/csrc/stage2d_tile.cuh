@@ -118,8 +118,6 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         mbar_init_fence();
     }
     __syncthreads();
-    griddep_wait();
-    griddep_launch_dependents();
 
     // Producer side (thread 0): input row j, epilogue row e.
     auto issue_in = [&](int j) {

@@ -54,8 +54,9 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     // Consecutive stages walk the rows in opposite directions, so that each
     // stage starts on the rows the previous one wrote last (still in L2).
     const int dir = (STAGE % 2 == 0 && STAGE != 0) ? -1 : 1;
-    return launch_programmatic(kern, grid, dim3(NT), smem, st, m_in, m_in2, m_V, m_psi, m_acc, m_lo, make_io<R>(L),
-                               make_coef<R>(L.h, L.a, L.s), nx, ny, dir);
+    kern<<<grid, NT, smem, st>>>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx,
+                                 ny, dir);
+    return cudaGetLastError();
 }
 
 template <typename R, bool CD, int TY>

@@ -100,8 +100,6 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         mbar_init_fence();
     }
     __syncthreads();
-    griddep_wait();
-    griddep_launch_dependents();
 
     auto issue_in = [&](int j) {
         const int s = j % S;
@@ -355,8 +353,9 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     // Consecutive stages walk z in opposite directions.
     const int dir = (STAGE % 2 == 0 && STAGE != 0) ? -1 : 1;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ);
-    return launch_programmatic(kern, grid, dim3(NT), smem, st, m_in, m_V, m_psi, m_acc, m_lo, make_io<float>(L),
-                               make_coef<float>(L.h, L.a, L.s), nx, ny, nz, dir);
+    kern<<<grid, NT, smem, st>>>(m_in, m_V, m_psi, m_acc, m_lo, make_io<float>(L), make_coef<float>(L.h, L.a, L.s),
+                                 nx, ny, nz, dir);
+    return cudaGetLastError();
 }
 
 template <bool CD, int TZ>

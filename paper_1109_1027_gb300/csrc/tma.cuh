@@ -7,44 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <utility>
-
 namespace nlse {
-
-// Programmatic dependent launch.  A stage kernel launched with the
-// programmatic stream-serialisation attribute may be scheduled while the
-// previous kernel of the stream is still running; griddep_wait() then blocks
-// until that kernel has completed and its writes are visible (it returns at
-// once for a launch without such a dependency), and
-// griddep_launch_dependents() lets the next such launch be scheduled once
-// every CTA of this grid has run it or exited.  A CTA calls both after its
-// prologue (barrier set-up, descriptor prefetch) and before touching any
-// global memory that another stage reads or writes, so only launch latency and
-// the prologue overlap the previous kernel.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-constexpr bool kProgrammaticLaunch = true;
-
-// kern<<<grid, block, smem, st>>>(args...) with the programmatic
-// stream-serialisation attribute (see griddep_wait).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_programmatic(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                                Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = kProgrammaticLaunch ? 1 : 0;
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
