@@ -32,6 +32,7 @@ BC_DIRICHLET = 0
 BC_MSD = 1
 LAP_2SHOC = 0
 LAP_CD = 1
+LAP_2SHOC_MS = 2     # multi-storage 2SHOC (Eqs. 2d2shocMs1-2, 3d2shocMs1-2); 1D: same as LAP_2SHOC
 
 _lib = None
 

@@ -29,6 +29,13 @@
  *  - MSD "b-1" is the closest interior point: every coordinate clamped into
  *    [1, n-2] (for a face point that is its inward normal neighbour; for an
  *    edge or corner it is the diagonal inward neighbour).
+ *  - Multi-storage 2SHOC needs the step-1 boundary value of each separate
+ *    second derivative, which Sec. 3.2 does not give for Dirichlet.  At a
+ *    point on the boundary of axis a only, D^a_b = D_b - sum of the other
+ *    axes' second differences there, D_b from Eq. (dbc_lap), so that the
+ *    separate derivatives add up to the boundary Laplacian.  Points on the
+ *    boundary of two or more axes never enter an interior Laplacian; their
+ *    separate derivatives are set to 0.
  *  - Mass M = h^d sum_all |psi|^2; energy (the paper defines none) is the
  *    discrete Hamiltonian of Eq. (NLSE):
  *    E = h^d sum_interior [ -a Re(conj(psi) Lap psi) + V|psi|^2 - (s/2)|psi|^4 ].
@@ -48,7 +55,8 @@ typedef struct {
     double a;      /* dispersion coefficient, a > 0 (Eq. NLSE) */
     double s;      /* nonlinearity coefficient (Eq. NLSE) */
     int bc;        /* 0: Dirichlet (Eqs. dbc_lap, dbc_ut); 1: MSD (Eqs. msdbc_ut, msdbc_lap) */
-    int lap;       /* 0: 2SHOC single storage (Sec. 2); 1: second-order central difference (CD) */
+    int lap;       /* 0: 2SHOC single storage (Sec. 2); 1: second-order central difference (CD);
+                      2: 2SHOC multi storage (Eqs. 2d2shocMs1-2, 3d2shocMs1-2; in 1D the same as 0) */
 } or_problem;
 
 typedef struct { double re, im; } cplx;
@@ -175,11 +183,95 @@ static cplx boundary_D(const or_problem* P, const double* psi, const double* V, 
     return c_scale(factor, pb);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Multi-storage 2SHOC (Eqs. 2d2shocMs1-2 in 2D, 3d2shocMs1-2 in 3D).        */
+/* ------------------------------------------------------------------------ */
+
+/* The second difference of psi along axis ax at (x, y, z): Eq. (2d2shocMs1),
+ * Eq. (3d2shocMs1). */
+static cplx delta2(const or_problem* P, const double* psi, int ax, long x, long y, long z) {
+    long dx = ax == 0, dy = ax == 1, dz = ax == 2;
+    cplx sum = c_add(get(psi, idx(P, x + dx, y + dy, z + dz)), get(psi, idx(P, x - dx, y - dy, z - dz)));
+    return c_scale(1.0 / (P->h * P->h), c_sub(sum, c_scale(2.0, get(psi, idx(P, x, y, z)))));
+}
+
+/* Whether coordinate ax of (x, y, z) is 0 or n-1. */
+static int on_axis_boundary(const or_problem* P, int ax, long x, long y, long z) {
+    long c = ax == 0 ? x : (ax == 1 ? y : z);
+    return c == 0 || c == P->n[ax] - 1;
+}
+
+/* Multi-storage Laplacian into lap.  Dsep: caller work space of 3 * 2N doubles
+ * for D^x, D^y, D^z; Dsum (2N doubles) receives D^x + D^y (+ D^z). */
+static void laplacian_ms(const or_problem* P, const double* psi, const double* V, double* Dsep,
+                         double* Dsum, double* lap) {
+    long N = npoints(P);
+    /* Step 1 at interior points: one second difference per axis. */
+    for (long z = 0; z < P->n[2]; ++z)
+        for (long y = 0; y < P->n[1]; ++y)
+            for (long x = 0; x < P->n[0]; ++x)
+                if (!is_boundary(P, x, y, z))
+                    for (int ax = 0; ax < P->dim; ++ax)
+                        put(Dsep + 2 * N * ax, idx(P, x, y, z), delta2(P, psi, ax, x, y, z));
+    /* Step-1 boundary values (Dirichlet, Eq. dbc_lap, split as stated above). */
+    for (long z = 0; z < P->n[2]; ++z)
+        for (long y = 0; y < P->n[1]; ++y)
+            for (long x = 0; x < P->n[0]; ++x) {
+                if (!is_boundary(P, x, y, z)) continue;
+                long b = idx(P, x, y, z);
+                int nb = 0, axb = -1;
+                for (int ax = 0; ax < P->dim; ++ax)
+                    if (on_axis_boundary(P, ax, x, y, z)) { ++nb; axb = ax; }
+                for (int ax = 0; ax < P->dim; ++ax) put(Dsep + 2 * N * ax, b, c_make(0.0, 0.0));
+                if (nb != 1) continue;
+                cplx pb = get(psi, b);
+                cplx rest = c_scale(-nonlin(P, pb, V[b]) / P->a, pb);
+                for (int ax = 0; ax < P->dim; ++ax) {
+                    if (ax == axb) continue;
+                    cplx d = delta2(P, psi, ax, x, y, z);
+                    put(Dsep + 2 * N * ax, b, d);
+                    rest = c_sub(rest, d);
+                }
+                put(Dsep + 2 * N * axb, b, rest);
+            }
+    /* Step 2 at interior points, Eq. (2d2shocMs2) / Eq. (3d2shocMs2):
+     * (7/6) sum_a D^a_c - (1/12) sum_a (D^a at the two neighbours along a).
+     * Boundary points take D_b of Eq. (dbc_lap), as in the single-storage form. */
+    for (long z = 0; z < P->n[2]; ++z)
+        for (long y = 0; y < P->n[1]; ++y)
+            for (long x = 0; x < P->n[0]; ++x) {
+                long p = idx(P, x, y, z);
+                cplx centre = c_make(0.0, 0.0), nbrs = c_make(0.0, 0.0);
+                for (int ax = 0; ax < P->dim; ++ax) {
+                    const double* Da = Dsep + 2 * N * ax;
+                    long dx = ax == 0, dy = ax == 1, dz = ax == 2;
+                    centre = c_add(centre, get(Da, p));
+                    if (!is_boundary(P, x, y, z))
+                        nbrs = c_add(nbrs, c_add(get(Da, idx(P, x + dx, y + dy, z + dz)),
+                                                 get(Da, idx(P, x - dx, y - dy, z - dz))));
+                }
+                put(Dsum, p, centre);
+                if (is_boundary(P, x, y, z)) {
+                    cplx pb = get(psi, p);
+                    put(lap, p, c_scale(-nonlin(P, pb, V[p]) / P->a, pb));
+                } else {
+                    put(lap, p, c_sub(c_scale(7.0 / 6.0, centre), c_scale(1.0 / 12.0, nbrs)));
+                }
+            }
+}
+
 /* Laplacian of psi into lap (2N doubles).  With P->lap == 0 this is the
- * 2SHOC scheme; with P->lap == 1 it is the second-order CD scheme (D itself).
- * D is caller-provided work space of 2N doubles and holds step 1 on return. */
+ * 2SHOC scheme; with P->lap == 1 it is the second-order CD scheme (D itself);
+ * with P->lap == 2 (d >= 2) the multi-storage 2SHOC scheme.  D is
+ * caller-provided work space of 2N doubles (8N for the multi-storage form)
+ * and holds step 1 (for the multi-storage form: the sum of the separate
+ * second derivatives) on return. */
 static void laplacian(const or_problem* P, const double* psi, const double* V, double* D,
                       double* lap) {
+    if (P->lap == 2 && P->dim >= 2) {
+        laplacian_ms(P, psi, V, D + 2 * npoints(P), D, lap);
+        return;
+    }
     /* Step 1, interior points first. */
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
@@ -211,11 +303,11 @@ static void laplacian(const or_problem* P, const double* psi, const double* V, d
 /* F = i [ a Lap psi + (s|psi|^2 - V) psi ] at interior points (Sec. 3.1).
  * Boundary: Dirichlet, Eq. (dbc_ut): F_b = 0.
  *           MSD, Eq. (msdbc_ut): F_b = i Im(F_{b-1} / psi_{b-1}) psi_b.
- * work: 4N doubles (D and Lap). */
+ * work: 10N doubles (D work space and Lap). */
 static void rhs(const or_problem* P, const double* psi, const double* V, double* F, double* work) {
     long N = npoints(P);
     double* D = work;
-    double* lap = work + 2 * N;
+    double* lap = work + 8 * N;
     laplacian(P, psi, V, D, lap);
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
@@ -253,7 +345,7 @@ static int rk4_alloc(rk4_space* W, long N) {
     W->Ktot = (double*)malloc(sizeof(double) * 2 * N);
     W->Ktmp = (double*)malloc(sizeof(double) * 2 * N);
     W->ptmp = (double*)malloc(sizeof(double) * 2 * N);
-    W->work = (double*)malloc(sizeof(double) * 4 * N);
+    W->work = (double*)malloc(sizeof(double) * 10 * N);
     return !(W->Ktot && W->Ktmp && W->ptmp && W->work);
 }
 
@@ -339,7 +431,8 @@ static int make_problem(or_problem* P, int dim, const long* n, double h, double 
     for (int ax = 0; ax < dim; ++ax) if (P->n[ax] < 3) return 1;
     if (!(h > 0.0) || !(a > 0.0)) return 1;
     if (bc != 0 && bc != 1) return 1;
-    if (lap != 0 && lap != 1) return 1;
+    if (lap != 0 && lap != 1 && lap != 2) return 1;
+    if (lap == 2 && bc != 0 && dim > 1) return 1;    /* multi storage: Dirichlet only (Sec. 3.2) */
     P->h = h; P->a = a; P->s = s; P->bc = bc; P->lap = lap;
     return 0;
 }
@@ -351,9 +444,10 @@ int oracle_laplacian(int dim, const long* n, double h, double a, double s, int b
     or_problem P;
     if (make_problem(&P, dim, n, h, a, s, bc, lap)) return 1;
     long N = npoints(&P);
-    double* D = D_out ? D_out : (double*)malloc(sizeof(double) * 2 * N);
+    double* D = (double*)malloc(sizeof(double) * 8 * N);
     laplacian(&P, psi, V, D, lap_out);
-    if (!D_out) free(D);
+    if (D_out) memcpy(D_out, D, sizeof(double) * 2 * N);
+    free(D);
     return 0;
 }
 
@@ -362,7 +456,7 @@ int oracle_rhs(int dim, const long* n, double h, double a, double s, int bc, int
                const double* psi, const double* V, double* F) {
     or_problem P;
     if (make_problem(&P, dim, n, h, a, s, bc, lap)) return 1;
-    double* work = (double*)malloc(sizeof(double) * 4 * npoints(&P));
+    double* work = (double*)malloc(sizeof(double) * 10 * npoints(&P));
     rhs(&P, psi, V, F, work);
     free(work);
     return 0;
@@ -388,7 +482,7 @@ int oracle_invariants(int dim, const long* n, double h, double a, double s, int 
     if (make_problem(&P, dim, n, h, a, s, bc, lap)) return 1;
     long N = npoints(&P);
     double hd = pow(P.h, (double)P.dim);
-    double* D = (double*)malloc(sizeof(double) * 2 * N);
+    double* D = (double*)malloc(sizeof(double) * 8 * N);
     double* lap_f = (double*)malloc(sizeof(double) * 2 * N);
     laplacian(&P, psi, V, D, lap_f);
     double m = 0.0, e = 0.0;

@@ -53,6 +53,53 @@ def test_interior_equals_noncompact_stencil(shape):
     assert np.abs(lap[core] - ref).max() <= 1e-13 * scale
 
 
+@pytest.mark.parametrize("shape", SHAPES[1:])
+def test_multi_storage_interior_equals_noncompact_stencil(shape):
+    """Eqs. (2d2shocMs1-2) and (3d2shocMs1-2): the multi-storage 2SHOC is the
+    1D fourth-order stencil along each axis, i.e. the non-compact stencil."""
+    h = 0.37
+    psi = wl.random_field(shape, seed=13)
+    V = wl.random_potential(shape, seed=14)
+    prob = oracle.Problem(shape, h, 0.8, -1.3, lap=oracle.LAP_2SHOC_MS)
+    lap = oracle.laplacian(prob, psi, V)
+    core = tuple(slice(2, -2) for _ in shape)
+    scale = np.abs(psi).max() * 64 / 12 * len(shape) / h ** 2
+    assert np.abs(lap[core] - noncompact_lap(psi, h)).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("shape", [(9, 11), (17, 6), (6, 7, 8), (9, 5, 7)])
+def test_multi_storage_boundary_split_matches_single_storage(shape):
+    """With D^a_b = D_b(Eq. dbc_lap) - (the other axes' second differences) at a
+    point on the boundary of axis a only, the two storage forms are the same
+    operator at every point, including the ring next to the boundary (where
+    the single-storage form reads D_b directly); boundary points carry D_b in
+    both.  A wrong split (e.g. one axis left out in 3D) breaks the ring."""
+    h = 0.41
+    psi = wl.random_field(shape, seed=15) + 0.7
+    V = wl.random_potential(shape, seed=16, scale=2.0)
+    single = oracle.laplacian(oracle.Problem(shape, h, 0.6, 1.1), psi, V)
+    multi = oracle.laplacian(oracle.Problem(shape, h, 0.6, 1.1, lap=oracle.LAP_2SHOC_MS), psi, V)
+    scale = np.abs(psi).max() * 64 / 12 * len(shape) / h ** 2
+    assert np.abs(multi - single).max() <= 1e-13 * scale
+    ring = np.zeros(shape, bool)
+    ring[tuple(slice(1, -1) for _ in shape)] = True
+    ring[tuple(slice(2, -2) for _ in shape)] = False
+    assert np.abs(single[ring]).max() > 1e-3 * scale          # the ring is exercised
+
+
+def test_multi_storage_is_single_storage_in_1d_and_rejects_msd_in_2d():
+    shape = (37,)
+    psi = wl.random_field(shape, seed=17) + 2.0
+    V = wl.random_potential(shape, seed=18)
+    for bc in (oracle.BC_DIRICHLET, oracle.BC_MSD):
+        a = oracle.run(oracle.Problem(shape, 0.3, 0.9, -1.0, bc=bc), psi, V, 1e-3, 5)
+        b = oracle.run(oracle.Problem(shape, 0.3, 0.9, -1.0, bc=bc, lap=oracle.LAP_2SHOC_MS), psi, V, 1e-3, 5)
+        assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        oracle.laplacian(oracle.Problem((6, 6), 0.3, 0.9, -1.0, bc=oracle.BC_MSD, lap=oracle.LAP_2SHOC_MS),
+                         np.ones((6, 6), complex), np.zeros((6, 6)))
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_polynomial_exactness(dim):
     """The fourth-order stencil's error term is h^4 times sixth derivatives, so
