@@ -61,10 +61,20 @@ typedef enum {
     NLSE_FP64 = 1           /* complex128 throughout                                  */
 } nlse_prec;
 
-/* Laplacian inside F (Sec. 3.1 names both). */
+/* Laplacian inside F (Sec. 3.1 names 2SHOC and CD). */
 typedef enum {
     NLSE_LAP_2SHOC = 0,     /* fourth-order 2SHOC, Secs. 2.1-2.3 (single storage)    */
-    NLSE_LAP_CD = 1         /* second-order central difference, Eq. (dx2)            */
+    NLSE_LAP_CD = 1,        /* second-order central difference, Eq. (dx2)            */
+    NLSE_LAP_2SHOC_MS = 2   /* 2SHOC in its multi-storage form, Eqs. (2d2shocMs1-2),
+                               (3d2shocMs1-2): one second difference per axis kept
+                               apart, then (7/6) sum_a D^a - (1/12) sum_a (D^a at
+                               the two neighbours along a); the same operator as
+                               NLSE_LAP_2SHOC (results equal up to rounding) with
+                               fewer operations.  Dirichlet only in 2D/3D; at a
+                               point on the boundary of axis a only, D^a_b is D_b
+                               of Eq. (dbc_lap) minus the other axes' second
+                               differences (the paper gives no split).  In 1D it
+                               is NLSE_LAP_2SHOC.                                  */
 } nlse_lap;
 
 /* nlse_params.flags */

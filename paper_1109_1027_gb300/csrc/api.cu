@@ -94,11 +94,14 @@ int validate(const nlse_params* p) {
     if (!std::isfinite(p->s)) return fail(NLSE_EINVAL, "s must be finite");
     if (p->bc != NLSE_BC_DIRICHLET && p->bc != NLSE_BC_MSD) return fail(NLSE_EINVAL, "unknown bc %d", p->bc);
     if (p->prec != NLSE_FP32 && p->prec != NLSE_FP64) return fail(NLSE_EINVAL, "unknown prec %d", p->prec);
-    if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD) return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
+    if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD && p->lap != NLSE_LAP_2SHOC_MS)
+        return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
     if (p->bc == NLSE_BC_MSD && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "MSD boundaries are implemented for dim = 1 only");
     if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->bc != NLSE_BC_DIRICHLET)
         return fail(NLSE_EUNSUPPORTED, "the unfused schedule supports Dirichlet boundaries only");
+    if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
+        return fail(NLSE_EUNSUPPORTED, "the unfused schedule has the single-storage 2SHOC and CD only");
     return NLSE_OK;
 }
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "nlse_internal.h"
@@ -40,7 +41,7 @@ struct BatchDesc {
     double c_acc[5], c_y[5];                  // stage weights from this instance's dt
 };
 
-template <typename R, bool CD, int STAGE, int NT>
+template <typename R, int LP, int STAGE, int NT>
 __global__ void __launch_bounds__(NT)
 stage2d_batch_kernel(const BatchDesc* __restrict__ descs, const int4* __restrict__ tiles, StageIO<R> io,
                      const int dir) {
@@ -56,14 +57,14 @@ stage2d_batch_kernel(const BatchDesc* __restrict__ descs, const int4* __restrict
     c.inv_h2 = (R)d.inv_h2; c.inv_6h2 = (R)d.inv_6h2; c.a = (R)d.a; c.s = (R)d.s; c.inv_a = (R)d.inv_a;
     // Stage input: Psi for the Laplacian and stage 1, Y0 for stages 2 and 4, Y1 for stage 3.
     constexpr int sel = STAGE <= 1 ? 0 : (STAGE == 3 ? 2 : 1);
-    tile2d::stage2d_tile<R, CD, STAGE, NT, TYB>(&d.in[sel][0], &d.in[sel][1], &d.V, &d.psi, &d.acc, &d.lo, io, c,
+    tile2d::stage2d_tile<R, LP, STAGE, NT, TYB>(&d.in[sel][0], &d.in[sel][1], &d.V, &d.psi, &d.acc, &d.lo, io, c,
                                                 d.nx, d.ny, tl.y, tl.z, dir);
 }
 
-template <typename R, bool CD, int STAGE, int NT>
+template <typename R, int LP, int STAGE, int NT>
 cudaError_t launch_group(const BatchDesc* descs, const int4* tiles, int ntiles, const StageIO<R>& io, int dir,
                          cudaStream_t st) {
-    auto kern = stage2d_batch_kernel<R, CD, STAGE, NT>;
+    auto kern = stage2d_batch_kernel<R, LP, STAGE, NT>;
     const int smem = tile2d::Lay<R, NT>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -73,15 +74,15 @@ cudaError_t launch_group(const BatchDesc* descs, const int4* tiles, int ntiles, 
     return cudaGetLastError();
 }
 
-template <typename R, bool CD, int NT>
+template <typename R, int LP, int NT>
 cudaError_t launch_stage_nt(int stage, const BatchDesc* descs, const int4* tiles, int ntiles,
                             const StageIO<R>& io, int dir, cudaStream_t st) {
     switch (stage) {
-        case 0: return launch_group<R, CD, 0, NT>(descs, tiles, ntiles, io, dir, st);
-        case 1: return launch_group<R, CD, 1, NT>(descs, tiles, ntiles, io, dir, st);
-        case 2: return launch_group<R, CD, 2, NT>(descs, tiles, ntiles, io, dir, st);
-        case 3: return launch_group<R, CD, 3, NT>(descs, tiles, ntiles, io, dir, st);
-        case 4: return launch_group<R, CD, 4, NT>(descs, tiles, ntiles, io, dir, st);
+        case 0: return launch_group<R, LP, 0, NT>(descs, tiles, ntiles, io, dir, st);
+        case 1: return launch_group<R, LP, 1, NT>(descs, tiles, ntiles, io, dir, st);
+        case 2: return launch_group<R, LP, 2, NT>(descs, tiles, ntiles, io, dir, st);
+        case 3: return launch_group<R, LP, 3, NT>(descs, tiles, ntiles, io, dir, st);
+        case 4: return launch_group<R, LP, 4, NT>(descs, tiles, ntiles, io, dir, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -89,10 +90,16 @@ cudaError_t launch_stage_nt(int stage, const BatchDesc* descs, const int4* tiles
 template <typename R>
 cudaError_t launch_stage_r(int stage, int lap, int nt, const BatchDesc* descs, const int4* tiles, int ntiles,
                            const StageIO<R>& io, int dir, cudaStream_t st) {
-    if (nt == 32) return lap ? launch_stage_nt<R, true, 32>(stage, descs, tiles, ntiles, io, dir, st)
-                             : launch_stage_nt<R, false, 32>(stage, descs, tiles, ntiles, io, dir, st);
-    return lap ? launch_stage_nt<R, true, 128>(stage, descs, tiles, ntiles, io, dir, st)
-               : launch_stage_nt<R, false, 128>(stage, descs, tiles, ntiles, io, dir, st);
+    auto by_lap = [&](auto nt_c) -> cudaError_t {
+        constexpr int NTC = decltype(nt_c)::value;
+        switch (lap) {
+            case 0: return launch_stage_nt<R, 0, NTC>(stage, descs, tiles, ntiles, io, dir, st);
+            case 1: return launch_stage_nt<R, 1, NTC>(stage, descs, tiles, ntiles, io, dir, st);
+            case 2: return launch_stage_nt<R, 2, NTC>(stage, descs, tiles, ntiles, io, dir, st);
+        }
+        return cudaErrorInvalidValue;
+    };
+    return nt == 32 ? by_lap(std::integral_constant<int, 32>()) : by_lap(std::integral_constant<int, 128>());
 }
 
 template <typename R>

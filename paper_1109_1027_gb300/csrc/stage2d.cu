@@ -10,7 +10,11 @@
 //     Lap = -(1/12)[D_E + D_W + D_N + D_S - 12 D_c]
 //           + (1/(6h^2))[Psi_NE + Psi_NW + Psi_SE + Psi_SW - 4 Psi_c],
 // followed by F (Sec. 3.1), the Dirichlet rule F_b = 0 (Eq. dbc_ut) and the
-// stage epilogue.  D lives only in shared memory.
+// stage epilogue.  D lives only in shared memory.  The multi-storage form
+// (LP = 2) keeps D^x and D^y apart, Eq. (2d2shocMs1), with the Dirichlet
+// split of D_b at points on the boundary of one axis (D^a_b = D_b minus the
+// other axis' second difference), and takes step 2 from Eq. (2d2shocMs2):
+//     Lap = (7/6)(D^x_c + D^y_c) - (1/12)(D^x_E + D^x_W + D^y_N + D^y_S).
 #include "nlse_device.cuh"
 #include "tmap.cuh"
 
@@ -24,13 +28,16 @@ constexpr int PX = TX + 4, PY = TY + 4;   // stage input with a 2-point halo
 constexpr int DX = TX + 2, DY = TY + 2;   // D with a 1-point halo
 
 // STAGE 0 writes the Laplacian (boundary = D_b); STAGE 1..4 are RK4 stages.
-template <typename R, bool CD, int STAGE>
+// LP: 0 single-storage 2SHOC, 1 CD, 2 multi-storage 2SHOC.
+template <typename R, int LP, int STAGE>
 __global__ void __launch_bounds__(NT)
 stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
     using C = cplx<R>;
+    constexpr bool CD = LP == 1, MS = LP == 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sP = reinterpret_cast<C*>(smem_raw);          // [PY][PX]
-    C* sD = sP + PX * PY;                            // [DY][DX]
+    C* sD = sP + PX * PY;                            // [DY][DX]; multi storage: D^x
+    C* sDy = sD + DX * DY;                           // multi storage: D^y [DY][DX]
 
     const int x0 = blockIdx.x * TX;
     const int y0 = blockIdx.y * TY;
@@ -52,6 +59,24 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const C* q = sP + (ly + 1) * PX + (lx + 1);
         C d = czero<C>();
+        if constexpr (MS) {
+            C dx = czero<C>(), dy = czero<C>();
+            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                const C pc = q[0];
+                dx = cscale(c.inv_h2, csub(cadd(q[-1], q[1]), cscale((R)2, pc)));
+                dy = cscale(c.inv_h2, csub(cadd(q[-PX], q[PX]), cscale((R)2, pc)));
+                const bool bx = gx == 0 || gx == nx - 1, by = gy == 0 || gy == ny - 1;
+                if (bx || by) {
+                    const C lb = dirichlet_D(c, pc, io.V[(int64_t)gy * nx + gx]);
+                    if (bx && by) dx = dy = czero<C>();
+                    else if (bx) dx = csub(lb, dy);
+                    else dy = csub(lb, dx);
+                }
+            }
+            sD[i] = dx;
+            sDy[i] = dy;
+            continue;
+        }
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             C pc = q[0];
             if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
@@ -77,7 +102,15 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         const C y = q[0];
         const bool bnd = (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1);
         C lap;
-        if (bnd || CD) {
+        if (MS) {
+            const C* ey = sDy + (ly + 1) * DX + (lx + 1);
+            if (bnd) {
+                lap = dirichlet_D(c, y, io.V[p]);
+            } else {
+                const C nb = cadd(cadd(e[-1], e[1]), cadd(ey[-DX], ey[DX]));
+                lap = csub(cscale((R)(7.0 / 6.0), cadd(e[0], ey[0])), cscale((R)(1.0 / 12.0), nb));
+            }
+        } else if (bnd || CD) {
             lap = e[0];
         } else {
             C dsum = cadd(cadd(e[1], e[-1]), cadd(e[DX], e[-DX]));
@@ -98,12 +131,12 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
     }
 }
 
-template <typename R, bool CD, int STAGE>
+template <typename R, int LP, int STAGE>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     const int nx = (int)L.n[0], ny = (int)L.n[1];
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
-    size_t smem = sizeof(cplx<R>) * (PX * PY + DX * DY);
-    auto kern = stage2d_kernel<R, CD, STAGE>;
+    size_t smem = sizeof(cplx<R>) * (PX * PY + (LP == 2 ? 2 : 1) * DX * DY);
+    auto kern = stage2d_kernel<R, LP, STAGE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -112,14 +145,24 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename R, bool CD>
+template <typename R, int LP>
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     switch (L.stage) {
-        case 0: return launch_t<R, CD, 0>(L, st);
-        case 1: return launch_t<R, CD, 1>(L, st);
-        case 2: return launch_t<R, CD, 2>(L, st);
-        case 3: return launch_t<R, CD, 3>(L, st);
-        case 4: return launch_t<R, CD, 4>(L, st);
+        case 0: return launch_t<R, LP, 0>(L, st);
+        case 1: return launch_t<R, LP, 1>(L, st);
+        case 2: return launch_t<R, LP, 2>(L, st);
+        case 3: return launch_t<R, LP, 3>(L, st);
+        case 4: return launch_t<R, LP, 4>(L, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t launch_lap(const StageLaunch& L, cudaStream_t st) {
+    switch (L.lap) {
+        case 0: return launch_stage<R, 0>(L, st);
+        case 1: return launch_stage<R, 1>(L, st);
+        case 2: return launch_stage<R, 2>(L, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -149,9 +192,7 @@ cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st) {
 
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st) {
     if (stage_2d_tma_eligible(L)) return launch_stage_2d_tma(L, st);
-    const bool cd = L.lap == 1;
-    if (L.prec == 0) return cd ? launch_stage<float, true>(L, st) : launch_stage<float, false>(L, st);
-    return cd ? launch_stage<double, true>(L, st) : launch_stage<double, false>(L, st);
+    return L.prec == 0 ? launch_lap<float>(L, st) : launch_lap<double>(L, st);
 }
 
 }  // namespace nlse

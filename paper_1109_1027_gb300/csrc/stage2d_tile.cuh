@@ -21,6 +21,13 @@
 //                           boundary points D_b of Eq. (dbc_lap);
 //   step 2 (Eq. 2d2shocs2): Lap = D_c - (1/12) sum of the four axial D
 //                           + (1/(6h^2)) (four corner Psi - 4 Psi_c);
+// With the multi-storage form (LP = 2) step 1 keeps the two second
+// differences apart, Eq. (2d2shocMs1), D^y in the register window and D^x in
+// the shared ring, and step 2 is Eq. (2d2shocMs2):
+//   Lap = (7/6)(D^x_c + D^y_c) - (1/12)(D^x of the two x neighbours + D^y of
+//   the two y neighbours);
+// at a point on the boundary of one axis only, that axis' D^a is D_b of
+// Eq. (dbc_lap) minus the other axis' second difference.
 //   F = i[a Lap + (s|Psi|^2 - V) Psi] (Sec. 3.1), F_b = 0 (Eq. dbc_ut);
 //   the RK4 stage epilogue (Eq. RK4, accumulated-increment form).
 // Complex64 arithmetic uses the packed f32x2 instructions.  Every mbarrier
@@ -84,12 +91,14 @@ __device__ __forceinline__ void st2(float2* p, Two<float2> v) {
 }
 __device__ __forceinline__ void st2(double2* p, Two<double2> v) { p[0] = v.a; p[1] = v.b; }
 
-template <typename R, bool CD, int STAGE, int NT, int TY>
+// LP: 0 single-storage 2SHOC, 1 CD, 2 multi-storage 2SHOC.
+template <typename R, int LP, int STAGE, int NT, int TY>
 __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUtensorMap* m_in2,
                                              const CUtensorMap* m_V, const CUtensorMap* m_psi,
                                              const CUtensorMap* m_acc, const CUtensorMap* m_lo,
                                              const StageIO<R>& io, const Coef<R>& c, const int nx, const int ny,
                                              const int x0, const int y0, const int dir) {
+    constexpr bool CD = LP == 1, MS = LP == 2;
     constexpr int TXC = 2 * NT;          // columns per CTA
     constexpr int HB = TXC;              // first input TMA box: x0-2 .. x0+TXC-3; the second: 4 points
     using C = cplx<R>;
@@ -162,7 +171,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         if (ok) ok = mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kWaitNs);
     };
 
-    const C m4 = pair<C>(-4, -4), m12 = pair<C>(R(-1.0 / 12.0), R(-1.0 / 12.0));
+    const C m4 = pair<C>(-4, -4), m2 = pair<C>(-2, -2), m12 = pair<C>(R(-1.0 / 12.0), R(-1.0 / 12.0));
+    const C c76 = pair<C>(R(7.0 / 6.0), R(7.0 / 6.0));
     const C ih2 = pair<C>(c.inv_h2, c.inv_h2), i6h2 = pair<C>(c.inv_6h2, c.inv_6h2);
     const C a2 = pair<C>(c.a, c.a);
     const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
@@ -176,6 +186,21 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
 
+    // Multi-storage step 1 at grid point (x, r): (D^x, D^y).  Outside the grid:
+    // 0; on the boundary of both axes: 0 (never used).
+    auto ms_point = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> Two<C> {
+        if (x < 0 || x >= nx || r < 0 || r >= ny) return {czero<C>(), czero<C>()};
+        Two<C> d{mul2(fma2(m2, ctr, add2(lf, rt)), ih2), mul2(fma2(m2, ctr, add2(up, dn)), ih2)};
+        const bool bx = x == 0 || x == nx - 1, by = r == 0 || r == ny - 1;
+        if (bx || by) {
+            const C lb = dirichlet_D(c, ctr, io.V[(int64_t)r * nx + x]);
+            if (bx && by) d = {czero<C>(), czero<C>()};
+            else if (bx) d.a = sub2(lb, d.b);
+            else d.b = sub2(lb, d.a);
+        }
+        return d;
+    };
+
     const int xa = x0 + 2 * t;                   // this thread's columns xa, xa + 1
     const int k = 2 * t + 2;                     // xa in the row buffers
     const bool xin = xa < nx;                    // nx is even: then xa + 1 < nx too
@@ -185,7 +210,25 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     bool alive = __syncthreads_and(ok);
     T2 cm, c0, c1, dm, d0;
     C lm, rm, l0, r0;
-    if (alive) {
+    T2 dx0;                                      // multi storage: D^x of row y (D^y is in dm, d0, d1)
+    if (alive && MS) {
+        const C* q0 = irow(0); const C* q1 = irow(1); const C* q2 = irow(2); const C* q3 = irow(3);
+        const T2 cmm = ld2(q0 + k);
+        cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
+        lm = q1[k - 1]; rm = q1[k + 2];
+        l0 = q2[k - 1]; r0 = q2[k + 2];
+        const int yb = ybase - dir;
+        dm.a = ms_point(xa, yb, cm.a, cmm.a, c0.a, lm, cm.b).b;
+        dm.b = ms_point(xa + 1, yb, cm.b, cmm.b, c0.b, cm.a, rm).b;
+        const Two<C> pa = ms_point(xa, ybase, c0.a, cm.a, c1.a, l0, c0.b);
+        const Two<C> pb = ms_point(xa + 1, ybase, c0.b, cm.b, c1.b, c0.a, r0);
+        dx0 = T2{pa.a, pb.a};
+        d0 = T2{pa.b, pb.b};
+        C* drow = dring;                                   // D^x of input row 2 -> ring row 0
+        st2(drow + k, dx0);
+        if (t == 0) drow[1] = ms_point(x0 - 1, ybase, l0, q1[1], q3[1], q2[0], c0.a).a;
+        if (t == NT - 1) drow[TXC + 2] = ms_point(x0 + TXC, ybase, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]).a;
+    } else if (alive) {
         const C* q0 = irow(0); const C* q1 = irow(1); const C* q2 = irow(2); const C* q3 = irow(3);
         const T2 cmm = ld2(q0 + k);
         cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
@@ -224,13 +267,23 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         const C* q2 = irow(j + 2);
         const T2 c2 = ld2(q2 + k);
         const C l1 = q1[k - 1], r1 = q1[k + 2];
-        T2 d1;
-        d1.a = dpoint(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
-        d1.b = dpoint(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+        T2 d1, dx1;
         C* dn = dring + ((j + 1) & 1) * L::ROW;
-        st2(dn + k, d1);
-        if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
-        if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+        if constexpr (MS) {
+            const Two<C> pa = ms_point(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
+            const Two<C> pb = ms_point(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+            dx1 = T2{pa.a, pb.a};
+            d1 = T2{pa.b, pb.b};
+            st2(dn + k, dx1);
+            if (t == 0) dn[1] = ms_point(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a).a;
+            if (t == NT - 1) dn[TXC + 2] = ms_point(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]).a;
+        } else {
+            d1.a = dpoint(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
+            d1.b = dpoint(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+            st2(dn + k, d1);
+            if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
+            if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+        }
         if (NEED_E) wait_e(i);
         if (!__syncthreads_and(ok)) { alive = false; break; }
 
@@ -239,7 +292,17 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
             const bool rowb = y == 0 || y == ny - 1;
             const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
             T2 lap = d0;
-            if (!CD) {
+            if constexpr (MS) {
+                // dr holds D^x of row y; d0 / dm / d1 hold D^y of rows y, y -+ 1.
+                const C sa = add2(add2(dr[k - 1], dx0.b), add2(dm.a, d1.a));
+                const C sb = add2(add2(dx0.a, dr[k + 2]), add2(dm.b, d1.b));
+                lap.a = fma2(c76, add2(dx0.a, d0.a), mul2(m12, sa));
+                lap.b = fma2(c76, add2(dx0.b, d0.b), mul2(m12, sb));
+                if (STAGE == 0) {
+                    if (ba) lap.a = dirichlet_D(c, c0.a, io.V[(int64_t)y * nx + xa]);
+                    if (bb) lap.b = dirichlet_D(c, c0.b, io.V[(int64_t)y * nx + xa + 1]);
+                }
+            } else if (!CD) {
                 const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));
                 const C dsb = add2(add2(d0.a, dr[k + 2]), add2(dm.b, d1.b));
                 const C cna = add2(add2(lm, cm.b), add2(l1, c1.b));
@@ -294,6 +357,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         lm = l0; rm = r0; l0 = l1; r0 = r1;
         cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
+        if constexpr (MS) dx0 = dx1;
     }
 
     if (!alive) {

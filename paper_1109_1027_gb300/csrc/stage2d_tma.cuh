@@ -17,20 +17,20 @@ constexpr int TXC = 2 * NT;          // columns per CTA
 constexpr int HB = TXC;              // first input TMA box; the second is 4 points
 constexpr int HB2 = 4;
 
-template <typename R, bool CD, int STAGE, int TY>
+template <typename R, int LP, int STAGE, int TY>
 __global__ void __launch_bounds__(NT)
 stage2d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_in2,
                    const __grid_constant__ CUtensorMap m_V,
                    const __grid_constant__ CUtensorMap m_psi, const __grid_constant__ CUtensorMap m_acc,
                    const __grid_constant__ CUtensorMap m_lo, const StageIO<R> io, const Coef<R> c,
                    const int nx, const int ny, const int dir) {
-    tile2d::stage2d_tile<R, CD, STAGE, NT, TY>(&m_in, &m_in2, &m_V, &m_psi, &m_acc, &m_lo, io, c, nx, ny,
+    tile2d::stage2d_tile<R, LP, STAGE, NT, TY>(&m_in, &m_in2, &m_V, &m_psi, &m_acc, &m_lo, io, c, nx, ny,
                                                blockIdx.x * TXC, blockIdx.y * TY, dir);
 }
 
 // ---- host side -------------------------------------------------------------
 
-template <typename R, bool CD, int STAGE, int TY>
+template <typename R, int LP, int STAGE, int TY>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     using tile2d::Lay;
     const int nx = (int)L.n[0], ny = (int)L.n[1];
@@ -44,7 +44,7 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
             return cudaErrorInvalidValue;
     }
     if (STAGE == 4 && sizeof(R) == 4 && !complex_map<R>(&m_lo, L.lo, nx, ny, TXC)) return cudaErrorInvalidValue;
-    auto kern = stage2d_tma_kernel<R, CD, STAGE, TY>;
+    auto kern = stage2d_tma_kernel<R, LP, STAGE, TY>;
     const int smem = Lay<R, NT>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -59,23 +59,31 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename R, bool CD, int TY>
+template <typename R, int LP, int TY>
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     switch (L.stage) {
-        case 0: return launch_t<R, CD, 0, TY>(L, st);
-        case 1: return launch_t<R, CD, 1, TY>(L, st);
-        case 2: return launch_t<R, CD, 2, TY>(L, st);
-        case 3: return launch_t<R, CD, 3, TY>(L, st);
-        case 4: return launch_t<R, CD, 4, TY>(L, st);
+        case 0: return launch_t<R, LP, 0, TY>(L, st);
+        case 1: return launch_t<R, LP, 1, TY>(L, st);
+        case 2: return launch_t<R, LP, 2, TY>(L, st);
+        case 3: return launch_t<R, LP, 3, TY>(L, st);
+        case 4: return launch_t<R, LP, 4, TY>(L, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename R, int TY>
+cudaError_t launch_lap(const StageLaunch& L, cudaStream_t st) {
+    switch (L.lap) {
+        case 0: return launch_stage<R, 0, TY>(L, st);
+        case 1: return launch_stage<R, 1, TY>(L, st);
+        case 2: return launch_stage<R, 2, TY>(L, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <int TY>
 cudaError_t launch_rows(const StageLaunch& L, cudaStream_t st) {
-    const bool cd = L.lap == 1;
-    if (L.prec == 0) return cd ? launch_stage<float, true, TY>(L, st) : launch_stage<float, false, TY>(L, st);
-    return cd ? launch_stage<double, true, TY>(L, st) : launch_stage<double, false, TY>(L, st);
+    return L.prec == 0 ? launch_lap<float, TY>(L, st) : launch_lap<double, TY>(L, st);
 }
 
 }  // namespace tma2d

@@ -136,8 +136,152 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     }
 }
 
+// The multi-storage form, Eqs. (3d2shocMs1) and (3d2shocMs2), on the same
+// 2.5D walk.  Per plane z: D^x and D^y of plane z on the tile plus a 1-point
+// ring (one shared buffer each); D^z of this thread's two points of plane
+// z+1 (registers, with those of z and z-1 kept from earlier planes);
+//     Lap = (7/6)(D^x + D^y + D^z)_c - (1/12)(D^x_E + D^x_W + D^y_N + D^y_S
+//                                             + D^z_{z+1} + D^z_{z-1}).
+// At a point on the boundary of one axis only, that axis' D^a is D_b of
+// Eq. (dbc_lap) minus the other axes' second differences; points on two or
+// more boundaries take 0 (never used).
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(NT)
+stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
+    using C = cplx<R>;
+    constexpr int PPT = TX * TY / NT;         // points per thread (2)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sP = reinterpret_cast<C*>(smem_raw);   // [4][PY][PX]
+    C* sDx = sP + 4 * PP;                     // [DY][DX]
+    C* sDy = sDx + DP;                        // [DY][DX]
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int z1 = min(z0 + TZ, nz);
+    const int tid = threadIdx.x;
+    const int64_t plane = (int64_t)nx * ny;
+
+    auto load_plane = [&](int gz) {
+        C* dst = sP + pslot(gz) * PP;
+        const bool zin = gz >= 0 && gz < nz;
+        for (int i = tid; i < PP; i += NT) {
+            int ly = i / PX, lx = i - ly * PX;
+            int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
+            C v = czero<C>();
+            if (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                v = io.yin[gz * plane + (int64_t)gy * nx + gx];
+            dst[i] = v;
+        }
+    };
+    auto d2 = [&](C m, C ctr, C p) { return cscale(c.inv_h2, csub(cadd(m, p), cscale((R)2, ctr))); };
+    // (D^x, D^y, D^z) at a grid point from its seven stencil values (k: index
+    // in the input planes pm / pc / pp), with the boundary split.
+    struct D3 { C x, y, z; };
+    auto ms_point = [&](int gx, int gy, int gz, const C* pm, const C* pc, const C* pp, int k) -> D3 {
+        const C zero = czero<C>();
+        if (gz < 0 || gz >= nz || gx < 0 || gx >= nx || gy < 0 || gy >= ny) return {zero, zero, zero};
+        const C ctr = pc[k];
+        D3 d{d2(pc[k - 1], ctr, pc[k + 1]), d2(pc[k - PX], ctr, pc[k + PX]), d2(pm[k], ctr, pp[k])};
+        const bool bx = gx == 0 || gx == nx - 1, by = gy == 0 || gy == ny - 1, bz = gz == 0 || gz == nz - 1;
+        const int nb = (int)bx + (int)by + (int)bz;
+        if (nb) {
+            const C lb = dirichlet_D(c, ctr, io.V[gz * plane + (int64_t)gy * nx + gx]);
+            if (nb > 1) d = {zero, zero, zero};
+            else if (bx) d.x = csub(csub(lb, d.y), d.z);
+            else if (by) d.y = csub(csub(lb, d.x), d.z);
+            else d.z = csub(csub(lb, d.x), d.y);
+        }
+        return d;
+    };
+    // D^z of this thread's m-th point at plane gz (input planes gz-1 .. gz+1 loaded).
+    auto dz_own = [&](int m, int gz) -> C {
+        const int i = tid + m * NT, ly = i / TX, lx = i - ly * TX;
+        const int k = (ly + 2) * PX + (lx + 2);
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) return czero<C>();
+        return ms_point(gx, gy, gz, sP + pslot(gz - 1) * PP, sP + pslot(gz) * PP, sP + pslot(gz + 1) * PP, k).z;
+    };
+
+    for (int gz = z0 - 2; gz <= z0 + 1; ++gz) load_plane(gz);
+    __syncthreads();
+    C dzm[PPT], dz0[PPT];
+#pragma unroll
+    for (int m = 0; m < PPT; ++m) {
+        dzm[m] = dz_own(m, z0 - 1);
+        dz0[m] = dz_own(m, z0);
+    }
+
+    bool bad = false;
+    for (int gz = z0; gz < z1; ++gz) {
+        load_plane(gz + 2);
+        // D^x, D^y of plane gz on the tile plus a 1-point ring.
+        {
+            const C* pm = sP + pslot(gz - 1) * PP;
+            const C* pc = sP + pslot(gz) * PP;
+            const C* pp = sP + pslot(gz + 1) * PP;
+            for (int i = tid; i < DP; i += NT) {
+                int ly = i / DX, lx = i - ly * DX;
+                const D3 d = ms_point(x0 - 1 + lx, y0 - 1 + ly, gz, pm, pc, pp, (ly + 1) * PX + (lx + 1));
+                sDx[i] = d.x;
+                sDy[i] = d.y;
+            }
+        }
+        __syncthreads();
+        const C* pc = sP + pslot(gz) * PP;
+        const bool zb = gz == 0 || gz == nz - 1;
+#pragma unroll
+        for (int m = 0; m < PPT; ++m) {
+            const int i = tid + m * NT, ly = i / TX, lx = i - ly * TX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            const C dz1 = dz_own(m, gz + 1);
+            if (gx < nx && gy < ny) {
+                const int64_t p = gz * plane + (int64_t)gy * nx + gx;
+                const int k = (ly + 2) * PX + (lx + 2);
+                const int kd = (ly + 1) * DX + (lx + 1);
+                const C y = pc[k];
+                const bool bnd = zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1;
+                C lap;
+                if (bnd) {
+                    lap = dirichlet_D(c, y, io.V[p]);
+                } else {
+                    const C nbs = cadd(cadd(cadd(sDx[kd - 1], sDx[kd + 1]), cadd(sDy[kd - DX], sDy[kd + DX])),
+                                       cadd(dzm[m], dz1));
+                    const C ctr = cadd(cadd(sDx[kd], sDy[kd]), dz0[m]);
+                    lap = csub(cscale((R)(7.0 / 6.0), ctr), cscale((R)(1.0 / 12.0), nbs));
+                }
+                if constexpr (STAGE == 0) {
+                    io.lap[p] = lap;
+                } else {
+                    C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[p]);
+                    bad |= stage_epilogue<STAGE>(io, p, y, F);
+                }
+            }
+            dzm[m] = dz0[m];
+            dz0[m] = dz1;
+        }
+        __syncthreads();
+    }
+    if constexpr (STAGE == 4) {
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(io.flag, 1);
+    }
+}
+
+template <typename R, int STAGE>
+cudaError_t launch_ms(const StageLaunch& L, cudaStream_t st) {
+    const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
+    dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ);
+    size_t smem = sizeof(cplx<R>) * (4 * PP + 2 * DP);
+    auto kern = stage3d_ms_kernel<R, STAGE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, NT, smem, st>>>(make_io<R>(L), make_coef<R>(L.h, L.a, L.s), nx, ny, nz);
+    return cudaGetLastError();
+}
+
 template <typename R, bool CD, int STAGE>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
+    if (!CD && L.lap == 2) return launch_ms<R, STAGE>(L, st);
     const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ);
     size_t smem = sizeof(cplx<R>) * (4 * PP + 3 * DP);

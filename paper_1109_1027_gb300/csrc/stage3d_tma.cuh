@@ -21,6 +21,14 @@
 //                          + (1/(6h^2)) (sum of the twelve edge Psi - 12 Psi_c);
 //   F = i[a Lap + (s|Psi|^2 - V) Psi] (Sec. 3.1), F_b = 0 (Eq. dbc_ut);
 //   the RK4 stage epilogue (Eq. RK4, accumulated-increment form).
+// With the multi-storage form (LP = 2), step 1 keeps the three second
+// differences apart, Eq. (3d2shocMs1): D^z in the register window, D^x and
+// D^y in two shared rings (with the x and the y halo respectively), the
+// Dirichlet D_b split over them at points on the boundary of one axis
+// (D^a_b = D_b minus the other axes' second differences); step 2 is
+// Eq. (3d2shocMs2): Lap = (7/6)(D^x + D^y + D^z)_c - (1/12)(the two axial
+// neighbours of each D^a along its own axis).  Its step 2 reads no input
+// plane, so a 4-slot input ring suffices and the two D rings fit.
 // Consecutive stages walk z in opposite directions so that each starts on
 // planes the previous one wrote last.  Every mbarrier wait is bounded (1 s);
 // on timeout the CTA sets bit 2 of the status flag, lets its copies land and
@@ -38,13 +46,13 @@ constexpr int TX = 32, TY = 16;
 constexpr int TXP = TX / 2;                  // thread columns (pairs)
 constexpr int NT = TXP * TY;                 // 256 threads
 constexpr int PW = TX + 4, PH = TY + 4;      // input plane with a 2-point halo (36 x 20)
-constexpr int S = 5;                         // input ring slots
-constexpr int NHALO = 2 * TY + 2 * TX;       // D halo points per plane (96)
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint64_t kDrainNs = 50000000ull;
 
 constexpr int al128(int v) { return (v + 127) / 128 * 128; }
 
+// S input-ring slots, ND D-plane buffers.
+template <int S, int ND>
 struct Lay3 {
     static constexpr int CB = 8;                                  // complex64
     static constexpr int IN_BYTES = PW * PH * CB;                 // 5760
@@ -56,7 +64,7 @@ struct Lay3 {
     static constexpr int IN_OFF = 0;
     static constexpr int E_OFF = S * IN_SLOT;
     static constexpr int D_OFF = E_OFF + 2 * E_SLOT;              // D planes use the input-plane indexing
-    static constexpr int BAR_OFF = al128(D_OFF + 2 * IN_BYTES);
+    static constexpr int BAR_OFF = al128(D_OFF + ND * IN_BYTES);
     static constexpr int TOTAL = BAR_OFF + 8 * (S + 2) + 128;
 };
 
@@ -71,14 +79,22 @@ __device__ __forceinline__ void st2(float2* p, Two v) {
     *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
 
-template <bool CD, int STAGE, int TZ>
+// LP: 0 single-storage 2SHOC, 1 CD, 2 multi-storage 2SHOC.
+template <int LP> struct Ring3 {
+    static constexpr int S = LP == 2 ? 4 : 5;                     // input ring slots
+    using L = Lay3<S, LP == 2 ? 4 : 2>;
+};
+
+template <int LP, int STAGE, int TZ>
 __global__ void __launch_bounds__(NT, 3)      // three CTAs per SM (shared memory allows three)
 stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_constant__ CUtensorMap m_V,
                    const __grid_constant__ CUtensorMap m_psi, const __grid_constant__ CUtensorMap m_acc,
                    const __grid_constant__ CUtensorMap m_lo, const StageIO<float> io, const Coef<float> c,
                    const int nx, const int ny, const int nz, const int dir) {
     using C = float2;
-    using L = Lay3;
+    constexpr bool CD = LP == 1, MS = LP == 2;
+    constexpr int S = Ring3<LP>::S;
+    using L = typename Ring3<LP>::L;
     constexpr bool NEED_E = STAGE >= 1;
     constexpr bool NEED_PA = STAGE >= 2;
     constexpr bool NEED_LO = STAGE == 4;
@@ -149,6 +165,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
 
     const C m6 = pair<C>(-6.f, -6.f), m12 = pair<C>(-1.f / 12.f, -1.f / 12.f), c10 = pair<C>(10.f / 12.f, 10.f / 12.f);
     const C m12c = pair<C>(-12.f, -12.f);
+    const C m2 = pair<C>(-2.f, -2.f), c76 = pair<C>(7.f / 6.f, 7.f / 6.f);
     const C ih2 = pair<C>(c.inv_h2, c.inv_h2), i6h2 = pair<C>(c.inv_6h2, c.inv_6h2);
     const C a2 = pair<C>(c.a, c.a);
     const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
@@ -159,6 +176,24 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         if (out) return czero<C>();
         if (bnd) return dirichlet_D(c, ctr, io.V[gp]);
         return mul2(fma2(m6, ctr, s6), ih2);
+    };
+    // Multi-storage step 1 at one point, (D^x, D^y, D^z), from the centre and
+    // the neighbour sums along x, y, z; the Dirichlet split at points on the
+    // boundary of one axis; 0 outside the grid and where two or more axes are
+    // on the boundary (never used by an interior Laplacian).
+    struct D3 { C x, y, z; };
+    auto ms_val = [&](bool out, bool bx, bool by, bool bz, int64_t gp, C ctr, C xs, C ys, C zs) -> D3 {
+        if (out) return {czero<C>(), czero<C>(), czero<C>()};
+        D3 d{mul2(fma2(m2, ctr, xs), ih2), mul2(fma2(m2, ctr, ys), ih2), mul2(fma2(m2, ctr, zs), ih2)};
+        const int nb = (int)bx + (int)by + (int)bz;
+        if (nb) {
+            const C lb = dirichlet_D(c, ctr, io.V[gp]);
+            if (nb > 1) d = {czero<C>(), czero<C>(), czero<C>()};
+            else if (bx) d.x = sub2(sub2(lb, d.y), d.z);
+            else if (by) d.y = sub2(sub2(lb, d.x), d.z);
+            else d.z = sub2(sub2(lb, d.x), d.y);
+        }
+        return d;
     };
     auto xout = [&](int x) { return x < 0 || x >= nx; };
     auto yout = [&](int y) { return y < 0 || y >= ny; };
@@ -178,7 +213,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     if (t < TY) { hy = y0 + t; hx = x0 - 1; hk = (t + 2) * PW + 1; }
     else if (t < 2 * TY) { hy = y0 + t - TY; hx = x0 + TX; hk = (t - TY + 2) * PW + TX + 2; }
     else if (t < 2 * TY + TX) { hx = x0 + t - 2 * TY; hy = y0 - 1; hk = PW + (t - 2 * TY) + 2; }
-    else if (t < NHALO) { hx = x0 + t - 2 * TY - TX; hy = y0 + TY; hk = (TY + 2) * PW + (t - 2 * TY - TX) + 2; }
+    else if (t < 2 * TY + 2 * TX) { hx = x0 + t - 2 * TY - TX; hy = y0 + TY; hk = (TY + 2) * PW + (t - 2 * TY - TX) + 2; }
     const bool hout = xout(hx) || yout(hy), hbnd = xbnd(hx) || ybnd(hy);
     auto halo_d = [&](int j, int z) -> C {
         const C* pc = iplane(j);
@@ -186,6 +221,12 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         const C s6 = add2(add2(add2(pc[hk - 1], pc[hk + 1]), add2(pc[hk - PW], pc[hk + PW])),
                           add2(iplane(j - 1)[hk], iplane(j + 1)[hk]));
         return dval(o, b, ((int64_t)z * ny + hy) * nx + hx, pc[hk], s6);
+    };
+    auto halo_ms = [&](int j, int z) -> D3 {
+        const C* pc = iplane(j);
+        return ms_val(hout || zout(z), xbnd(hx), ybnd(hy), zbnd(z), ((int64_t)z * ny + hy) * nx + hx, pc[hk],
+                      add2(pc[hk - 1], pc[hk + 1]), add2(pc[hk - PW], pc[hk + PW]),
+                      add2(iplane(j - 1)[hk], iplane(j + 1)[hk]));
     };
     // In-plane axial neighbours of this thread's pair in input plane j.
     struct Nbr { Two up, dn; C l, r; };
@@ -210,11 +251,43 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         return d;
     };
 
+    // Multi-storage step 1 of this thread's pair at input plane j (grid plane
+    // z): D^x and D^y out, D^z returned.
+    const bool bxa = xbnd(xa), bxb = xbnd(xa + 1), byy = ybnd(y);
+    auto pair_ms = [&](const Nbr& nb, int z, Two cm, Two cc, Two cp, Two& dx, Two& dy) -> Two {
+        const bool zo = zout(z), zb = zbnd(z);
+        const int64_t gp = ((int64_t)z * ny + y) * nx + xa;
+        const D3 pa = ms_val(oa || zo, bxa, byy, zb, gp, cc.a, add2(nb.l, cc.b), add2(nb.up.a, nb.dn.a),
+                             add2(cm.a, cp.a));
+        const D3 pb = ms_val(ob || zo, bxb, byy, zb, gp + 1, cc.b, add2(cc.a, nb.r), add2(nb.up.b, nb.dn.b),
+                             add2(cm.b, cp.b));
+        dx = Two{pa.x, pb.x};
+        dy = Two{pa.y, pb.y};
+        return Two{pa.z, pb.z};
+    };
+    // Multi storage: D^x ring (2 planes, x halo) then D^y ring (2 planes, y halo).
+    C* dxring = dring;
+    C* dyring = dring + 2 * (PW * PH);
+
     // Prologue: input planes 0 .. 3 (z0-2 .. z0+1 in walk order).
     wait_in(0); wait_in(1); wait_in(2); wait_in(3);
     bool alive = __syncthreads_and(ok);
     Two cm, c0, c1, dm, d0, qm, q0;
-    if (alive) {
+    Two dx0, dy0;                                 // multi storage: D^x, D^y at plane z (D^z in dm, d0, d1)
+    if (alive && MS) {
+        const Two cmm = ld2(iplane(0) + k);
+        cm = ld2(iplane(1) + k); c0 = ld2(iplane(2) + k); c1 = ld2(iplane(3) + k);
+        Two ux, uy;
+        dm = pair_ms(nbrs(1), zbase - dir, cmm, cm, c0, ux, uy);
+        d0 = pair_ms(nbrs(2), zbase, cm, c0, c1, dx0, dy0);
+        st2(dxring + k, dx0);
+        st2(dyring + k, dy0);
+        if (hk >= 0) {
+            const D3 hd = halo_ms(2, zbase);
+            if (t < 2 * TY) dxring[hk] = hd.x;
+            else dyring[hk] = hd.y;
+        }
+    } else if (alive) {
         const Two cmm = ld2(iplane(0) + k);
         cm = ld2(iplane(1) + k); c0 = ld2(iplane(2) + k); c1 = ld2(iplane(3) + k);
         dm = pair_d(nbrs(1), zbase - dir, cmm, cm, c0, qm);
@@ -223,6 +296,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         if (hk >= 0) dring[hk] = halo_d(2, zbase);
     }
     __syncthreads();
+    // With a 4-slot ring, input plane 4 reuses plane 0's slot, free only now.
+    if (S == 4 && t == 0 && next < jmax) issue_in(next++);
 
     bool bad = false;
 #pragma unroll 3
@@ -239,10 +314,25 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         // D of the plane ahead (za).
         const Two c2 = ld2(iplane(j + 2) + k);
         Two q1;                                  // also the z+1 edge terms of Lap(z)
-        const Two d1 = pair_d(nbrs(j + 1), za, c0, c1, c2, q1);
-        C* dn = dring + ((j + 1) & 1) * (PW * PH);
-        st2(dn + k, d1);
-        if (hk >= 0) dn[hk] = halo_d(j + 1, za);
+        Two dx1, dy1;
+        Two d1;
+        if constexpr (MS) {
+            d1 = pair_ms(nbrs(j + 1), za, c0, c1, c2, dx1, dy1);
+            C* dxn = dxring + ((j + 1) & 1) * (PW * PH);
+            C* dyn = dyring + ((j + 1) & 1) * (PW * PH);
+            st2(dxn + k, dx1);
+            st2(dyn + k, dy1);
+            if (hk >= 0) {
+                const D3 hd = halo_ms(j + 1, za);
+                if (t < 2 * TY) dxn[hk] = hd.x;
+                else dyn[hk] = hd.y;
+            }
+        } else {
+            d1 = pair_d(nbrs(j + 1), za, c0, c1, c2, q1);
+            C* dn = dring + ((j + 1) & 1) * (PW * PH);
+            st2(dn + k, d1);
+            if (hk >= 0) dn[hk] = halo_d(j + 1, za);
+        }
         if (NEED_E) wait_e(i);
         if (!__syncthreads_and(ok)) { alive = false; break; }
 
@@ -252,7 +342,21 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
             const bool zb = zbnd(z);
             const bool bA = ba || zb, bB = bb || zb;
             Two lap = d0;
-            if (!CD) {
+            if constexpr (MS) {
+                // D^x of the x neighbours, D^y of the y neighbours, D^z of the z neighbours
+                const C* dxz = dxring + (j & 1) * (PW * PH);
+                const C* dyz = dyring + (j & 1) * (PW * PH);
+                const Two dyu = ld2(dyz + k - PW), dyd = ld2(dyz + k + PW);
+                const C sa = add2(add2(add2(dxz[k - 1], dx0.b), add2(dyu.a, dyd.a)), add2(dm.a, d1.a));
+                const C sb = add2(add2(add2(dx0.a, dxz[k + 2]), add2(dyu.b, dyd.b)), add2(dm.b, d1.b));
+                lap.a = fma2(c76, add2(add2(dx0.a, dy0.a), d0.a), mul2(m12, sa));
+                lap.b = fma2(c76, add2(add2(dx0.b, dy0.b), d0.b), mul2(m12, sb));
+                if (STAGE == 0) {
+                    const int64_t pg = ((int64_t)z * ny + y) * nx + xa;
+                    if (bA) lap.a = dirichlet_D(c, c0.a, io.V[pg]);
+                    if (bB) lap.b = dirichlet_D(c, c0.b, io.V[pg + 1]);
+                }
+            } else if (!CD) {
                 // six axial D
                 const Two dup = ld2(dz + k - PW), ddn = ld2(dz + k + PW);
                 const C dsa = add2(add2(add2(dz[k - 1], d0.b), add2(dup.a, ddn.a)), add2(dm.a, d1.a));
@@ -307,7 +411,11 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         }
         cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
-        qm = q0; q0 = q1;
+        if constexpr (MS) {
+            dx0 = dx1; dy0 = dy1;
+        } else {
+            qm = q0; q0 = q1;
+        }
     }
 
     if (!alive) {
@@ -334,7 +442,7 @@ inline bool map3(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const v
     return encode(m, type, 3, base, dims, strides, box);
 }
 
-template <bool CD, int STAGE, int TZ>
+template <int LP, int STAGE, int TZ>
 cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
     const CUtensorMapDataType CX = CU_TENSOR_MAP_DATA_TYPE_UINT64, RF = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -346,8 +454,8 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
                        !map3(&m_acc, CX, 8, L.acc, nx, ny, nz, TX, TY)))
         return cudaErrorInvalidValue;
     if (STAGE == 4 && !map3(&m_lo, CX, 8, L.lo, nx, ny, nz, TX, TY)) return cudaErrorInvalidValue;
-    auto kern = stage3d_tma_kernel<CD, STAGE, TZ>;
-    const int smem = Lay3::TOTAL;
+    auto kern = stage3d_tma_kernel<LP, STAGE, TZ>;
+    const int smem = Ring3<LP>::L::TOTAL;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // Consecutive stages walk z in opposite directions.
@@ -358,21 +466,26 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <bool CD, int TZ>
+template <int LP, int TZ>
 cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     switch (L.stage) {
-        case 0: return launch_t<CD, 0, TZ>(L, st);
-        case 1: return launch_t<CD, 1, TZ>(L, st);
-        case 2: return launch_t<CD, 2, TZ>(L, st);
-        case 3: return launch_t<CD, 3, TZ>(L, st);
-        case 4: return launch_t<CD, 4, TZ>(L, st);
+        case 0: return launch_t<LP, 0, TZ>(L, st);
+        case 1: return launch_t<LP, 1, TZ>(L, st);
+        case 2: return launch_t<LP, 2, TZ>(L, st);
+        case 3: return launch_t<LP, 3, TZ>(L, st);
+        case 4: return launch_t<LP, 4, TZ>(L, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <int TZ>
 cudaError_t launch_planes(const StageLaunch& L, cudaStream_t st) {
-    return L.lap == 1 ? launch_stage<true, TZ>(L, st) : launch_stage<false, TZ>(L, st);
+    switch (L.lap) {
+        case 0: return launch_stage<0, TZ>(L, st);
+        case 1: return launch_stage<1, TZ>(L, st);
+        case 2: return launch_stage<2, TZ>(L, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace tma3d

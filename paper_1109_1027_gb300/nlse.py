@@ -23,7 +23,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(8)
 BC = {"dirichlet": 0, "msd": 1}
 PREC = {"fp32": 0, "fp64": 1}
-LAP = {"2shoc": 0, "cd": 1}
+LAP = {"2shoc": 0, "cd": 1, "2shoc_ms": 2}
 FLAG_NO_STABILITY_CHECK = 1
 FLAG_PLAIN_SCHEDULE = 2
 TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW, TILE_1D_RESIDENT = 1, 2, 3, 4

@@ -49,21 +49,21 @@ def _dts(insts, prec):
     return dts
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_batch_equals_single_grid_runs(prec):
+@pytest.mark.parametrize("prec,lap", [("fp32", "2shoc"), ("fp64", "2shoc"), ("fp32", "2shoc_ms"), ("fp64", "2shoc_ms")])
+def test_batch_equals_single_grid_runs(prec, lap):
     insts = _batch(SIDES)
     cdt, rdt = (torch.complex64, torch.float32) if prec == "fp32" else (torch.complex128, torch.float64)
     dts = _dts(insts, prec)
     V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
     bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
-                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec)
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec, lap=lap)
     psi = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
     bs.run(psi, 40)
     bs.check()
     got = [g.cpu().numpy() for g in bs.unpack(psi)]
     for i, q in enumerate(insts):
         Vi = torch.from_numpy(q["V"]).to(DEV).to(rdt).contiguous()
-        sv = nlse.Solver(Vi, q["h"], dts[i], q["a"], q["s"], prec=prec)
+        sv = nlse.Solver(Vi, q["h"], dts[i], q["a"], q["s"], prec=prec, lap=lap)
         x = torch.from_numpy(q["psi"]).to(DEV).to(cdt).contiguous()
         sv.run(x, 40)
         ref = x.cpu().numpy()
@@ -71,21 +71,22 @@ def test_batch_equals_single_grid_runs(prec):
         assert np.abs(got[i] - ref).max() <= tol, (i, q["shape"])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_batch_matches_oracle_on_small_instances(prec):
+@pytest.mark.parametrize("prec,lap", [("fp32", "2shoc"), ("fp64", "2shoc"), ("fp64", "2shoc_ms")])
+def test_batch_matches_oracle_on_small_instances(prec, lap):
     insts = _batch([(64, 64), (40, 68), (33, 64), (17, 132)], seed=11)
     cdt, rdt = (torch.complex64, torch.float32) if prec == "fp32" else (torch.complex128, torch.float64)
     dts = _dts(insts, prec)
     V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
     bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
-                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec)
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec, lap=lap)
     psi = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
     bs.run(psi, 10)
     for i, (g, q) in enumerate(zip(bs.unpack(psi), insts)):
         r = lambda a_, dt_: a_.astype(dt_).astype(np.complex128 if np.iscomplexobj(a_) else np.float64)
         p0 = r(q["psi"], np.complex64) if prec == "fp32" else q["psi"]
         V0 = r(q["V"], np.float32) if prec == "fp32" else q["V"]
-        ref = oracle.run(oracle.Problem(q["shape"], q["h"], q["a"], q["s"]), p0, V0, dts[i], 10)
+        olap = oracle.LAP_2SHOC_MS if lap == "2shoc_ms" else oracle.LAP_2SHOC
+        ref = oracle.run(oracle.Problem(q["shape"], q["h"], q["a"], q["s"], lap=olap), p0, V0, dts[i], 10)
         tol = (1e-12 if prec == "fp64" else 1e-5) * np.abs(ref).max()
         assert np.abs(g.cpu().numpy() - ref).max() <= tol, i
 

@@ -61,8 +61,10 @@ SHAPES = {
     # and z, z spanning two 64-plane chunks); the others the generic kernel
     3: [(3, 3, 3), (9, 20, 37), (35, 18, 40), (70, 33, 19), (70, 40, 100), (5, 17, 64)],
 }
+LAPS = ("2shoc", "cd", "2shoc_ms")
+OLAP = {"2shoc": oracle.LAP_2SHOC, "cd": oracle.LAP_CD, "2shoc_ms": oracle.LAP_2SHOC_MS}
 CASES = [(shape, prec, lap) for d in (1, 2, 3) for shape in SHAPES[d]
-         for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
+         for prec in ("fp64", "fp32") for lap in LAPS]
 
 
 def _problem(shape, seed):
@@ -76,8 +78,7 @@ def test_laplacian_matches_oracle(shape, prec, lap):
     h, a, s = 0.37, 0.8, -1.3
     psi, V = _problem(shape, 100 + len(shape))
     psi_r, V_r = rounded(psi, prec), rounded(V, prec)
-    ref = oracle.laplacian(oracle.Problem(shape, h, a, s, lap=oracle.LAP_CD if lap == "cd" else 0),
-                           psi_r, V_r)
+    ref = oracle.laplacian(oracle.Problem(shape, h, a, s, lap=OLAP[lap]), psi_r, V_r)
     solver = nlse.Solver(to_dev(V, prec), h, 1e-3, a, s, prec=prec, lap=lap)
     got = solver.lap2shoc(to_dev(psi, prec)).cpu().numpy()
     tol = (1e-12 if prec == "fp64" else 2e-6) * lap_scale(psi_r, h, len(shape))
@@ -99,7 +100,7 @@ def test_laplacian_msd_1d_matches_oracle():
 
 
 STEP_CASES = [(shape, prec, lap, "dirichlet") for d in (1, 2, 3) for shape in SHAPES[d][1:]
-              for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
+              for prec in ("fp64", "fp32") for lap in LAPS]
 STEP_CASES += [((n,), prec, "2shoc", "msd") for n in (5, 1030, 3001) for prec in ("fp64", "fp32")]
 
 
@@ -111,8 +112,7 @@ def test_rk4_steps_match_oracle(shape, prec, lap, bc):
     if bc == "msd":
         psi = psi + 2.5
     psi_r, V_r = rounded(psi, prec), rounded(V, prec)
-    prob = oracle.Problem(shape, h, a, s, bc=oracle.BC_MSD if bc == "msd" else 0,
-                          lap=oracle.LAP_CD if lap == "cd" else 0)
+    prob = oracle.Problem(shape, h, a, s, bc=oracle.BC_MSD if bc == "msd" else 0, lap=OLAP[lap])
     _, _, dtmax = oracle.invariants(prob, psi_r, V_r)
     k = 0.5 * dtmax
     nsteps = 5
@@ -456,14 +456,16 @@ def test_compensation_resets_when_the_state_changes():
 
 def test_tiling_variants_give_identical_results():
     from paper_1109_1027_gb300 import autotune
-    for shape, prec, key, values in [((100, 388), "fp32", nlse.TILE_ROWS, (8, 16, 32)),
-                                     ((45, 260), "fp64", nlse.TILE_ROWS, (8, 16, 32)),
-                                     ((70, 40, 100), "fp32", nlse.TILE_PLANES, (32, 64, 128))]:
+    for shape, prec, key, values, lap in [((100, 388), "fp32", nlse.TILE_ROWS, (8, 16, 32), "2shoc"),
+                                          ((45, 260), "fp64", nlse.TILE_ROWS, (8, 16, 32), "2shoc"),
+                                          ((70, 40, 100), "fp32", nlse.TILE_PLANES, (32, 64, 128), "2shoc"),
+                                          ((100, 388), "fp32", nlse.TILE_ROWS, (8, 16, 32), "2shoc_ms"),
+                                          ((70, 40, 100), "fp32", nlse.TILE_PLANES, (32, 64, 128), "2shoc_ms")]:
         psi, V = _problem(shape, 600)
         h, a, s = 0.5, 0.9, -1.0
         prob = oracle.Problem(shape, h, a, s)
         _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
-        solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, prec=prec)
+        solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, prec=prec, lap=lap)
         outs = []
         for v in values:
             solver.set_tiling(key, v)
