@@ -300,10 +300,14 @@ static void laplacian(const or_problem* P, const double* psi, const double* V, d
 /* Right-hand side F(psi) (Sec. 3.1) with the boundary conditions.          */
 /* ------------------------------------------------------------------------ */
 
+/* Doubles of work space that rhs() needs for N points: the Laplacian's D
+ * work space (8N, room for the multi-storage form) and Lap (2N). */
+static long rhs_work_len(long N) { return 10 * N; }
+
 /* F = i [ a Lap psi + (s|psi|^2 - V) psi ] at interior points (Sec. 3.1).
  * Boundary: Dirichlet, Eq. (dbc_ut): F_b = 0.
  *           MSD, Eq. (msdbc_ut): F_b = i Im(F_{b-1} / psi_{b-1}) psi_b.
- * work: 10N doubles (D work space and Lap). */
+ * work: rhs_work_len(N) doubles. */
 static void rhs(const or_problem* P, const double* psi, const double* V, double* F, double* work) {
     long N = npoints(P);
     double* D = work;
@@ -345,7 +349,7 @@ static int rk4_alloc(rk4_space* W, long N) {
     W->Ktot = (double*)malloc(sizeof(double) * 2 * N);
     W->Ktmp = (double*)malloc(sizeof(double) * 2 * N);
     W->ptmp = (double*)malloc(sizeof(double) * 2 * N);
-    W->work = (double*)malloc(sizeof(double) * 10 * N);
+    W->work = (double*)malloc(sizeof(double) * rhs_work_len(N));
     return !(W->Ktot && W->Ktmp && W->ptmp && W->work);
 }
 
@@ -403,7 +407,7 @@ static double stability_dt(const or_problem* P, const double* psi, const double*
     }
     if (P->bc == 1) {
         double* F = (double*)malloc(sizeof(double) * 2 * N);
-        double* work = (double*)malloc(sizeof(double) * 4 * N);
+        double* work = (double*)malloc(sizeof(double) * rhs_work_len(N));
         rhs(P, psi, V, F, work);
         for (long z = 0; z < P->n[2]; ++z)
             for (long y = 0; y < P->n[1]; ++y)
@@ -456,7 +460,7 @@ int oracle_rhs(int dim, const long* n, double h, double a, double s, int bc, int
                const double* psi, const double* V, double* F) {
     or_problem P;
     if (make_problem(&P, dim, n, h, a, s, bc, lap)) return 1;
-    double* work = (double*)malloc(sizeof(double) * 10 * npoints(&P));
+    double* work = (double*)malloc(sizeof(double) * rhs_work_len(npoints(&P)));
     rhs(&P, psi, V, F, work);
     free(work);
     return 0;
