@@ -192,13 +192,21 @@ stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
         }
         return d;
     };
-    // D^z of this thread's m-th point at plane gz (input planes gz-1 .. gz+1 loaded).
+    auto on_bnd = [&](int gx, int gy, int gz) {
+        return gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1 || gz == 0 || gz == nz - 1;
+    };
+    // D^z of this thread's m-th point at plane gz (input planes gz-1 .. gz+1
+    // loaded): the z difference alone, except at the boundary.
     auto dz_own = [&](int m, int gz) -> C {
         const int i = tid + m * NT, ly = i / TX, lx = i - ly * TX;
         const int k = (ly + 2) * PX + (lx + 2);
         const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= nx || gy >= ny) return czero<C>();
-        return ms_point(gx, gy, gz, sP + pslot(gz - 1) * PP, sP + pslot(gz) * PP, sP + pslot(gz + 1) * PP, k).z;
+        if (gx >= nx || gy >= ny || gz < 0 || gz >= nz) return czero<C>();
+        const C* pm = sP + pslot(gz - 1) * PP;
+        const C* pc = sP + pslot(gz) * PP;
+        const C* pp = sP + pslot(gz + 1) * PP;
+        if (on_bnd(gx, gy, gz)) return ms_point(gx, gy, gz, pm, pc, pp, k).z;
+        return d2(pm[k], pc[k], pp[k]);
     };
 
     for (int gz = z0 - 2; gz <= z0 + 1; ++gz) load_plane(gz);
@@ -219,10 +227,20 @@ stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             const C* pc = sP + pslot(gz) * PP;
             const C* pp = sP + pslot(gz + 1) * PP;
             for (int i = tid; i < DP; i += NT) {
-                int ly = i / DX, lx = i - ly * DX;
-                const D3 d = ms_point(x0 - 1 + lx, y0 - 1 + ly, gz, pm, pc, pp, (ly + 1) * PX + (lx + 1));
-                sDx[i] = d.x;
-                sDy[i] = d.y;
+                const int ly = i / DX, lx = i - ly * DX;
+                const int gx = x0 - 1 + lx, gy = y0 - 1 + ly, k = (ly + 1) * PX + (lx + 1);
+                C dx = czero<C>(), dy = czero<C>();
+                if (gx < 0 || gx >= nx || gy < 0 || gy >= ny) {
+                } else if (on_bnd(gx, gy, gz)) {
+                    const D3 d = ms_point(gx, gy, gz, pm, pc, pp, k);
+                    dx = d.x;
+                    dy = d.y;
+                } else {
+                    dx = d2(pc[k - 1], pc[k], pc[k + 1]);
+                    dy = d2(pc[k - PX], pc[k], pc[k + PX]);
+                }
+                sDx[i] = dx;
+                sDy[i] = dy;
             }
         }
         __syncthreads();
