@@ -217,6 +217,7 @@ stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
         dzm[m] = dz_own(m, z0 - 1);
         dz0[m] = dz_own(m, z0);
     }
+    __syncthreads();                          // plane z0-2 is read above and overwritten below
 
     bool bad = false;
     for (int gz = z0; gz < z1; ++gz) {
