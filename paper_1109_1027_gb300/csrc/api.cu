@@ -96,10 +96,8 @@ int validate(const nlse_params* p) {
     if (p->prec != NLSE_FP32 && p->prec != NLSE_FP64) return fail(NLSE_EINVAL, "unknown prec %d", p->prec);
     if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD && p->lap != NLSE_LAP_2SHOC_MS)
         return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
-    if (p->bc == NLSE_BC_MSD && p->dim > 1)
-        return fail(NLSE_EUNSUPPORTED, "MSD boundaries are implemented for dim = 1 only");
-    if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->bc != NLSE_BC_DIRICHLET)
-        return fail(NLSE_EUNSUPPORTED, "the unfused schedule supports Dirichlet boundaries only");
+    if (p->bc == NLSE_BC_MSD && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
+        return fail(NLSE_EUNSUPPORTED, "the multi-storage 2SHOC has no MSD boundary rule (Sec. 3.2)");
     if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "the unfused schedule has the single-storage 2SHOC and CD only");
     return NLSE_OK;
@@ -136,24 +134,34 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
     }
 }
 
-// One step of the paper's unfused schedule (plain.cu).
-int enqueue_plain_step(nlse_ctx* c, void* psi, cudaStream_t st) {
+// Whether the unfused kernels (plain.cu) run this context's steps: on
+// request, or for MSD boundaries in 2D and 3D, which only they implement.
+bool unfused(const nlse_params& p) {
+    return (p.flags & NLSE_FLAG_PLAIN_SCHEDULE) || (p.bc == NLSE_BC_MSD && p.dim > 1);
+}
+
+nlse::PlainLaunch plain_launch(const nlse_ctx* c, const void* psi) {
     nlse::PlainLaunch L;
     L.dim = c->p.dim;
     for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
-    L.prec = c->p.prec; L.lap = c->p.lap;
+    L.prec = c->p.prec; L.lap = c->p.lap; L.bc = c->p.bc;
     L.h = c->p.h; L.a = c->p.a; L.s = c->p.s; L.dt = c->p.dt;
-    L.psi = psi; L.V = c->V;
+    L.psi = const_cast<void*>(psi); L.lo = c->lo; L.V = c->V;
     L.D = c->plain[0]; L.Ktot = c->plain[1]; L.Ktmp = c->plain[2]; L.ptmp = c->plain[3];
     L.flag = c->flag;
-    cudaError_t e = nlse::launch_plain_step(L, st);
+    return L;
+}
+
+// One step of the unfused schedule (plain.cu).
+int enqueue_plain_step(nlse_ctx* c, void* psi, cudaStream_t st) {
+    cudaError_t e = nlse::launch_plain_step(plain_launch(c, psi), st);
     if (e != cudaSuccess) return cuda_fail(e, "unfused RK4 step launch");
     return NLSE_OK;
 }
 
 // The four fused stages of one RK4 step (Eq. RK4) on psi, in place.
 int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
-    if (c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) return enqueue_plain_step(c, psi, st);
+    if (unfused(c->p)) return enqueue_plain_step(c, psi, st);
     StageLaunch L = base_launch(c);
     L.psi = psi;
     L.psi_out = psi;
@@ -360,7 +368,7 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
 #define TRY(call, what) do { e = (call); if (e != cudaSuccess) { rc = cuda_fail(e, what); release(c); return rc; } } while (0)
     TRY(cudaGetDevice(&c->device), "cudaGetDevice");
     TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device), "device query");
-    if (p->flags & NLSE_FLAG_PLAIN_SCHEDULE) {
+    if (unfused(*p)) {
         for (int i = 0; i < 4; ++i) TRY(cudaMalloc(&c->plain[i], c->cbytes), "allocating RK4 work array");
     } else {
         TRY(cudaMalloc(&c->Y[0], c->cbytes), "allocating stage buffer");
@@ -638,6 +646,11 @@ int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     if (((uintptr_t)psi | (uintptr_t)lap) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
     const char *a0 = (const char*)psi, *b0 = (const char*)lap;
     if (a0 < b0 + c->cbytes && b0 < a0 + c->cbytes) return fail(NLSE_EINVAL, "psi and lap overlap");
+    if (c->p.bc == NLSE_BC_MSD && c->p.dim > 1) {
+        cudaError_t e = nlse::launch_plain_laplacian(plain_launch(c, psi), lap, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "Laplacian launch");
+        return NLSE_OK;
+    }
     StageLaunch L = base_launch(c);
     L.stage = 0;
     L.yin = psi;

@@ -56,15 +56,18 @@ cudaError_t launch_stage_3d_tma_planes128(const StageLaunch& L, cudaStream_t st)
 struct PlainLaunch {
     int dim;
     int64_t n[3];
-    int prec, lap;
+    int prec, lap, bc;
     double h, a, s, dt;
     void* psi;
+    void* lo;               // FP32 compensated part, or nullptr
     const void* V;
     void *D, *Ktot, *Ktmp, *ptmp;
     int* flag;
 };
 
 cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st);
+// The Laplacian (boundary points: D_b) through the same unfused kernels.
+cudaError_t launch_plain_laplacian(const PlainLaunch& L, void* lap_out, cudaStream_t st);
 
 // Whole RK4 time loops of a small 1D grid in one thread-block cluster
 // (rk4_1d_resident.cu).

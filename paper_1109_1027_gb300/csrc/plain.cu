@@ -5,7 +5,17 @@
 // RK4 work arrays K_tot, K_tmp and Psi_tmp, are full grids in device memory;
 // every F(Psi) is two launches (D, then step 2 + F), and each axpy line of
 // Eq. (RK4) is its own launch -- fourteen launches per step.  One thread per
-// grid point, no shared memory.  Dirichlet boundaries only.
+// grid point, no shared memory.
+//
+// The same kernels carry the MSD boundary rule in every dimension (the fused
+// 2D and 3D kernels are Dirichlet only): with the D and F fields in global
+// memory, the paper's sweep order -- interior D, then D_b from the interior
+// D at the inward point (Eq. msdbc_lap), interior F, then F_b from the
+// interior F at the inward point (Eq. msdbc_ut) -- is one more launch per
+// field.  The inward point of a boundary point has every coordinate clamped
+// into [1, n-2] (the normal neighbour on a face, the diagonal one on an edge
+// or corner).  In FP32 the last line of Eq. (RK4) adds to the state with the
+// compensated (Kahan) sum of the fused path.
 #include "nlse_device.cuh"
 
 namespace nlse {
@@ -30,6 +40,12 @@ __device__ __forceinline__ bool decompose(const Grid3& g, int64_t p, int* c) {
     return false;
 }
 
+__device__ __forceinline__ int64_t inward(const Grid3& g, const int* x) {
+    int64_t q = 0;
+    for (int ax = 0; ax < g.dim; ++ax) q += (int64_t)min(max(x[ax], 1), g.n[ax] - 2) * g.stride[ax];
+    return q;
+}
+
 // Step 1 everywhere: interior D (Eqs. 2shoc1d, 2d2shocs1, 3d2shocs) and the
 // Dirichlet boundary value D_b of Eq. (dbc_lap).
 template <typename R>
@@ -49,8 +65,34 @@ __global__ void __launch_bounds__(NT) plain_d(const cplx<R>* psi, const R* V, cp
     D[p] = cscale(c.inv_h2, csub(sum, cscale((R)(2 * g.dim), ctr)));
 }
 
-// Step 2 (or CD) and F (Sec. 3.1) into K; F_b = 0 (Eq. dbc_ut).
-template <typename R, bool CD>
+// MSD: the step-1 boundary value D_b of Eq. (msdbc_lap) from the interior D
+// at the inward point (overwrites the Dirichlet value plain_d left there).
+template <typename R>
+__global__ void __launch_bounds__(NT) plain_d_msd(const cplx<R>* psi, const R* V, cplx<R>* D, Grid3 g,
+                                                  Coef<R> c) {
+    int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
+    if (p >= g.npts) return;
+    int x[3];
+    if (!decompose(g, p, x)) return;
+    const int64_t q = inward(g, x);
+    D[p] = msd_D(c, psi[p], V[p], psi[q], V[q], D[q]);
+}
+
+// MSD: F_b = i Im(F_q / psi_q) psi_b, Eq. (msdbc_ut), from the interior F at
+// the inward point q.
+template <typename R>
+__global__ void __launch_bounds__(NT) plain_f_msd(const cplx<R>* psi, cplx<R>* K, Grid3 g) {
+    int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
+    if (p >= g.npts) return;
+    int x[3];
+    if (!decompose(g, p, x)) return;
+    const int64_t q = inward(g, x);
+    K[p] = msd_F(psi[p], psi[q], K[q]);
+}
+
+// Step 2 (or CD) and F (Sec. 3.1) into K; F_b = 0 (Eq. dbc_ut).  With LAP
+// the Laplacian itself goes to K instead (boundary points: D_b).
+template <typename R, bool CD, bool LAP = false>
 __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>* D, const R* V,
                                               cplx<R>* K, Grid3 g, Coef<R> c) {
     using C = cplx<R>;
@@ -58,7 +100,7 @@ __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>*
     if (p >= g.npts) return;
     int x[3];
     if (decompose(g, p, x)) {
-        K[p] = czero<C>();
+        K[p] = LAP ? D[p] : czero<C>();
         return;
     }
     C lap = D[p];
@@ -79,7 +121,7 @@ __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>*
         C ppart = cscale(c.inv_6h2, csub(edges, cscale((R)(2 * d * (d - 1)), y)));
         lap = cadd(dpart, ppart);
     }
-    K[p] = rhs_point(c, y, lap, V[p]);
+    K[p] = LAP ? lap : rhs_point(c, y, lap, V[p]);
 }
 
 // out = a + w b   (lines 2, 5, 8 of Eq. RK4)
@@ -97,20 +139,32 @@ __global__ void __launch_bounds__(NT) plain_acc(cplx<R>* acc, R w, const cplx<R>
     if (p < n) acc[p] = caxpy(acc[p], w, b[p]);
 }
 
-// psi += w (a + b)  (line 10)
+// psi += w (a + b)  (line 10); compensated in FP32 when lo is given
 template <typename R>
-__global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, R w, const cplx<R>* a, const cplx<R>* b,
-                                                  int64_t n, int* flag) {
+__global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, cplx<R>* lo, R w, const cplx<R>* a,
+                                                  const cplx<R>* b, int64_t n, int* flag) {
     int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
     if (p >= n) return;
-    cplx<R> v = caxpy(psi[p], w, cadd(a[p], b[p]));
+    cplx<R> v;
+    if constexpr (sizeof(R) == 4) {
+        if (lo) {
+            const cplx<R> d = cscale(w, cadd(a[p], b[p]));
+            v = psi[p];
+            cplx<R> l = lo[p];
+            kahan_add(v.x, l.x, d.x);
+            kahan_add(v.y, l.y, d.y);
+            lo[p] = l;
+        } else {
+            v = caxpy(psi[p], w, cadd(a[p], b[p]));
+        }
+    } else {
+        v = caxpy(psi[p], w, cadd(a[p], b[p]));
+    }
     psi[p] = v;
     if (!(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
 }
 
-template <typename R>
-cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
-    using C = cplx<R>;
+Grid3 make_grid(const PlainLaunch& L) {
     Grid3 g;
     g.dim = L.dim;
     for (int ax = 0; ax < 3; ++ax) g.n[ax] = ax < L.dim ? (int)L.n[ax] : 1;
@@ -118,6 +172,13 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
     g.stride[1] = g.n[0];
     g.stride[2] = (int64_t)g.n[0] * g.n[1];
     g.npts = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    return g;
+}
+
+template <typename R>
+cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
+    using C = cplx<R>;
+    const Grid3 g = make_grid(L);
     Coef<R> c = make_coef<R>(L.h, L.a, L.s);
     C* psi = (C*)L.psi;
     C* D = (C*)L.D;
@@ -128,10 +189,13 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
     const int64_t n = g.npts;
     const unsigned blocks = (unsigned)((n + NT - 1) / NT);
     const R k = (R)L.dt;
+    const bool msd = L.bc == 1;
     auto F = [&](const C* in, C* out) {
         plain_d<R><<<blocks, NT, 0, st>>>(in, V, D, g, c);
+        if (msd) plain_d_msd<R><<<blocks, NT, 0, st>>>(in, V, D, g, c);
         if (L.lap == 1) plain_f<R, true><<<blocks, NT, 0, st>>>(in, D, V, out, g, c);
         else plain_f<R, false><<<blocks, NT, 0, st>>>(in, D, V, out, g, c);
+        if (msd) plain_f_msd<R><<<blocks, NT, 0, st>>>(in, out, g);
     };
     F(psi, Ktot);                                                          // 1
     plain_axpy<R><<<blocks, NT, 0, st>>>(ptmp, psi, k / 2, Ktot, n);      // 2
@@ -142,7 +206,23 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
     plain_acc<R><<<blocks, NT, 0, st>>>(Ktot, (R)2, Ktmp, n);             // 7
     plain_axpy<R><<<blocks, NT, 0, st>>>(ptmp, psi, k, Ktmp, n);          // 8
     F(ptmp, Ktmp);                                                         // 9
-    plain_final<R><<<blocks, NT, 0, st>>>(psi, k / 6, Ktot, Ktmp, n, L.flag);  // 10
+    plain_final<R><<<blocks, NT, 0, st>>>(psi, (C*)L.lo, k / 6, Ktot, Ktmp, n, L.flag);  // 10
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t lap_r(const PlainLaunch& L, void* lap_out, cudaStream_t st) {
+    using C = cplx<R>;
+    const Grid3 g = make_grid(L);
+    const Coef<R> c = make_coef<R>(L.h, L.a, L.s);
+    const unsigned blocks = (unsigned)((g.npts + NT - 1) / NT);
+    const C* psi = (const C*)L.psi;
+    const R* V = (const R*)L.V;
+    C* D = (C*)L.D;
+    plain_d<R><<<blocks, NT, 0, st>>>(psi, V, D, g, c);
+    if (L.bc == 1) plain_d_msd<R><<<blocks, NT, 0, st>>>(psi, V, D, g, c);
+    if (L.lap == 1) plain_f<R, true, true><<<blocks, NT, 0, st>>>(psi, D, V, (C*)lap_out, g, c);
+    else plain_f<R, false, true><<<blocks, NT, 0, st>>>(psi, D, V, (C*)lap_out, g, c);
     return cudaGetLastError();
 }
 
@@ -150,6 +230,10 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
 
 cudaError_t launch_plain_step(const PlainLaunch& L, cudaStream_t st) {
     return L.prec == 0 ? step_r<float>(L, st) : step_r<double>(L, st);
+}
+
+cudaError_t launch_plain_laplacian(const PlainLaunch& L, void* lap_out, cudaStream_t st) {
+    return L.prec == 0 ? lap_r<float>(L, lap_out, st) : lap_r<double>(L, lap_out, st);
 }
 
 }  // namespace nlse

@@ -59,8 +59,7 @@ def _params(**kw):
     (dict(bc=5), nlse.EINVAL),
     (dict(prec=7), nlse.EINVAL),
     (dict(lap=3), nlse.EINVAL),
-    (dict(bc="msd"), nlse.EUNSUPPORTED),              # MSD is 1D only
-    (dict(bc="msd", lap="2shoc_ms"), nlse.EUNSUPPORTED),
+    (dict(bc="msd", lap="2shoc_ms"), nlse.EUNSUPPORTED),     # no MSD rule for the multi-storage form
     (dict(lap="2shoc_ms", plain=True), nlse.EUNSUPPORTED),   # unfused schedule: single storage only
 ])
 def test_invalid_parameters_are_rejected_on_the_host(lib, kw, code):

@@ -85,6 +85,22 @@ def test_laplacian_matches_oracle(shape, prec, lap):
     assert np.abs(got - ref).max() <= tol
 
 
+@pytest.mark.parametrize("shape", [(3, 3), (17, 70), (40, 131), (3, 3, 3), (9, 20, 37), (35, 18, 40)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_laplacian_msd_multi_d_matches_oracle(shape, prec):
+    """MSD step-1 boundary values in 2D/3D, Eq. (msdbc_lap) at the inward
+    point (faces: normal neighbour; edges and corners: the diagonal one)."""
+    psi, V = _problem(shape, 8)
+    psi = psi + 3.0
+    h, a, s = 0.21, 1.1, 0.7
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    ref = oracle.laplacian(oracle.Problem(shape, h, a, s, bc=oracle.BC_MSD), psi_r, V_r)
+    solver = nlse.Solver(to_dev(V, prec), h, 1e-3, a, s, bc="msd", prec=prec)
+    got = solver.lap2shoc(to_dev(psi, prec)).cpu().numpy()
+    tol = (1e-12 if prec == "fp64" else 4e-6) * lap_scale(psi_r, h, len(shape))
+    assert np.abs(got - ref).max() <= tol
+
+
 def test_laplacian_msd_1d_matches_oracle():
     for n in (3, 4, 1025, 2049):
         for prec in ("fp64", "fp32"):
@@ -102,6 +118,9 @@ def test_laplacian_msd_1d_matches_oracle():
 STEP_CASES = [(shape, prec, lap, "dirichlet") for d in (1, 2, 3) for shape in SHAPES[d][1:]
               for prec in ("fp64", "fp32") for lap in LAPS]
 STEP_CASES += [((n,), prec, "2shoc", "msd") for n in (5, 1030, 3001) for prec in ("fp64", "fp32")]
+# MSD in 2D and 3D (the unfused kernels carry it), both Laplacians that have it
+STEP_CASES += [(shape, prec, lap, "msd") for shape in [(17, 70), (40, 131), (9, 20, 37), (35, 18, 40)]
+               for prec in ("fp64", "fp32") for lap in ("2shoc", "cd")]
 
 
 @pytest.mark.parametrize("shape,prec,lap,bc", STEP_CASES)
