@@ -51,7 +51,12 @@ typedef enum {
 /* Boundary conditions of Sec. 3.2. */
 typedef enum {
     NLSE_BC_DIRICHLET = 0,  /* Eqs. (dbc_lap), (dbc_ut): Psi_t = 0 on the boundary   */
-    NLSE_BC_MSD = 1         /* Eqs. (msdbc_ut), (msdbc_lap): |Psi|^2 held constant   */
+    NLSE_BC_MSD = 1         /* Eqs. (msdbc_ut), (msdbc_lap): |Psi|^2 held constant;
+                               "b-1" is the inward point with every coordinate
+                               clamped into [1, n-2].  1D: fused kernels; 2D and
+                               3D: the unfused kernels (interior D, then D_b,
+                               interior F, then F_b, each field in device memory).
+                               Not with NLSE_LAP_2SHOC_MS in 2D/3D, nor batches.   */
 } nlse_bc;
 
 /* Arithmetic of the state and the stencil. */
