@@ -30,6 +30,8 @@ _BUILD = os.path.join(_HERE, "_build")
 
 BC_DIRICHLET = 0
 BC_MSD = 1
+BC_PERIODIC = 2      # n points per axis, spacing h, indices wrap (x_n = x_0)
+BC_LAPZERO = 3       # D_b = 0, F_b = i (s|psi_b|^2 - V_b) psi_b
 LAP_2SHOC = 0
 LAP_CD = 1
 LAP_2SHOC_MS = 2     # multi-storage 2SHOC (Eqs. 2d2shocMs1-2, 3d2shocMs1-2); 1D: same as LAP_2SHOC

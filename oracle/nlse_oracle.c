@@ -36,6 +36,12 @@
  *    separate derivatives add up to the boundary Laplacian.  Points on the
  *    boundary of two or more axes never enter an interior Laplacian; their
  *    separate derivatives are set to 0.
+ *  - Periodic (named, not defined, in Sec. 3.2): n points per axis with
+ *    spacing h and no duplicated end point (x_n = x_0); every point is
+ *    interior and neighbour indices wrap.
+ *  - Laplacian-zero (named in Sec. 3.2): the step-1 boundary value is
+ *    D_b = 0 (Lap Psi = 0 at the boundary), and the boundary then follows the
+ *    equation itself with that Laplacian, F_b = i (s|Psi_b|^2 - V_b) Psi_b.
  *  - Mass M = h^d sum_all |psi|^2; energy (the paper defines none) is the
  *    discrete Hamiltonian of Eq. (NLSE):
  *    E = h^d sum_interior [ -a Re(conj(psi) Lap psi) + V|psi|^2 - (s/2)|psi|^4 ].
@@ -54,7 +60,9 @@ typedef struct {
     double h;      /* grid spacing */
     double a;      /* dispersion coefficient, a > 0 (Eq. NLSE) */
     double s;      /* nonlinearity coefficient (Eq. NLSE) */
-    int bc;        /* 0: Dirichlet (Eqs. dbc_lap, dbc_ut); 1: MSD (Eqs. msdbc_ut, msdbc_lap) */
+    int bc;        /* 0: Dirichlet (Eqs. dbc_lap, dbc_ut); 1: MSD (Eqs. msdbc_ut, msdbc_lap);
+                      2: periodic; 3: Laplacian-zero (the two further compact-friendly
+                      conditions Sec. 3.2 names) */
     int lap;       /* 0: 2SHOC single storage (Sec. 2); 1: second-order central difference (CD);
                       2: 2SHOC multi storage (Eqs. 2d2shocMs1-2, 3d2shocMs1-2; in 1D the same as 0) */
 } or_problem;
@@ -77,11 +85,18 @@ static void put(double* f, long p, cplx z) { f[2 * p] = z.re; f[2 * p + 1] = z.i
 
 static long npoints(const or_problem* P) { return P->n[0] * P->n[1] * P->n[2]; }
 
+/* Storage index of (x, y, z); coordinates wrap on a periodic grid. */
 static long idx(const or_problem* P, long x, long y, long z) {
+    if (P->bc == 2) {
+        x = (x % P->n[0] + P->n[0]) % P->n[0];
+        y = (y % P->n[1] + P->n[1]) % P->n[1];
+        z = (z % P->n[2] + P->n[2]) % P->n[2];
+    }
     return x + P->n[0] * (y + P->n[1] * z);
 }
 
 static int is_boundary(const or_problem* P, long x, long y, long z) {
+    if (P->bc == 2) return 0;                       /* periodic: no boundary points */
     if (x == 0 || x == P->n[0] - 1) return 1;
     if (P->dim >= 2 && (y == 0 || y == P->n[1] - 1)) return 1;
     if (P->dim >= 3 && (z == 0 || z == P->n[2] - 1)) return 1;
@@ -174,6 +189,7 @@ static cplx boundary_D(const or_problem* P, const double* psi, const double* V, 
     long b = idx(P, x, y, z);
     cplx pb = get(psi, b);
     double Nb = nonlin(P, pb, V[b]);
+    if (P->bc == 3) return c_make(0.0, 0.0);           /* Laplacian-zero */
     if (P->bc == 0) return c_scale(-Nb / P->a, pb);
     long q = inward(P, x, y, z);
     cplx pq = get(psi, q);
@@ -329,6 +345,10 @@ static void rhs(const or_problem* P, const double* psi, const double* V, double*
                 long b = idx(P, x, y, z);
                 if (P->bc == 0) {
                     put(F, b, c_make(0.0, 0.0));
+                } else if (P->bc == 3) {
+                    /* Laplacian-zero: the equation with Lap_b = 0 */
+                    cplx pb = get(psi, b);
+                    put(F, b, c_times_i(c_scale(nonlin(P, pb, V[b]), pb)));
                 } else {
                     long q = inward(P, x, y, z);
                     double w = c_div(get(F, q), get(psi, q)).im;
@@ -434,9 +454,9 @@ static int make_problem(or_problem* P, int dim, const long* n, double h, double 
     for (int ax = 0; ax < 3; ++ax) P->n[ax] = ax < dim ? n[ax] : 1;
     for (int ax = 0; ax < dim; ++ax) if (P->n[ax] < 3) return 1;
     if (!(h > 0.0) || !(a > 0.0)) return 1;
-    if (bc != 0 && bc != 1) return 1;
+    if (bc < 0 || bc > 3) return 1;
     if (lap != 0 && lap != 1 && lap != 2) return 1;
-    if (lap == 2 && bc != 0 && dim > 1) return 1;    /* multi storage: Dirichlet only (Sec. 3.2) */
+    if (lap == 2 && (bc == 1 || bc == 3) && dim > 1) return 1;   /* multi storage: Dirichlet or periodic */
     P->h = h; P->a = a; P->s = s; P->bc = bc; P->lap = lap;
     return 0;
 }

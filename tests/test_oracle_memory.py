@@ -21,9 +21,9 @@ from paper_1109_1027_gb300 import workloads as wl
 for shape in [(3,), (4,), (37,), (3, 3), (17, 12), (3, 3, 3), (6, 7, 8)]:
     psi = wl.random_field(shape, seed=1) + 2.5
     V = wl.random_potential(shape, seed=2)
-    for bc in (oracle.BC_DIRICHLET, oracle.BC_MSD):
+    for bc in (oracle.BC_DIRICHLET, oracle.BC_MSD, oracle.BC_PERIODIC, oracle.BC_LAPZERO):
         for lap in (oracle.LAP_2SHOC, oracle.LAP_CD, oracle.LAP_2SHOC_MS):
-            if bc == oracle.BC_MSD and lap == oracle.LAP_2SHOC_MS and len(shape) > 1:
+            if bc in (oracle.BC_MSD, oracle.BC_LAPZERO) and lap == oracle.LAP_2SHOC_MS and len(shape) > 1:
                 continue
             prob = oracle.Problem(shape, 0.3, 0.8, -1.0, bc=bc, lap=lap)
             oracle.laplacian(prob, psi, V, return_D=True)

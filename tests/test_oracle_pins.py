@@ -100,6 +100,86 @@ def test_multi_storage_is_single_storage_in_1d_and_rejects_msd_in_2d():
                          np.ones((6, 6), complex), np.zeros((6, 6)))
 
 
+PERIODIC = [((24,), 3), ((12, 10), 2), ((8, 6, 10), 2)]
+
+
+@pytest.mark.parametrize("shape,modes", PERIODIC)
+@pytest.mark.parametrize("lap", [oracle.LAP_2SHOC, oracle.LAP_2SHOC_MS])
+def test_periodic_plane_wave_is_an_exact_eigenfunction(shape, modes, lap):
+    """On a periodic grid (n points, spacing h = L/n, wrapping indices) every
+    point is interior and a plane wave exp(i sum_a theta_a j_a) is an exact
+    eigenfunction of 2SHOC with the closed-form symbol
+    sum_a (-2 cos 2theta_a + 32 cos theta_a - 30) / (12 h^2)."""
+    h = 0.3
+    idx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    thetas = [2 * np.pi * (modes + a) / n for a, n in enumerate(shape)]
+    phase = sum(t * j for t, j in zip(thetas, idx))
+    psi = 1.7 * np.exp(1j * phase)
+    lam = sum(symbol(t) for t in thetas) / h ** 2
+    prob = oracle.Problem(shape, h, 1.0, 0.0, bc=oracle.BC_PERIODIC, lap=lap)
+    lap_f = oracle.laplacian(prob, psi, np.zeros(shape))
+    assert np.abs(lap_f - lam * psi).max() <= 1e-12 * abs(lam) * 1.7
+
+
+@pytest.mark.parametrize("shape,modes", PERIODIC)
+def test_periodic_nonlinear_plane_wave_follows_the_scalar_rk4(shape, modes):
+    """With V constant a plane wave stays a plane wave; its amplitude then obeys
+    y' = i (a lam + s|y|^2 - V) y exactly, stepped by a textbook scalar RK4."""
+    h, a, s, V0, k = 0.3, 0.8, -1.2, 0.4, 2e-3
+    idx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    thetas = [2 * np.pi * (modes + a_) / n for a_, n in enumerate(shape)]
+    wave = np.exp(1j * sum(t * j for t, j in zip(thetas, idx)))
+    lam = sum(symbol(t) for t in thetas) / h ** 2
+    y0 = 0.9 + 0.3j
+    prob = oracle.Problem(shape, h, a, s, bc=oracle.BC_PERIODIC)
+    out = oracle.run(prob, y0 * wave, np.full(shape, V0), k, 7)
+    y = scalar_rk4(y0, lambda v: 1j * (a * lam + s * abs(v) ** 2 - V0) * v, k, 7)
+    assert np.abs(out - y * wave).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_laplacian_zero_boundary_on_a_harmonic_field(dim):
+    """Laplacian-zero: on a harmonic polynomial (degree 2, where 2SHOC is exact)
+    the Laplacian vanishes everywhere, interior by exactness and boundary by
+    the rule.  With s = 0 and a constant V every point then turns by the same
+    factor, y' = -i V y, which keeps the field harmonic: one step is exactly
+    the RK4 polynomial R(-i k V) at every point, boundary included (Dirichlet
+    would hold the boundary still)."""
+    n = {1: 13, 2: 9, 3: 7}[dim]
+    shape = (n,) * dim
+    coords = wl.mesh(shape, -1.0, 1.0)
+    h = wl.spacing(n, -1.0, 1.0)
+    if dim == 1:
+        psi = (0.5 + 0.3 * coords[0]) + 1j * (0.2 - 0.4 * coords[0])
+    elif dim == 2:
+        x, y = coords
+        psi = (x * x - y * y + 1.0) + 1j * (x * y + 0.5)
+    else:
+        x, y, z = coords
+        psi = (x * x - z * z + 1.0) + 1j * (x * y + y * z + 0.5)
+    V0, a, k = 0.7, 0.9, 1e-2
+    V = np.full(shape, V0)
+    prob = oracle.Problem(shape, h, a, 0.0, bc=oracle.BC_LAPZERO)
+    assert np.abs(oracle.laplacian(prob, psi, V)).max() <= 1e-11 / h ** 2
+    out = oracle.run(prob, psi, V, k, 5)
+    assert np.abs(out - stability_poly(-1j * k * V0) ** 5 * psi).max() <= 1e-12
+    dirichlet = oracle.run(oracle.Problem(shape, h, a, 0.0), psi, V, k, 5)
+    assert np.abs(out[(0,) * dim] - dirichlet[(0,) * dim]) > 1e-3
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_laplacian_zero_nonlinear_constant_state(dim):
+    """A constant state has zero Laplacian everywhere under the
+    Laplacian-zero rule; every point, boundary included, then follows
+    y' = i (s|y|^2 - V) y, stepped exactly by the scalar RK4."""
+    shape = ({1: 11, 2: 7, 3: 5}[dim],) * dim
+    y0, s, V0, k = 0.8 - 0.6j, 1.4, 0.3, 5e-3
+    prob = oracle.Problem(shape, 0.2, 0.9, s, bc=oracle.BC_LAPZERO)
+    out = oracle.run(prob, np.full(shape, y0), np.full(shape, V0), k, 6)
+    y = scalar_rk4(y0, lambda v: 1j * (s * abs(v) ** 2 - V0) * v, k, 6)
+    assert np.abs(out - y).max() <= 1e-13
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_polynomial_exactness(dim):
     """The fourth-order stencil's error term is h^4 times sixth derivatives, so
