@@ -51,12 +51,21 @@ typedef enum {
 /* Boundary conditions of Sec. 3.2. */
 typedef enum {
     NLSE_BC_DIRICHLET = 0,  /* Eqs. (dbc_lap), (dbc_ut): Psi_t = 0 on the boundary   */
-    NLSE_BC_MSD = 1         /* Eqs. (msdbc_ut), (msdbc_lap): |Psi|^2 held constant;
+    NLSE_BC_MSD = 1,        /* Eqs. (msdbc_ut), (msdbc_lap): |Psi|^2 held constant;
                                "b-1" is the inward point with every coordinate
                                clamped into [1, n-2].  1D: fused kernels; 2D and
                                3D: the unfused kernels (interior D, then D_b,
                                interior F, then F_b, each field in device memory).
                                Not with NLSE_LAP_2SHOC_MS in 2D/3D, nor batches.   */
+    NLSE_BC_PERIODIC = 2,   /* named in Sec. 3.2, not defined there: n points per
+                               axis with spacing h and x_n = x_0 (no duplicated end
+                               point); every point interior, indices wrap          */
+    NLSE_BC_LAPZERO = 3     /* named in Sec. 3.2: Laplacian-zero, D_b = 0 and the
+                               boundary follows the equation with Lap_b = 0,
+                               F_b = i (s|Psi_b|^2 - V_b) Psi_b.  Periodic and
+                               Laplacian-zero run on the unfused kernels in every
+                               dimension; not with NLSE_LAP_2SHOC_MS in 2D/3D,
+                               nor batches or nlse_adjoint                         */
 } nlse_bc;
 
 /* Arithmetic of the state and the stencil. */

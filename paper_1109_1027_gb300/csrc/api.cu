@@ -92,12 +92,12 @@ int validate(const nlse_params* p) {
     if (!(std::isfinite(p->dt) && p->dt > 0)) return fail(NLSE_EINVAL, "dt must be positive and finite");
     if (!(std::isfinite(p->a) && p->a > 0)) return fail(NLSE_EINVAL, "a must be positive and finite (Eq. NLSE)");
     if (!std::isfinite(p->s)) return fail(NLSE_EINVAL, "s must be finite");
-    if (p->bc != NLSE_BC_DIRICHLET && p->bc != NLSE_BC_MSD) return fail(NLSE_EINVAL, "unknown bc %d", p->bc);
+    if (p->bc < NLSE_BC_DIRICHLET || p->bc > NLSE_BC_LAPZERO) return fail(NLSE_EINVAL, "unknown bc %d", p->bc);
     if (p->prec != NLSE_FP32 && p->prec != NLSE_FP64) return fail(NLSE_EINVAL, "unknown prec %d", p->prec);
     if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD && p->lap != NLSE_LAP_2SHOC_MS)
         return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
-    if (p->bc == NLSE_BC_MSD && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
-        return fail(NLSE_EUNSUPPORTED, "the multi-storage 2SHOC has no MSD boundary rule (Sec. 3.2)");
+    if (p->bc != NLSE_BC_DIRICHLET && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
+        return fail(NLSE_EUNSUPPORTED, "the multi-storage 2SHOC is built for Dirichlet boundaries only");
     if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "the unfused schedule has the single-storage 2SHOC and CD only");
     return NLSE_OK;
@@ -137,7 +137,8 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 // Whether the unfused kernels (plain.cu) run this context's steps: on
 // request, or for MSD boundaries in 2D and 3D, which only they implement.
 bool unfused(const nlse_params& p) {
-    return (p.flags & NLSE_FLAG_PLAIN_SCHEDULE) || (p.bc == NLSE_BC_MSD && p.dim > 1);
+    return (p.flags & NLSE_FLAG_PLAIN_SCHEDULE) || (p.bc == NLSE_BC_MSD && p.dim > 1) ||
+           p.bc == NLSE_BC_PERIODIC || p.bc == NLSE_BC_LAPZERO;
 }
 
 nlse::PlainLaunch plain_launch(const nlse_ctx* c, const void* psi) {
@@ -201,7 +202,7 @@ int resident_cluster(const nlse_ctx* c) {
 
 // Whether this context's steps run as one resident launch (small 1D grids).
 bool resident_1d(const nlse_ctx* c) {
-    return !c->batch && c->p.dim == 1 && resident_cluster(c) > 0 && !(c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE) &&
+    return !c->batch && c->p.dim == 1 && resident_cluster(c) > 0 && !unfused(c->p) &&
            nlse::rk4_1d_resident_fits(c->p.n[0]);
 }
 
@@ -646,7 +647,7 @@ int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     if (((uintptr_t)psi | (uintptr_t)lap) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
     const char *a0 = (const char*)psi, *b0 = (const char*)lap;
     if (a0 < b0 + c->cbytes && b0 < a0 + c->cbytes) return fail(NLSE_EINVAL, "psi and lap overlap");
-    if (c->p.bc == NLSE_BC_MSD && c->p.dim > 1) {
+    if (unfused(c->p) && c->p.bc != NLSE_BC_DIRICHLET) {
         cudaError_t e = nlse::launch_plain_laplacian(plain_launch(c, psi), lap, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "Laplacian launch");
         return NLSE_OK;

@@ -44,14 +44,34 @@ __device__ __forceinline__ double2 psi_at(const InvView<R>& v, int64_t p) {
 
 template <typename R>
 __device__ __forceinline__ bool on_boundary(const InvView<R>& v, const int* c) {
+    if (v.bc == 2) return false;                     // periodic: no boundary points
     for (int ax = 0; ax < v.dim; ++ax)
         if (c[ax] == 0 || c[ax] == v.n[ax] - 1) return true;
     return false;
 }
 
+// Storage index of coordinates c; on a periodic grid they wrap.
 template <typename R>
 __device__ __forceinline__ int64_t index_of(const InvView<R>& v, const int* c) {
-    return c[0] * v.stride[0] + c[1] * v.stride[1] + c[2] * v.stride[2];
+    int64_t p = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        int x = c[ax];
+        if (v.bc == 2) x = x < 0 ? x + v.n[ax] : (x >= v.n[ax] ? x - v.n[ax] : x);
+        p += x * v.stride[ax];
+    }
+    return p;
+}
+
+// Index of the point at offsets (d0, d1, d2) from c.
+template <typename R>
+__device__ __forceinline__ int64_t index_at(const InvView<R>& v, const int* c, int d0, int d1, int d2) {
+    const int q[3] = {c[0] + d0, c[1] + d1, c[2] + d2};
+    return index_of(v, q);
+}
+
+template <typename R>
+__device__ __forceinline__ int64_t axial(const InvView<R>& v, const int* c, int ax, int d) {
+    return index_at(v, c, ax == 0 ? d : 0, ax == 1 ? d : 0, ax == 2 ? d : 0);
 }
 
 // Step-1 D at an interior point: sum of axial neighbours minus 2d centre, / h^2.
@@ -61,8 +81,8 @@ __device__ double2 d_interior(const InvView<R>& v, const int* c) {
     double2 ctr = psi_at(v, p);
     double2 sum = make_double2(0.0, 0.0);
     for (int ax = 0; ax < v.dim; ++ax) {
-        double2 u = psi_at(v, p + v.stride[ax]);
-        double2 w = psi_at(v, p - v.stride[ax]);
+        double2 u = psi_at(v, axial(v, c, ax, 1));
+        double2 w = psi_at(v, axial(v, c, ax, -1));
         sum.x += u.x + w.x;
         sum.y += u.y + w.y;
     }
@@ -84,6 +104,7 @@ __device__ double2 d_any(const InvView<R>& v, const int* c) {
     int64_t b = index_of(v, c);
     double2 pb = psi_at(v, b);
     double Nb = v.s * (pb.x * pb.x + pb.y * pb.y) - (double)v.V[b];
+    if (v.bc == 3) return make_double2(0.0, 0.0);                 // Laplacian-zero
     if (v.bc == 0) return make_double2(-Nb * v.inv_a * pb.x, -Nb * v.inv_a * pb.y);
     int q[3];
     inward(v, c, q);
@@ -119,7 +140,10 @@ __device__ double2 lap_interior(const InvView<R>& v, const int* c) {
         for (int a2 = a1 + 1; a2 < d; ++a2)
             for (int s1 = -1; s1 <= 1; s1 += 2)
                 for (int s2 = -1; s2 <= 1; s2 += 2) {
-                    double2 t = psi_at(v, p + s1 * v.stride[a1] + s2 * v.stride[a2]);
+                    int off[3] = {0, 0, 0};
+                    off[a1] = s1;
+                    off[a2] = s2;
+                    double2 t = psi_at(v, index_at(v, c, off[0], off[1], off[2]));
                     edges.x += t.x;
                     edges.y += t.y;
                 }

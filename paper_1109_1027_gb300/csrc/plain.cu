@@ -14,7 +14,10 @@
 // interior F at the inward point (Eq. msdbc_ut) -- is one more launch per
 // field.  The inward point of a boundary point has every coordinate clamped
 // into [1, n-2] (the normal neighbour on a face, the diagonal one on an edge
-// or corner).  In FP32 the last line of Eq. (RK4) adds to the state with the
+// or corner).  They also carry the two further conditions Sec. 3.2 names:
+// periodic (no boundary points, neighbour indices wrap) and Laplacian-zero
+// (D_b = 0 and F_b = i (s|Psi_b|^2 - V_b) Psi_b, the equation with a zero
+// Laplacian).  In FP32 the last line of Eq. (RK4) adds to the state with the
 // compensated (Kahan) sum of the fused path.
 #include "nlse_device.cuh"
 
@@ -26,6 +29,7 @@ constexpr int NT = 256;
 struct Grid3 {
     int n[3];
     int dim;
+    int bc;                 // 0 Dirichlet, 1 MSD, 2 periodic, 3 Laplacian-zero
     int64_t stride[3];
     int64_t npts;
 };
@@ -35,9 +39,19 @@ __device__ __forceinline__ bool decompose(const Grid3& g, int64_t p, int* c) {
     c[0] = (int)(r % g.n[0]); r /= g.n[0];
     c[1] = (int)(r % g.n[1]); r /= g.n[1];
     c[2] = (int)r;
+    if (g.bc == 2) return false;                     // periodic: no boundary points
     for (int ax = 0; ax < g.dim; ++ax)
         if (c[ax] == 0 || c[ax] == g.n[ax] - 1) return true;
     return false;
+}
+
+// Index of the neighbour of point p (coordinates x) at offset d along axis
+// ax; on a periodic grid the coordinate wraps.
+__device__ __forceinline__ int64_t nbr(const Grid3& g, const int* x, int64_t p, int ax, int d) {
+    if (g.bc != 2) return p + d * g.stride[ax];
+    int c = x[ax] + d;
+    c = c < 0 ? c + g.n[ax] : (c >= g.n[ax] ? c - g.n[ax] : c);
+    return p + (int64_t)(c - x[ax]) * g.stride[ax];
 }
 
 __device__ __forceinline__ int64_t inward(const Grid3& g, const int* x) {
@@ -57,11 +71,11 @@ __global__ void __launch_bounds__(NT) plain_d(const cplx<R>* psi, const R* V, cp
     int x[3];
     C ctr = psi[p];
     if (decompose(g, p, x)) {
-        D[p] = dirichlet_D(c, ctr, V[p]);
+        D[p] = g.bc == 3 ? czero<C>() : dirichlet_D(c, ctr, V[p]);   // MSD: corrected by plain_d_msd
         return;
     }
     C sum = czero<C>();
-    for (int ax = 0; ax < g.dim; ++ax) sum = cadd(sum, cadd(psi[p + g.stride[ax]], psi[p - g.stride[ax]]));
+    for (int ax = 0; ax < g.dim; ++ax) sum = cadd(sum, cadd(psi[nbr(g, x, p, ax, 1)], psi[nbr(g, x, p, ax, -1)]));
     D[p] = cscale(c.inv_h2, csub(sum, cscale((R)(2 * g.dim), ctr)));
 }
 
@@ -100,7 +114,9 @@ __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>*
     if (p >= g.npts) return;
     int x[3];
     if (decompose(g, p, x)) {
-        K[p] = LAP ? D[p] : czero<C>();
+        // Dirichlet F_b = 0 (MSD: replaced by plain_f_msd); Laplacian-zero: the
+        // equation with Lap_b = 0.
+        K[p] = LAP ? D[p] : (g.bc == 3 ? rhs_point(c, psi[p], czero<C>(), V[p]) : czero<C>());
         return;
     }
     C lap = D[p];
@@ -108,13 +124,13 @@ __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>*
     if (!CD) {
         const int d = g.dim;
         C dsum = czero<C>();
-        for (int ax = 0; ax < d; ++ax) dsum = cadd(dsum, cadd(D[p + g.stride[ax]], D[p - g.stride[ax]]));
+        for (int ax = 0; ax < d; ++ax) dsum = cadd(dsum, cadd(D[nbr(g, x, p, ax, 1)], D[nbr(g, x, p, ax, -1)]));
         C edges = czero<C>();
         for (int a1 = 0; a1 < d; ++a1)
             for (int a2 = a1 + 1; a2 < d; ++a2) {
-                int64_t s1 = g.stride[a1], s2 = g.stride[a2];
-                edges = cadd(edges, cadd(cadd(psi[p + s1 + s2], psi[p + s1 - s2]),
-                                         cadd(psi[p - s1 + s2], psi[p - s1 - s2])));
+                const int64_t pp = nbr(g, x, p, a1, 1), pm = nbr(g, x, p, a1, -1);
+                edges = cadd(edges, cadd(cadd(psi[nbr(g, x, pp, a2, 1)], psi[nbr(g, x, pp, a2, -1)]),
+                                         cadd(psi[nbr(g, x, pm, a2, 1)], psi[nbr(g, x, pm, a2, -1)])));
             }
         // ((16 - 2d)/12) D_c - (1/12) sum_axial D + (1/(6h^2)) (edges - 2d(d-1) psi_c)
         C dpart = csub(cscale((R)((16.0 - 2.0 * d) / 12.0), lap), cscale((R)(1.0 / 12.0), dsum));
@@ -167,6 +183,7 @@ __global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, cplx<R>* lo, R w
 Grid3 make_grid(const PlainLaunch& L) {
     Grid3 g;
     g.dim = L.dim;
+    g.bc = L.bc;
     for (int ax = 0; ax < 3; ++ax) g.n[ax] = ax < L.dim ? (int)L.n[ax] : 1;
     g.stride[0] = 1;
     g.stride[1] = g.n[0];

@@ -21,7 +21,7 @@ import torch
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(8)
-BC = {"dirichlet": 0, "msd": 1}
+BC = {"dirichlet": 0, "msd": 1, "periodic": 2, "lapzero": 3}
 PREC = {"fp32": 0, "fp64": 1}
 LAP = {"2shoc": 0, "cd": 1, "2shoc_ms": 2}
 FLAG_NO_STABILITY_CHECK = 1

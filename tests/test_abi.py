@@ -60,6 +60,8 @@ def _params(**kw):
     (dict(prec=7), nlse.EINVAL),
     (dict(lap=3), nlse.EINVAL),
     (dict(bc="msd", lap="2shoc_ms"), nlse.EUNSUPPORTED),     # no MSD rule for the multi-storage form
+    (dict(bc="periodic", lap="2shoc_ms"), nlse.EUNSUPPORTED),
+    (dict(bc="lapzero", lap="2shoc_ms"), nlse.EUNSUPPORTED),
     (dict(lap="2shoc_ms", plain=True), nlse.EUNSUPPORTED),   # unfused schedule: single storage only
 ])
 def test_invalid_parameters_are_rejected_on_the_host(lib, kw, code):

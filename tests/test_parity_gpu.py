@@ -116,6 +116,49 @@ def test_laplacian_msd_multi_d_matches_oracle(shape, prec):
     assert np.abs(got - ref).max() <= tol
 
 
+OBC = {"periodic": oracle.BC_PERIODIC, "lapzero": oracle.BC_LAPZERO}
+MORE_BC = [(shape, prec, bc, lap) for shape in [(3,), (40,), (3, 3), (17, 70), (3, 3, 3), (9, 20, 37)]
+           for prec in ("fp64", "fp32") for bc in ("periodic", "lapzero") for lap in ("2shoc", "cd")]
+
+
+@pytest.mark.parametrize("shape,prec,bc,lap", MORE_BC)
+def test_laplacian_periodic_and_lapzero_match_oracle(shape, prec, bc, lap):
+    h, a, s = 0.37, 0.8, -1.3
+    psi, V = _problem(shape, 120 + len(shape))
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    ref = oracle.laplacian(oracle.Problem(shape, h, a, s, bc=OBC[bc], lap=OLAP[lap]), psi_r, V_r)
+    solver = nlse.Solver(to_dev(V, prec), h, 1e-3, a, s, bc=bc, prec=prec, lap=lap)
+    got = solver.lap2shoc(to_dev(psi, prec)).cpu().numpy()
+    tol = (1e-12 if prec == "fp64" else 2e-6) * lap_scale(psi_r, h, len(shape))
+    assert np.abs(got - ref).max() <= tol
+
+
+@pytest.mark.parametrize("shape,prec,bc", [(s_, p_, b_) for s_ in [(1030,), (40, 131), (9, 20, 37)]
+                                           for p_ in ("fp64", "fp32") for b_ in ("periodic", "lapzero")])
+def test_rk4_steps_periodic_and_lapzero_match_oracle(shape, prec, bc):
+    a, s, h = 0.7, -1.1, 0.5
+    psi, V = _problem(shape, 330 + sum(shape))
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    prob = oracle.Problem(shape, h, a, s, bc=OBC[bc])
+    m0, e0, dtmax = oracle.invariants(prob, psi_r, V_r)
+    k = 0.5 * dtmax
+    ref = oracle.run(prob, psi_r, V_r, k, 5)
+    solver = nlse.Solver(to_dev(V, prec), h, k, a, s, bc=bc, prec=prec)
+    m, e, d = solver.invariants(to_dev(psi, prec))
+    if prec == "fp64":
+        assert (m, e, d) == (pytest.approx(m0, rel=1e-12), pytest.approx(e0, rel=1e-11), pytest.approx(dtmax, rel=1e-12))
+    x = to_dev(psi, prec)
+    solver.run(x, 5)
+    solver.check()
+    got = x.cpu().numpy()
+    scale = np.abs(ref).max()
+    if prec == "fp64":
+        assert np.abs(got - ref).max() <= 1e-12 * scale
+    else:
+        assert np.abs(got - ref).max() <= 1e-5 * scale
+        assert rel_l2(got, ref) <= 1e-5
+
+
 def test_laplacian_msd_1d_matches_oracle():
     for n in (3, 4, 1025, 2049):
         for prec in ("fp64", "fp32"):
