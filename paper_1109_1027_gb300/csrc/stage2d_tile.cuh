@@ -284,8 +284,11 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
             if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
             if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
         }
+        // No barrier here: the step below reads the D ring slot written in the
+        // previous iteration and this thread's own registers, both ordered by
+        // the barrier at the top of the loop, and a thread whose wait gave up
+        // carries ok = false to that barrier, where the CTA stops together.
         if (NEED_E) wait_e(i);
-        if (!__syncthreads_and(ok)) { alive = false; break; }
 
         if (xin) {
             const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)

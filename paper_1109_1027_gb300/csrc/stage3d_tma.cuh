@@ -333,8 +333,11 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
             st2(dn + k, d1);
             if (hk >= 0) dn[hk] = halo_d(j + 1, za);
         }
+        // No barrier here: the step below reads the D ring slot written in the
+        // previous iteration and this thread's own registers, both ordered by
+        // the barrier at the top of the loop, and a thread whose wait gave up
+        // carries ok = false to that barrier, where the CTA stops together.
         if (NEED_E) wait_e(i);
-        if (!__syncthreads_and(ok)) { alive = false; break; }
 
         if (pin) {
             const C* pz = iplane(j);
