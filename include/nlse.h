@@ -171,6 +171,15 @@ int nlse_rk4_step(nlse_ctx* ctx, void* psi_dev, void* stream);
  * returns NLSE_EUNSTABLE without stepping when dt exceeds it. */
 int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
 
+/* nlse_run on a state in host memory, for callers that keep Psi on the host:
+ * copies psi_host (cbytes of the context's grid or batch; page-locked memory
+ * makes the copies asynchronous DMA) into a device buffer the context owns
+ * (allocated on first use), runs nsteps steps there, copies the result back
+ * into psi_host and synchronises the stream.  A host state has no FP32
+ * compensated part: each call starts from psi_host with it zero.  Errors as
+ * nlse_run; on an error psi_host is left as it was. */
+int nlse_run_host(nlse_ctx* ctx, void* psi_host, int64_t nsteps, void* stream);
+
 /* Mass M = h^d sum |Psi|^2, energy
  * E = h^d sum_interior [ -a Re(conj(Psi) Lap Psi) + V |Psi|^2 - (s/2)|Psi|^4 ]
  * (the paper defines neither; this is the discrete Hamiltonian of Eq. NLSE)

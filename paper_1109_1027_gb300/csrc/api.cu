@@ -71,6 +71,8 @@ struct nlse_ctx {
     // Adjoint work space (nlse_adjoint), allocated on first use.
     void* adj_buf;
     size_t adj_bytes;
+    // Device copy of a host state (nlse_run_host), allocated on first use.
+    void* host_state;
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
     int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
@@ -320,6 +322,7 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
 void release(nlse_ctx* c) {
     if (!c) return;
     cudaFree(c->adj_buf);
+    cudaFree(c->host_state);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     nlse::batch2d_destroy(c->batch);
     delete[] c->bparams;
@@ -746,6 +749,21 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
         rc = enqueue_step(c, psi, st);
         if (rc) return rc;
     }
+    return NLSE_OK;
+}
+
+int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
+    g_err[0] = 0;
+    if (!c || !psi_host) return fail(NLSE_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->host_state) NLSE_CUDA(cudaMalloc(&c->host_state, c->cbytes), "allocating the device state");
+    NLSE_CUDA(cudaMemcpyAsync(c->host_state, psi_host, c->cbytes, cudaMemcpyHostToDevice, st), "state copy in");
+    if (c->state_psi == c->host_state) c->state_psi = nullptr;    // a new state: no compensated part yet
+    int rc = nlse_run(c, c->host_state, nsteps, stream);
+    if (rc) return rc;
+    NLSE_CUDA(cudaMemcpyAsync(psi_host, c->host_state, c->cbytes, cudaMemcpyDeviceToHost, st), "state copy out");
+    NLSE_CUDA(cudaStreamSynchronize(st), "synchronise");
     return NLSE_OK;
 }
 

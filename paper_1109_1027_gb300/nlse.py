@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -70,6 +71,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_lap2shoc": ([vp, vp, vp, vp], ctypes.c_int),
         "nlse_rk4_step": ([vp, vp, vp], ctypes.c_int),
         "nlse_run": ([vp, vp, i64, vp], ctypes.c_int),
+        "nlse_run_host": ([vp, vp, i64, vp], ctypes.c_int),
         "nlse_invariants": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
         "nlse_reset_compensation": ([vp, vp], ctypes.c_int),
         "nlse_check": ([vp, vp], ctypes.c_int),
@@ -159,6 +161,15 @@ def nlse_rk4_step(ctx, psi_ptr: int, stream=None) -> None:
 
 def nlse_run(ctx, psi_ptr: int, nsteps: int, stream=None) -> None:
     _raise(load_library().nlse_run(ctx, ctypes.c_void_p(psi_ptr), int(nsteps), _stream(stream)))
+
+
+def nlse_run_host(ctx, host_ptr: int, nsteps: int, stream=None) -> None:
+    _raise(load_library().nlse_run_host(ctx, ctypes.c_void_p(host_ptr), int(nsteps), _stream(stream)))
+
+
+def _check_host(t: torch.Tensor, dtype, numel: int):
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"expected a contiguous host tensor of {numel} {dtype}")
 
 
 def nlse_invariants(ctx, psi_ptr: int, stream=None, energy: bool = True):
@@ -252,6 +263,12 @@ class Solver:
         nlse_run(self.ctx, psi.data_ptr(), nsteps)
         return psi
 
+    def run_host(self, psi_host: torch.Tensor, nsteps: int) -> torch.Tensor:
+        """nsteps steps of a state held in (preferably pinned) host memory, in place."""
+        _check_host(psi_host, self.cdtype, int(np.prod(self.shape)))
+        nlse_run_host(self.ctx, psi_host.data_ptr(), nsteps)
+        return psi_host
+
     def invariants(self, psi: torch.Tensor, energy: bool = True):
         """(mass, energy, dt_max) in FP64 (energy None when not asked for)."""
         self._check_psi(psi)
@@ -341,6 +358,12 @@ class BatchSolver:
         self._check_psi(psi)
         nlse_run(self.ctx, psi.data_ptr(), nsteps)
         return psi
+
+    def run_host(self, psi_host, nsteps):
+        """nsteps steps of the flat batch state held in host memory, in place."""
+        _check_host(psi_host, self.cdtype, sum(int(np.prod(s_)) for s_ in self.shapes))
+        nlse_run_host(self.ctx, psi_host.data_ptr(), nsteps)
+        return psi_host
 
     def rk4_step(self, psi):
         self._check_psi(psi)

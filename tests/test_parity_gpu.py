@@ -588,3 +588,23 @@ def test_1d_resident_loop_equals_tiled_steps(n, prec, bc):
     for bad in (3, 32, -1):
         with pytest.raises(nlse.NLSEError):
             solver.set_tiling(nlse.TILE_1D_RESIDENT, bad)
+
+
+@pytest.mark.parametrize("shape,prec", [((67, 200), "fp32"), ((35, 18, 40), "fp64"), ((1030,), "fp32")])
+def test_run_host_equals_a_device_run(shape, prec):
+    """nlse_run_host on a pinned host state gives the bits of nlse_run on the
+    same state in device memory (fresh compensated part in both)."""
+    psi, V = _problem(shape, 57)
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    _, _, dtmax = oracle.invariants(prob, rounded(psi, prec), rounded(V, prec))
+    solver = nlse.Solver(to_dev(V, prec), h, 0.5 * dtmax, a, s, prec=prec)
+    x = to_dev(psi, prec)
+    solver.run(x, 40)
+    host = to_dev(psi, prec).cpu().pin_memory()
+    solver.run_host(host, 40)
+    assert torch.equal(host, x.cpu())
+    solver.run_host(host, 0)
+    assert torch.equal(host, x.cpu())
+    with pytest.raises(ValueError):
+        solver.run_host(x, 1)                       # a device tensor is not a host state
