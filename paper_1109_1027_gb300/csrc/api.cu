@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <algorithm>
 #include <new>
 #include <string>
@@ -73,6 +74,8 @@ struct nlse_ctx {
     size_t adj_bytes;
     // Device copy of a host state (nlse_run_host), allocated on first use.
     void* host_state;
+    // Batch: per-instance table of the one-launch invariants (device).
+    nlse::InvBatchEntry* inv_table;
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
     int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
@@ -280,28 +283,23 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     return NLSE_OK;
 }
 
-// Per-instance invariants of a batch: the reductions of each instance into
-// its own rows of partials and its own result row, one copy, one sync.
+// Per-instance invariants of a batch: one launch over every instance's rows
+// of partials, one launch reducing each instance's rows into its result row,
+// one copy, one sync.
 int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
                           cudaStream_t st) {
-    const size_t cb = c->p.prec == NLSE_FP32 ? 8 : 16, rb = c->p.prec == NLSE_FP32 ? 4 : 8;
-    const bool with_lo = c->lo && psi == c->state_psi;
-    for (int i = 0; i < c->count; ++i) {
-        const nlse_params& q = c->bparams[i];
-        nlse::InvLaunch L;
-        L.dim = 2;
-        L.n[0] = q.n[0]; L.n[1] = q.n[1]; L.n[2] = 1;
-        L.prec = q.prec; L.lap = q.lap; L.bc = q.bc;
-        L.h = q.h; L.a = q.a; L.s = q.s;
-        L.psi = static_cast<const char*>(psi) + c->boff[i] * cb;
-        L.lo = with_lo ? static_cast<const char*>(c->lo) + c->boff[i] * cb : nullptr;
-        L.V = static_cast<const char*>(c->V) + c->boff[i] * rb;
-        L.energy = energy != nullptr;
-        NLSE_CUDA(nlse::launch_invariants(L, c->partials + (size_t)c->brow[i] * nlse::kPartialWidth,
-                                          c->brow[i + 1] - c->brow[i],
-                                          c->red_out + (size_t)i * nlse::kPartialWidth, st),
-                  "invariants launch");
-    }
+    nlse::InvBatchLaunch B;
+    B.table = c->inv_table;
+    B.count = c->count;
+    B.nrows = c->nblocks;
+    B.prec = c->p.prec; B.bc = c->p.bc; B.lap = c->p.lap;
+    B.psi = psi;
+    B.lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
+    B.V = c->V;
+    B.energy = energy != nullptr;
+    B.partials = c->partials;
+    B.out = c->red_out;
+    NLSE_CUDA(nlse::launch_invariants_batch(B, st), "invariants launch");
     NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth * c->count,
                               cudaMemcpyDeviceToHost, st), "invariants copy");
     NLSE_CUDA(cudaStreamSynchronize(st), "invariants synchronise");
@@ -323,6 +321,7 @@ void release(nlse_ctx* c) {
     if (!c) return;
     cudaFree(c->adj_buf);
     cudaFree(c->host_state);
+    cudaFree(c->inv_table);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     nlse::batch2d_destroy(c->batch);
     delete[] c->bparams;
@@ -464,6 +463,20 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
     TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth * count), "allocating results");
     TRY(cudaMallocHost((void**)&c->host_out, sizeof(double) * nlse::kPartialWidth * count),
         "allocating pinned results");
+    {
+        std::vector<nlse::InvBatchEntry> tab(count);
+        for (int i = 0; i < count; ++i) {
+            tab[i].off = c->boff[i];
+            tab[i].nx = (int)p[i].n[0];
+            tab[i].ny = (int)p[i].n[1];
+            tab[i].h = p[i].h; tab[i].a = p[i].a; tab[i].s = p[i].s;
+            tab[i].row0 = c->brow[i];
+            tab[i].row1 = c->brow[i + 1];
+        }
+        TRY(cudaMalloc((void**)&c->inv_table, sizeof(nlse::InvBatchEntry) * count), "allocating the instance table");
+        TRY(cudaMemcpy(c->inv_table, tab.data(), sizeof(nlse::InvBatchEntry) * count, cudaMemcpyHostToDevice),
+            "uploading the instance table");
+    }
     TRY(nlse::batch2d_create(count, p, V_dev, c->Y[0], c->Y[1], c->acc, c->lo, &c->batch), "building the batch plan");
 #undef TRY
     *out = c;

@@ -203,12 +203,10 @@ __device__ Acc block_reduce(Acc a) {
 // ENERGY = false leaves the energy sum at zero: the time-step bound needs
 // only the pointwise extremes (and, for MSD, the boundary term), which read
 // each point once, while the energy's FP64 Laplacian is the costly part.
+// Accumulates the points first, first + stride, ... of one grid into a.
 template <typename R, bool ENERGY>
-__global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, int64_t npts,
-                                                                  double* partials) {
-    Acc a = acc_identity();
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts;
-         p += (int64_t)gridDim.x * blockDim.x) {
+__device__ void accumulate(const InvView<R>& v, int64_t npts, int64_t first, int64_t stride, Acc& a) {
+    for (int64_t p = first; p < npts; p += stride) {
         int c[3];
         int64_t r = p;
         c[0] = (int)(r % v.n[0]); r /= v.n[0];
@@ -240,16 +238,76 @@ __global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, 
             a.bmax = fmax(a.bmax, B);
         }
     }
-    a = block_reduce(a);
-    if (threadIdx.x == 0) {
-        double* row = partials + (int64_t)blockIdx.x * kPartialWidth;
-        row[0] = a.mass; row[1] = a.energy; row[2] = a.lmin;
-        row[3] = a.lmax; row[4] = a.bmax; row[5] = a.nonfinite;
-    }
 }
+
+__device__ __forceinline__ void write_row(double* row, const Acc& a) {
+    row[0] = a.mass; row[1] = a.energy; row[2] = a.lmin;
+    row[3] = a.lmax; row[4] = a.bmax; row[5] = a.nonfinite;
+}
+
+template <typename R, bool ENERGY>
+__global__ void __launch_bounds__(kInvThreads) invariants_partial(InvView<R> v, int64_t npts,
+                                                                  double* partials) {
+    Acc a = acc_identity();
+    accumulate<R, ENERGY>(v, npts, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                          a);
+    a = block_reduce(a);
+    if (threadIdx.x == 0) write_row(partials + (int64_t)blockIdx.x * kPartialWidth, a);
+}
+
+// A batch of 2D instances in one launch: block b belongs to the instance whose
+// rows [row0, row1) of partials contain b and covers the points that block
+// b - row0 of a single-instance launch of row1 - row0 blocks would, so the
+// partial rows are those of one launch per instance, bit for bit.
+template <typename R, bool ENERGY>
+__global__ void __launch_bounds__(kInvThreads) invariants_batch_partial(const InvBatchEntry* tab, int count,
+                                                                        const cplx<R>* psi, const cplx<R>* lo,
+                                                                        const R* V, int bc, int lap,
+                                                                        double* partials) {
+    const int b = blockIdx.x;
+    int lo_i = 0, hi_i = count - 1;                 // last instance with row0 <= b
+    while (lo_i < hi_i) {
+        const int mid = (lo_i + hi_i + 1) / 2;
+        if (tab[mid].row0 <= b) lo_i = mid;
+        else hi_i = mid - 1;
+    }
+    const InvBatchEntry e = tab[lo_i];
+    InvView<R> v;
+    v.psi = psi + e.off;
+    v.lo = lo ? lo + e.off : nullptr;
+    v.V = V + e.off;
+    v.dim = 2;
+    v.n[0] = e.nx; v.n[1] = e.ny; v.n[2] = 1;
+    v.stride[0] = 1; v.stride[1] = e.nx; v.stride[2] = (int64_t)e.nx * e.ny;
+    v.h2a = e.h * e.h / e.a;
+    v.inv_h2 = 1.0 / (e.h * e.h);
+    v.inv_6h2 = 1.0 / (6.0 * e.h * e.h);
+    v.a = e.a; v.s = e.s; v.inv_a = 1.0 / e.a;
+    v.bc = bc; v.lap = lap;
+    const int nblk = e.row1 - e.row0;
+    Acc a = acc_identity();
+    accumulate<R, ENERGY>(v, (int64_t)e.nx * e.ny, (b - e.row0) * (int64_t)blockDim.x + threadIdx.x,
+                          (int64_t)nblk * blockDim.x, a);
+    a = block_reduce(a);
+    if (threadIdx.x == 0) write_row(partials + (int64_t)b * kPartialWidth, a);
+}
+
+__device__ void reduce_rows(const double* partials, int nrows, double* out);
 
 __global__ void __launch_bounds__(kInvThreads) invariants_final(const double* partials, int nrows,
                                                                 double* out) {
+    reduce_rows(partials, nrows, out);
+}
+
+// One block per instance: its rows [row0, row1) into its result row.
+__global__ void __launch_bounds__(kInvThreads) invariants_batch_final(const InvBatchEntry* tab,
+                                                                      const double* partials, double* out) {
+    const InvBatchEntry e = tab[blockIdx.x];
+    reduce_rows(partials + (int64_t)e.row0 * kPartialWidth, e.row1 - e.row0,
+                out + (int64_t)blockIdx.x * kPartialWidth);
+}
+
+__device__ void reduce_rows(const double* partials, int nrows, double* out) {
     Acc a = acc_identity();
     for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
         const double* row = partials + (int64_t)i * kPartialWidth;
@@ -305,6 +363,29 @@ cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks,
                               cudaStream_t st) {
     return L.prec == 0 ? launch_r<float>(L, partials, nblocks, out, st)
                        : launch_r<double>(L, partials, nblocks, out, st);
+}
+
+namespace {
+template <typename R>
+cudaError_t launch_batch_r(const InvBatchLaunch& B, cudaStream_t st) {
+    const cplx<R>* psi = (const cplx<R>*)B.psi;
+    const cplx<R>* lo = (const cplx<R>*)B.lo;
+    const R* V = (const R*)B.V;
+    if (B.energy)
+        invariants_batch_partial<R, true><<<B.nrows, kInvThreads, 0, st>>>(B.table, B.count, psi, lo, V, B.bc, B.lap,
+                                                                           B.partials);
+    else
+        invariants_batch_partial<R, false><<<B.nrows, kInvThreads, 0, st>>>(B.table, B.count, psi, lo, V, B.bc, B.lap,
+                                                                            B.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    invariants_batch_final<<<B.count, kInvThreads, 0, st>>>(B.table, B.partials, B.out);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_invariants_batch(const InvBatchLaunch& B, cudaStream_t st) {
+    return B.prec == 0 ? launch_batch_r<float>(B, st) : launch_batch_r<double>(B, st);
 }
 
 }  // namespace nlse

@@ -137,6 +137,27 @@ struct InvLaunch {
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);
 
+// Invariants of every instance of a batch in one launch (plus one for the
+// per-instance reduction), with the partial rows a launch per instance gives.
+struct InvBatchEntry {
+    int64_t off;            // first element of the instance in the flat buffers
+    int nx, ny;
+    double h, a, s;
+    int row0, row1;         // its rows of partials
+};
+struct InvBatchLaunch {
+    const InvBatchEntry* table;   // device, count entries, row0 ascending
+    int count, nrows;
+    int prec, bc, lap;
+    const void* psi;
+    const void* lo;         // FP32 compensated part or nullptr
+    const void* V;
+    bool energy;
+    double* partials;       // nrows x kPartialWidth
+    double* out;            // count x kPartialWidth
+};
+cudaError_t launch_invariants_batch(const InvBatchLaunch& B, cudaStream_t st);
+
 // Records msg as the calling thread's nlse_last_error() and returns code.
 int report_error(int code, const char* msg);
 cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks, double* out,

@@ -170,3 +170,21 @@ def test_batch_tiling_variants_give_identical_results():
         outs.append(psi)
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_invariants_equal_the_single_grid_ones(prec):
+    """The one-launch batch reduction covers each instance with the blocks a
+    single-grid launch uses, so mass, energy and dt_max agree bit for bit."""
+    insts = _batch(SIDES, seed=9)
+    cdt, rdt = (torch.complex64, torch.float32) if prec == "fp32" else (torch.complex128, torch.float64)
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], 1e-4,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec)
+    psi = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
+    m, e, d = bs.invariants(psi)
+    for i, q in enumerate(insts):
+        sv = nlse.Solver(torch.from_numpy(q["V"]).to(DEV).to(rdt).contiguous(), q["h"], 1e-4, q["a"], q["s"],
+                         prec=prec)
+        mi, ei, di = sv.invariants(torch.from_numpy(q["psi"]).to(DEV).to(cdt).contiguous())
+        assert (m[i], e[i], d[i]) == (mi, ei, di), (i, q["shape"])
