@@ -232,9 +232,11 @@ int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const voi
  * context's precision (not modified); dpsi0_dev (same type) receives
  * dL/dRe(psi0) + i dL/dIm(psi0); dV_dev receives dL/dV as FP64 (double,
  * accumulated in FP64); *loss the FP64 loss.  The context allocates its work
- * space on first use (state + (nsteps/ckpt_every) checkpoints + ckpt_every
- * states + 7 fields).  Uses the context's compensated part, which then no
- * longer belongs to any caller state.  Synchronises the stream. */
+ * space on first use: (5 + 4 ckpt_every + c nsteps/ckpt_every) fields of the
+ * state's size (c = 2 in FP32, 1 in FP64), as the reverse sweep keeps the four
+ * stage inputs of every step of a segment.  Uses the context's compensated
+ * part, which then no longer belongs to any caller state.  Synchronises the
+ * stream. */
 int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
                  int64_t ckpt_every, void* dpsi0_dev, void* dV_dev, double* loss, void* stream);
 

@@ -498,10 +498,11 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
     const int64_t seglen = nsteps < ckpt_every ? nsteps : ckpt_every;
     const int nb = nlse::loss_num_blocks(c->npts);
-    // Work space: state S, checkpoints (state + compensated part), one
-    // segment of states, Y2 Y3 Y4, two cotangents, two adjoint states, loss partials.
+    // Work space: state S, checkpoints (state + compensated part), the four
+    // stage inputs (Psi_n, Y2, Y3, Y4) of every step of one segment, two
+    // cotangents, two adjoint states, loss partials.
     const size_t ck_bytes = (size_t)nseg * cb * (has_lo ? 2 : 1);
-    const size_t need = cb + ck_bytes + (size_t)seglen * cb + 7 * cb + sizeof(double) * (nb + 1);
+    const size_t need = cb + ck_bytes + 4 * (size_t)seglen * cb + 4 * cb + sizeof(double) * (nb + 1);
     if (need > c->adj_bytes) {
         cudaFree(c->adj_buf);
         c->adj_buf = nullptr;
@@ -512,17 +513,15 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     char* base = static_cast<char*>(c->adj_buf);
     char* S = base;
     char* ck = S + cb;
-    char* seg = ck + ck_bytes;
-    char* Y2 = seg + (size_t)seglen * cb;
-    char* Y3 = Y2 + cb;
-    char* Y4 = Y3 + cb;
-    char* W = Y4 + cb;
+    char* seg = ck + ck_bytes;                   // [seglen][4] stage inputs
+    char* W = seg + 4 * (size_t)seglen * cb;
     char* WN = W + cb;
     char* LA = WN + cb;
     char* LB = LA + cb;
     double* part = reinterpret_cast<double*>(LB + cb);
     double* lossd = part + nb;
     auto ckp = [&](int64_t i) { return ck + (size_t)i * cb * (has_lo ? 2 : 1); };
+    auto yin = [&](int64_t m, int j) { return seg + ((size_t)m * 4 + (size_t)(j - 1)) * cb; };   // Y_j of step m
 
     // Forward pass with checkpoints.  S is the state; the context's
     // compensated part belongs to S for the duration of the call.
@@ -544,6 +543,7 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     char* lam = LB;
     StageLaunch F = base_launch(c);
     F.acc = c->acc;
+    F.lo = c->lo;
     nlse::AdjLaunch A;
     A.prec = c->p.prec; A.lap = c->p.lap;
     A.nx = c->p.n[0]; A.ny = c->p.n[1];
@@ -554,25 +554,29 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     const double k = c->p.dt;
     for (int64_t g = nseg - 1; g >= 0; --g) {
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
-        NLSE_CUDA(cudaMemcpyAsync(S, ckp(g), cb, cudaMemcpyDeviceToDevice, st), "restore");
+        // Recompute the segment from its checkpoint with the fused stage
+        // kernels, keeping every stage input: stage j of step m reads
+        // Y_j(m) and writes Y_{j+1}(m); stage 4 writes Psi_{m+1} = Y_1(m+1).
+        // Same arithmetic, and so the same bits, as the forward pass.
+        NLSE_CUDA(cudaMemcpyAsync(yin(0, 1), ckp(g), cb, cudaMemcpyDeviceToDevice, st), "restore");
         if (has_lo) NLSE_CUDA(cudaMemcpyAsync(c->lo, ckp(g) + cb, cb, cudaMemcpyDeviceToDevice, st), "restore");
         for (int64_t m = 0; m < steps; ++m) {
-            NLSE_CUDA(cudaMemcpyAsync(seg + (size_t)m * cb, S, cb, cudaMemcpyDeviceToDevice, st), "segment state");
-            if (m + 1 < steps && (rc = enqueue_step(c, S, st))) return rc;
+            for (int sg = 1; sg <= 4; ++sg) {
+                if (sg == 4 && m + 1 == steps) break;     // the segment's last state is not needed
+                F.stage = sg;
+                F.psi = yin(m, 1);
+                F.psi_out = sg == 4 ? yin(m + 1, 1) : nullptr;
+                F.yin = yin(m, sg);
+                F.yout = sg < 4 ? yin(m, sg + 1) : nullptr;
+                cudaError_t e = launch_stage(F, st);
+                if (e != cudaSuccess) return cuda_fail(e, "segment recompute");
+            }
         }
         for (int64_t m = steps - 1; m >= 0; --m) {
-            const void* psi_n = seg + (size_t)m * cb;
-            // Stage inputs Y2, Y3, Y4 of this step, recomputed by the forward stage kernels.
-            const void* fin[4] = {nullptr, psi_n, Y2, Y3};
-            void* fout[4] = {nullptr, Y2, Y3, Y4};
-            for (int sg = 1; sg <= 3; ++sg) {
-                F.stage = sg;
-                F.psi = psi_n;
-                F.yin = fin[sg];
-                F.yout = fout[sg];
-                cudaError_t e = launch_stage(F, st);
-                if (e != cudaSuccess) return cuda_fail(e, "stage recompute");
-            }
+            const void* psi_n = yin(m, 1);
+            const void* Y2 = yin(m, 2);
+            const void* Y3 = yin(m, 3);
+            const void* Y4 = yin(m, 4);
             // Stages 4 .. 1 reversed.
             const void* w[5] = {nullptr, W, WN, W, lamp};
             const double sw[5] = {0, 1, 1, 1, k / 6.0};

@@ -176,7 +176,7 @@ bool stage_2d_tma_eligible(const StageLaunch& L) {
     if (L.bc != 0) return false;
     const int64_t nx = L.n[0];
     if (nx % (L.prec == 0 ? 4 : 2) != 0) return false;
-    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
+    const void* ptrs[8] = {L.yin, L.V, L.psi, L.psi_out, L.acc, L.lo, L.yout, L.lap_out};
     for (const void* p : ptrs)
         if ((uintptr_t)p % 16) return false;
     return encoder() != nullptr;

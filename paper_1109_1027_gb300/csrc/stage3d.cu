@@ -331,7 +331,7 @@ cudaError_t launch_stage(const StageLaunch& L, cudaStream_t st) {
 // 16-byte aligned buffers; other 3D grids use the generic kernel.
 bool stage_3d_tma_eligible(const StageLaunch& L) {
     if (L.prec != 0 || L.bc != 0 || L.n[0] % 4 != 0) return false;
-    const void* ptrs[7] = {L.yin, L.V, L.psi, L.acc, L.lo, L.yout, L.lap_out};
+    const void* ptrs[8] = {L.yin, L.V, L.psi, L.psi_out, L.acc, L.lo, L.yout, L.lap_out};
     for (const void* p : ptrs)
         if ((uintptr_t)p % 16) return false;
     return encoder() != nullptr;
