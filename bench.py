@@ -481,6 +481,37 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
         out[prec] = {"value": world * npts * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
         bs.close()
     out["fp32"]["achieved_gbs"] = BYTES_PER_UPDATE_FP32 * npts / (out["fp32"]["ms_per_step"] * 1e-3) / 1e9
+
+    # The paper's unfused FP64 schedule run instance by instance (one context
+    # each, the per-instance baseline), on every 8th instance for a few steps.
+    sample = list(range(0, len(insts), 8))
+    pst = 10
+    V64c = V64.cpu()
+    psi64c = psi64.cpu()
+    offs = np.cumsum([0] + [q.shape[0] * q.shape[1] for q in insts])
+    solvers, states = [], []
+    for i in sample:
+        q = insts[i]
+        Vi = V64c[offs[i]:offs[i + 1]].reshape(q.shape).to(dev).contiguous()
+        solvers.append(nlse.Solver(Vi, q.h, dts[i], q.a, q.s, prec="fp64", plain=True, check_stability=False))
+        states.append(psi64c[offs[i]:offs[i + 1]].reshape(q.shape).to(dev).contiguous())
+    for sv, xs in zip(solvers, states):
+        sv.run(xs, 2)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for sv, xs in zip(solvers, states):
+        sv.run(xs, pst)
+    p1.record()
+    torch.cuda.synchronize()
+    msp = max_over_ranks(p0.elapsed_time(p1))
+    spts = sum(insts[i].shape[0] * insts[i].shape[1] for i in sample)
+    for sv in solvers:
+        sv.close()
+    out["fp64_plain_per_instance"] = {"value": world * spts * pst / (msp * 1e-3), "unit": UNIT,
+                                      "instances": len(sample), "points": int(spts), "steps": pst,
+                                      "what": "paper's unfused FP64 schedule, one context per instance, "
+                                              "instances in sequence (every 8th instance of the batch)"}
     errs, collapsed = {-1: [], 1: []}, 0
     a64 = res["fp64"]
     a32 = res["fp32"].to(torch.complex128)
