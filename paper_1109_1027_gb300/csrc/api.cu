@@ -121,6 +121,7 @@ StageLaunch base_launch(const nlse_ctx* c) {
     L.flag = c->flag;
     L.tile_rows = c->tile_rows ? c->tile_rows : 16;
     L.tile_planes = c->tile_planes ? c->tile_planes : 32;
+    L.keep_v = nlse::keep_v_in_l2((size_t)c->npts * (c->p.prec == NLSE_FP32 ? 4 : 8)) ? 1 : 0;
     return L;
 }
 

@@ -63,6 +63,7 @@ struct StageIO {
     int* flag;
     R c_acc;      // weight of F in the accumulated increment: k/6, k/3, k/3, k/6
     R c_y;        // weight of F in the next stage input: k/2, k/2, k
+    int keep_v;   // TMA kernels: load V with an L2 evict-last hint
 };
 
 template <typename R>
@@ -77,6 +78,7 @@ StageIO<R> make_io(const StageLaunch& L) {
     io.lap = (cplx<R>*)L.lap_out;
     io.V = (const R*)L.V;
     io.flag = L.flag;
+    io.keep_v = L.keep_v;
     const double k = L.dt;
     const double wa[5] = {0.0, k / 6.0, k / 3.0, k / 3.0, k / 6.0};
     const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};

@@ -31,7 +31,12 @@ struct StageLaunch {
                             // 2 = a bounded device-side wait timed out
     int tile_rows;          // 2D TMA kernel: rows per CTA (8, 16, 32)
     int tile_planes;        // 3D TMA kernel: z planes per CTA (32, 64, 128)
+    int keep_v;             // TMA kernels: load V with an L2 evict-last hint (V small enough
+                            // to stay in L2 across the four stages of a step)
 };
+
+// Whether V of the given size should be kept resident in L2 (a quarter of it).
+bool keep_v_in_l2(size_t v_bytes);
 
 cudaError_t launch_stage_1d(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);

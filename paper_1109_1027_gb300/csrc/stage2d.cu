@@ -169,6 +169,17 @@ cudaError_t launch_lap(const StageLaunch& L, cudaStream_t st) {
 
 }  // namespace
 
+bool keep_v_in_l2(size_t v_bytes) {
+    static int l2 = -1;
+    if (l2 < 0) {
+        int dev = 0, bytes = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+            bytes = 0;
+        l2 = bytes;
+    }
+    return v_bytes <= (size_t)l2 / 4;
+}
+
 // TMA needs 16-byte aligned bases and row pitches: nx a multiple of 4
 // (complex64 rows and float V rows) or of 2 (complex128 rows, double V).
 // The column pairs also need nx even.

@@ -11,7 +11,9 @@
 //     on 128-byte aligned shared addresses);
 //   * the epilogue ring (2 slots, one output row ahead): V, and for stages
 //     2-4 Psi^n and the RK4 accumulator (stage 4 in FP32: the compensated
-//     part too) on the output row.
+//     part too) on the output row.  When V fits in a quarter of L2 its loads
+//     carry an evict-last policy, so that V, read by every stage, stays in L2
+//     while the other fields stream through.
 // Each thread keeps its two columns' stage input, their outer x neighbours
 // and D in registers as a sliding window; the x neighbours of D travel
 // through a two-row shared ring.  The walk runs down the grid on odd stages
@@ -146,7 +148,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
         mbar_expect_tx(bar, bytes);
-        tma_load_2d(dst + L::E_V, m_V, x0, r, bar);
+        if (io.keep_v) tma_load_2d_hint(dst + L::E_V, m_V, x0, r, bar, l2_evict_last());
+        else tma_load_2d(dst + L::E_V, m_V, x0, r, bar);
         if (NEED_PA) {
             load_cplx_box<R>(dst + L::E_PSI, m_psi, x0, r, bar);
             load_cplx_box<R>(dst + L::E_ACC, m_acc, x0, r, bar);

@@ -139,7 +139,15 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
         mbar_expect_tx(bar, bytes);
-        load_e(dst + L::E_V, &m_V, z, bar);
+        if (io.keep_v) {
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint "
+                "[%0], [%1, {%2, %3, %4}], [%5], %6;"
+                ::"r"(dst + L::E_V), "l"(reinterpret_cast<uint64_t>(&m_V)), "r"(x0), "r"(y0), "r"(z), "r"(bar),
+                  "l"(l2_evict_last()) : "memory");
+        } else {
+            load_e(dst + L::E_V, &m_V, z, bar);
+        }
         if (NEED_PA) {
             load_e(dst + L::E_PSI, &m_psi, z, bar);
             load_e(dst + L::E_ACC, &m_acc, z, bar);
