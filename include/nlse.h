@@ -250,11 +250,6 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
 #define NLSE_TILE_PLANES 2        /* 3D FP32: z planes per CTA, 32 (default), 64 or 128 */
 #define NLSE_TILE_BATCH_NARROW 3  /* batch: instances with n[0] <= value get 64-column
                                      tiles, the others 256-column tiles (default 64)    */
-#define NLSE_TILE_BATCH_L2 5      /* batch: a budget in MiB (0: off, the default).  The
-                                     instances are cut into blocks whose working set
-                                     (Psi, Y0, Y1, acc, lo, V) fits the budget, and a
-                                     step runs its four stages block by block, so that a
-                                     block's fields can stay in L2 between its stages   */
 #define NLSE_TILE_1D_RESIDENT 4   /* 1D grids of up to 4096 points: a power of two
                                      c <= 16 runs nlse_run / nlse_rk4_step as one
                                      launch for all steps on a cluster of at most c

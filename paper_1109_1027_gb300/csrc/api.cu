@@ -176,16 +176,13 @@ int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
     L.lo = c->lo;
     const void* in[5] = {nullptr, psi, c->Y[0], c->Y[1], c->Y[0]};
     void* out[5] = {nullptr, c->Y[0], c->Y[1], c->Y[0], nullptr};
-    // A batch cut into L2 blocks runs the four stages block by block.
-    const int nblk = c->batch ? nlse::batch2d_blocks(c->batch) : 1;
-    for (int blk = 0; blk < nblk; ++blk)
-        for (int s = 1; s <= 4; ++s) {
-            L.stage = s;
-            L.yin = in[s];
-            L.yout = out[s];
-            cudaError_t e = c->batch ? nlse::batch2d_launch_block(c->batch, L, blk, st) : launch_stage(L, st);
-            if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
-        }
+    for (int s = 1; s <= 4; ++s) {
+        L.stage = s;
+        L.yin = in[s];
+        L.yout = out[s];
+        cudaError_t e = c->batch ? nlse::batch2d_launch(c->batch, L, st) : launch_stage(L, st);
+        if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
+    }
     return NLSE_OK;
 }
 
@@ -638,16 +635,9 @@ int nlse_set_tiling(nlse_ctx* c, int key, int value) {
         case NLSE_TILE_BATCH_NARROW: {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             if (value < 0) return fail(NLSE_EINVAL, "the narrow-tile width bound must be >= 0");
-            cudaError_t e = nlse::batch2d_retile(c->batch, value, nlse::batch2d_l2_mb(c->batch));
+            cudaError_t e = nlse::batch2d_retile(c->batch, value);
             if (e != cudaSuccess) return cuda_fail(e, "rebuilding the batch tiles");
             c->maps_psi = nullptr;                       // re-encode the maps for the new box widths
-            break;
-        }
-        case NLSE_TILE_BATCH_L2: {
-            if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
-            if (value < 0 || value > 4096) return fail(NLSE_EINVAL, "the L2 block budget must be 0 to 4096 MiB");
-            cudaError_t e = nlse::batch2d_retile(c->batch, nlse::batch2d_narrow(c->batch), value);
-            if (e != cudaSuccess) return cuda_fail(e, "rebuilding the batch tiles");
             break;
         }
         default:
@@ -668,10 +658,6 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
             *value = nlse::batch2d_narrow(c->batch);
             return NLSE_OK;
         case NLSE_TILE_1D_RESIDENT: *value = resident_cluster(c); return NLSE_OK;
-        case NLSE_TILE_BATCH_L2:
-            if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
-            *value = nlse::batch2d_l2_mb(c->batch);
-            return NLSE_OK;
     }
     return fail(NLSE_EINVAL, "unknown tiling key %d", key);
 }

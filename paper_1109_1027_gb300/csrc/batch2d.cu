@@ -133,10 +133,6 @@ struct BatchPlan {
     int ntiles[2] = {0, 0};
     int nt[2] = {32, 128};
     int narrow = 64;
-    // L2 blocking: instances are cut into blocks whose working set fits the
-    // budget, and a step runs its four stages block by block (0: one block).
-    int l2_mb = 0;
-    std::vector<int> blk_start[2], blk_count[2];   // per block, per tile group: range in the list
     const void* bases[6] = {};                // psi, Y0, Y1, acc, lo, V
 };
 
@@ -148,7 +144,7 @@ int64_t batch2d_points(const nlse_params& p) { return p.n[0] * p.n[1]; }
 
 // Tile lists: instances with n[0] <= narrow get 64-column tiles (one warp),
 // the rest 256-column tiles; largest instances first.
-cudaError_t build_tiles(BatchPlan* b, int narrow, int l2_mb) {
+cudaError_t build_tiles(BatchPlan* b, int narrow) {
     std::vector<int> order(b->count);
     for (int i = 0; i < b->count; ++i) {
         order[i] = i;
@@ -158,35 +154,12 @@ cudaError_t build_tiles(BatchPlan* b, int narrow, int l2_mb) {
         return (int64_t)b->host[x].nx * b->host[x].ny > (int64_t)b->host[y].nx * b->host[y].ny;
     });
     std::vector<int4> lists[2];
-    // Bytes per point of the fields a step touches: Psi, Y0, Y1, acc (and the
-    // FP32 compensated part), V.
-    const int64_t bpp = b->prec == 0 ? 5 * 8 + 4 : 4 * 16 + 8;
-    const int64_t budget = (int64_t)l2_mb << 20;
-    for (int g = 0; g < 2; ++g) {
-        b->blk_start[g].clear();
-        b->blk_count[g].clear();
-    }
-    int64_t used = 0;
-    auto open_block = [&]() {
-        for (int g = 0; g < 2; ++g) {
-            b->blk_start[g].push_back((int)lists[g].size());
-            b->blk_count[g].push_back(0);
-        }
-        used = 0;
-    };
-    open_block();
     for (int i : order) {
         const BatchDesc& d = b->host[i];
-        const int64_t bytes = (int64_t)d.nx * d.ny * bpp;
-        if (budget > 0 && used > 0 && used + bytes > budget) open_block();
-        used += bytes;
         const int g = d.nt == 32 ? 0 : 1;
         const int txc = 2 * d.nt;
         for (int y0 = 0; y0 < d.ny; y0 += TYB)
-            for (int x0 = 0; x0 < d.nx; x0 += txc) {
-                lists[g].push_back(make_int4(i, x0, y0, 0));
-                ++b->blk_count[g].back();
-            }
+            for (int x0 = 0; x0 < d.nx; x0 += txc) lists[g].push_back(make_int4(i, x0, y0, 0));
     }
     const size_t total = lists[0].size() + lists[1].size();
     cudaFree(b->tiles);
@@ -200,19 +173,16 @@ cudaError_t build_tiles(BatchPlan* b, int narrow, int l2_mb) {
         e = cudaMemcpy(b->tiles + lists[0].size(), lists[1].data(), sizeof(int4) * lists[1].size(),
                        cudaMemcpyHostToDevice);
     b->narrow = narrow;
-    b->l2_mb = l2_mb;
     return e;
 }
 
-cudaError_t batch2d_retile(BatchPlan* b, int narrow, int l2_mb) {
+cudaError_t batch2d_retile(BatchPlan* b, int narrow) {
     cudaError_t e = cudaDeviceSynchronize();          // no launch may still read the old lists
     if (e != cudaSuccess) return e;
-    return build_tiles(b, narrow, l2_mb);              // the maps are re-encoded at the next bind
+    return build_tiles(b, narrow);                     // the maps are re-encoded at the next bind
 }
 
 int batch2d_narrow(const BatchPlan* b) { return b->narrow; }
-int batch2d_l2_mb(const BatchPlan* b) { return b->l2_mb; }
-int batch2d_blocks(const BatchPlan* b) { return (int)b->blk_start[0].size(); }
 
 cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
                            void* lo, BatchPlan** out) {
@@ -247,7 +217,7 @@ cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void*
         const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};
         for (int s = 0; s < 5; ++s) { d.c_acc[s] = wa[s]; d.c_y[s] = wy[s]; }
     }
-    e = build_tiles(b, 64, 0);
+    e = build_tiles(b, 64);
     if (e != cudaSuccess) { batch2d_destroy(b); return e; }
     *out = b;
     return cudaSuccess;
@@ -270,26 +240,17 @@ cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st) {
     return cudaMemcpyAsync(b->dev, b->host, sizeof(BatchDesc) * b->count, cudaMemcpyHostToDevice, st);
 }
 
-cudaError_t batch2d_launch_block(BatchPlan* b, const StageLaunch& L, int blk, cudaStream_t st) {
+cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st) {
     // Same walk-direction alternation between stages as the single-grid kernel.
     const int dir = (L.stage % 2 == 0 && L.stage != 0) ? -1 : 1;
     const int4* lists[2] = {b->tiles, b->tiles + b->ntiles[0]};
     for (int g = 0; g < 2; ++g) {
-        const int n = b->blk_count[g][blk];
-        if (!n) continue;
-        const int4* tl = lists[g] + b->blk_start[g][blk];
+        if (!b->ntiles[g]) continue;
         cudaError_t e;
-        if (b->prec == 0) e = launch_stage_r<float>(L.stage, b->lap, b->nt[g], b->dev, tl, n, make_io<float>(L),
-                                                    dir, st);
-        else e = launch_stage_r<double>(L.stage, b->lap, b->nt[g], b->dev, tl, n, make_io<double>(L), dir, st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st) {
-    for (int blk = 0; blk < batch2d_blocks(b); ++blk) {
-        cudaError_t e = batch2d_launch_block(b, L, blk, st);
+        if (b->prec == 0) e = launch_stage_r<float>(L.stage, b->lap, b->nt[g], b->dev, lists[g], b->ntiles[g],
+                                                    make_io<float>(L), dir, st);
+        else e = launch_stage_r<double>(L.stage, b->lap, b->nt[g], b->dev, lists[g], b->ntiles[g],
+                                        make_io<double>(L), dir, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -98,13 +98,9 @@ bool batch2d_instance_ok(const nlse_params& p);
 cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
                            void* lo, BatchPlan** out);
 cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st);
-cudaError_t batch2d_retile(BatchPlan* b, int narrow, int l2_mb);   // synchronises the device
+cudaError_t batch2d_retile(BatchPlan* b, int narrow);   // synchronises the device
 int batch2d_narrow(const BatchPlan* b);
-int batch2d_l2_mb(const BatchPlan* b);
-int batch2d_blocks(const BatchPlan* b);
-// One stage over every instance, or over the instances of one L2 block.
 cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st);
-cudaError_t batch2d_launch_block(BatchPlan* b, const StageLaunch& L, int blk, cudaStream_t st);
 void batch2d_destroy(BatchPlan* b);
 
 // Adjoint of one RK4 stage on a 2D grid (adjoint2d.cu).
