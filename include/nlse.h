@@ -93,6 +93,19 @@ typedef enum {
 
 /* nlse_params.flags */
 #define NLSE_FLAG_NO_STABILITY_CHECK 1u  /* nlse_run skips the entry check of dt  */
+#define NLSE_FLAG_STACK 4u               /* dim = 2 only: the state holds n[2] >= 1
+                                            instances of the n[0] x n[1] grid, instance
+                                            i in rows i n[1] .. (i+1) n[1] - 1 of an
+                                            n[0] x (n[1] n[2]) array; all share h, dt,
+                                            a, s and V (n[0] x n[1]); each has its own
+                                            Dirichlet boundary.  One launch per stage
+                                            covers the stack; results per instance
+                                            equal a single-grid run bit for bit.
+                                            nlse_invariants gives totals over the stack
+                                            (dt_max: the smallest bound); nlse_adjoint
+                                            the summed loss, dL/dpsi0 per instance and
+                                            dL/dV summed over the instances.  Dirichlet
+                                            and the fused schedule only.           */
 #define NLSE_FLAG_PLAIN_SCHEDULE 2u      /* step with the paper's unfused schedule
                                             (Sec. 3.1): D, K_tot, K_tmp, Psi_tmp as
                                             full device arrays, one launch per

@@ -46,13 +46,18 @@ struct AdjIO {
 };
 
 template <typename R, bool CD, int J>
-__global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int nx, int ny) {
+__global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int nx, int ny, int rows1) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sU = reinterpret_cast<C*>(smem_raw);   // [PY][PX]
     C* sE = sU + PX * PY;                     // [DY][DX]
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, tid = threadIdx.x;
-    auto interior = [&](int x, int y) { return x > 0 && x < nx - 1 && y > 0 && y < ny - 1; };
+    // Interior of its stacked instance (rows1 rows each; one instance when rows1 = ny).
+    auto interior = [&](int x, int y) {
+        if (x <= 0 || x >= nx - 1 || y < 0 || y >= ny) return false;
+        const int yl = y % rows1;
+        return yl > 0 && yl < rows1 - 1;
+    };
 
     for (int i = tid; i < PX * PY; i += NT) {
         const int ly = i / PX, lx = i - ly * PX;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int n
             ybar = cadd(ybar, cscale(c.inv_6h2, csub(corners, cscale((R)4, u[0]))));
         }
         const C Y = io.Y[p];
-        const R v = io.V[p];
+        const R v = io.V[(int64_t)(gy % rows1) * nx + gx];     // V is shared by stacked instances
         const R rho = Y.x * Y.x + Y.y * Y.y;
         const C Y2 = cmake<C>(Y.x * Y.x - Y.y * Y.y, 2 * Y.x * Y.y);   // Y^2
         R gv;
@@ -139,7 +144,7 @@ cudaError_t launch_j(const AdjLaunch& L, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, NT, smem, st>>>(io, make_coef<R>(L.h, L.a, L.s), nx, ny);
+    kern<<<grid, NT, smem, st>>>(io, make_coef<R>(L.h, L.a, L.s), nx, ny, (int)(L.rows1 ? L.rows1 : L.ny));
     return cudaGetLastError();
 }
 
@@ -184,12 +189,26 @@ __global__ void sum_kernel(const double* partials, int n, double* out) {
     }
 }
 
+__global__ void stack_sum_kernel(const double* src, int count, int64_t n, double* dst) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < count; ++i) s += src[(int64_t)i * n + q];
+        dst[q] = s;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st) {
     const bool cd = L.lap == 1;
     if (L.prec == 0) return cd ? launch_r<float, true>(L, st) : launch_r<float, false>(L, st);
     return cd ? launch_r<double, true>(L, st) : launch_r<double, false>(L, st);
+}
+
+cudaError_t launch_stack_sum(const double* src, int count, int64_t n, double* dst, cudaStream_t st) {
+    const int64_t b = (n + 255) / 256;
+    stack_sum_kernel<<<(unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096), 256, 0, st>>>(src, count, n, dst);
+    return cudaGetLastError();
 }
 
 int loss_num_blocks(int64_t n) {

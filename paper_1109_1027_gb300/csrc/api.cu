@@ -76,6 +76,8 @@ struct nlse_ctx {
     void* host_state;
     // Batch: per-instance table of the one-launch invariants (device).
     nlse::InvBatchEntry* inv_table;
+    // Instances of a stack (NLSE_FLAG_STACK), else 1.
+    int stack;
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
     int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
@@ -92,6 +94,12 @@ int validate(const nlse_params* p) {
     }
     int64_t npts = 1;
     for (int ax = 0; ax < p->dim; ++ax) npts *= p->n[ax];
+    if (p->flags & NLSE_FLAG_STACK) {
+        if (p->dim != 2) return fail(NLSE_EINVAL, "NLSE_FLAG_STACK needs dim = 2");
+        if (p->n[2] < 1 || p->n[2] > (1 << 20)) return fail(NLSE_EINVAL, "stack of %lld instances", (long long)p->n[2]);
+        if (p->n[1] * p->n[2] > ((int64_t)1 << 30)) return fail(NLSE_EINVAL, "stack too tall");
+        npts *= p->n[2];
+    }
     if (npts > ((int64_t)1 << 34)) return fail(NLSE_EINVAL, "grid too large (%lld points)", (long long)npts);
     if (!(std::isfinite(p->h) && p->h > 0)) return fail(NLSE_EINVAL, "h must be positive and finite");
     if (!(std::isfinite(p->dt) && p->dt > 0)) return fail(NLSE_EINVAL, "dt must be positive and finite");
@@ -103,6 +111,8 @@ int validate(const nlse_params* p) {
         return fail(NLSE_EINVAL, "unknown lap %d", p->lap);
     if (p->bc != NLSE_BC_DIRICHLET && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "the multi-storage 2SHOC is built for Dirichlet boundaries only");
+    if ((p->flags & NLSE_FLAG_STACK) && (p->bc != NLSE_BC_DIRICHLET || (p->flags & NLSE_FLAG_PLAIN_SCHEDULE)))
+        return fail(NLSE_EUNSUPPORTED, "stacks run Dirichlet boundaries on the fused schedule only");
     if ((p->flags & NLSE_FLAG_PLAIN_SCHEDULE) && p->lap == NLSE_LAP_2SHOC_MS && p->dim > 1)
         return fail(NLSE_EUNSUPPORTED, "the unfused schedule has the single-storage 2SHOC and CD only");
     return NLSE_OK;
@@ -113,6 +123,10 @@ StageLaunch base_launch(const nlse_ctx* c) {
     std::memset(&L, 0, sizeof L);
     L.dim = c->p.dim;
     for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+    if (c->stack > 1) {                          // a stack is one tall grid with a boundary every n[1] rows
+        L.n[1] = c->p.n[1] * c->stack;
+        L.rows1 = c->p.n[1];
+    }
     L.prec = c->p.prec;
     L.lap = c->p.lap;
     L.bc = c->p.bc;
@@ -121,7 +135,7 @@ StageLaunch base_launch(const nlse_ctx* c) {
     L.flag = c->flag;
     L.tile_rows = c->tile_rows ? c->tile_rows : 16;
     L.tile_planes = c->tile_planes ? c->tile_planes : 32;
-    L.keep_v = nlse::keep_v_in_l2((size_t)c->npts * (c->p.prec == NLSE_FP32 ? 4 : 8)) ? 1 : 0;
+    L.keep_v = nlse::keep_v_in_l2((size_t)(c->npts / c->stack) * (c->p.prec == NLSE_FP32 ? 4 : 8)) ? 1 : 0;
     return L;
 }
 
@@ -264,6 +278,10 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     nlse::InvLaunch L;
     L.dim = c->p.dim;
     for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+    if (c->stack > 1) {
+        L.n[1] = c->p.n[1] * c->stack;
+        L.rows1 = c->p.n[1];
+    }
     L.prec = c->p.prec; L.lap = c->p.lap; L.bc = c->p.bc;
     L.h = c->p.h; L.a = c->p.a; L.s = c->p.s;
     L.psi = psi;
@@ -363,7 +381,8 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
     if (!c) return fail(NLSE_ENOMEM, "host allocation failed");
     c->p = *p;
     c->V = V_dev;
-    c->npts = 1;
+    c->stack = (p->flags & NLSE_FLAG_STACK) ? (int)p->n[2] : 1;
+    c->npts = c->stack;
     for (int ax = 0; ax < p->dim; ++ax) c->npts *= p->n[ax];
     c->cbytes = (size_t)c->npts * (p->prec == NLSE_FP32 ? 8 : 16);
 
@@ -417,8 +436,8 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
         if (rc) return fail(rc, "instance %d: %s", i, std::string(g_err).c_str());
         if (p[i].prec != p[0].prec || p[i].lap != p[0].lap || p[i].bc != p[0].bc || p[i].flags != p[0].flags)
             return fail(NLSE_EINVAL, "instance %d: prec, lap, bc and flags must match instance 0", i);
-        if (p[i].flags & NLSE_FLAG_PLAIN_SCHEDULE)
-            return fail(NLSE_EUNSUPPORTED, "batches run the fused schedule only");
+        if (p[i].flags & (NLSE_FLAG_PLAIN_SCHEDULE | NLSE_FLAG_STACK))
+            return fail(NLSE_EUNSUPPORTED, "batches run the fused schedule on unstacked grids only");
         if (!nlse::batch2d_instance_ok(p[i]))
             return fail(NLSE_EUNSUPPORTED, "instance %d: batches need 2D Dirichlet grids with n[0] a multiple of "
                         "%d", i, p[0].prec == NLSE_FP32 ? 4 : 2);
@@ -428,6 +447,7 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
     if (!c) return fail(NLSE_ENOMEM, "host allocation failed");
     c->p = p[0];
     c->V = V_dev;
+    c->stack = 1;
     c->count = count;
     c->npts = total;
     c->cbytes = (size_t)total * (p[0].prec == NLSE_FP32 ? 8 : 16);
@@ -503,7 +523,10 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     // stage inputs (Psi_n, Y2, Y3, Y4) of every step of one segment, two
     // cotangents, two adjoint states, loss partials.
     const size_t ck_bytes = (size_t)nseg * cb * (has_lo ? 2 : 1);
-    const size_t need = cb + ck_bytes + 4 * (size_t)seglen * cb + 4 * cb + sizeof(double) * (nb + 1);
+    const int64_t vpts = c->npts / c->stack;
+    // A stack accumulates dL/dV per instance, summed at the end.
+    const size_t gv_bytes = c->stack > 1 ? sizeof(double) * (size_t)c->npts : 0;
+    const size_t need = cb + ck_bytes + 4 * (size_t)seglen * cb + 4 * cb + sizeof(double) * (nb + 1) + gv_bytes;
     if (need > c->adj_bytes) {
         cudaFree(c->adj_buf);
         c->adj_buf = nullptr;
@@ -521,6 +544,7 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     char* LB = LA + cb;
     double* part = reinterpret_cast<double*>(LB + cb);
     double* lossd = part + nb;
+    double* gvs = c->stack > 1 ? lossd + 1 : static_cast<double*>(dV);
     auto ckp = [&](int64_t i) { return ck + (size_t)i * cb * (has_lo ? 2 : 1); };
     auto yin = [&](int64_t m, int j) { return seg + ((size_t)m * 4 + (size_t)(j - 1)) * cb; };   // Y_j of step m
 
@@ -547,11 +571,12 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     F.lo = c->lo;
     nlse::AdjLaunch A;
     A.prec = c->p.prec; A.lap = c->p.lap;
-    A.nx = c->p.n[0]; A.ny = c->p.n[1];
+    A.nx = c->p.n[0]; A.ny = c->p.n[1] * c->stack;
+    A.rows1 = c->p.n[1];
     A.h = c->p.h; A.a = c->p.a; A.s = c->p.s;
     A.V = c->V;
-    A.gV = static_cast<double*>(dV);
-    NLSE_CUDA(cudaMemsetAsync(dV, 0, sizeof(double) * c->npts, st), "zeroing dV");
+    A.gV = gvs;
+    NLSE_CUDA(cudaMemsetAsync(gvs, 0, sizeof(double) * c->npts, st), "zeroing dV");
     const double k = c->p.dt;
     for (int64_t g = nseg - 1; g >= 0; --g) {
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
@@ -597,6 +622,8 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
         }
     }
     NLSE_CUDA(cudaMemcpyAsync(dpsi0, lamp, cb, cudaMemcpyDeviceToDevice, st), "gradient copy");
+    if (c->stack > 1)
+        NLSE_CUDA(nlse::launch_stack_sum(gvs, c->stack, vpts, static_cast<double*>(dV), st), "summing dV over the stack");
     double h_loss = 0.0;
     NLSE_CUDA(cudaMemcpyAsync(&h_loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, st), "loss copy");
     NLSE_CUDA(cudaStreamSynchronize(st), "adjoint synchronise");

@@ -51,6 +51,7 @@ stage2d_batch_kernel(const BatchDesc* __restrict__ descs, const int4* __restrict
     auto at = [&](auto* ptr) { return ptr ? ptr + d.off : ptr; };
     io.yin = at(io.yin); io.psi = at(io.psi); io.psi_out = at(io.psi_out); io.acc = at(io.acc);
     io.yout = at(io.yout); io.V = at(io.V); io.lo = at(io.lo); io.lap = at(io.lap);
+    io.rows1 = d.ny;
     io.c_acc = (R)d.c_acc[STAGE];
     io.c_y = (R)d.c_y[STAGE];
     Coef<R> c;

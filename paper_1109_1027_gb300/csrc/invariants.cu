@@ -28,7 +28,13 @@ struct InvView {
     double h2a;        // h^2 / a
     double inv_h2, inv_6h2, a, s, inv_a;
     int bc, lap;
+    int rows1;         // 2D: rows per stacked instance (n[1] when not stacked)
+    int64_t vpts;      // points of V (one instance: V is shared by a stack)
 };
+
+// V at point p (a stack's instances share V).
+template <typename R>
+__device__ __forceinline__ double v_at(const InvView<R>& v, int64_t p) { return (double)v.V[p % v.vpts]; }
 
 template <typename R>
 __device__ __forceinline__ double2 psi_at(const InvView<R>& v, int64_t p) {
@@ -45,6 +51,11 @@ __device__ __forceinline__ double2 psi_at(const InvView<R>& v, int64_t p) {
 template <typename R>
 __device__ __forceinline__ bool on_boundary(const InvView<R>& v, const int* c) {
     if (v.bc == 2) return false;                     // periodic: no boundary points
+    if (v.dim == 2 && v.rows1 != v.n[1]) {           // a stack: boundary rows of every instance
+        const int yl = c[1] % v.rows1;
+        if (yl == 0 || yl == v.rows1 - 1) return true;
+        return c[0] == 0 || c[0] == v.n[0] - 1;
+    }
     for (int ax = 0; ax < v.dim; ++ax)
         if (c[ax] == 0 || c[ax] == v.n[ax] - 1) return true;
     return false;
@@ -103,7 +114,7 @@ __device__ double2 d_any(const InvView<R>& v, const int* c) {
     if (!on_boundary(v, c)) return d_interior(v, c);
     int64_t b = index_of(v, c);
     double2 pb = psi_at(v, b);
-    double Nb = v.s * (pb.x * pb.x + pb.y * pb.y) - (double)v.V[b];
+    double Nb = v.s * (pb.x * pb.x + pb.y * pb.y) - v_at(v, b);
     if (v.bc == 3) return make_double2(0.0, 0.0);                 // Laplacian-zero
     if (v.bc == 0) return make_double2(-Nb * v.inv_a * pb.x, -Nb * v.inv_a * pb.y);
     int q[3];
@@ -111,7 +122,7 @@ __device__ double2 d_any(const InvView<R>& v, const int* c) {
     int64_t qi = index_of(v, q);
     double2 pq = psi_at(v, qi);
     double2 dq = d_interior(v, q);
-    double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - (double)v.V[qi];
+    double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - v_at(v, qi);
     double re_ratio = (dq.x * pq.x + dq.y * pq.y) / (pq.x * pq.x + pq.y * pq.y);
     double f = re_ratio + (Nq - Nb) * v.inv_a;
     return make_double2(f * pb.x, f * pb.y);
@@ -214,7 +225,7 @@ __device__ void accumulate(const InvView<R>& v, int64_t npts, int64_t first, int
         c[2] = (int)r;
         double2 ps = psi_at(v, p);
         double rho = ps.x * ps.x + ps.y * ps.y;
-        double Vp = (double)v.V[p];
+        double Vp = v_at(v, p);
         if (!isfinite(rho)) { a.nonfinite += 1.0; continue; }
         a.mass += rho;
         double L = v.h2a * (v.s * rho - Vp);
@@ -231,7 +242,7 @@ __device__ void accumulate(const InvView<R>& v, int64_t npts, int64_t first, int
             int64_t qi = index_of(v, q);
             double2 pq = psi_at(v, qi);
             double2 lq = lap_interior(v, q);
-            double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - (double)v.V[qi];
+            double Nq = v.s * (pq.x * pq.x + pq.y * pq.y) - v_at(v, qi);
             // F_q / i = a Lap + N Psi; |F_q / Psi_q| = |a Lap + N Psi| / |Psi|.
             double fx = v.a * lq.x + Nq * pq.x, fy = v.a * lq.y + Nq * pq.y;
             double B = v.h2a * sqrt((fx * fx + fy * fy) / (pq.x * pq.x + pq.y * pq.y));
@@ -284,6 +295,8 @@ __global__ void __launch_bounds__(kInvThreads) invariants_batch_partial(const In
     v.inv_6h2 = 1.0 / (6.0 * e.h * e.h);
     v.a = e.a; v.s = e.s; v.inv_a = 1.0 / e.a;
     v.bc = bc; v.lap = lap;
+    v.rows1 = e.ny;
+    v.vpts = (int64_t)e.nx * e.ny;
     const int nblk = e.row1 - e.row0;
     Acc a = acc_identity();
     accumulate<R, ENERGY>(v, (int64_t)e.nx * e.ny, (b - e.row0) * (int64_t)blockDim.x + threadIdx.x,
@@ -341,6 +354,8 @@ cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* 
     v.a = L.a; v.s = L.s; v.inv_a = 1.0 / L.a;
     v.bc = L.bc; v.lap = L.lap;
     int64_t npts = (int64_t)v.n[0] * v.n[1] * v.n[2];
+    v.rows1 = (int)(L.rows1 ? L.rows1 : v.n[1]);
+    v.vpts = (int64_t)v.n[0] * v.rows1 * v.n[2];
     if (L.energy) invariants_partial<R, true><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     else invariants_partial<R, false><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     cudaError_t e = cudaGetLastError();

@@ -64,6 +64,8 @@ struct StageIO {
     R c_acc;      // weight of F in the accumulated increment: k/6, k/3, k/3, k/6
     R c_y;        // weight of F in the next stage input: k/2, k/2, k
     int keep_v;   // TMA kernels: load V with an L2 evict-last hint
+    int rows1;    // 2D: rows per stacked instance (the Dirichlet rows are 0 and rows1-1 of
+                  // each; V has rows1 rows, shared)
 };
 
 template <typename R>
@@ -79,6 +81,7 @@ StageIO<R> make_io(const StageLaunch& L) {
     io.V = (const R*)L.V;
     io.flag = L.flag;
     io.keep_v = L.keep_v;
+    io.rows1 = (int)(L.rows1 ? L.rows1 : L.n[1]);
     const double k = L.dt;
     const double wa[5] = {0.0, k / 6.0, k / 3.0, k / 3.0, k / 6.0};
     const double wy[5] = {0.0, k / 2.0, k / 2.0, k, 0.0};

@@ -33,6 +33,8 @@ struct StageLaunch {
     int tile_planes;        // 3D TMA kernel: z planes per CTA (32, 64, 128)
     int keep_v;             // TMA kernels: load V with an L2 evict-last hint (V small enough
                             // to stay in L2 across the four stages of a step)
+    int64_t rows1;          // 2D: rows of one instance of a stack (n[1] when not stacked);
+                            // instance i holds rows i*rows1 .. (i+1)*rows1-1, all share V
 };
 
 // Whether V of the given size should be kept resident in L2 (a quarter of it).
@@ -115,10 +117,13 @@ struct AdjLaunch {
     const void* lamp;       // dL/dPsi_{n+1}
     void* lam;              // dL/dPsi_n being accumulated
     void* w_next;           // cotangent of K_{j-1} = cw lam' + cy Ybar_j
-    double* gV;             // dL/dV (FP64, accumulated)
+    double* gV;             // dL/dV (FP64, accumulated), one value per point of the state
     double cw, cy;
+    int64_t rows1;          // rows per stacked instance (ny when not stacked); V has rows1 rows
 };
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st);
+// dst[q] = sum over i of src[i n + q], i = 0 .. count-1 in order (stacked dL/dV).
+cudaError_t launch_stack_sum(const double* src, int count, int64_t n, double* dst, cudaStream_t st);
 int loss_num_blocks(int64_t n);
 cudaError_t launch_loss(int prec, const void* psi, const void* target, void* lam, int64_t n, double* partials,
                         int nblocks, double* out, cudaStream_t st);
@@ -138,6 +143,7 @@ struct InvLaunch {
     const void* lo;         // FP32 compensated part or nullptr
     const void* V;
     bool energy = true;     // false: skip the energy sum (mass, extremes and count only)
+    int64_t rows1 = 0;      // 2D stack: rows per instance (0: not stacked)
 };
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);

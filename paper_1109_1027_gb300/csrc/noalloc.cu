@@ -70,11 +70,12 @@ int check_params(const nlse_params* p, int64_t* npts) {
     if (!(std::isfinite(p->h) && p->h > 0)) return nlse::report_error(NLSE_EINVAL, "h must be positive and finite");
     if (!(std::isfinite(p->a) && p->a > 0)) return nlse::report_error(NLSE_EINVAL, "a must be positive and finite");
     if (!std::isfinite(p->s)) return nlse::report_error(NLSE_EINVAL, "s must be finite");
-    if (p->bc != NLSE_BC_DIRICHLET && p->bc != NLSE_BC_MSD) return nlse::report_error(NLSE_EINVAL, "unknown bc");
+    if (p->bc < NLSE_BC_DIRICHLET || p->bc > NLSE_BC_LAPZERO) return nlse::report_error(NLSE_EINVAL, "unknown bc");
     if (p->prec != NLSE_FP32 && p->prec != NLSE_FP64) return nlse::report_error(NLSE_EINVAL, "unknown prec");
-    if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD) return nlse::report_error(NLSE_EINVAL, "unknown lap");
-    if (p->bc == NLSE_BC_MSD && p->dim > 1)
-        return nlse::report_error(NLSE_EUNSUPPORTED, "MSD boundaries are implemented for dim = 1 only");
+    if (p->lap != NLSE_LAP_2SHOC && p->lap != NLSE_LAP_CD && p->lap != NLSE_LAP_2SHOC_MS)
+        return nlse::report_error(NLSE_EINVAL, "unknown lap");
+    if (p->flags & NLSE_FLAG_STACK)
+        return nlse::report_error(NLSE_EUNSUPPORTED, "stacked grids: use nlse_invariants");
     *npts = n;
     return NLSE_OK;
 }

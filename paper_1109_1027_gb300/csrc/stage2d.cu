@@ -65,9 +65,10 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
                 const C pc = q[0];
                 dx = cscale(c.inv_h2, csub(cadd(q[-1], q[1]), cscale((R)2, pc)));
                 dy = cscale(c.inv_h2, csub(cadd(q[-PX], q[PX]), cscale((R)2, pc)));
-                const bool bx = gx == 0 || gx == nx - 1, by = gy == 0 || gy == ny - 1;
+                const int gyl = gy % io.rows1;
+                const bool bx = gx == 0 || gx == nx - 1, by = gyl == 0 || gyl == io.rows1 - 1;
                 if (bx || by) {
-                    const C lb = dirichlet_D(c, pc, io.V[(int64_t)gy * nx + gx]);
+                    const C lb = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
                     if (bx && by) dx = dy = czero<C>();
                     else if (bx) dx = csub(lb, dy);
                     else dy = csub(lb, dx);
@@ -79,8 +80,9 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         }
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             C pc = q[0];
-            if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
-                d = dirichlet_D(c, pc, io.V[(int64_t)gy * nx + gx]);
+            const int gyl = gy % io.rows1;
+            if (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1) {
+                d = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
             } else {
                 C sum = cadd(cadd(q[1], q[-1]), cadd(q[PX], q[-PX]));
                 d = cscale(c.inv_h2, csub(sum, cscale((R)4, pc)));
@@ -100,12 +102,14 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         const C* q = sP + (ly + 2) * PX + (lx + 2);
         const C* e = sD + (ly + 1) * DX + (lx + 1);
         const C y = q[0];
-        const bool bnd = (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1);
+        const int gyl = gy % io.rows1;
+        const int64_t pv = (int64_t)gyl * nx + gx;     // V is shared by stacked instances
+        const bool bnd = (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1);
         C lap;
         if (MS) {
             const C* ey = sDy + (ly + 1) * DX + (lx + 1);
             if (bnd) {
-                lap = dirichlet_D(c, y, io.V[p]);
+                lap = dirichlet_D(c, y, io.V[pv]);
             } else {
                 const C nb = cadd(cadd(e[-1], e[1]), cadd(ey[-DX], ey[DX]));
                 lap = csub(cscale((R)(7.0 / 6.0), cadd(e[0], ey[0])), cscale((R)(1.0 / 12.0), nb));
@@ -122,7 +126,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         if constexpr (STAGE == 0) {
             io.lap[p] = lap;
         } else {
-            C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[p]);
+            C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[pv]);
             bad |= stage_epilogue<STAGE>(io, p, y, F);
         }
     }

@@ -148,8 +148,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
         mbar_expect_tx(bar, bytes);
-        if (io.keep_v) tma_load_2d_hint(dst + L::E_V, m_V, x0, r, bar, l2_evict_last());
-        else tma_load_2d(dst + L::E_V, m_V, x0, r, bar);
+        if (io.keep_v) tma_load_2d_hint(dst + L::E_V, m_V, x0, r % io.rows1, bar, l2_evict_last());
+        else tma_load_2d(dst + L::E_V, m_V, x0, r % io.rows1, bar);
         if (NEED_PA) {
             load_cplx_box<R>(dst + L::E_PSI, m_psi, x0, r, bar);
             load_cplx_box<R>(dst + L::E_ACC, m_acc, x0, r, bar);
@@ -184,8 +184,9 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     // V read from global memory; outside the grid: 0, never used).
     auto dpoint = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> C {
         if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
-        if (x == 0 || x == nx - 1 || r == 0 || r == ny - 1)
-            return dirichlet_D(c, ctr, io.V[(int64_t)r * nx + x]);
+        const int rl = r % io.rows1;             // row within its stacked instance
+        if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
+            return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
 
@@ -194,9 +195,10 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     auto ms_point = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> Two<C> {
         if (x < 0 || x >= nx || r < 0 || r >= ny) return {czero<C>(), czero<C>()};
         Two<C> d{mul2(fma2(m2, ctr, add2(lf, rt)), ih2), mul2(fma2(m2, ctr, add2(up, dn)), ih2)};
-        const bool bx = x == 0 || x == nx - 1, by = r == 0 || r == ny - 1;
+        const int rl = r % io.rows1;
+        const bool bx = x == 0 || x == nx - 1, by = rl == 0 || rl == io.rows1 - 1;
         if (bx || by) {
-            const C lb = dirichlet_D(c, ctr, io.V[(int64_t)r * nx + x]);
+            const C lb = dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
             if (bx && by) d = {czero<C>(), czero<C>()};
             else if (bx) d.a = sub2(lb, d.b);
             else d.b = sub2(lb, d.a);
@@ -295,7 +297,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
 
         if (xin) {
             const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
-            const bool rowb = y == 0 || y == ny - 1;
+            const int yl = y % io.rows1;
+            const bool rowb = yl == 0 || yl == io.rows1 - 1;
             const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
             T2 lap = d0;
             if constexpr (MS) {
@@ -305,8 +308,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
                 lap.a = fma2(c76, add2(dx0.a, d0.a), mul2(m12, sa));
                 lap.b = fma2(c76, add2(dx0.b, d0.b), mul2(m12, sb));
                 if (STAGE == 0) {
-                    if (ba) lap.a = dirichlet_D(c, c0.a, io.V[(int64_t)y * nx + xa]);
-                    if (bb) lap.b = dirichlet_D(c, c0.b, io.V[(int64_t)y * nx + xa + 1]);
+                    if (ba) lap.a = dirichlet_D(c, c0.a, io.V[(int64_t)yl * nx + xa]);
+                    if (bb) lap.b = dirichlet_D(c, c0.b, io.V[(int64_t)yl * nx + xa + 1]);
                 }
             } else if (!CD) {
                 const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));

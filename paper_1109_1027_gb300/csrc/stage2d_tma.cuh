@@ -38,7 +38,8 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     if (!complex_map<R>(&m_in, L.yin, nx, ny, HB) || !complex_map<R>(&m_in2, L.yin, nx, ny, HB2))
         return cudaErrorInvalidValue;
     m_V = m_psi = m_acc = m_lo = m_in;
-    if (STAGE >= 1 && !real_map<R>(&m_V, L.V, nx, ny, TXC)) return cudaErrorInvalidValue;
+    const int rows1 = (int)(L.rows1 ? L.rows1 : ny);    // V has the rows of one stacked instance
+    if (STAGE >= 1 && !real_map<R>(&m_V, L.V, nx, rows1, TXC)) return cudaErrorInvalidValue;
     if (STAGE >= 2) {
         if (!complex_map<R>(&m_psi, L.psi, nx, ny, TXC) || !complex_map<R>(&m_acc, L.acc, nx, ny, TXC))
             return cudaErrorInvalidValue;

@@ -27,6 +27,7 @@ PREC = {"fp32": 0, "fp64": 1}
 LAP = {"2shoc": 0, "cd": 1, "2shoc_ms": 2}
 FLAG_NO_STABILITY_CHECK = 1
 FLAG_PLAIN_SCHEDULE = 2
+FLAG_STACK = 4
 TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW, TILE_1D_RESIDENT = 1, 2, 3, 4
 
 _STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
@@ -223,11 +224,13 @@ class Solver:
     ``V`` is a CUDA tensor shaped (nx,), (ny, nx) or (nz, ny, nx); float32 for
     ``prec="fp32"`` (state complex64) or float64 for ``prec="fp64"``
     (complex128).  The solver keeps a reference to V.  ``plain=True`` selects
-    the paper's unfused schedule (a baseline, Dirichlet only)."""
+    the paper's unfused schedule (a baseline).  ``stack=n`` (2D, n >= 1) makes
+    the state a stack of n instances of V's grid, shape (n, ny, nx), that share
+    V and advance together (NLSE_FLAG_STACK)."""
 
     def __init__(self, V: torch.Tensor, h: float, dt: float, a: float, s: float,
                  bc: str = "dirichlet", prec: str = "fp32", lap: str = "2shoc",
-                 check_stability: bool = True, plain: bool = False):
+                 check_stability: bool = True, plain: bool = False, stack: int = 0):
         load_library()
         want = torch.float32 if prec == "fp32" else torch.float64
         if not V.is_cuda or V.dtype != want or not V.is_contiguous():
@@ -237,6 +240,12 @@ class Solver:
         self.prec = prec
         self.cdtype = torch.complex64 if prec == "fp32" else torch.complex128
         self.params = make_params(self.shape, h, dt, a, s, bc, prec, lap, check_stability, plain)
+        if stack:
+            if V.dim() != 2:
+                raise ValueError("stacks are of 2D grids")
+            self.params.n[2] = int(stack)
+            self.params.flags |= FLAG_STACK
+            self.shape = (int(stack),) + self.shape
         with torch.cuda.device(V.device):
             self.ctx = nlse_create(self.params, V.data_ptr())
 
@@ -281,7 +290,7 @@ class Solver:
         self._check_psi(psi0)
         self._check_psi(target)
         g_psi = torch.empty_like(psi0)
-        g_V = torch.empty(self.shape, dtype=torch.float64, device=psi0.device)
+        g_V = torch.empty(tuple(self.V.shape), dtype=torch.float64, device=psi0.device)
         loss = nlse_adjoint(self.ctx, psi0.data_ptr(), target.data_ptr(), nsteps, ckpt_every,
                             g_psi.data_ptr(), g_V.data_ptr())
         return loss, g_psi, g_V

@@ -46,7 +46,12 @@ def _params(**kw):
     base = dict(shape=(16, 16), h=0.1, dt=1e-3, a=1.0, s=1.0)
     base.update(kw)
     shape = base.pop("shape")
-    return nlse.make_params(shape, **base)
+    stack = base.pop("stack", 0)
+    p = nlse.make_params(shape, **base)
+    if stack:
+        p.n[2] = stack
+        p.flags |= nlse.FLAG_STACK
+    return p
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -62,6 +67,9 @@ def _params(**kw):
     (dict(bc="msd", lap="2shoc_ms"), nlse.EUNSUPPORTED),     # no MSD rule for the multi-storage form
     (dict(bc="periodic", lap="2shoc_ms"), nlse.EUNSUPPORTED),
     (dict(bc="lapzero", lap="2shoc_ms"), nlse.EUNSUPPORTED),
+    (dict(shape=(8, 8, 8), stack=2), nlse.EINVAL),          # stacks are of 2D grids
+    (dict(bc="msd", stack=2), nlse.EUNSUPPORTED),
+    (dict(plain=True, stack=2), nlse.EUNSUPPORTED),
     (dict(lap="2shoc_ms", plain=True), nlse.EUNSUPPORTED),   # unfused schedule: single storage only
 ])
 def test_invalid_parameters_are_rejected_on_the_host(lib, kw, code):

@@ -141,3 +141,31 @@ def test_concurrent_adjoints_equal_sequential_ones():
         assert torch.equal(g, gps[i])
         total += g_V
     assert torch.allclose(total, gV, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_stack_adjoint_equals_per_instance_adjoints(prec):
+    """A stack's adjoint gives each instance's dL/dpsi0 bit for bit, the loss
+    as the sum of the instances' losses and dL/dV as the sum of theirs, added
+    in instance order."""
+    n = 3
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=n)
+    rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(DEV).to(rdt).contiguous()
+    dt = 1e-3
+    st = nlse.Solver(Vd, h, dt, a, s, prec=prec, check_stability=False, stack=n)
+    x0 = torch.stack([torch.from_numpy(p).to(DEV).to(cdt) for p in psis]).contiguous()
+    tg = torch.stack([torch.from_numpy(t).to(DEV).to(cdt) for t in targets]).contiguous()
+    loss, g_psi, g_V = st.adjoint(x0, tg, 30, 7)
+    one = nlse.Solver(Vd, h, dt, a, s, prec=prec, check_stability=False)
+    losses, gVs = [], []
+    for i in range(n):
+        li, gi, gVi = one.adjoint(x0[i].contiguous(), tg[i].contiguous(), 30, 7)
+        assert torch.equal(gi, g_psi[i]), i
+        losses.append(li)
+        gVs.append(gVi)
+    total = gVs[0]
+    for g in gVs[1:]:
+        total = total + g
+    assert torch.equal(total, g_V)
+    assert loss == pytest.approx(sum(losses), rel=1e-12)

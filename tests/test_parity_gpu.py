@@ -608,3 +608,45 @@ def test_run_host_equals_a_device_run(shape, prec):
     assert torch.equal(host, x.cpu())
     with pytest.raises(ValueError):
         solver.run_host(x, 1)                       # a device tensor is not a host state
+
+
+# -- stacks of equal-shape instances sharing V (NLSE_FLAG_STACK) ---------------
+
+@pytest.mark.parametrize("shape,prec,lap", [((70, 128), "fp32", "2shoc"), ((70, 128), "fp64", "2shoc"),
+                                            ((40, 131), "fp32", "cd"), ((45, 260), "fp32", "2shoc_ms"),
+                                            ((17, 68), "fp64", "2shoc_ms")])
+def test_stack_equals_single_grid_runs(shape, prec, lap):
+    """Each instance of a stack advances exactly as it would alone (same bits),
+    and the stack's Laplacian is the instances' Laplacians."""
+    n = 5
+    _, V = _problem(shape, 900)
+    psis = [_problem(shape, 910 + i)[0] for i in range(n)]
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    dt = 0.5 * min(oracle.invariants(prob, rounded(p, prec), rounded(V, prec))[2] for p in psis)
+    Vd = to_dev(V, prec)
+    st = nlse.Solver(Vd, h, dt, a, s, prec=prec, lap=lap, stack=n)
+    xs = torch.stack([to_dev(p, prec) for p in psis]).contiguous()
+    lap_stack = st.lap2shoc(xs)
+    st.run(xs, 37)
+    st.check()
+    one = nlse.Solver(Vd, h, dt, a, s, prec=prec, lap=lap)
+    for i, p in enumerate(psis):
+        x = to_dev(p, prec)
+        assert torch.equal(one.lap2shoc(x), lap_stack[i]), i
+        one.run(x, 37)
+        assert torch.equal(x, xs[i]), i
+
+
+def test_stack_invariants_are_the_instances_totals():
+    shape, n = (70, 128), 4
+    _, V = _problem(shape, 930)
+    psis = [_problem(shape, 931 + i)[0] for i in range(n)]
+    h, a, s = 0.5, 0.9, -1.0
+    st = nlse.Solver(to_dev(V, "fp64"), h, 1e-4, a, s, prec="fp64", stack=n)
+    m, e, d = st.invariants(torch.stack([to_dev(p, "fp64") for p in psis]).contiguous())
+    one = nlse.Solver(to_dev(V, "fp64"), h, 1e-4, a, s, prec="fp64")
+    parts = [one.invariants(to_dev(p, "fp64")) for p in psis]
+    assert m == pytest.approx(sum(q[0] for q in parts), rel=1e-13)
+    assert e == pytest.approx(sum(q[1] for q in parts), rel=1e-12)
+    assert d == min(q[2] for q in parts)
