@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int n
     // Interior of its stacked instance (rows1 rows each; one instance when rows1 = ny).
     auto interior = [&](int x, int y) {
         if (x <= 0 || x >= nx - 1 || y < 0 || y >= ny) return false;
-        const int yl = y % rows1;
+        const int yl = inst_row(y, rows1);
         return yl > 0 && yl < rows1 - 1;
     };
 
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int n
             ybar = cadd(ybar, cscale(c.inv_6h2, csub(corners, cscale((R)4, u[0]))));
         }
         const C Y = io.Y[p];
-        const R v = io.V[(int64_t)(gy % rows1) * nx + gx];     // V is shared by stacked instances
+        const R v = io.V[(int64_t)inst_row(gy, rows1) * nx + gx];     // V is shared by stacked instances
         const R rho = Y.x * Y.x + Y.y * Y.y;
         const C Y2 = cmake<C>(Y.x * Y.x - Y.y * Y.y, 2 * Y.x * Y.y);   // Y^2
         R gv;

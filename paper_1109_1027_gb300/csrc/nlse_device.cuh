@@ -32,6 +32,10 @@ template <typename C> __device__ __forceinline__ decltype(C::x) cabs2(C a) { ret
 // i * a
 template <typename C> __device__ __forceinline__ C ctimesi(C a) { return cmake<C>(-a.y, a.x); }
 
+// Row within its stacked instance of grid row r >= 0 (instances of rows1 rows;
+// without a stack rows1 is the grid's row count and r is returned undivided).
+__device__ __forceinline__ int inst_row(int r, int rows1) { return r < rows1 ? r : r % rows1; }
+
 // Scalars of one problem, in the stage arithmetic R.
 template <typename R>
 struct Coef {

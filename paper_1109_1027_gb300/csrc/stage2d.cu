@@ -65,7 +65,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
                 const C pc = q[0];
                 dx = cscale(c.inv_h2, csub(cadd(q[-1], q[1]), cscale((R)2, pc)));
                 dy = cscale(c.inv_h2, csub(cadd(q[-PX], q[PX]), cscale((R)2, pc)));
-                const int gyl = gy % io.rows1;
+                const int gyl = inst_row(gy, io.rows1);
                 const bool bx = gx == 0 || gx == nx - 1, by = gyl == 0 || gyl == io.rows1 - 1;
                 if (bx || by) {
                     const C lb = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
@@ -80,7 +80,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         }
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             C pc = q[0];
-            const int gyl = gy % io.rows1;
+            const int gyl = inst_row(gy, io.rows1);
             if (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1) {
                 d = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
             } else {
@@ -102,7 +102,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         const C* q = sP + (ly + 2) * PX + (lx + 2);
         const C* e = sD + (ly + 1) * DX + (lx + 1);
         const C y = q[0];
-        const int gyl = gy % io.rows1;
+        const int gyl = inst_row(gy, io.rows1);
         const int64_t pv = (int64_t)gyl * nx + gx;     // V is shared by stacked instances
         const bool bnd = (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1);
         C lap;

@@ -121,6 +121,13 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     const uint32_t sbase = smem_u32(smem);
     const uint32_t ibar0 = sbase + L::BAR_OFF;   // S input barriers, then 2 epilogue barriers
     const uint32_t ebar0 = ibar0 + 8 * S;
+    // Row within its stacked instance (the grid row itself without a stack),
+    // one division per CTA and then stepped along the walk.
+    auto rstep = [&](int rl, int d) {
+        rl += d;
+        return rl < 0 ? io.rows1 - 1 : (rl == io.rows1 ? 0 : rl);
+    };
+    const int rl_base = ybase % io.rows1;
 
     if (t == 0) {
         tma_prefetch_desc(m_in);
@@ -140,6 +147,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         load_cplx_box<R>(dst, m_in, x0 - 2, r, bar);
         load_cplx_box<R>(dst + HB * L::CB, m_in2, x0 - 2 + HB, r, bar);
     };
+    int erl = rl_base;                           // instance row of the next epilogue row
     auto issue_e = [&](int e) {
         const uint32_t dst = sbase + L::E_OFF + (e & 1) * L::E_SLOT;
         const uint32_t bar = ebar0 + 8 * (e & 1);
@@ -148,8 +156,9 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
         mbar_expect_tx(bar, bytes);
-        if (io.keep_v) tma_load_2d_hint(dst + L::E_V, m_V, x0, r % io.rows1, bar, l2_evict_last());
-        else tma_load_2d(dst + L::E_V, m_V, x0, r % io.rows1, bar);
+        if (io.keep_v) tma_load_2d_hint(dst + L::E_V, m_V, x0, erl, bar, l2_evict_last());
+        else tma_load_2d(dst + L::E_V, m_V, x0, erl, bar);
+        erl = rstep(erl, dir);
         if (NEED_PA) {
             load_cplx_box<R>(dst + L::E_PSI, m_psi, x0, r, bar);
             load_cplx_box<R>(dst + L::E_ACC, m_acc, x0, r, bar);
@@ -180,11 +189,11 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     const C a2 = pair<C>(c.a, c.a);
     const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
 
-    // D at grid point (x, r) from its five stencil values (boundary: Eq. dbc_lap,
-    // V read from global memory; outside the grid: 0, never used).
-    auto dpoint = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> C {
+    // D at grid point (x, r), rl its row within its instance, from its five
+    // stencil values (boundary: Eq. dbc_lap, V read from global memory;
+    // outside the grid: 0, never used).
+    auto dpoint = [&](int x, int r, int rl, C ctr, C up, C dn, C lf, C rt) -> C {
         if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
-        const int rl = r % io.rows1;             // row within its stacked instance
         if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
             return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
@@ -192,10 +201,9 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
 
     // Multi-storage step 1 at grid point (x, r): (D^x, D^y).  Outside the grid:
     // 0; on the boundary of both axes: 0 (never used).
-    auto ms_point = [&](int x, int r, C ctr, C up, C dn, C lf, C rt) -> Two<C> {
+    auto ms_point = [&](int x, int r, int rl, C ctr, C up, C dn, C lf, C rt) -> Two<C> {
         if (x < 0 || x >= nx || r < 0 || r >= ny) return {czero<C>(), czero<C>()};
         Two<C> d{mul2(fma2(m2, ctr, add2(lf, rt)), ih2), mul2(fma2(m2, ctr, add2(up, dn)), ih2)};
-        const int rl = r % io.rows1;
         const bool bx = x == 0 || x == nx - 1, by = rl == 0 || rl == io.rows1 - 1;
         if (bx || by) {
             const C lb = dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
@@ -222,36 +230,37 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
         lm = q1[k - 1]; rm = q1[k + 2];
         l0 = q2[k - 1]; r0 = q2[k + 2];
-        const int yb = ybase - dir;
-        dm.a = ms_point(xa, yb, cm.a, cmm.a, c0.a, lm, cm.b).b;
-        dm.b = ms_point(xa + 1, yb, cm.b, cmm.b, c0.b, cm.a, rm).b;
-        const Two<C> pa = ms_point(xa, ybase, c0.a, cm.a, c1.a, l0, c0.b);
-        const Two<C> pb = ms_point(xa + 1, ybase, c0.b, cm.b, c1.b, c0.a, r0);
+        const int yb = ybase - dir, rlb = rstep(rl_base, -dir);
+        dm.a = ms_point(xa, yb, rlb, cm.a, cmm.a, c0.a, lm, cm.b).b;
+        dm.b = ms_point(xa + 1, yb, rlb, cm.b, cmm.b, c0.b, cm.a, rm).b;
+        const Two<C> pa = ms_point(xa, ybase, rl_base, c0.a, cm.a, c1.a, l0, c0.b);
+        const Two<C> pb = ms_point(xa + 1, ybase, rl_base, c0.b, cm.b, c1.b, c0.a, r0);
         dx0 = T2{pa.a, pb.a};
         d0 = T2{pa.b, pb.b};
         C* drow = dring;                                   // D^x of input row 2 -> ring row 0
         st2(drow + k, dx0);
-        if (t == 0) drow[1] = ms_point(x0 - 1, ybase, l0, q1[1], q3[1], q2[0], c0.a).a;
-        if (t == NT - 1) drow[TXC + 2] = ms_point(x0 + TXC, ybase, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]).a;
+        if (t == 0) drow[1] = ms_point(x0 - 1, ybase, rl_base, l0, q1[1], q3[1], q2[0], c0.a).a;
+        if (t == NT - 1) drow[TXC + 2] = ms_point(x0 + TXC, ybase, rl_base, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]).a;
     } else if (alive) {
         const C* q0 = irow(0); const C* q1 = irow(1); const C* q2 = irow(2); const C* q3 = irow(3);
         const T2 cmm = ld2(q0 + k);
         cm = ld2(q1 + k); c0 = ld2(q2 + k); c1 = ld2(q3 + k);
         lm = q1[k - 1]; rm = q1[k + 2];
         l0 = q2[k - 1]; r0 = q2[k + 2];
-        const int yb = ybase - dir;              // the row before the first output row
-        dm.a = dpoint(xa, yb, cm.a, cmm.a, c0.a, lm, cm.b);
-        dm.b = dpoint(xa + 1, yb, cm.b, cmm.b, c0.b, cm.a, rm);
-        d0.a = dpoint(xa, ybase, c0.a, cm.a, c1.a, l0, c0.b);
-        d0.b = dpoint(xa + 1, ybase, c0.b, cm.b, c1.b, c0.a, r0);
+        const int yb = ybase - dir, rlb = rstep(rl_base, -dir);   // the row before the first output row
+        dm.a = dpoint(xa, yb, rlb, cm.a, cmm.a, c0.a, lm, cm.b);
+        dm.b = dpoint(xa + 1, yb, rlb, cm.b, cmm.b, c0.b, cm.a, rm);
+        d0.a = dpoint(xa, ybase, rl_base, c0.a, cm.a, c1.a, l0, c0.b);
+        d0.b = dpoint(xa + 1, ybase, rl_base, c0.b, cm.b, c1.b, c0.a, r0);
         C* drow = dring;                                   // input row 2 -> D ring row 0
         st2(drow + k, d0);
-        if (t == 0) drow[1] = dpoint(x0 - 1, ybase, l0, q1[1], q3[1], q2[0], c0.a);
-        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, ybase, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
+        if (t == 0) drow[1] = dpoint(x0 - 1, ybase, rl_base, l0, q1[1], q3[1], q2[0], c0.a);
+        if (t == NT - 1) drow[TXC + 2] = dpoint(x0 + TXC, ybase, rl_base, r0, q1[TXC + 2], q3[TXC + 2], c0.b, q2[TXC + 3]);
     }
     __syncthreads();
 
     bool bad = false;
+    int yl = rl_base;                            // instance row of y
     // Unrolled by 3, the period of the three-row register windows, so that
     // sliding them is register renaming rather than moves.
 #pragma unroll 3
@@ -260,6 +269,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         const int j = i + 2;                     // input row of y
         const int y = ybase + dir * i;
         const int ya = y + dir;                  // the row after y in walk order
+        const int yla = rstep(yl, dir);
         wait_in(j + 2);
         if (!__syncthreads_and(ok)) { alive = false; break; }
         if (t == 0) {
@@ -275,19 +285,19 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         T2 d1, dx1;
         C* dn = dring + ((j + 1) & 1) * L::ROW;
         if constexpr (MS) {
-            const Two<C> pa = ms_point(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
-            const Two<C> pb = ms_point(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+            const Two<C> pa = ms_point(xa, ya, yla, c1.a, c0.a, c2.a, l1, c1.b);
+            const Two<C> pb = ms_point(xa + 1, ya, yla, c1.b, c0.b, c2.b, c1.a, r1);
             dx1 = T2{pa.a, pb.a};
             d1 = T2{pa.b, pb.b};
             st2(dn + k, dx1);
-            if (t == 0) dn[1] = ms_point(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a).a;
-            if (t == NT - 1) dn[TXC + 2] = ms_point(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]).a;
+            if (t == 0) dn[1] = ms_point(x0 - 1, ya, yla, l1, l0, q2[1], q1[0], c1.a).a;
+            if (t == NT - 1) dn[TXC + 2] = ms_point(x0 + TXC, ya, yla, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]).a;
         } else {
-            d1.a = dpoint(xa, ya, c1.a, c0.a, c2.a, l1, c1.b);
-            d1.b = dpoint(xa + 1, ya, c1.b, c0.b, c2.b, c1.a, r1);
+            d1.a = dpoint(xa, ya, yla, c1.a, c0.a, c2.a, l1, c1.b);
+            d1.b = dpoint(xa + 1, ya, yla, c1.b, c0.b, c2.b, c1.a, r1);
             st2(dn + k, d1);
-            if (t == 0) dn[1] = dpoint(x0 - 1, ya, l1, l0, q2[1], q1[0], c1.a);
-            if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
+            if (t == 0) dn[1] = dpoint(x0 - 1, ya, yla, l1, l0, q2[1], q1[0], c1.a);
+            if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, yla, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
         }
         // No barrier here: the step below reads the D ring slot written in the
         // previous iteration and this thread's own registers, both ordered by
@@ -297,7 +307,6 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
 
         if (xin) {
             const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
-            const int yl = y % io.rows1;
             const bool rowb = yl == 0 || yl == io.rows1 - 1;
             const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
             T2 lap = d0;
@@ -367,6 +376,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
         cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
         if constexpr (MS) dx0 = dx1;
+        yl = yla;
     }
 
     if (!alive) {

@@ -121,11 +121,21 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 // a - b, elementwise (negation is exact, so this rounds once like a subtraction)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return add2(a, make_float2(-b.x, -b.y)); }
-__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+// FP64: explicitly rounded intrinsics, like the FP32 instructions above, so
+// that the compiler cannot fuse a product into a later sum.  Whether it would
+// depends on the basic block the two land in, i.e. on where a row falls in its
+// tile, and a launch shape must not change a result.
+__device__ __forceinline__ double2 add2(double2 a, double2 b) {
+    return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) {
+    return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) {
+    return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
 __device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
-    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
 }
 
 }  // namespace nlse
