@@ -268,6 +268,14 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
                                      launch for all steps on a cluster of at most c
                                      CTAs (fewer where the grid is too short); 0 the
                                      four tiled launches per step.  Default 16       */
+#define NLSE_TILE_2D_FUSE 5       /* 2D FP32 Dirichlet contexts (single grids and
+                                     stacks; 2SHOC or CD; rows 16-byte aligned): 1
+                                     runs each RK4 step as two launches of two stages
+                                     each (temporal blocking: stages 1+2, then 3+4,
+                                     with Y_1 and Y_3 kept on chip; 80 instead of
+                                     168 bytes moved per point and step), 0 as four
+                                     single-stage launches (default).  Other
+                                     contexts accept the key and ignore it.        */
 int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 

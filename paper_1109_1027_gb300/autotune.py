@@ -22,6 +22,7 @@ CANDIDATES = {
     nlse.TILE_PLANES: (32, 64, 128),
     nlse.TILE_BATCH_NARROW: (0, 64, 128, 192, 256),
     nlse.TILE_1D_RESIDENT: (0, 1, 2, 4, 8, 16),
+    nlse.TILE_2D_FUSE: (0, 1),
 }
 
 
@@ -57,6 +58,8 @@ def _key(solver, tile_key) -> str:
         shape = f"batch{solver.count}:{sum(solver.sizes)}"
     else:
         shape = "x".join(str(v) for v in solver.shape)
+        if p.flags & nlse.FLAG_STACK:
+            shape += f"s{p.n[2]}"
     return f"{dev}|key{tile_key}|dim{p.dim}|prec{p.prec}|lap{p.lap}|{shape}"
 
 
@@ -67,6 +70,11 @@ def _keys_for(solver):
     if d == 1 and solver.shape[0] <= 4096:
         return [nlse.TILE_1D_RESIDENT]
     if d == 2:
+        p = solver.params
+        if (solver.prec == "fp32" and p.bc == nlse.BC["dirichlet"] and p.lap in (nlse.LAP["2shoc"], nlse.LAP["cd"])
+                and not p.flags & nlse.FLAG_PLAIN_SCHEDULE):
+            # Rows per CTA first (single-stage launches), then one against two stages per launch.
+            return [nlse.TILE_ROWS, nlse.TILE_2D_FUSE]
         return [nlse.TILE_ROWS]
     if d == 3 and solver.prec == "fp32":
         return [nlse.TILE_PLANES]

@@ -81,6 +81,7 @@ struct nlse_ctx {
     // Tiling choices (nlse_set_tiling); 0 = the default.
     int tile_rows, tile_planes;
     int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
+    int fuse2;                // 2D FP32: two stages per launch (NLSE_TILE_2D_FUSE)
 };
 
 namespace {
@@ -197,6 +198,62 @@ int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
         cudaError_t e = c->batch ? nlse::batch2d_launch(c->batch, L, st) : launch_stage(L, st);
         if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
     }
+    return NLSE_OK;
+}
+
+// Whether this context's steps run as two stage pairs (NLSE_TILE_2D_FUSE).
+// The caller's state must be 16-byte aligned, which the entry points check.
+bool fused_steps(const nlse_ctx* c) {
+    if (!c->fuse2 || c->batch || unfused(c->p)) return false;
+    StageLaunch L = base_launch(c);
+    L.psi = L.yin = c->Y[0];
+    L.psi_out = c->Y[0];
+    L.acc = c->acc;
+    L.lo = c->lo;
+    L.yout = c->Y[1];
+    return nlse::rk4_2d_fused_eligible(L);
+}
+
+// One RK4 step as two stage pairs, Psi^n read from psi_in and Psi^{n+1}
+// written to psi_out, another buffer: the second pair reads Psi^n on rows
+// next to its block, which the neighbouring CTAs are overwriting meanwhile.
+// Stages 1+2 write Y_2 into Y[1]; stages 3+4 read it.
+int enqueue_fused_step(nlse_ctx* c, const void* psi_in, void* psi_out, cudaStream_t st) {
+    StageLaunch L = base_launch(c);
+    L.psi = psi_in;
+    L.psi_out = psi_out;
+    L.acc = c->acc;
+    L.lo = c->lo;
+    L.stage = 1;
+    L.yin = psi_in;
+    L.yout = c->Y[1];
+    cudaError_t e = nlse::launch_rk4_2d_fused(L, 0, st);
+    if (e == cudaSuccess) {
+        L.stage = 3;
+        L.yin = c->Y[1];
+        L.yout = nullptr;
+        e = nlse::launch_rk4_2d_fused(L, 1, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fused RK4 stage-pair launch");
+    return NLSE_OK;
+}
+
+// n RK4 steps on psi in place.  Fused steps alternate between psi and the
+// context's Y[0] (free on that path); an odd count ends with a copy back.
+int enqueue_steps(nlse_ctx* c, void* psi, int64_t n, cudaStream_t st) {
+    if (!fused_steps(c)) {
+        for (int64_t i = 0; i < n; ++i) {
+            int rc = enqueue_step(c, psi, st);
+            if (rc) return rc;
+        }
+        return NLSE_OK;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const bool even = i % 2 == 0;
+        int rc = enqueue_fused_step(c, even ? psi : c->Y[0], even ? c->Y[0] : psi, st);
+        if (rc) return rc;
+    }
+    if (n % 2) NLSE_CUDA(cudaMemcpyAsync(psi, c->Y[0], c->cbytes, cudaMemcpyDeviceToDevice, st), "state copy");
     return NLSE_OK;
 }
 
@@ -558,8 +615,7 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
         NLSE_CUDA(cudaMemcpyAsync(ckp(g), S, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
         if (has_lo) NLSE_CUDA(cudaMemcpyAsync(ckp(g) + cb, c->lo, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
-        for (int64_t m = 0; m < steps; ++m)
-            if ((rc = enqueue_step(c, S, st))) return rc;
+        if ((rc = enqueue_steps(c, S, steps, st))) return rc;
     }
     NLSE_CUDA(nlse::launch_loss(c->p.prec, S, target, LA, c->npts, part, nb, lossd, st), "loss launch");
 
@@ -659,6 +715,10 @@ int nlse_set_tiling(nlse_ctx* c, int key, int value) {
                 return fail(NLSE_EINVAL, "1D resident loop: 0 or a power of two up to %d", nlse::rk4_1d_max_cluster());
             c->resident = value ? value : -1;
             break;
+        case NLSE_TILE_2D_FUSE:
+            if (value != 0 && value != 1) return fail(NLSE_EINVAL, "two stages per launch: 0 or 1");
+            c->fuse2 = value;
+            break;
         case NLSE_TILE_BATCH_NARROW: {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             if (value < 0) return fail(NLSE_EINVAL, "the narrow-tile width bound must be >= 0");
@@ -685,6 +745,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
             *value = nlse::batch2d_narrow(c->batch);
             return NLSE_OK;
         case NLSE_TILE_1D_RESIDENT: *value = resident_cluster(c); return NLSE_OK;
+        case NLSE_TILE_2D_FUSE: *value = c->fuse2; return NLSE_OK;
     }
     return fail(NLSE_EINVAL, "unknown tiling key %d", key);
 }
@@ -722,7 +783,7 @@ int nlse_rk4_step(nlse_ctx* c, void* psi, void* stream) {
     int rc = bind_state(c, psi, st);
     if (rc) return rc;
     if (resident_1d(c)) return enqueue_resident(c, psi, 1, st);
-    return enqueue_step(c, psi, st);
+    return enqueue_steps(c, psi, 1, st);
 }
 
 int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
@@ -769,7 +830,7 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
             cudaStreamDestroy(cs);
             return cuda_fail(e, "begin capture");
         }
-        for (int64_t i = 0; i < kGraphSteps && rc == NLSE_OK; ++i) rc = enqueue_step(c, psi, cs);
+        rc = enqueue_steps(c, psi, kGraphSteps, cs);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -790,11 +851,7 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
     if (c->graph && c->graph_psi == psi)
         for (; done + kGraphSteps <= nsteps; done += kGraphSteps)
             NLSE_CUDA(cudaGraphLaunch(c->graph, st), "graph launch");
-    for (; done < nsteps; ++done) {
-        rc = enqueue_step(c, psi, st);
-        if (rc) return rc;
-    }
-    return NLSE_OK;
+    return enqueue_steps(c, psi, nsteps - done, st);
 }
 
 int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {

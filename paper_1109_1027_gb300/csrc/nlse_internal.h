@@ -45,6 +45,13 @@ cudaError_t launch_stage_2d(const StageLaunch& L, cudaStream_t st);
 // The TMA-fed y-streaming 2D kernel (stage2d_tma.cuh) and when it applies;
 // one entry per compiled rows-per-CTA variant.
 bool stage_2d_tma_eligible(const StageLaunch& L);
+// Temporal blocking (stage2d_fused.cu): two RK4 stages per launch, pair 0 =
+// stages 1+2 (yin unused: reads psi; writes acc and yout = Y_2), pair 1 =
+// stages 3+4 (reads yin = Y_2, psi, acc, lo; writes psi_out and lo).  FP32 2D
+// Dirichlet grids on the TMA path, 2SHOC or CD; the same bits as the
+// single-stage launches.
+bool rk4_2d_fused_eligible(const StageLaunch& L);
+cudaError_t launch_rk4_2d_fused(const StageLaunch& L, int pair, cudaStream_t st);
 cudaError_t launch_stage_2d_tma(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d_tma_rows8(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_2d_tma_rows16(const StageLaunch& L, cudaStream_t st);

@@ -363,11 +363,12 @@ def _crop_one_step(psi, V, inst, k, y, x, r=10):
     return out[y - y0, x - x0]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_dark_vortex_2d_full_size_sampled(prec):
-    """The 2048^2 workload in the benchmark's launch configuration: one RK4
-    step through nlse_run, checked at sampled points (incl. corners, edges
-    and the vortex core) against the oracle on windows."""
+@pytest.mark.parametrize("prec,fuse", [("fp32", 0), ("fp32", 1), ("fp64", 0)])
+def test_dark_vortex_2d_full_size_sampled(prec, fuse):
+    """The 2048^2 workload in the benchmark's launch configurations (four
+    single-stage launches per step, or two stage pairs): one RK4 step through
+    nlse_run, checked at sampled points (incl. corners, edges and the vortex
+    core) against the oracle on windows."""
     inst = wl.dark_vortex_2d()
     prob_small = oracle.Problem((64, 64), inst.h, inst.a, inst.s)
     psi_r, V_r = rounded(inst.psi0, prec), rounded(inst.V, prec)
@@ -376,6 +377,7 @@ def test_dark_vortex_2d_full_size_sampled(prec):
     k = 0.5 * dtmax
     solver = nlse.Solver(to_dev(inst.V, prec), inst.h, k, inst.a, inst.s, prec=prec,
                          check_stability=False)
+    solver.set_tiling(nlse.TILE_2D_FUSE, fuse)
     x = to_dev(inst.psi0, prec)
     solver.run(x, 1)
     got = x.cpu().numpy()
@@ -650,3 +652,94 @@ def test_stack_invariants_are_the_instances_totals():
     assert m == pytest.approx(sum(q[0] for q in parts), rel=1e-13)
     assert e == pytest.approx(sum(q[1] for q in parts), rel=1e-12)
     assert d == min(q[2] for q in parts)
+
+
+# -- temporal blocking: two RK4 stages per launch (NLSE_TILE_2D_FUSE) ------------
+
+FUSE_SHAPES = [(3, 4), (17, 68), (70, 128), (100, 388), (45, 260), (9, 1024), (301, 516)]
+
+
+@pytest.mark.parametrize("shape", FUSE_SHAPES)
+@pytest.mark.parametrize("lap", ["2shoc", "cd"])
+def test_two_stages_per_launch_equal_four_launches(shape, lap):
+    """Stages 1+2 and 3+4 in one launch each give the bits of the four
+    single-stage launches: ragged CTA tails in x and y, grids narrower than
+    one CTA and than the extra rows of the first stage of a pair, steps
+    through nlse_run (graph) and nlse_rk4_step."""
+    psi, V = _problem(shape, 1200 + shape[1])
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    _, _, dtmax = oracle.invariants(prob, rounded(psi, "fp32"), rounded(V, "fp32"))
+    solver = nlse.Solver(to_dev(V, "fp32"), h, 0.5 * dtmax, a, s, prec="fp32", lap=lap)
+    outs = []
+    for fuse in (0, 1):
+        solver.set_tiling(nlse.TILE_2D_FUSE, fuse)
+        assert solver.get_tiling(nlse.TILE_2D_FUSE) == fuse
+        x = to_dev(psi, "fp32")
+        solver.run(x, 37)
+        solver.rk4_step(x)
+        solver.check()
+        outs.append(x)
+    assert torch.equal(outs[1], outs[0])
+
+
+def test_two_stages_per_launch_match_oracle():
+    """The fused path against the oracle directly (10 steps, FP32 tolerance)."""
+    shape = (100, 388)
+    psi, V = _problem(shape, 1300)
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    psi_r, V_r = rounded(psi, "fp32"), rounded(V, "fp32")
+    _, _, dtmax = oracle.invariants(prob, psi_r, V_r)
+    k = 0.5 * dtmax
+    solver = nlse.Solver(to_dev(V, "fp32"), h, k, a, s, prec="fp32")
+    solver.set_tiling(nlse.TILE_2D_FUSE, 1)
+    x = to_dev(psi, "fp32")
+    solver.run(x, 10)
+    ref = oracle.run(prob, psi_r, V_r, k, 10)
+    got = x.cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, ref) < 1e-5
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape,lap", [((17, 68), "2shoc"), ((45, 260), "cd"), ((70, 128), "2shoc")])
+def test_stack_two_stages_per_launch(shape, lap):
+    """A stack on the fused path: every instance equals its own single-grid run
+    on the four-launch path, the stage pairs crossing instance boundaries
+    inside a CTA's rows."""
+    n = 5
+    _, V = _problem(shape, 1400)
+    psis = [_problem(shape, 1410 + i)[0] for i in range(n)]
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    dt = 0.5 * min(oracle.invariants(prob, rounded(p, "fp32"), rounded(V, "fp32"))[2] for p in psis)
+    Vd = to_dev(V, "fp32")
+    st = nlse.Solver(Vd, h, dt, a, s, prec="fp32", lap=lap, stack=n)
+    st.set_tiling(nlse.TILE_2D_FUSE, 1)
+    xs = torch.stack([to_dev(p, "fp32") for p in psis]).contiguous()
+    st.run(xs, 37)
+    st.check()
+    one = nlse.Solver(Vd, h, dt, a, s, prec="fp32", lap=lap)
+    for i, p in enumerate(psis):
+        x = to_dev(p, "fp32")
+        one.run(x, 37)
+        assert torch.equal(x, xs[i]), i
+
+
+def test_two_stages_per_launch_key_validation():
+    """Values other than 0 and 1 are refused; contexts the fused kernels do not
+    cover (FP64, multi storage) accept the key and keep their results."""
+    shape = (45, 260)
+    psi, V = _problem(shape, 1500)
+    for prec, lap in (("fp64", "2shoc"), ("fp32", "2shoc_ms")):
+        solver = nlse.Solver(to_dev(V, prec), 0.5, 1e-4, 0.9, -1.0, prec=prec, lap=lap)
+        outs = []
+        for fuse in (0, 1):
+            solver.set_tiling(nlse.TILE_2D_FUSE, fuse)
+            x = to_dev(psi, prec)
+            solver.run(x, 5)
+            outs.append(x)
+        assert torch.equal(outs[0], outs[1])
+        for bad in (2, -1):
+            with pytest.raises(nlse.NLSEError):
+                solver.set_tiling(nlse.TILE_2D_FUSE, bad)
