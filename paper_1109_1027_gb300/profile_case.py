@@ -6,6 +6,7 @@ takes a few warm-up steps, then a few more, and exits.
 
 Workloads: vortex2d (2D dark vortex), ring3d (3D vortex ring), soliton1d
 (1D bright soliton), batch2d (512 uneven 2D instances).  FP32 unless --fp64.
+--fuse runs the 2D steps as two launches of two RK4 stages each.
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--fuse", action="store_true", help="2D: two RK4 stages per launch")
     args = ap.parse_args()
     prec = "fp64" if args.fp64 else "fp32"
     rdt, cdt = (torch.float64, torch.complex128) if args.fp64 else (torch.float32, torch.complex64)
@@ -48,6 +50,8 @@ def main():
         dt = 0.5 * probe.invariants(x)[2]
         probe.close()
         solver = nlse.Solver(V, inst.h, dt, inst.a, inst.s, prec=prec, check_stability=False)
+        if args.fuse:
+            solver.set_tiling(nlse.TILE_2D_FUSE, 1)
     for _ in range(args.warmup):
         solver.rk4_step(x)
     for _ in range(args.steps):
