@@ -93,9 +93,11 @@ __device__ __forceinline__ void st2(float2* p, Two<float2> v) {
 }
 __device__ __forceinline__ void st2(double2* p, Two<double2> v) { p[0] = v.a; p[1] = v.b; }
 
-// LP: 0 single-storage 2SHOC, 1 CD, 2 multi-storage 2SHOC.
-template <typename R, int LP, int STAGE, int NT, int TY>
-__device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUtensorMap* m_in2,
+// LP: 0 single-storage 2SHOC, 1 CD, 2 multi-storage 2SHOC.  INNER: every
+// point whose D or output the CTA forms is an interior grid point, so the
+// per-point boundary and grid-edge tests drop out (the arithmetic is the same).
+template <typename R, int LP, int STAGE, int NT, int TY, bool INNER>
+__device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUtensorMap* m_in2,
                                              const CUtensorMap* m_V, const CUtensorMap* m_psi,
                                              const CUtensorMap* m_acc, const CUtensorMap* m_lo,
                                              const StageIO<R>& io, const Coef<R>& c, const int nx, const int ny,
@@ -193,17 +195,20 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     // stencil values (boundary: Eq. dbc_lap, V read from global memory;
     // outside the grid: 0, never used).
     auto dpoint = [&](int x, int r, int rl, C ctr, C up, C dn, C lf, C rt) -> C {
-        if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
-        if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
-            return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
+        if constexpr (!INNER) {
+            if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
+            if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
+                return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
+        }
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
 
     // Multi-storage step 1 at grid point (x, r): (D^x, D^y).  Outside the grid:
     // 0; on the boundary of both axes: 0 (never used).
     auto ms_point = [&](int x, int r, int rl, C ctr, C up, C dn, C lf, C rt) -> Two<C> {
-        if (x < 0 || x >= nx || r < 0 || r >= ny) return {czero<C>(), czero<C>()};
+        if (!INNER && (x < 0 || x >= nx || r < 0 || r >= ny)) return {czero<C>(), czero<C>()};
         Two<C> d{mul2(fma2(m2, ctr, add2(lf, rt)), ih2), mul2(fma2(m2, ctr, add2(up, dn)), ih2)};
+        if constexpr (INNER) return d;
         const bool bx = x == 0 || x == nx - 1, by = rl == 0 || rl == io.rows1 - 1;
         if (bx || by) {
             const C lb = dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
@@ -216,7 +221,7 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
 
     const int xa = x0 + 2 * t;                   // this thread's columns xa, xa + 1
     const int k = 2 * t + 2;                     // xa in the row buffers
-    const bool xin = xa < nx;                    // nx is even: then xa + 1 < nx too
+    const bool xin = INNER || xa < nx;           // nx is even: then xa + 1 < nx too
 
     // Prologue: input rows y0-2 .. y0+1 give D(., y0-1) and D(., y0).
     wait_in(0); wait_in(1); wait_in(2); wait_in(3);
@@ -307,8 +312,8 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
 
         if (xin) {
             const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
-            const bool rowb = yl == 0 || yl == io.rows1 - 1;
-            const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;
+            const bool rowb = !INNER && (yl == 0 || yl == io.rows1 - 1);
+            const bool ba = !INNER && (rowb || xa == 0), bb = !INNER && (rowb || xa + 1 == nx - 1);
             T2 lap = d0;
             if constexpr (MS) {
                 // dr holds D^x of row y; d0 / dm / d1 hold D^y of rows y, y -+ 1.
@@ -392,6 +397,34 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
     }
     if constexpr (STAGE == 4) {
         if (__syncthreads_or(bad) && t == 0) atomicOr(io.flag, 1);
+    }
+}
+
+// One CTA's walk.  In FP64, whose rate on this GPU bounds the walk, CTAs in
+// which no point whose D the CTA forms (columns x0-1 .. x0+TXC, rows y0-1 ..
+// y0+nrows) is a boundary point of its instance or lies outside the grid take
+// the variant without per-point boundary tests (5% faster).  In FP32 the
+// walk is bound by memory and latency; there the second variant gained
+// nothing on single grids and cost 20% on batches, so FP32 has one.
+template <typename R, int LP, int STAGE, int NT, int TY>
+__device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUtensorMap* m_in2,
+                                             const CUtensorMap* m_V, const CUtensorMap* m_psi,
+                                             const CUtensorMap* m_acc, const CUtensorMap* m_lo,
+                                             const StageIO<R>& io, const Coef<R>& c, const int nx, const int ny,
+                                             const int x0, const int y0, const int dir) {
+    if constexpr (sizeof(R) == 4) {
+        stage2d_walk<R, LP, STAGE, NT, TY, false>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, io, c, nx, ny, x0, y0, dir);
+    } else {
+        const int ylo = y0 - 1, yhi = y0 + min(TY, ny - y0);
+        const bool inner = x0 >= 2 && x0 + 2 * NT <= nx - 2 && ylo >= 1 && yhi <= ny - 2 &&
+                           ylo / io.rows1 == yhi / io.rows1 && ylo % io.rows1 >= 1 &&
+                           yhi % io.rows1 <= io.rows1 - 2;
+        if (inner)
+            stage2d_walk<R, LP, STAGE, NT, TY, true>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, io, c, nx, ny, x0, y0,
+                                                     dir);
+        else
+            stage2d_walk<R, LP, STAGE, NT, TY, false>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, io, c, nx, ny, x0, y0,
+                                                      dir);
     }
 }
 
