@@ -169,3 +169,26 @@ def test_stack_adjoint_equals_per_instance_adjoints(prec):
         total = total + g
     assert torch.equal(total, g_V)
     assert loss == pytest.approx(sum(losses), rel=1e-12)
+
+
+@pytest.mark.parametrize("stack", [0, 3])
+def test_adjoint_with_two_stages_per_launch(stack):
+    """The adjoint's forward pass and checkpoints on the fused schedule (two
+    RK4 stages per launch) give the bits of the four-launch schedule: the
+    loss, dL/dpsi0 and dL/dV are identical (odd segment lengths included)."""
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=max(stack, 1))
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(DEV).to(torch.float32).contiguous()
+    if stack:
+        x0 = torch.stack([torch.from_numpy(p).to(DEV).to(torch.complex64) for p in psis]).contiguous()
+        tg = torch.stack([torch.from_numpy(t).to(DEV).to(torch.complex64) for t in targets]).contiguous()
+    else:
+        x0 = torch.from_numpy(psis[0]).to(DEV).to(torch.complex64).contiguous()
+        tg = torch.from_numpy(targets[0]).to(DEV).to(torch.complex64).contiguous()
+    sv = nlse.Solver(Vd, h, 1e-3, a, s, prec="fp32", check_stability=False, stack=stack)
+    out = []
+    for fuse in (0, 1):
+        sv.set_tiling(nlse.TILE_2D_FUSE, fuse)
+        out.append(sv.adjoint(x0, tg, 31, 7))
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.equal(out[0][2], out[1][2])
