@@ -187,8 +187,18 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
 
     const C m4 = pair<C>(-4, -4), m2 = pair<C>(-2, -2), m12 = pair<C>(R(-1.0 / 12.0), R(-1.0 / 12.0));
     const C c76 = pair<C>(R(7.0 / 6.0), R(7.0 / 6.0));
-    const C ih2 = pair<C>(c.inv_h2, c.inv_h2), i6h2 = pair<C>(c.inv_6h2, c.inv_6h2);
+    // FP64 stages carry a Lap instead of Lap: the a of F folds into the
+    // difference weights and the boundary value a D_b = -N Psi_b (Eq. dbc_lap),
+    // two FP64 multiplies fewer per point.  FP64 runs at its arithmetic rate
+    // on this GPU; FP32 and the standalone Laplacian keep the unscaled form.
+    constexpr bool SC = sizeof(R) == 8 && STAGE >= 1;
+    const R wd = SC ? c.a * c.inv_h2 : c.inv_h2, we = SC ? c.a * c.inv_6h2 : c.inv_6h2;
+    const C ih2 = pair<C>(wd, wd), i6h2 = pair<C>(we, we);
     const C a2 = pair<C>(c.a, c.a);
+    auto bnd_D = [&](C ctr, R v) -> C {
+        if constexpr (SC) return cscale(-nonlin(c.s, ctr, v), ctr);
+        else return dirichlet_D(c, ctr, v);
+    };
     const C ca2 = pair<C>(-io.c_acc, io.c_acc), cy2 = pair<C>(-io.c_y, io.c_y);
 
     // D at grid point (x, r), rl its row within its instance, from its five
@@ -198,7 +208,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         if constexpr (!INNER) {
             if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
             if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
-                return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
+                return bnd_D(ctr, io.V[(int64_t)rl * nx + x]);
         }
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
@@ -211,7 +221,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         if constexpr (INNER) return d;
         const bool bx = x == 0 || x == nx - 1, by = rl == 0 || rl == io.rows1 - 1;
         if (bx || by) {
-            const C lb = dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
+            const C lb = bnd_D(ctr, io.V[(int64_t)rl * nx + x]);
             if (bx && by) d = {czero<C>(), czero<C>()};
             else if (bx) d.a = sub2(lb, d.b);
             else d.b = sub2(lb, d.a);
@@ -343,7 +353,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
                 auto swapped_w = [&](C y_, C lap_, R v_, bool b_) -> C {
                     if (b_) return czero<C>();
                     const R N = nonlin(c.s, y_, v_);
-                    const C w = fma2(pair<C>(N, N), y_, mul2(a2, lap_));
+                    const C w = SC ? fma2(pair<C>(N, N), y_, lap_) : fma2(pair<C>(N, N), y_, mul2(a2, lap_));
                     return pair<C>(w.y, w.x);
                 };
                 const C swa = swapped_w(c0.a, lap.a, vv[0], ba);
