@@ -45,7 +45,10 @@ template <typename R, int LP, int STAGE, int NT>
 __global__ void __launch_bounds__(NT)
 stage2d_batch_kernel(const BatchDesc* __restrict__ descs, const int4* __restrict__ tiles, StageIO<R> io,
                      const int dir) {
-    const int4 tl = tiles[blockIdx.x];
+    // Stages that walk their rows upwards also take the tiles in reverse order:
+    // the batch spans many waves of CTAs, and each stage then starts on the
+    // tiles the previous stage wrote last, which are still in L2.
+    const int4 tl = tiles[dir > 0 ? blockIdx.x : gridDim.x - 1 - blockIdx.x];
     const BatchDesc& d = descs[tl.x];
     // This instance's slice of every flat buffer (unused buffers stay null).
     auto at = [&](auto* ptr) { return ptr ? ptr + d.off : ptr; };
