@@ -743,3 +743,63 @@ def test_two_stages_per_launch_key_validation():
         for bad in (2, -1):
             with pytest.raises(nlse.NLSEError):
                 solver.set_tiling(nlse.TILE_2D_FUSE, bad)
+
+
+# -- degenerate cases of the method ----------------------------------------------
+
+@pytest.mark.parametrize("shape", [(1030,), (45, 260), (40, 131), (9, 20, 37), (70, 40, 100)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_linear_free_equation_matches_oracle(shape, prec):
+    """s = 0 and V = 0: the free linear Schroedinger equation, where F is a
+    times the Laplacian alone; 12 steps against the oracle."""
+    psi = wl.random_field(shape, seed=1600)
+    V = np.zeros(shape)
+    h, a, s = 0.5, 0.7, 0.0
+    prob = oracle.Problem(shape, h, a, s)
+    psi_r = rounded(psi, prec)
+    _, _, dtmax = oracle.invariants(prob, psi_r, V)
+    k = 0.5 * dtmax
+    solver = nlse.Solver(to_dev(V, prec), h, k, a, s, prec=prec)
+    x = to_dev(psi, prec)
+    solver.run(x, 12)
+    ref = oracle.run(prob, psi_r, V, k, 12)
+    got = x.cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert rel_l2(got, ref) < tol
+
+
+@pytest.mark.parametrize("shape", [(1030,), (45, 260), (70, 40, 100)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_zero_state_stays_zero(shape, prec):
+    """Psi = 0 is a fixed point of Eq. (NLSE) for any V: every step returns
+    exact zeros (no rounding can create a value from nothing)."""
+    V = wl.random_potential(shape, seed=1700, scale=2.0)
+    solver = nlse.Solver(to_dev(V, prec), 0.5, 1e-3, 0.9, -1.0, prec=prec)
+    x = to_dev(np.zeros(shape, complex), prec)
+    solver.run(x, 33)
+    solver.check()
+    assert not torch.any(x != 0)
+
+
+@pytest.mark.parametrize("shape", [(45, 260), (70, 40, 100)])
+def test_constant_state_turns_at_the_nonlinear_frequency(shape):
+    """A constant field with V = 0 has Lap = 0 at interior points, so each
+    interior point follows dPsi/dt = i s |Psi|^2 Psi, whose RK4 step is the
+    stability polynomial R(i k s |c|^2) applied to c; the Dirichlet boundary
+    holds c.  The boundary's D_b reaches distance 1 in stage 1 and the radius-2
+    stencil carries it 2 points further per stage, so after one step the
+    points at distance >= 8 follow the scalar step (FP64)."""
+    c = 0.8 - 0.6j
+    psi = np.full(shape, c)
+    V = np.zeros(shape)
+    h, a, s, k = 0.5, 0.9, -1.0, 0.01
+    solver = nlse.Solver(to_dev(V, "fp64"), h, k, a, s, prec="fp64")
+    x = to_dev(psi, "fp64")
+    solver.rk4_step(x)
+    z = 1j * k * s * abs(c) ** 2
+    expect = c * (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24)
+    got = x.cpu().numpy()
+    inner = got[tuple(slice(8, n - 8) for n in shape)]
+    assert np.abs(inner - expect).max() < 1e-14
+    edge = got[(0,) * len(shape)]
+    assert edge == c
