@@ -612,6 +612,29 @@ def test_run_host_equals_a_device_run(shape, prec):
         solver.run_host(x, 1)                       # a device tensor is not a host state
 
 
+@pytest.mark.parametrize("shape,prec,stack", [((300, 516), "fp32", 0), ((300, 516), "fp64", 0),
+                                              ((2048, 260), "fp32", 0), ((64, 128), "fp32", 5)])
+@pytest.mark.parametrize("check", [False, True])
+def test_run_host_tall_grids_and_stacks_equal_a_device_run(shape, prec, stack, check):
+    """nlse_run_host on taller 2D grids and on a stack, with and without the
+    entry check: 1, 2 and 33 steps give the bits of nlse_run on the device."""
+    _, V = _problem(shape, 1800)
+    n = max(stack, 1)
+    psis = [_problem(shape, 1810 + i)[0] for i in range(n)]
+    h, a, s = 0.5, 0.9, -1.0
+    prob = oracle.Problem(shape, h, a, s)
+    dt = 0.5 * min(oracle.invariants(prob, rounded(p, prec), rounded(V, prec))[2] for p in psis)
+    psi = np.stack(psis) if stack else psis[0]
+    solver = nlse.Solver(to_dev(V, prec), h, dt, a, s, prec=prec, stack=stack, check_stability=check)
+    for steps in (1, 2, 33):
+        x = to_dev(psi, prec)
+        solver.run(x, steps)
+        host = to_dev(psi, prec).cpu().pin_memory()
+        solver.run_host(host, steps)
+        assert torch.equal(host, x.cpu()), steps
+    solver.check()
+
+
 # -- stacks of equal-shape instances sharing V (NLSE_FLAG_STACK) ---------------
 
 @pytest.mark.parametrize("shape,prec,lap", [((70, 128), "fp32", "2shoc"), ((70, 128), "fp64", "2shoc"),
