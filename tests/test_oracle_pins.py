@@ -465,3 +465,37 @@ def test_oracle_rejects_invalid_problems():
         oracle.laplacian(oracle.Problem((2,), 0.1, 1.0, 0.0), np.zeros(2), np.zeros(2))
     with pytest.raises(ValueError):
         oracle.laplacian(oracle.Problem((5,), 0.1, -1.0, 0.0), np.zeros(5), np.zeros(5))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_cd_laplacian_symbol_and_order(dim):
+    """The second-order CD Laplacian (the paper's comparison scheme, Sec. 4):
+    on a periodic plane wave it is the exact eigenvalue sum_a 2(cos theta_a - 1)/h^2;
+    it is exact on cubics and not on quartics, where 2SHOC is exact (so a CD
+    silently replaced by 2SHOC, or the reverse, fails here)."""
+    shape = {1: (24,), 2: (12, 10), 3: (8, 6, 10)}[dim]
+    h = 0.3
+    idx = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    thetas = [2 * np.pi * (2 + a) / n for a, n in enumerate(shape)]
+    psi = 1.3 * np.exp(1j * sum(t * j for t, j in zip(thetas, idx)))
+    lam2 = sum(2 * np.cos(t) - 2 for t in thetas) / h ** 2
+    prob = oracle.Problem(shape, h, 1.0, 0.0, bc=oracle.BC_PERIODIC, lap=oracle.LAP_CD)
+    lap = oracle.laplacian(prob, psi, np.zeros(shape))
+    assert np.abs(lap - lam2 * psi).max() <= 1e-12 * abs(lam2) * 1.3
+
+    n = {1: 15, 2: 11, 3: 9}[dim]
+    grid = (n,) * dim
+    coords = wl.mesh(grid, -1.0, 1.3)
+    hh = wl.spacing(n, -1.0, 1.3)
+    core = tuple(slice(2, -2) for _ in grid)
+    cubic = sum((1.0 + 0.5j) * c ** 3 - 0.7 * c ** 2 for c in coords)
+    cubic_lap = sum((6.0 + 3.0j) * c - 1.4 for c in coords)
+    cd = oracle.laplacian(oracle.Problem(grid, hh, 1.0, 0.0, lap=oracle.LAP_CD), cubic, np.zeros(grid))
+    assert np.abs(cd[core] - cubic_lap[core]).max() <= 1e-9 * np.abs(cubic_lap).max()
+    quartic = sum(c ** 4 for c in coords).astype(complex)
+    quartic_lap = sum(12 * c ** 2 for c in coords)
+    cd = oracle.laplacian(oracle.Problem(grid, hh, 1.0, 0.0, lap=oracle.LAP_CD), quartic, np.zeros(grid))
+    shoc = oracle.laplacian(oracle.Problem(grid, hh, 1.0, 0.0), quartic, np.zeros(grid))
+    # CD's error on x^4 is h^2 f''''/12 = 2 h^2 per axis; 2SHOC's is zero
+    assert np.allclose(cd[core] - quartic_lap[core], 2 * dim * hh ** 2, rtol=1e-9)
+    assert np.abs(shoc[core] - quartic_lap[core]).max() <= 1e-9 * np.abs(quartic_lap).max()
