@@ -115,3 +115,31 @@ def test_batch_validation_on_the_host(lib):
     assert lib.nlse_create_batch(1, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EUNSUPPORTED
     assert lib.nlse_create_batch(0, arr, ctypes.c_void_p(4096), ctypes.byref(ctx)) == nlse.EINVAL
     assert ctx.value is None
+
+
+def _header_constants():
+    """#define values and enum members of include/nlse.h, by name."""
+    with open(os.path.join(HEADER_DIR, "nlse.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    consts = {m[0]: int(m[1]) for m in re.findall(r"#define\s+(NLSE_\w+)\s+(\d+)u?\b", text)}
+    consts.update({m[0]: int(m[1]) for m in re.findall(r"\b(NLSE_\w+)\s*=\s*(\d+)", text)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's status codes, enums, flags and tiling keys are the
+    header's values (marshalling only: a mismatch would pass the wrong
+    boundary, precision or schedule to the library)."""
+    h = _header_constants()
+    statuses = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE", "NLSE_ENONFINITE",
+                "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
+    assert [h[n] for n in statuses] == [nlse.OK, nlse.EINVAL, nlse.ENOMEM, nlse.ECUDA, nlse.EUNSTABLE,
+                                        nlse.ENONFINITE, nlse.ETIMEOUT, nlse.EUNSUPPORTED]
+    assert {k: h["NLSE_BC_" + {"lapzero": "LAPZERO"}.get(k, k.upper())] for k in nlse.BC} == nlse.BC
+    assert {k: h["NLSE_" + k.upper()] for k in nlse.PREC} == nlse.PREC
+    assert {k: h["NLSE_LAP_" + k.upper()] for k in nlse.LAP} == nlse.LAP
+    assert h["NLSE_FLAG_NO_STABILITY_CHECK"] == nlse.FLAG_NO_STABILITY_CHECK
+    assert h["NLSE_FLAG_PLAIN_SCHEDULE"] == nlse.FLAG_PLAIN_SCHEDULE
+    assert h["NLSE_FLAG_STACK"] == nlse.FLAG_STACK
+    for key in ("ROWS", "PLANES", "BATCH_NARROW", "1D_RESIDENT", "2D_FUSE"):
+        assert h["NLSE_TILE_" + key] == getattr(nlse, "TILE_" + key), key
