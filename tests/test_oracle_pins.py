@@ -499,3 +499,37 @@ def test_cd_laplacian_symbol_and_order(dim):
     # CD's error on x^4 is h^2 f''''/12 = 2 h^2 per axis; 2SHOC's is zero
     assert np.allclose(cd[core] - quartic_lap[core], 2 * dim * hh ** 2, rtol=1e-9)
     assert np.abs(shoc[core] - quartic_lap[core]).max() <= 1e-9 * np.abs(quartic_lap).max()
+
+
+_D, _M, _P, _Z = oracle.BC_DIRICHLET, oracle.BC_MSD, oracle.BC_PERIODIC, oracle.BC_LAPZERO
+SYM_CASES = [((17,), _D, oracle.LAP_2SHOC), ((17,), _M, oracle.LAP_2SHOC),
+             ((9, 9), _D, oracle.LAP_2SHOC), ((9, 9), _D, oracle.LAP_CD), ((9, 9), _D, oracle.LAP_2SHOC_MS),
+             ((9, 9), _M, oracle.LAP_2SHOC), ((8, 8), _P, oracle.LAP_2SHOC), ((9, 9), _Z, oracle.LAP_CD),
+             ((7, 7, 7), _D, oracle.LAP_2SHOC), ((7, 7, 7), _D, oracle.LAP_2SHOC_MS),
+             ((7, 7, 7), _M, oracle.LAP_2SHOC), ((6, 6, 6), _P, oracle.LAP_CD)]
+
+
+@pytest.mark.parametrize("shape,bc,lap", SYM_CASES)
+def test_laplacian_and_steps_commute_with_grid_symmetries(shape, bc, lap):
+    """The continuous operator has no preferred direction, and neither has any
+    boundary rule of Sec. 3.2: reflecting the grid along an axis, or (on cubic
+    grids) exchanging two axes, commutes with the Laplacian, with F and with
+    an RK4 step, boundaries included.  A stencil or boundary applied on one
+    side only, a swapped extent or a shifted index breaks this."""
+    psi = wl.random_field(shape, seed=77) + (1.5 if bc == oracle.BC_MSD else 0.0)
+    V = wl.random_potential(shape, seed=78)
+    h = 0.4
+    prob = oracle.Problem(shape, h, 0.8, -1.0, bc=bc, lap=lap)
+    lap0 = oracle.laplacian(prob, psi, V)
+    F0 = oracle.rhs(prob, psi, V)
+    k = 0.2 * oracle.invariants(prob, psi, V)[2]
+    step0 = oracle.run(prob, psi, V, k, 2)
+    scale = np.abs(lap0).max()
+    maps = [lambda z, ax=ax: np.flip(z, axis=ax) for ax in range(len(shape))]
+    if len(shape) > 1:
+        maps.append(lambda z: np.swapaxes(z, 0, len(shape) - 1))
+    for m in maps:
+        ps, Vs = np.ascontiguousarray(m(psi)), np.ascontiguousarray(m(V))
+        assert np.abs(oracle.laplacian(prob, ps, Vs) - m(lap0)).max() <= 1e-13 * scale
+        assert np.abs(oracle.rhs(prob, ps, Vs) - m(F0)).max() <= 1e-13 * np.abs(F0).max()
+        assert np.abs(oracle.run(prob, ps, Vs, k, 2) - m(step0)).max() <= 1e-13 * np.abs(step0).max()
