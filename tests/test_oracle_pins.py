@@ -273,6 +273,35 @@ def test_dirichlet_boundary_laplacian_is_exact_on_stationary_state():
     assert abs(lap[0] - d2[0]) < 1e-14 and abs(lap[-1] - d2[-1]) < 1e-14
 
 
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_dirichlet_boundary_value_on_a_stationary_state_with_general_a(dim):
+    """Eq. (dbc_lap) for any a: with V = s|psi|^2 + a Lap(psi)/psi, the smooth
+    real field psi = 1 + exp(-r^2) is a stationary state (psi_t = 0
+    everywhere), so D_b = -(s|psi_b|^2 - V_b) psi_b / a must be the analytic
+    Laplacian at every boundary point; a = 0.6, s = -1.3 (a D_b missing its 1/a,
+    or with the sign of N reversed, is off by a visible factor)."""
+    n = {1: 21, 2: 13, 3: 9}[dim]
+    shape = (n,) * dim
+    coords = wl.mesh(shape, -1.5, 1.5)
+    h = wl.spacing(n, -1.5, 1.5)
+    a, s = 0.6, -1.3
+    r2 = sum(c * c for c in coords)
+    g = np.exp(-r2)
+    psi = 1.0 + g
+    lap_exact = g * (4.0 * r2 - 2.0 * dim)
+    V = s * psi ** 2 + a * lap_exact / psi
+    lap = oracle.laplacian(oracle.Problem(shape, h, a, s), psi.astype(complex), V)
+    bnd = np.zeros(shape, bool)
+    for ax in range(dim):
+        sl = [slice(None)] * dim
+        sl[ax] = 0
+        bnd[tuple(sl)] = True
+        sl[ax] = -1
+        bnd[tuple(sl)] = True
+    assert np.abs(lap[bnd] - lap_exact[bnd]).max() <= 1e-13 * np.abs(lap_exact).max()
+    assert np.abs(oracle.rhs(oracle.Problem(shape, h, a, s), psi.astype(complex), V)[bnd]).max() == 0.0
+
+
 def test_stationary_state_is_kept_to_fourth_order():
     """RK4+2SHOC with Dirichlet holds the stationary sech state; the error
     falls ~16x per halving of h, and boundary values never move."""
