@@ -127,7 +127,9 @@ typedef struct {
 
 typedef struct nlse_ctx nlse_ctx;
 
-/* Creates a solver context for one grid on the current CUDA device.
+/* Creates a solver context for one grid on the current CUDA device: the
+ * problem of Eq. (NLSE) (Sec. 1) on the grid of Sec. 2.1, stepped by the RK4
+ * of Sec. 3.1 with the boundary rule of Sec. 3.2.
  * V_dev: the potential V (float for FP32, double for FP64), borrowed: it must
  * stay valid and unchanged while the context is used.  The context allocates
  * its own device work space: two stage buffers, the RK4 accumulator, the
@@ -138,7 +140,9 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out);
 
 /* Creates one context for `count` independent 2D instances of uneven sizes
  * and parameters, advanced together (one launch per RK4 stage covers every
- * instance).  p[i] gives instance i's grid, h, dt, a and s; prec, lap, bc
+ * instance): each is the problem of Eq. (NLSE) on its own grid (Sec. 2.1)
+ * with the Dirichlet rule of Sec. 3.2; the batching has no counterpart in the
+ * paper.  p[i] gives instance i's grid, h, dt, a and s; prec, lap, bc
  * and flags must be the same for all, bc Dirichlet, and n[0] a multiple of 4
  * (FP32) or 2 (FP64).  Psi, V and every work array are single flat device
  * buffers: instance i occupies n[0](i) * n[1](i) points starting at element
@@ -148,17 +152,19 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out);
  * refuses when any instance's dt exceeds its own bound. */
 int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_ctx** out);
 
-/* Number of instances of a batch context (0 for a single-grid context). */
+/* Number of instances of a batch context (0 for a single-grid context).  No
+ * counterpart in the paper, which treats one grid at a time. */
 int nlse_batch_count(const nlse_ctx* ctx);
 
-/* Per-instance mass, energy and dt_max (arrays of nlse_batch_count entries,
- * any may be NULL) of a batch context, as nlse_invariants computes them for
- * one grid.  Synchronises the stream.  Returns NLSE_ENONFINITE if any
+/* Per-instance mass, energy and dt_max (Eq. kdfull) (arrays of
+ * nlse_batch_count entries, any may be NULL) of a batch context, as
+ * nlse_invariants computes them for one grid.  Synchronises the stream.  Returns NLSE_ENONFINITE if any
  * instance holds a NaN or Inf. */
 int nlse_invariants_batch(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy, double* dt_max,
                           void* stream);
 
-/* Releases the context and its device memory (synchronises the device). */
+/* Releases the context and its device memory (synchronises the device).  No
+ * counterpart in the paper. */
 void nlse_destroy(nlse_ctx* ctx);
 
 /* 2SHOC Laplacian (or CD, per params.lap) of psi into lap_dev (same layout).
@@ -184,7 +190,8 @@ int nlse_rk4_step(nlse_ctx* ctx, void* psi_dev, void* stream);
  * returns NLSE_EUNSTABLE without stepping when dt exceeds it. */
 int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
 
-/* nlse_run on a state in host memory, for callers that keep Psi on the host:
+/* nlse_run (Eq. RK4, Sec. 3.1) on a state in host memory, for callers that
+ * keep Psi on the host (no counterpart in the paper):
  * copies psi_host (cbytes of the context's grid or batch; page-locked memory
  * makes the copies asynchronous DMA) into a device buffer the context owns
  * (allocated on first use), runs nsteps steps there, copies the result back
@@ -208,10 +215,12 @@ int nlse_run_host(nlse_ctx* ctx, void* psi_host, int64_t nsteps, void* stream);
 int nlse_invariants(nlse_ctx* ctx, const void* psi_dev, double* mass, double* energy,
                     double* dt_max, void* stream);   /* single-grid contexts only */
 
-/* Zeroes the FP32 compensated low part (call after writing psi externally). */
+/* Zeroes the FP32 compensated low part (call after writing psi externally).
+ * No counterpart in the paper, which computes in FP64 throughout (Sec. 4). */
 int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
 
-/* Synchronises the stream and reports NLSE_ENONFINITE if any RK4 step since
+/* No counterpart in the paper.
+ * Synchronises the stream and reports NLSE_ENONFINITE if any RK4 step since
  * the last check produced a NaN or Inf (a device flag set by the last stage
  * kernel), or NLSE_ETIMEOUT if a kernel gave up a bounded wait for its own
  * data transfers; clears the flag. */
@@ -276,10 +285,16 @@ int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, in
                                      168 bytes moved per point and step), 0 as four
                                      single-stage launches (default).  Other
                                      contexts accept the key and ignore it.        */
+/* Sets one tiling key of the context (no counterpart in the paper).  Returns
+ * NLSE_EINVAL for an unknown key or a value outside its range (the context is
+ * then unchanged). */
 int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
+/* Reads one tiling key into *value (its default if never set); no counterpart
+ * in the paper.  NLSE_EINVAL for an unknown key or NULL arguments. */
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 
-/* Human-readable description of the calling thread's last error ("" if none). */
+/* Human-readable description of the calling thread's last error ("" if none).
+ * No counterpart in the paper; the string belongs to the library. */
 const char* nlse_last_error(void);
 
 #ifdef __cplusplus

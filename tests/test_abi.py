@@ -143,3 +143,18 @@ def test_binding_constants_match_the_header():
     assert h["NLSE_FLAG_STACK"] == nlse.FLAG_STACK
     for key in ("ROWS", "PLANES", "BATCH_NARROW", "1D_RESIDENT", "2D_FUSE"):
         assert h["NLSE_TILE_" + key] == getattr(nlse, "TILE_" + key), key
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration in include/nlse.h is preceded by a comment that cites
+    the passage of the paper defining the operation (Sec., Eq., Table) or says
+    that the paper has no counterpart, and states its errors or result."""
+    with open(os.path.join(HEADER_DIR, "nlse.h")) as f:
+        text = f.read()
+    decls = list(re.finditer(r"(/\*(?:[^*]|\*(?!/))*\*/)\s*((?:int|void|const char\*)\s+(nlse_\w+)\s*\([^;]*\);)",
+                             text))
+    found = {m.group(3) for m in decls}
+    assert set(declared_functions()) <= found, set(declared_functions()) - found
+    for m in decls:
+        comment, name = re.sub(r"\s*\n\s*\*?\s*", " ", m.group(1)), m.group(3)   # one line of prose
+        assert re.search(r"Sec\.|Eqs?\.|Table|no counterpart", comment, flags=re.I), name
