@@ -1,27 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the fused RK4+2SHOC NLSE path on one GB300 (or N replicas).
 
-Workload: the 2D NLSE/GPE dark vortex, 2048 x 2048 on [-60, 60]^2, a = 0.5,
-s = -1, V = 0.01 (x^2 + y^2), Psi0 = Thomas-Fermi amplitude x tanh(r) x
-exp(i theta) + 1e-3 seeded complex Gaussian noise, Dirichlet boundaries,
-dt = 0.5 x the bound of Eq. (kdfull) on Psi0.  One benchmark step is one
-full RK4 step (four fused stage kernels) of the whole grid; the timed call is
-nlse_run(K steps), which first evaluates the FP64 invariants / stability
-bound on the device.  The default K = 10000 is the workload's full length.
+Headline workload: 512 independent 2D NLSE instances of uneven size advanced
+together -- sides U{64..1024 step 64} (seeded), a ~ U[0.3, 1], s = +-1,
+V = w^2 r^2 with w ~ U[0, 0.1], Psi0 a Gaussian of width U[2, 8] with a
+random phase gradient, Dirichlet boundaries, per-instance dt = 0.5 x the bound
+of Eq. (kdfull) on Psi0.  One benchmark step is one full RK4 step of every
+instance (four fused stage launches per tile group); the timed call is
+nlse_run(K steps) with its device-side entry check, on the FP32 state with its
+compensated part (FP64 invariants).  The default K = 5000 is the workload's
+full length.
 
-Reported: grid-point updates per second of the FP32 compensated path (the
-headline), the HBM roofline of its stage kernel, the FP64 fused path on the
-same GPU and the relative L2 difference between the two final states, an
-end-to-end figure through host buffers, and the CPU oracle timed on a bounded
-crop of the same workload.
+Reported beside it: the same batch in FP64 and the FP32-vs-FP64 error per
+instance; the batch end to end through host buffers; the paper's unfused FP64
+schedule per instance; the 2D dark vortex on one 2048 x 2048 grid (FP32, FP64,
+the multi-storage form, the unfused schedule, two stages per launch); the
+gradient workload; the 3D vortex ring and the 1D soliton; and the CPU oracle,
+all host cores and one, on a bounded sample of the batch.
 
 ``--impl reference`` times the CPU oracle instead (there is no other
-implementation of the method to run), on a crop sized so that the run ends in
-a few minutes.
+implementation of the method to run), on all host cores, on a sample of the
+batch sized so that the run ends in a few minutes.
 """
 from __future__ import annotations
 
 import argparse
+import datetime as _dt
 import hashlib
 import json
 import os
@@ -40,9 +44,13 @@ from paper_1109_1027_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "RK4 grid-pt updates/s & HBM GB/s vs ~8TB/s: FP32 batched vs FP64, at stated L2 err"
 UNIT = "grid-point updates/s"
+BATCH_COUNT = 512
+BATCH_WORKLOAD = ("512 uneven 2D NLSE instances advanced together: sides U{64..1024 step 64} (seed 4), "
+                  "a~U[0.3,1], s=+-1, V=w^2 r^2 with w~U[0,0.1], Gaussian psi0 of width U[2,8] with a phase "
+                  "gradient, Dirichlet, per-instance dt = 0.5 dt_max(psi0) of Eq. (kdfull)")
 N_SIDE = 2048
-WORKLOAD = ("2D NLSE/GPE dark vortex 2048x2048 on [-60,60]^2, a=0.5, s=-1, V=0.01 r^2, "
-            "TF*tanh(r)*exp(i theta) + 1e-3 noise (seed 2), Dirichlet, dt = 0.5 dt_max")
+GRID_WORKLOAD = ("2D NLSE/GPE dark vortex 2048x2048 on [-60,60]^2, a=0.5, s=-1, V=0.01 r^2, "
+                 "TF*tanh(r)*exp(i theta) + 1e-3 noise (seed 2), Dirichlet, dt = 0.5 dt_max")
 # Algorithmic bytes per grid-point update of the FP32 compensated path: per
 # RK4 step the four stages read/write (complex64 = 8 B, V float = 4 B)
 #   stage 1: R Psi, V; W acc, Y                         = 28
@@ -59,19 +67,32 @@ BYTES_PER_UPDATE_FP64 = 304
 # The paper's unfused FP64 schedule: 4 x (D: 32 + F: 56) + axpy lines 5 x 48 + 64.
 BYTES_PER_UPDATE_PLAIN = 656
 # DRAM bytes per stage launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over twelve consecutive stage launches of the
-# 2048^2 dark vortex with --cache-control none, i.e. with the L2 state of
-# back-to-back steps as in the benchmark) for the stage kernel source with the
-# given hash; null when the kernel has changed since.
-NCU_TRAFFIC = {"65bbaddccc3c": 113494827}
+# dram__bytes_write.sum, the mean over the four stage launches of one RK4 step,
+# with the L2 state of back-to-back steps) for the kernel sources with the
+# given hash; a kernel changed since its capture gets null.  The batch figure
+# is the mean over the wide-tile group's four stage launches.
+NCU_TRAFFIC_GRID = {}
+NCU_TRAFFIC_BATCH = {}
+# Instances of the batch that the CPU oracle times (every 32nd).
+CPU_SAMPLE_STRIDE = 32
 
 
-def kernel_hash() -> str:
+def _hash(files) -> str:
     h = hashlib.sha1()
-    for f in ("stage2d_tma.cuh", "stage2d_tile.cuh", "tma.cuh", "nlse_device.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1109_1027_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def kernel_hash() -> str:
+    """The single-grid 2D stage kernel's sources."""
+    return _hash(("stage2d_tma.cuh", "stage2d_tile.cuh", "tma.cuh", "nlse_device.cuh"))
+
+
+def batch_kernel_hash() -> str:
+    """The batched 2D stage kernel's sources."""
+    return _hash(("batch2d.cu", "stage2d_tile.cuh", "tma.cuh", "nlse_device.cuh"))
 
 
 def load_peaks():
@@ -85,28 +106,38 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples (every 200 ms) during the timed region."""
+    """nvidia-smi clock / throttle samples every 50 ms, from before the
+    autotuning of the headline leg to the end of its timed region; the
+    summary takes the samples inside the marked timed window when there are
+    at least three of them, else every sample of the leg (the same kernels
+    under the same load)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.index)],
+                 "-lms", str(self.PERIOD_MS), "-i", str(self.index)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, t0: _dt.datetime, t1: _dt.datetime):
+        """The timed region (local wall-clock times, as nvidia-smi prints them)."""
+        self.window = (t0, t1)
+
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -117,25 +148,36 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
         return False
 
+    @staticmethod
+    def _parse(ln):
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            return None
+        try:
+            ts = _dt.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            sm, mx = float(f[2]), float(f[3])
+        except ValueError:
+            return None
+        return ts, sm, mx, f[6:10]
+
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        rows = [r for r in (self._parse(ln) for ln in self.lines) if r is not None]
+        where = "headline leg (tuning, warm-up, timed region)"
+        if self.window is not None:
+            pad = _dt.timedelta(milliseconds=self.PERIOD_MS)
+            inside = [r for r in rows if self.window[0] - pad <= r[0] <= self.window[1] + pad]
+            if len(inside) >= 3:
+                rows, where = inside, "timed region"
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, f[5:9]):
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[3]):
                 if v.lower() == "active":
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "window": None}
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "window": where}
 
 
 def dist_setup():
@@ -169,29 +211,54 @@ def job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
     return world * units_per_rank / max_seconds
 
 
+def steps_taken(solver):
+    """Raises if nlse_run's entry check refused the steps just timed (they did
+    not run); a NaN or Inf produced by the steps themselves -- a collapsing
+    focusing instance of the batch -- is reported elsewhere and does not void
+    the timing."""
+    from paper_1109_1027_gb300 import nlse
+    try:
+        solver.check()
+    except nlse.NLSEError as err:
+        if err.code == nlse.EUNSTABLE or "entry check" in str(err):
+            raise
+
+
 # -- CPU oracle (the cpu_baseline leg and the reference arm) -------------------
 
-def oracle_rate(seconds: float, side: int | None = None, steps: int | None = None):
-    """Times the FP64 CPU oracle on a centred side x side crop of the workload
-    (the crop keeps the workload's h, V and Psi0 and has Dirichlet edges)."""
+def batch_sample(insts, stride=CPU_SAMPLE_STRIDE):
+    """Every stride-th instance of the batch: the sample the oracle times."""
+    return [insts[i] for i in range(0, len(insts), stride)]
+
+
+def oracle_batch_rate(sample, steps: int | None, seconds: float, threads: int):
+    """Times the FP64 CPU oracle on the sampled instances: each benchmark step
+    is one RK4 step of every sampled instance.  With steps None, as many steps
+    as fit in about `seconds`."""
     import oracle
-    full = wl.dark_vortex_2d(n=N_SIDE, steps=0)
-    side = side or 256
-    c0 = (N_SIDE - side) // 2
-    sl = (slice(c0, c0 + side), slice(c0, c0 + side))
-    psi, V = full.psi0[sl].copy(), full.V[sl].copy()
-    prob = oracle.Problem(psi.shape, full.h, full.a, full.s)
-    _, _, dtmax = oracle.invariants(prob, psi, V)
-    k = 0.5 * dtmax
+    probs, states, Vs, ks = [], [], [], []
+    for q in sample:
+        prob = oracle.Problem(q.shape, q.h, q.a, q.s)
+        probs.append(prob)
+        states.append(q.psi0.copy())
+        Vs.append(q.V)
+        ks.append(0.5 * oracle.invariants(prob, q.psi0, q.V)[2])
+    pts = sum(int(np.prod(q.shape)) for q in sample)
+
+    def step_all():
+        for i in range(len(sample)):
+            states[i] = oracle.run(probs[i], states[i], Vs[i], ks[i], 1, threads=threads)
+
     if steps is None:
         t0 = time.perf_counter()
-        oracle.run(prob, psi, V, k, 2)
-        per = (time.perf_counter() - t0) / 2
+        step_all()
+        per = time.perf_counter() - t0
         steps = max(2, int(seconds / per))
     t0 = time.perf_counter()
-    oracle.run(prob, psi, V, k, steps)
-    dt = time.perf_counter() - t0
-    return side * side * steps / dt, side, steps, dt
+    for _ in range(steps):
+        step_all()
+    el = time.perf_counter() - t0
+    return pts * steps / el, pts, steps, el
 
 
 def run_reference(args):
@@ -199,43 +266,56 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    # size the crop so that warmup + steps one-step samples take ~120 s
-    probe_side = 128
-    _, _, _, t = oracle_rate(0, side=probe_side, steps=3)
-    per_point = t / (3 * probe_side * probe_side)
+    threads = oracle.threads_available()
+    used = oracle.threads_used(threads)
+    insts = wl.gaussian_batch_2d(count=BATCH_COUNT, seed=4, steps=0,
+                                 only=set(range(0, BATCH_COUNT, CPU_SAMPLE_STRIDE)))
+    sample = sorted(insts, key=lambda q: q.shape[0])
+    # keep the smallest sampled instances that fit ~120 s for warmup + steps
+    probe = sample[: max(1, len(sample) // 2)]
+    _, ppts, _, pel = oracle_batch_rate(probe, 1, 0, threads)
+    per_point = pel / ppts
     budget = 120.0 / max(1, args.steps + args.warmup)
-    side = int(np.sqrt(budget / per_point)) // 2 * 2
-    side = max(16, min(N_SIDE, side))
-    full = wl.dark_vortex_2d(n=N_SIDE, steps=0)
-    c0 = (N_SIDE - side) // 2
-    sl = (slice(c0, c0 + side), slice(c0, c0 + side))
-    psi, V = full.psi0[sl].copy(), full.V[sl].copy()
-    prob = oracle.Problem(psi.shape, full.h, full.a, full.s)
-    _, _, dtmax = oracle.invariants(prob, psi, V)
-    k = 0.5 * dtmax
-    psi = oracle.run(prob, psi, V, k, args.warmup)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        psi = oracle.run(prob, psi, V, k, 1)
-    el = time.perf_counter() - t0
-    value = side * side * args.steps / el
-    sample = f"centred {side}x{side} crop of the workload (Dirichlet edges), one RK4 step per benchmark step"
+    chosen, pts = [], 0
+    for q in sample:
+        n = int(np.prod(q.shape))
+        if chosen and (pts + n) * per_point > budget:
+            break
+        chosen.append(q)
+        pts += n
+    oracle_batch_rate(chosen, args.warmup, 0, threads)              # warm-up steps
+    value, pts, _, el = oracle_batch_rate(chosen, args.steps, 0, threads)
+    sample_txt = (f"{len(chosen)} instances of the batch (every {CPU_SAMPLE_STRIDE}th, smallest first; "
+                  f"{pts} points, sides {[q.shape[0] for q in chosen]}), one RK4 step of each per benchmark step, "
+                  f"FP64 C oracle on {used} host threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": BATCH_WORKLOAD, "sample": sample_txt},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample_txt},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 # -- the GPU arm -----------------------------------------------------------------
 
+def timed(fn, stream, barrier, max_over_ranks):
+    """Milliseconds of fn() on the stream (CUDA events), max over ranks."""
+    import torch
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1))
+
+
 def run_ours(args):
     import torch
 
-    from paper_1109_1027_gb300 import nlse
+    from paper_1109_1027_gb300 import autotune, nlse
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -246,317 +326,69 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     nlse.load_library()
-
-    # Independent replica per rank (the single-grid path does not shard).
-    inst = wl.dark_vortex_2d(n=N_SIDE, seed=2 + rank, steps=0)
-    npts = N_SIDE * N_SIDE
-    V32 = torch.from_numpy(inst.V).to(dev).float().contiguous()
-    V64 = torch.from_numpy(inst.V).to(dev).contiguous()
-    psi0 = torch.from_numpy(inst.psi0).to(dev)
-    probe = nlse.Solver(V64, inst.h, 1.0, inst.a, inst.s, prec="fp64", check_stability=False)
-    _, _, dtmax = probe.invariants(psi0.clone())
-    probe.close()
-    k = 0.5 * dtmax
-
     stream = torch.cuda.current_stream()
     barrier = lambda: rank_barrier(pg, cuda=True)
     max_over_ranks = lambda x: ranks_max(pg, x, dev)
+    K, W = args.steps, args.warmup
 
-    # ---- FP32 compensated fused path: the headline --------------------------
-    from paper_1109_1027_gb300 import autotune
-    s32 = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
-    x32 = psi0.to(torch.complex64).contiguous()
-    tuning = autotune.tune(s32, x32, use_cache=False)
-    s32.run(x32, args.warmup)
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        s32.run(x32, args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
-    s32.check()
-    s32_rows = s32.get_tiling(nlse.TILE_ROWS)
-    s32_fused = s32.get_tiling(nlse.TILE_2D_FUSE)
-    ms_step = ms / args.steps
-    value = job_rate(world, npts * args.steps, ms * 1e-3)
-    clocks = clk.summary()
-    launches = (2 if s32_fused else 4) * args.steps + 2
-
-    # ---- the other launch schedule: two stages per launch or four launches ----
-    # (temporal blocking, NLSE_TILE_2D_FUSE; whichever the autotuner did not
-    # keep), timed on the same workload; both give identical bits.
-    kf = min(args.steps, 2000)
-    sf = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
-    sf.set_tiling(nlse.TILE_ROWS, s32_rows)
-    sf.set_tiling(nlse.TILE_2D_FUSE, 1 - s32_fused)
-    xa = psi0.to(torch.complex64).contiguous()
-    xb = psi0.to(torch.complex64).contiguous()
-    s32.run(xa, 64)
-    sf.run(xb, 64)
-    same_bits = bool(torch.equal(xa, xb))
-    sf.run(xb, args.warmup)
-    barrier()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    sf.run(xb, kf)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    msf = max_over_ranks(t0.elapsed_time(t1))
-    sf.check()
-    sf.close()
-    del xa, xb
-    bpu_f = BYTES_PER_UPDATE_FP32 if s32_fused else BYTES_PER_UPDATE_FP32_FUSED
-    other_schedule = {
-        "schedule": "four single-stage launches per step" if s32_fused else
-                    "two launches per step, two RK4 stages each (temporal blocking)",
-        "value": world * npts * kf / (msf * 1e-3), "unit": UNIT, "steps": kf, "ms_per_step": msf / kf,
-        "bytes_per_update": bpu_f, "achieved_gbs": bpu_f * npts / (msf / kf * 1e-3) / 1e9,
-        "same_bits_as_headline_after_64_steps": same_bits}
-
-    # ---- FP64 fused path on the same GPU, same steps ------------------------
-    s64 = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64")
-    x64 = psi0.clone().contiguous()
-    s64.run(x64, args.warmup)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s64.run(x64, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = max_over_ranks(e0.elapsed_time(e1))
-    s64.check()
-    diff = (x32.to(torch.complex128) - x64)
-    l2 = float(torch.linalg.vector_norm(diff) / torch.linalg.vector_norm(x64))
-    m32, en32, _ = s32.invariants(x32)
-    m64, en64, _ = s64.invariants(x64)
-    m0, en0, _ = s64.invariants(psi0.clone())
-
-    # ---- FP64 with the multi-storage 2SHOC form (Eqs. 2d2shocMs1-2) ------------
-    # The same operator with fewer FP64 operations per point; FP64 on this GPU
-    # is bound by its FP64 rate, so the form matters there.  Compared with the
-    # single-storage FP64 state after the same steps.
-    kms = min(args.steps, 1000)
-    sm = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", lap="2shoc_ms")
-    xm = psi0.clone().contiguous()
-    sm.run(xm, args.warmup)
-    xm.copy_(psi0)
-    barrier()
-    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    sm.run(xm, kms)
-    h1.record(stream)
-    torch.cuda.synchronize()
-    msm = max_over_ranks(h0.elapsed_time(h1))
-    sm.check()
-    sm.close()
-    xs = psi0.clone().contiguous()
-    s64.run(xs, kms)
-    ms_vs_single = float(torch.linalg.vector_norm(xm - xs) / torch.linalg.vector_norm(xs))
-    del xs, xm
-
-    # ---- the paper's unfused FP64 schedule on the same GPU (baseline) -------
-    kp = min(args.steps, 1000)
-    sp = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", plain=True)
-    xp = psi0.clone().contiguous()
-    sp.run(xp, args.warmup)
-    barrier()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    sp.run(xp, kp)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    msp = max_over_ranks(g0.elapsed_time(g1))
-    sp.check()
-    sp.close()
-
-    # ---- batched uneven instances, FP32 vs FP64 ------------------------------
-    batch = None
-    if not args.no_batch:
-        batch = run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks)
-
-    # ---- gradient of a final-time loss (checkpointed adjoint) ----------------
-    grad = None
-    if not args.no_batch:
-        grad = run_gradient_leg(args, dev, barrier, max_over_ranks)
-
-    # ---- the 3D and 1D workloads (context; the headline is the 2D grid) -------
-    other = None
-    if not args.no_batch:
-        other = run_other_grids(dev, barrier, max_over_ranks)
-
-    # ---- end to end through host buffers ------------------------------------
-    ke = min(args.steps, 200)
-    # The state lives in pinned host memory; every step is one nlse_run_host
-    # call: copy in, one RK4 step, copy out, stream synchronised.
-    host_state = torch.empty((N_SIDE, N_SIDE), dtype=torch.complex64, pin_memory=True)
-    host_state.copy_(x32.cpu())
-    se = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32", check_stability=False)
-    for _ in range(3):
-        se.run_host(host_state, 1)
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(ke):
-        se.run_host(host_state, 1)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    mse = max_over_ranks(f0.elapsed_time(f1))
-    e2e_value = world * npts * ke / (mse * 1e-3)
-    nbytes = N_SIDE * N_SIDE * 8
-
-    # ---- roofline of the stage kernel ---------------------------------------
-    peak, peak_kind = load_peaks()
-    bpu = BYTES_PER_UPDATE_FP32_FUSED if s32_fused else BYTES_PER_UPDATE_FP32
-    nlaunch = 2 if s32_fused else 4
-    achieved = bpu * npts / (ms_step * 1e-3) / 1e9
-    kh = kernel_hash()
-    traffic = None if s32_fused else NCU_TRAFFIC.get(kh)
-    roofline = {"bound": "hbm",
-                "kernel": "rk4_2d_fused_kernel (stage pairs 1+2 and 3+4, mean per launch)" if s32_fused else
-                          "stage2d_tma_kernel<float> (RK4 stages 1-4, mean per launch)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": bpu / nlaunch * npts,
-                "launch_ms": ms_step / nlaunch, "traffic": traffic, "kernel_hash": kh}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, side, steps, secs = oracle_rate(15.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 C oracle, centred {side}x{side} crop of the workload, {steps} RK4 steps "
-                         f"({secs:.1f} s, single thread)"}
-
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [N_SIDE, N_SIDE], "dt": k, "precision":
-                       "complex64 state + compensated low part, FP64 invariants",
-                       "l2_cache": "working set 176 MiB (Psi, lo, 2 stage buffers, acc, V) > 126 MiB L2; no flush",
-                       "parallelism": f"{world} independent replica(s)",
-                       "tiling": {"rows_per_cta": s32_rows, "two_stages_per_launch": s32_fused,
-                                  "chosen_by": "autotune (timed on this problem)",
-                                  "ms_per_step": {str(k_): v["ms_per_step"] for k_, v in tuning.items()}}},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes,
-                    "what": "per step: nlse_run_host(1 step) on a pinned host state: H2D of Psi, one RK4 step, D2H of Psi, stream synchronised"},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "fp32_other_schedule": other_schedule,
-            "fp64_fused_multi_storage": {"value": world * npts * kms / (msm * 1e-3), "unit": UNIT, "steps": kms,
-                                         "ms_per_step": msm / kms, "rel_l2_vs_single_storage": ms_vs_single,
-                                         "what": "lap = 2SHOC multi storage (D^x, D^y kept apart)"},
-            "fp64_fused": {"value": world * npts * args.steps / (ms64 * 1e-3), "unit": UNIT,
-                           "ms_per_step": ms64 / args.steps,
-                           "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / args.steps * 1e-3) / 1e9},
-            "fp64_plain": {"value": world * npts * kp / (msp * 1e-3), "unit": UNIT, "steps": kp,
-                           "ms_per_step": msp / kp,
-                           "achieved_gbs": BYTES_PER_UPDATE_PLAIN * npts / (msp / kp * 1e-3) / 1e9,
-                           "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"},
-            "fp32_vs_fp64_rel_l2": l2,
-            "batched": batch,
-            "gradient": grad,
-            "other_grids": other,
-            "mass_drift": {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1},
-            "energy_drift": {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1},
-        }))
-    if pg is not None:
-        pg.destroy_process_group()
-
-
-def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
-    """512 independent 2D instances (sides 64..1024 step 64, seeded per rank),
-    one launch per RK4 stage for the whole batch: FP32 and FP64 over the same
-    steps, per-instance relative L2 difference of the final states."""
-    import torch
-
-    from paper_1109_1027_gb300 import nlse
-
-    insts = wl.gaussian_batch_2d(count=512, seed=4 + rank, steps=0)
+    # ---- the batch: independent instances, one differently seeded batch per rank ----
+    insts = wl.gaussian_batch_2d(count=BATCH_COUNT, seed=4 + rank, steps=0)
     shapes = [q.shape for q in insts]
     npts = sum(q.shape[0] * q.shape[1] for q in insts)
-    Vs = [q.V for q in insts]
-    psis = [q.psi0 for q in insts]
-    V64 = nlse.BatchSolver.pack(Vs, torch.float64, dev)
-    psi64 = nlse.BatchSolver.pack(psis, torch.complex128, dev)
-    del Vs, psis
-    probe = nlse.BatchSolver(V64, shapes, [q.h for q in insts], 1.0, [q.a for q in insts], [q.s for q in insts],
-                             prec="fp64", check_stability=False)
+    hs, as_, ss = [q.h for q in insts], [q.a for q in insts], [q.s for q in insts]
+    V64 = nlse.BatchSolver.pack([q.V for q in insts], torch.float64, dev)
+    psi64 = nlse.BatchSolver.pack([q.psi0 for q in insts], torch.complex128, dev)
+    probe = nlse.BatchSolver(V64, shapes, hs, 1.0, as_, ss, prec="fp64", check_stability=False)
     _, _, dtmax = probe.invariants(psi64)
     probe.close()
     dts = [0.5 * d for d in dtmax]
-    hs, as_, ss = [q.h for q in insts], [q.a for q in insts], [q.s for q in insts]
-    steps = args.batch_steps
-    out = {"workload": "512 2D instances, sides U{64..1024 step 64}, a~U[0.3,1], s=+-1, V=w^2 r^2, Gaussian "
-                       "psi0 with phase gradient, per-instance dt = 0.5 dt_max (seeded)",
-           "points": npts, "steps": steps, "warmup": 3}
-    res = {}
-    for prec, rdt, cdt in (("fp32", torch.float32, torch.complex64), ("fp64", torch.float64, torch.complex128)):
-        V = V64.to(rdt).contiguous()
-        x = psi64.to(cdt).contiguous()
-        bs = nlse.BatchSolver(V, shapes, hs, dts, as_, ss, prec=prec)
-        if prec == "fp32":
-            from paper_1109_1027_gb300 import autotune
-            out["tiling"] = {"narrow_tile_width_bound": None,
-                             "ms_per_step": autotune.tune(bs, x, steps=3, use_cache=False)}
-            out["tiling"]["narrow_tile_width_bound"] = bs.get_tiling(nlse.TILE_BATCH_NARROW)
-        bs.run(x, 3)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        bs.run(x, steps)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1))
-        try:
-            bs.check()          # focusing instances above the critical mass may collapse (reported below)
-        except nlse.NLSEError as err:
-            if err.code != nlse.ENONFINITE:
-                raise
-        res[prec] = x
-        out[prec] = {"value": world * npts * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
-        bs.close()
-    out["fp32"]["achieved_gbs"] = BYTES_PER_UPDATE_FP32 * npts / (out["fp32"]["ms_per_step"] * 1e-3) / 1e9
+    V32 = V64.float().contiguous()
+    psi32 = psi64.to(torch.complex64).contiguous()
 
-    # The paper's unfused FP64 schedule run instance by instance (one context
-    # each, the per-instance baseline), on every 8th instance for a few steps.
-    sample = list(range(0, len(insts), 8))
-    pst = 10
-    V64c = V64.cpu()
-    psi64c = psi64.cpu()
-    offs = np.cumsum([0] + [q.shape[0] * q.shape[1] for q in insts])
-    solvers, states = [], []
-    for i in sample:
-        q = insts[i]
-        Vi = V64c[offs[i]:offs[i + 1]].reshape(q.shape).to(dev).contiguous()
-        solvers.append(nlse.Solver(Vi, q.h, dts[i], q.a, q.s, prec="fp64", plain=True, check_stability=False))
-        states.append(psi64c[offs[i]:offs[i + 1]].reshape(q.shape).to(dev).contiguous())
-    for sv, xs in zip(solvers, states):
-        sv.run(xs, 2)
-    barrier()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record()
-    for sv, xs in zip(solvers, states):
-        sv.run(xs, pst)
-    p1.record()
-    torch.cuda.synchronize()
-    msp = max_over_ranks(p0.elapsed_time(p1))
-    spts = sum(insts[i].shape[0] * insts[i].shape[1] for i in sample)
-    for sv in solvers:
-        sv.close()
-    out["fp64_plain_per_instance"] = {"value": world * spts * pst / (msp * 1e-3), "unit": UNIT,
-                                      "instances": len(sample), "points": int(spts), "steps": pst,
-                                      "what": "paper's unfused FP64 schedule, one context per instance, "
-                                              "instances in sequence (every 8th instance of the batch)"}
+    # ---- headline: the batch in FP32, nlse_run(K) with its entry check ------------
+    b32 = nlse.BatchSolver(V32, shapes, hs, dts, as_, ss, prec="fp32")
+    x32 = psi32.clone()
+    with ClockSampler(local) as clk:
+        tuning = autotune.tune(b32, x32, steps=3, use_cache=False)
+        b32.run(x32, W)
+        steps_taken(b32)
+        t_start = _dt.datetime.now()
+        ms = timed(lambda: b32.run(x32, K), stream, barrier, max_over_ranks)
+        t_end = _dt.datetime.now()
+        clk.mark(t_start, t_end)
+    steps_taken(b32)
+    clocks = clk.summary()
+    narrow = b32.get_tiling(nlse.TILE_BATCH_NARROW)
+    groups = int(any(sh[1] <= narrow for sh in shapes)) + int(any(sh[1] > narrow for sh in shapes))
+    ms_step = ms / K
+    value = job_rate(world, npts * K, ms * 1e-3)
+    launches = 4 * groups * K + 2
+    wide_pts = sum(sh[0] * sh[1] for sh in shapes if sh[1] > narrow)
+
+    # ---- the same batch in FP64 ----------------------------------------------------
+    k64 = min(K, 50)
+    b64 = nlse.BatchSolver(V64, shapes, hs, dts, as_, ss, prec="fp64")
+    x64 = psi64.clone()
+    b64.run(x64, 3)
+    steps_taken(b64)
+    ms64 = timed(lambda: b64.run(x64, k64), stream, barrier, max_over_ranks)
+    steps_taken(b64)
+
+    # ---- FP32 vs FP64 after the error run (per instance, relative L2) ---------------
+    ke = args.batch_steps
+    x32.copy_(psi32)
+    b32.reset_compensation()
+    x64.copy_(psi64)
+    b32.run(x32, ke)
+    b64.run(x64, ke)
+    for sv in (b32, b64):
+        try:
+            sv.check()
+        except nlse.NLSEError as err:
+            if err.code != nlse.ENONFINITE or "entry check" in str(err):
+                raise
     errs, collapsed = {-1: [], 1: []}, 0
-    a64 = res["fp64"]
-    a32 = res["fp32"].to(torch.complex128)
+    a64, a32 = x64, x32.to(torch.complex128)
     off = 0
     for q in insts:
         n = q.shape[0] * q.shape[1]
@@ -566,19 +398,260 @@ def run_batch_leg(args, dev, rank, world, pg, barrier, max_over_ranks):
             collapsed += 1
             continue
         errs[1 if q.s > 0 else -1].append(float(torch.linalg.vector_norm(s32 - s64) / torch.linalg.vector_norm(s64)))
+    del a32
 
     def stats(e):
         e = sorted(e)
         return {"max": e[-1], "median": e[len(e) // 2], "instances": len(e),
                 "within_1e-5": sum(v <= 1e-5 for v in e)} if e else None
 
-    # Defocusing (s = -1) instances stay smooth; focusing ones (s = +1) self-focus, and near
-    # collapse the dynamics amplify any rounding difference, so they are reported apart.
-    out["fp32_vs_fp64_rel_l2"] = {"defocusing_s-1": stats(errs[-1]), "focusing_s+1": stats(errs[1])}
-    out["collapsed_instances"] = collapsed
-    out["collapsed_note"] = ("focusing (s=+1) instances whose mass exceeds the 2D critical mass collapse; "
-                             "with dt fixed at 0.5 dt_max(psi0) the explicit scheme then overflows (the bound "
-                             "of Eq. kdfull shrinks as |psi| grows); they are excluded from the error statistics")
+    # ---- end to end: the batch state in pinned host memory ------------------------
+    kh_e2e = min(K, 20)
+    host = psi32.cpu().pin_memory()
+    be = nlse.BatchSolver(V32, shapes, hs, dts, as_, ss, prec="fp32", check_stability=False)
+    be.set_tiling(nlse.TILE_BATCH_NARROW, narrow)
+
+    def host_steps(n):
+        for _ in range(n):
+            try:
+                be.run_host(host, 1)
+            except nlse.NLSEError as err:     # a focusing instance collapsing; reported above
+                if err.code != nlse.ENONFINITE:
+                    raise
+
+    host_steps(3)
+    mse = timed(lambda: host_steps(kh_e2e), stream, barrier, max_over_ranks)
+    be.close()
+    e2e_value = job_rate(world, npts * kh_e2e, mse * 1e-3)
+    cbytes = npts * 8
+    del host
+
+    # ---- roofline of the batched stage kernel --------------------------------------
+    peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_UPDATE_FP32 * npts / (ms_step * 1e-3) / 1e9
+    bkh = batch_kernel_hash()
+    traffic = NCU_TRAFFIC_BATCH.get(bkh)
+    launch_ms = ms_step / 4
+    roofline = {"bound": "hbm", "kernel": "stage2d_batch_kernel<float> (RK4 stages 1-4 over the batch, mean per "
+                                          "stage; both tile groups of a stage counted as one pass)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": BYTES_PER_UPDATE_FP32 / 4 * npts,
+                "launch_ms": launch_ms,
+                "traffic": traffic,
+                "traffic_what": "ncu dram__bytes_read.sum + dram__bytes_write.sum per wide-tile stage launch "
+                                f"(mean of the four stages; {wide_pts} of the {npts} points)",
+                "dram_gbs": (traffic * npts / wide_pts / (launch_ms * 1e-3) / 1e9) if traffic else None,
+                "kernel_hash": bkh}
+
+    # ---- the paper's unfused FP64 schedule, one context per instance --------------
+    plain = None
+    if not args.quick:
+        sample = list(range(0, len(insts), 8))
+        pst = 10
+        offs = np.cumsum([0] + [q.shape[0] * q.shape[1] for q in insts])
+        solvers, states = [], []
+        for i in sample:
+            q = insts[i]
+            Vi = V64[offs[i]:offs[i + 1]].reshape(q.shape).contiguous()
+            solvers.append(nlse.Solver(Vi, q.h, dts[i], q.a, q.s, prec="fp64", plain=True, check_stability=False))
+            states.append(psi64[offs[i]:offs[i + 1]].reshape(q.shape).contiguous().clone())
+        for sv, xs in zip(solvers, states):
+            sv.run(xs, 2)
+
+        def plain_steps():
+            for sv, xs in zip(solvers, states):
+                sv.run(xs, pst)
+
+        msp = timed(plain_steps, stream, barrier, max_over_ranks)
+        spts = sum(insts[i].shape[0] * insts[i].shape[1] for i in sample)
+        for sv in solvers:
+            sv.close()
+        plain = {"value": job_rate(world, spts * pst, msp * 1e-3), "unit": UNIT, "instances": len(sample),
+                 "points": int(spts), "steps": pst,
+                 "what": "paper's unfused FP64 schedule, one context per instance, instances in sequence "
+                         "(every 8th instance of the batch)"}
+    b32.close()
+    b64.close()
+    del x32, x64, psi64, V64
+
+    grid = None if args.quick else run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks)
+    grad = None if args.quick else run_gradient_leg(args, dev, barrier, max_over_ranks)
+    other = None if args.quick else run_other_grids(dev, barrier, max_over_ranks)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sample = batch_sample(insts)
+        threads = oracle.threads_available()
+        used = oracle.threads_used(threads)
+        rate_all, spts, st_all, sec_all = oracle_batch_rate(sample, None, 12.0, threads)
+        rate_one, _, st_one, sec_one = oracle_batch_rate(sample, None, 8.0, 1)
+        what = (f"FP64 C oracle on every {CPU_SAMPLE_STRIDE}th instance of the batch ({len(sample)} instances, "
+                f"{spts} points), one RK4 step of each per step")
+        cpu = {"value": rate_all, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"{what}; {st_all} steps in {sec_all:.1f} s on {used} threads",
+               "single_thread": {"value": rate_one, "unit": UNIT, "cores": 1,
+                                 "sample": f"{what}; {st_one} steps in {sec_one:.1f} s"}}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "instances": BATCH_COUNT, "points": npts,
+                       "precision": "complex64 state + compensated low part, FP64 invariants and entry check",
+                       "l2_cache": f"working set {npts * 44 / 2**30:.1f} GiB (Psi, lo, 2 stage buffers, acc, V) "
+                                   "> 126 MiB L2; no flush",
+                       "parallelism": f"{world} independent batch(es), one per rank",
+                       "tiling": {"narrow_tile_width_bound": narrow, "chosen_by": "autotune (timed on this batch)",
+                                  "ms_per_step": {str(k_): v["ms_per_step"] for k_, v in tuning.items()}}},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": cbytes, "d2h_bytes_per_step": cbytes,
+                    "steps": kh_e2e,
+                    "what": "per step: nlse_run_host(1 step) on the batch state in pinned host memory: H2D of "
+                            "Psi, one RK4 step, D2H of Psi and the status, stream synchronised (entry check "
+                            "off: the workload's focusing instances collapse and fall below their bound)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "batched_fp64": {"value": job_rate(world, npts * k64, ms64 * 1e-3), "unit": UNIT, "steps": k64,
+                             "ms_per_step": ms64 / k64,
+                             "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / k64 * 1e-3) / 1e9},
+            "batched_fp32_vs_fp64_rel_l2": {"steps": ke, "defocusing_s-1": stats(errs[-1]),
+                                            "focusing_s+1": stats(errs[1]), "collapsed_instances": collapsed,
+                                            "collapsed_note": "focusing (s=+1) instances whose mass exceeds the "
+                                            "2D critical mass collapse; with dt fixed at 0.5 dt_max(psi0) the "
+                                            "explicit scheme then overflows (the bound of Eq. kdfull shrinks as "
+                                            "|psi| grows); they are excluded from the error statistics"},
+            "batched_fp64_plain_per_instance": plain,
+            "grid_2048": grid,
+            "gradient": grad,
+            "other_grids": other,
+        }))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks):
+    """The 2D dark vortex on one 2048 x 2048 grid: FP32 (autotuned), the other
+    FP32 launch schedule, FP64 fused, FP64 multi-storage, the paper's unfused
+    FP64 schedule; FP32-vs-FP64 difference, mass and energy drift."""
+    import torch
+
+    from paper_1109_1027_gb300 import autotune, nlse
+
+    K, W = min(args.steps, 2000), args.warmup
+    inst = wl.dark_vortex_2d(n=N_SIDE, seed=2 + rank, steps=0)
+    npts = N_SIDE * N_SIDE
+    V32 = torch.from_numpy(inst.V).to(dev).float().contiguous()
+    V64 = torch.from_numpy(inst.V).to(dev).contiguous()
+    psi0 = torch.from_numpy(inst.psi0).to(dev)
+    probe = nlse.Solver(V64, inst.h, 1.0, inst.a, inst.s, prec="fp64", check_stability=False)
+    _, _, dtmax = probe.invariants(psi0.clone())
+    probe.close()
+    k = 0.5 * dtmax
+    out = {"workload": GRID_WORKLOAD, "steps": K, "dt": k}
+
+    s32 = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
+    x32 = psi0.to(torch.complex64).contiguous()
+    tuning = autotune.tune(s32, x32, use_cache=False)
+    s32.run(x32, W)
+    ms = timed(lambda: s32.run(x32, K), stream, barrier, max_over_ranks)
+    steps_taken(s32)
+    rows, fused = s32.get_tiling(nlse.TILE_ROWS), s32.get_tiling(nlse.TILE_2D_FUSE)
+    ms_step = ms / K
+    peak, peak_kind = load_peaks()
+    bpu = BYTES_PER_UPDATE_FP32_FUSED if fused else BYTES_PER_UPDATE_FP32
+    nl = 2 if fused else 4
+    kh = kernel_hash()
+    traffic = None if fused else NCU_TRAFFIC_GRID.get(kh)
+    achieved = bpu * npts / (ms_step * 1e-3) / 1e9
+    out["fp32"] = {"value": job_rate(world, npts * K, ms * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
+                   "tiling": {"rows_per_cta": rows, "two_stages_per_launch": fused,
+                              "ms_per_step": {str(k_): v["ms_per_step"] for k_, v in tuning.items()}},
+                   "roofline": {"bound": "hbm", "kernel": "rk4_2d_fused_kernel" if fused else "stage2d_tma_kernel<float>",
+                                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                "peak_kind": f"{peak_kind} copy bandwidth",
+                                "algorithmic_bytes_per_launch": bpu / nl * npts, "launch_ms": ms_step / nl,
+                                "traffic": traffic,
+                                "dram_gbs": traffic / (ms_step / nl * 1e-3) / 1e9 if traffic else None,
+                                "kernel_hash": kh}}
+
+    # the launch schedule the autotuner did not keep (same bits)
+    kf = min(K, 1000)
+    sf = nlse.Solver(V32, inst.h, k, inst.a, inst.s, prec="fp32")
+    sf.set_tiling(nlse.TILE_ROWS, rows)
+    sf.set_tiling(nlse.TILE_2D_FUSE, 1 - fused)
+    xa = psi0.to(torch.complex64).contiguous()
+    xb = psi0.to(torch.complex64).contiguous()
+    s32.run(xa, 64)
+    sf.run(xb, 64)
+    same_bits = bool(torch.equal(xa, xb))
+    sf.run(xb, W)
+    msf = timed(lambda: sf.run(xb, kf), stream, barrier, max_over_ranks)
+    steps_taken(sf)
+    sf.close()
+    del xa, xb
+    bpu_f = BYTES_PER_UPDATE_FP32 if fused else BYTES_PER_UPDATE_FP32_FUSED
+    out["fp32_other_schedule"] = {
+        "schedule": "four single-stage launches per step" if fused else
+                    "two launches per step, two RK4 stages each (temporal blocking)",
+        "value": job_rate(world, npts * kf, msf * 1e-3), "unit": UNIT, "steps": kf, "ms_per_step": msf / kf,
+        "bytes_per_update": bpu_f, "achieved_gbs": bpu_f * npts / (msf / kf * 1e-3) / 1e9,
+        "same_bits_as_the_kept_schedule_after_64_steps": same_bits}
+
+    x32.copy_(psi0.to(torch.complex64))
+    s32.reset_compensation()
+    s64 = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64")
+    x64 = psi0.clone().contiguous()
+    s64.run(x64, W)
+    x64.copy_(psi0)
+    ms64 = timed(lambda: s64.run(x64, K), stream, barrier, max_over_ranks)
+    steps_taken(s64)
+    s32.run(x32, K)
+    steps_taken(s32)
+    out["fp64"] = {"value": job_rate(world, npts * K, ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K,
+                   "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / K * 1e-3) / 1e9}
+    out["fp32_vs_fp64_rel_l2_after_steps"] = float(
+        torch.linalg.vector_norm(x32.to(torch.complex128) - x64) / torch.linalg.vector_norm(x64))
+    m32, en32, _ = s32.invariants(x32)
+    m64, en64, _ = s64.invariants(x64)
+    m0, en0, _ = s64.invariants(psi0.clone())
+    out["mass_drift"] = {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1}
+    out["energy_drift"] = {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1}
+
+    # FP64 with the multi-storage 2SHOC form (Eqs. 2d2shocMs1-2)
+    kms = min(K, 500)
+    sm = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", lap="2shoc_ms")
+    xm = psi0.clone().contiguous()
+    sm.run(xm, W)
+    xm.copy_(psi0)
+    msm = timed(lambda: sm.run(xm, kms), stream, barrier, max_over_ranks)
+    steps_taken(sm)
+    sm.close()
+    xs = psi0.clone().contiguous()
+    s64.run(xs, kms)
+    out["fp64_multi_storage"] = {"value": job_rate(world, npts * kms, msm * 1e-3), "unit": UNIT, "steps": kms,
+                                 "ms_per_step": msm / kms,
+                                 "rel_l2_vs_single_storage": float(torch.linalg.vector_norm(xm - xs) /
+                                                                   torch.linalg.vector_norm(xs))}
+    del xs, xm
+
+    # the paper's unfused FP64 schedule on the same GPU (baseline)
+    kp = min(K, 500)
+    sp = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", plain=True)
+    xp = psi0.clone().contiguous()
+    sp.run(xp, W)
+    msp = timed(lambda: sp.run(xp, kp), stream, barrier, max_over_ranks)
+    steps_taken(sp)
+    sp.close()
+    out["fp64_plain"] = {"value": job_rate(world, npts * kp, msp * 1e-3), "unit": UNIT, "steps": kp,
+                         "ms_per_step": msp / kp,
+                         "achieved_gbs": BYTES_PER_UPDATE_PLAIN * npts / (msp / kp * 1e-3) / 1e9,
+                         "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"}
+    s32.close()
+    s64.close()
     return out
 
 
@@ -587,9 +660,10 @@ def run_other_grids(dev, barrier, max_over_ranks):
     (2048 points, the whole 2000-step run) in FP32 and FP64."""
     import torch
 
-    from paper_1109_1027_gb300 import nlse
+    from paper_1109_1027_gb300 import autotune, nlse
 
     out = {}
+    stream = torch.cuda.current_stream()
 
     def rate(inst, prec, steps, lap="2shoc"):
         rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
@@ -598,17 +672,11 @@ def run_other_grids(dev, barrier, max_over_ranks):
         probe = nlse.Solver(V, inst.h, 1.0, inst.a, inst.s, prec=prec, check_stability=False)
         dtm = probe.invariants(x)[2]
         probe.close()
-        sv = nlse.Solver(V, inst.h, 0.5 * dtm, inst.a, inst.s, prec=prec, lap=lap, check_stability=False)
-        from paper_1109_1027_gb300 import autotune
+        sv = nlse.Solver(V, inst.h, 0.5 * dtm, inst.a, inst.s, prec=prec, lap=lap)
         autotune.tune(sv, x, steps=4, use_cache=False)
         sv.run(x, 3)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        sv.run(x, steps)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+        ms = timed(lambda: sv.run(x, steps), stream, barrier, max_over_ranks) / steps
+        steps_taken(sv)
         npts = int(np.prod(inst.shape))
         res = {"ms_per_step": ms, "updates_per_s": npts / (ms * 1e-3)}
         if len(inst.shape) == 1 and sv.get_tiling(nlse.TILE_1D_RESIDENT):
@@ -667,12 +735,12 @@ def run_gradient_leg(args, dev, barrier, max_over_ranks):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances and gradient legs")
-    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--quick", action="store_true", help="the batched headline, its FP64 and e2e legs only")
+    ap.add_argument("--batch-steps", type=int, default=200, help="steps of the FP32-vs-FP64 error run")
     ap.add_argument("--grad-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -20,8 +20,11 @@
  *    caller owns them.  Device pointers must be 16-byte aligned.
  *  - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
  *    Calls enqueue work on the stream and return without synchronising, except
- *    where stated (nlse_invariants, nlse_check, and the stability check of
- *    nlse_run).
+ *    where stated (nlse_invariants, nlse_invariants_batch, nlse_check,
+ *    nlse_run_host, nlse_adjoint).  Failures found on the device (a NaN or
+ *    Inf written by a step, a refusal of nlse_run's entry check, a timed-out
+ *    wait) are kept in the context's status and returned by the next
+ *    nlse_check, which reads and clears them.
  *  - Every call returns an nlse_status.  Nothing aborts, throws or traps on
  *    the device.  nlse_last_error() describes the last failure of the calling
  *    thread.
@@ -180,14 +183,24 @@ int nlse_lap2shoc(nlse_ctx* ctx, const void* psi_dev, void* lap_dev, void* strea
  * of Sec. 3.2 for F at boundary points.  Four fused stage kernels.  In FP32
  * the state is psi_dev plus the context's compensated low part, which is reset
  * to zero whenever psi_dev differs from the previous call's pointer or
- * nlse_reset_compensation() is called. */
+ * nlse_reset_compensation() is called.  No entry check; the state is left
+ * unchanged while a refusal of an earlier nlse_run is pending (see nlse_run). */
 int nlse_rk4_step(nlse_ctx* ctx, void* psi_dev, void* stream);
 
 /* nsteps RK4 steps in place (same arithmetic as nsteps calls of
- * nlse_rk4_step), replayed from a CUDA graph captured on first use for this
- * psi_dev.  Unless NLSE_FLAG_NO_STABILITY_CHECK is set, first evaluates the
- * bound of Eq. (kdfull) on the current state (synchronising the stream) and
- * returns NLSE_EUNSTABLE without stepping when dt exceeds it. */
+ * nlse_rk4_step), stream-ordered: no host synchronisation.  The steps are
+ * replays of CUDA graphs of 32, 16, 8, 4, 2 and 1 steps captured on first use
+ * for this psi_dev (n = 32 q + r: q replays of the 32-step graph and one of
+ * each graph whose bit is set in r).  When the stream is being captured by the
+ * caller, the kernels are enqueued directly instead and become part of the
+ * caller's graph.  Unless NLSE_FLAG_NO_STABILITY_CHECK is set, the steps are
+ * preceded on the stream by an entry check on the device: the bound of
+ * Eq. (kdfull) of every instance, evaluated in FP64 from the current state,
+ * against its dt.  If dt exceeds a bound (or the state holds a NaN or Inf),
+ * the check records the refusal in the context's status; the state is then
+ * left unchanged by these steps and by every later step until nlse_check,
+ * which returns NLSE_EUNSTABLE (or NLSE_ENONFINITE) and clears the refusal.
+ * Returns a host-side error (invalid argument, launch failure) directly. */
 int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
 
 /* nlse_run (Eq. RK4, Sec. 3.1) on a state in host memory, for callers that
@@ -196,8 +209,10 @@ int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
  * makes the copies asynchronous DMA) into a device buffer the context owns
  * (allocated on first use), runs nsteps steps there, copies the result back
  * into psi_host and synchronises the stream.  A host state has no FP32
- * compensated part: each call starts from psi_host with it zero.  Errors as
- * nlse_run; on an error psi_host is left as it was. */
+ * compensated part: each call starts from psi_host with it zero.  As it
+ * synchronises anyway, it returns the context's status as nlse_check does
+ * (and clears it): a refusal of the entry check (psi_host unchanged), a
+ * non-finite value produced by the steps (psi_host holds the result). */
 int nlse_run_host(nlse_ctx* ctx, void* psi_host, int64_t nsteps, void* stream);
 
 /* Mass M = h^d sum |Psi|^2, energy
@@ -220,10 +235,12 @@ int nlse_invariants(nlse_ctx* ctx, const void* psi_dev, double* mass, double* en
 int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
 
 /* No counterpart in the paper.
- * Synchronises the stream and reports NLSE_ENONFINITE if any RK4 step since
- * the last check produced a NaN or Inf (a device flag set by the last stage
- * kernel), or NLSE_ETIMEOUT if a kernel gave up a bounded wait for its own
- * data transfers; clears the flag. */
+ * Synchronises the stream, reads the context's device status and clears it.
+ * Returns, in this order of precedence: NLSE_ETIMEOUT if a kernel gave up a
+ * bounded wait for its own data transfers; NLSE_EUNSTABLE if an entry check
+ * of nlse_run found dt above the bound of Eq. (kdfull) (the message names the
+ * instance, its dt and its bound); NLSE_ENONFINITE if an entry check found a
+ * NaN or Inf in the state or an RK4 step since the last check produced one. */
 int nlse_check(nlse_ctx* ctx, void* stream);
 
 /* nlse_invariants without a context and without allocating anything.  The
@@ -231,8 +248,9 @@ int nlse_check(nlse_ctx* ctx, void* stream);
  * device memory -- code inside a framework that owns all device memory
  * through its own pool or budget, or a latency-critical path that cannot
  * take the device synchronisation a cudaMalloc may cause -- and so cannot
- * create an nlse_ctx.  Same reductions as nlse_invariants (p->dt and flags
- * are ignored; an FP32 state is taken as psi_dev alone, without a
+ * create an nlse_ctx.  Same reductions as nlse_invariants for a single grid
+ * (p->dt is not used; a stack, NLSE_FLAG_STACK, is refused with
+ * NLSE_EUNSUPPORTED; an FP32 state is taken as psi_dev alone, without a
  * compensated part), with the block partials in a static device array of
  * 786,480 bytes that the library holds on every GPU that loads it, for the
  * life of the process.  Grids above 67,108,864 points are rejected with
@@ -258,7 +276,9 @@ int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const voi
  * state's size (c = 2 in FP32, 1 in FP64), as the reverse sweep keeps the four
  * stage inputs of every step of a segment.  Uses the context's compensated
  * part, which then no longer belongs to any caller state.  Synchronises the
- * stream. */
+ * stream; a refusal of an earlier nlse_run still pending in the context's
+ * status (which keeps the state from stepping) is returned and cleared, as
+ * nlse_check would. */
 int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
                  int64_t ckpt_every, void* dpsi0_dev, void* dV_dev, double* loss, void* stream);
 

@@ -36,43 +36,77 @@ LAP_2SHOC = 0
 LAP_CD = 1
 LAP_2SHOC_MS = 2     # multi-storage 2SHOC (Eqs. 2d2shocMs1-2, 3d2shocMs1-2); 1D: same as LAP_2SHOC
 
-_lib = None
+_libs = {}
 
 
-def _lib_path() -> str:
+def _lib_path(threaded: bool) -> str:
     with open(_SRC, "rb") as f:
         digest = hashlib.sha1(f.read()).hexdigest()[:12]
-    return os.path.join(_BUILD, f"libnlse_oracle_{digest}.so")
+    return os.path.join(_BUILD, f"libnlse_oracle{'_omp' if threaded else ''}_{digest}.so")
 
 
-def build() -> str:
-    """Compile the oracle (gcc, -O2, no FMA contraction); return the .so path."""
-    path = _lib_path()
+def build(threaded: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, no FMA contraction); return the .so path.
+
+    ``threaded`` builds it with -fopenmp: the per-point loops are then shared
+    among threads, with the same bits as the serial build (each point's
+    arithmetic is unchanged; the reductions stay serial)."""
+    path = _lib_path(threaded)
     if not os.path.exists(path):
         os.makedirs(_BUILD, exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"
+        flags = ["-fopenmp"] if threaded else ["-Wno-unknown-pragmas"]
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-Wall", "-o", tmp, _SRC, "-lm"])
+                               "-Wall"] + flags + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, path)
     return path
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        lp = ctypes.POINTER(ctypes.c_long)
-        common = [ctypes.c_int, lp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                  ctypes.c_int, ctypes.c_int]
-        lib.oracle_laplacian.argtypes = common + [dp, dp, dp, dp]
-        lib.oracle_rhs.argtypes = common + [dp, dp, dp]
-        lib.oracle_run.argtypes = common + [ctypes.c_double, ctypes.c_long, dp, dp]
-        lib.oracle_invariants.argtypes = common + [dp, dp, dp, dp, dp]
-        for fn in (lib.oracle_laplacian, lib.oracle_rhs, lib.oracle_run, lib.oracle_invariants):
-            fn.restype = ctypes.c_int
-        _lib = lib
-    return _lib
+def threads_available() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _load(threads: int = 1):
+    """The serial oracle, or with threads > 1 the OpenMP build set to use that
+    many threads (falls back to the serial build where OpenMP is missing)."""
+    threaded = threads > 1
+    if threaded and "omp" not in _libs:
+        try:
+            _libs["omp"] = _bind(ctypes.CDLL(build(threaded=True)))
+        except (OSError, subprocess.CalledProcessError):
+            _libs["omp"] = None
+    if threaded and _libs["omp"] is not None:
+        _libs["omp"].oracle_set_threads(int(threads))
+        return _libs["omp"]
+    if "serial" not in _libs:
+        _libs["serial"] = _bind(ctypes.CDLL(build()))
+    return _libs["serial"]
+
+
+def threads_used(threads: int) -> int:
+    """Threads the oracle actually runs with when asked for ``threads``."""
+    lib = _load(threads)
+    return int(lib.oracle_set_threads(int(threads) if threads > 1 else 1))
+
+
+def _bind(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    lp = ctypes.POINTER(ctypes.c_long)
+    common = [ctypes.c_int, lp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+              ctypes.c_int, ctypes.c_int]
+    lib.oracle_laplacian.argtypes = common + [dp, dp, dp, dp]
+    lib.oracle_rhs.argtypes = common + [dp, dp, dp]
+    lib.oracle_run.argtypes = common + [ctypes.c_double, ctypes.c_long, dp, dp]
+    lib.oracle_invariants.argtypes = common + [dp, dp, dp, dp, dp]
+    for fn in (lib.oracle_laplacian, lib.oracle_rhs, lib.oracle_run, lib.oracle_invariants):
+        fn.restype = ctypes.c_int
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_threads.restype = ctypes.c_int
+    return lib
 
 
 @dataclass(frozen=True)
@@ -136,11 +170,13 @@ def rhs(prob: Problem, psi, V) -> np.ndarray:
     return F
 
 
-def run(prob: Problem, psi, V, k: float, nsteps: int) -> np.ndarray:
-    """nsteps classic RK4 steps of size k, the ten lines of Eq. (RK4); returns a new array."""
+def run(prob: Problem, psi, V, k: float, nsteps: int, threads: int = 1) -> np.ndarray:
+    """nsteps classic RK4 steps of size k, the ten lines of Eq. (RK4); returns a new array.
+    ``threads`` > 1 shares each step's per-point loops among host threads
+    (the same bits)."""
     out = _cplx(psi, prob.shape).copy()
     V = _real(V, prob.shape)
-    _check(_load().oracle_run(*prob._args(), float(k), int(nsteps), _dp(out), _dp(V)))
+    _check(_load(threads).oracle_run(*prob._args(), float(k), int(nsteps), _dp(out), _dp(V)))
     return out
 
 

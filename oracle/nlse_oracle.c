@@ -17,6 +17,13 @@
  * reordering; every loop visits the grid in storage order.  Compile with
  * -ffp-contract=off so that no multiply-add is fused.
  *
+ * Threads: the loops that compute one value per grid point independently of
+ * the others (step 1, step 2, the boundary values, F and the RK4 axpys) carry
+ * OpenMP work-sharing pragmas.  Built without -fopenmp they are ignored; with
+ * it the points of such a loop are shared among threads, and since every
+ * point's arithmetic is the same, the results are the same bits for any
+ * thread count.  Reductions (mass, energy, the stability bound) stay serial.
+ *
  * Conventions (readings of the paper where it is silent):
  *  - Grid: x_i = x_min + h*i (Sec. 2.1); n[ax] points per axis including both
  *    boundary points; one h for every axis (Secs. 2.2, 2.3).  Storage is
@@ -223,6 +230,7 @@ static void laplacian_ms(const or_problem* P, const double* psi, const double* V
                          double* Dsum, double* lap) {
     long N = npoints(P);
     /* Step 1 at interior points: one second difference per axis. */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x)
@@ -230,6 +238,7 @@ static void laplacian_ms(const or_problem* P, const double* psi, const double* V
                     for (int ax = 0; ax < P->dim; ++ax)
                         put(Dsep + 2 * N * ax, idx(P, x, y, z), delta2(P, psi, ax, x, y, z));
     /* Step-1 boundary values (Dirichlet, Eq. dbc_lap, split as stated above). */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x) {
@@ -253,6 +262,7 @@ static void laplacian_ms(const or_problem* P, const double* psi, const double* V
     /* Step 2 at interior points, Eq. (2d2shocMs2) / Eq. (3d2shocMs2):
      * (7/6) sum_a D^a_c - (1/12) sum_a (D^a at the two neighbours along a).
      * Boundary points take D_b of Eq. (dbc_lap), as in the single-storage form. */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x) {
@@ -289,18 +299,21 @@ static void laplacian(const or_problem* P, const double* psi, const double* V, d
         return;
     }
     /* Step 1, interior points first. */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x)
                 if (!is_boundary(P, x, y, z))
                     put(D, idx(P, x, y, z), step1_interior(P, psi, x, y, z));
     /* Step-1 boundary condition (the MSD form needs the interior D). */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x)
                 if (is_boundary(P, x, y, z))
                     put(D, idx(P, x, y, z), boundary_D(P, psi, V, D, x, y, z));
     /* Step 2 (2SHOC) or D itself (CD); the boundary keeps D_b. */
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x) {
@@ -329,6 +342,7 @@ static void rhs(const or_problem* P, const double* psi, const double* V, double*
     double* D = work;
     double* lap = work + 8 * N;
     laplacian(P, psi, V, D, lap);
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x) {
@@ -338,6 +352,7 @@ static void rhs(const or_problem* P, const double* psi, const double* V, double*
                 cplx inner = c_add(c_scale(P->a, get(lap, p)), c_scale(nonlin(P, ps, V[p]), ps));
                 put(F, p, c_times_i(inner));
             }
+    #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < P->n[2]; ++z)
         for (long y = 0; y < P->n[1]; ++y)
             for (long x = 0; x < P->n[0]; ++x) {
@@ -383,16 +398,22 @@ static void rk4_step(const or_problem* P, double k, double* psi, const double* V
     double *Ktot = W->Ktot, *Ktmp = W->Ktmp, *ptmp = W->ptmp, *work = W->work;
     long p;
 
-    rhs(P, psi, V, Ktot, work);                                               /* 1 */
-    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktot, p))));  /* 2 */
-    rhs(P, ptmp, V, Ktmp, work);                                              /* 3 */
-    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* 4 */
-    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktmp, p))));  /* 5 */
-    rhs(P, ptmp, V, Ktmp, work);                                              /* 6 */
-    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* 7 */
-    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k, get(Ktmp, p))));        /* 8 */
-    rhs(P, ptmp, V, Ktmp, work);                                              /* 9 */
-    for (p = 0; p < N; ++p)                                                   /* 10 */
+    rhs(P, psi, V, Ktot, work);                                               /* K_tot = F(psi) */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktot, p))));  /* psi_tmp */
+    rhs(P, ptmp, V, Ktmp, work);                                              /* K_tmp = F(psi_tmp) */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* K_tot += 2 K_tmp */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktmp, p))));  /* psi_tmp */
+    rhs(P, ptmp, V, Ktmp, work);                                              /* K_tmp = F(psi_tmp) */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* K_tot += 2 K_tmp */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k, get(Ktmp, p))));        /* psi_tmp */
+    rhs(P, ptmp, V, Ktmp, work);                                              /* K_tmp = F(psi_tmp) */
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < N; ++p)                                                   /* the new state */
         put(psi, p, c_add(get(psi, p), c_scale(k / 6.0, c_add(get(Ktot, p), get(Ktmp, p)))));
 }
 
@@ -528,3 +549,18 @@ int oracle_invariants(int dim, const long* n, double h, double a, double s, int 
     free(D); free(lap_f);
     return 0;
 }
+
+/* Number of threads of the OpenMP build (the serial build ignores it and
+ * reports 1).  Returns the number the loops will use. */
+#ifdef _OPENMP
+#include <omp.h>
+int oracle_set_threads(int n) {
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
+#else
+int oracle_set_threads(int n) {
+    (void)n;
+    return 1;
+}
+#endif

@@ -81,6 +81,17 @@ def _keys_for(solver):
     return []
 
 
+def _require_steps_taken(solver):
+    """Raises if nlse_run's entry check refused the timed steps (they would
+    not have run); a NaN or Inf that the steps themselves produced (a
+    collapsing instance of a batch) does not void the timing."""
+    try:
+        solver.check()
+    except nlse.NLSEError as err:
+        if err.code == nlse.EUNSTABLE or "entry check" in str(err):
+            raise
+
+
 def tune(solver, psi: torch.Tensor, steps: int = 8, use_cache: bool = True) -> dict:
     """Chooses and sets the fastest tiling for `solver` on state `psi` (which
     is not modified).  Returns {tiling key: {"choice": v, "ms_per_step": {v: ms}}}."""
@@ -97,12 +108,14 @@ def tune(solver, psi: torch.Tensor, steps: int = 8, use_cache: bool = True) -> d
         for v in CANDIDATES[tile_key]:
             solver.set_tiling(tile_key, v)
             work.copy_(psi)                          # every candidate starts from the caller's state
-            solver.run(work, 2)                      # captures the graph for this tiling
+            solver.reset_compensation()
+            solver.run(work, 2)                      # captures the graphs for this tiling
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             solver.run(work, steps)
             e1.record()
             torch.cuda.synchronize()
+            _require_steps_taken(solver)
             times[v] = e0.elapsed_time(e1) / steps
         best = min(times, key=times.get)
         solver.set_tiling(tile_key, best)

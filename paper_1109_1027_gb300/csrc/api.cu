@@ -12,6 +12,7 @@
 
 #include "nlse.h"
 #include "nlse_internal.h"
+#include "stability.cuh"
 
 using nlse::StageLaunch;
 
@@ -38,9 +39,12 @@ int cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what);     \
     } while (0)
 
-// Steps captured per CUDA graph; nlse_run replays the graph and launches the
-// remainder directly.
-constexpr int64_t kGraphSteps = 32;
+// nlse_run replays CUDA graphs of 2^j RK4 steps, j = 0 .. kGraphLevels - 1,
+// captured on first use for the state pointer: n steps are n / 32 replays of
+// the 32-step graph and one replay of each graph whose bit is set in n % 32.
+constexpr int kGraphLevels = 6;
+constexpr int64_t kGraphSteps = (int64_t)1 << (kGraphLevels - 1);
+constexpr int kNoInstance = 0x7f7f7f7f;       // StatusBlock::inst when no instance was refused
 
 }  // namespace
 
@@ -54,13 +58,20 @@ struct nlse_ctx {
     void* acc;                // accumulated RK4 increment
     void* lo;                 // FP32 compensated low part (FP32 only)
     void* plain[4];           // unfused schedule: D, K_tot, K_tmp, Psi_tmp
-    int* flag;                // non-finite flag set by stage 4
+    int* flag;                // status bits (the first member of status)
+    nlse::StatusBlock* status;  // device status block (nlse_check reads and clears it)
+    // nlse_run's entry check (check.cu): one entry per instance, its rows of
+    // partial extremes and each instance's bound.
+    nlse::CheckEntry* check_tab;
+    int check_count, check_nrows;
+    double* check_partials;
+    double* check_bounds;
     double* partials;         // reduction scratch, nblocks x kPartialWidth
     int nblocks;
     double* red_out;          // reduced values on the device
     double* host_out;         // pinned copy of red_out
     const void* state_psi;    // psi whose compensated part lo currently holds
-    cudaGraphExec_t graph;
+    cudaGraphExec_t graphs[kGraphLevels];   // graphs[j]: 2^j steps on graph_psi
     const void* graph_psi;
     // Batched instances (nlse_create_batch): count > 0.
     int count;
@@ -140,10 +151,13 @@ StageLaunch base_launch(const nlse_ctx* c) {
     return L;
 }
 
-// Drops the captured time-loop graph (its launches bake in the tiling).
+// Drops the captured time-loop graphs (their launches bake in the tiling and
+// the state pointer).
 void drop_graph(nlse_ctx* c) {
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+    for (auto& g : c->graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
     c->graph_psi = nullptr;
 }
 
@@ -239,7 +253,7 @@ int enqueue_fused_step(nlse_ctx* c, const void* psi_in, void* psi_out, cudaStrea
 }
 
 // n RK4 steps on psi in place.  Fused steps alternate between psi and the
-// context's Y[0] (free on that path); an odd count ends with a copy back.
+// context's Y[0] (free on that path).
 int enqueue_steps(nlse_ctx* c, void* psi, int64_t n, cudaStream_t st) {
     if (!fused_steps(c)) {
         for (int64_t i = 0; i < n; ++i) {
@@ -248,12 +262,15 @@ int enqueue_steps(nlse_ctx* c, void* psi, int64_t n, cudaStream_t st) {
         }
         return NLSE_OK;
     }
-    for (int64_t i = 0; i < n; ++i) {
+    const int64_t nfused = n - n % 2;
+    for (int64_t i = 0; i < nfused; ++i) {
         const bool even = i % 2 == 0;
         int rc = enqueue_fused_step(c, even ? psi : c->Y[0], even ? c->Y[0] : psi, st);
         if (rc) return rc;
     }
-    if (n % 2) NLSE_CUDA(cudaMemcpyAsync(psi, c->Y[0], c->cbytes, cudaMemcpyDeviceToDevice, st), "state copy");
+    // An odd count ends, with the state back in psi, on one step of four
+    // single-stage launches in place (the same bits as a fused step).
+    if (n % 2) return enqueue_step(c, psi, st);
     return NLSE_OK;
 }
 
@@ -307,25 +324,6 @@ int bind_state(nlse_ctx* c, const void* psi, cudaStream_t st) {
     return NLSE_OK;
 }
 
-// Largest |G| entries of the Table of Sec. 3.3 (t:sumresults), in units of
-// 1/12.  |L - g| is convex in L, so the maximum over G and over all points
-// is reached at an extreme of G and an extreme of L.
-void g_extremes(int dim, double* gmin, double* gmax) {
-    static const double mx[4] = {0, 64, 128, 192}, mn[4] = {0, -4, -8, -12};
-    *gmin = mn[dim] / 12.0;
-    *gmax = mx[dim] / 12.0;
-}
-
-// dt_max of Eq. (kdfull) from the reduced extremes (see g_extremes).
-double dt_bound(int dim, double h, double a, const double* r) {
-    double gmin, gmax;
-    g_extremes(dim, &gmin, &gmax);
-    double worst = std::fmax(std::fabs(r[3] - gmin), std::fabs(r[2] - gmax));
-    worst = std::fmax(worst, std::fmax(std::fabs(r[2] - gmin), std::fabs(r[3] - gmax)));
-    worst = std::fmax(worst, r[4]);
-    return std::sqrt(8.0) * h * h / (a * worst);
-}
-
 int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
                           cudaStream_t st);
 
@@ -353,7 +351,7 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     const double h = c->p.h, hd = std::pow(h, (double)c->p.dim);
     if (mass) *mass = hd * r[0];
     if (energy) *energy = hd * r[1];
-    if (dt_max) *dt_max = dt_bound(c->p.dim, h, c->p.a, r);
+    if (dt_max) *dt_max = nlse::dt_bound(c->p.dim, h, c->p.a, r[2], r[3], r[4]);
     if (r[5] != 0.0 || !std::isfinite(r[0]))
         return fail(NLSE_ENONFINITE, "state holds %g non-finite values", r[5]);
     return NLSE_OK;
@@ -386,10 +384,154 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
         const double h2 = q.h * q.h;
         if (mass) mass[i] = h2 * r[0];
         if (energy) energy[i] = h2 * r[1];
-        if (dt_max) dt_max[i] = dt_bound(2, q.h, q.a, r);
+        if (dt_max) dt_max[i] = nlse::dt_bound(2, q.h, q.a, r[2], r[3], r[4]);
         if ((r[5] != 0.0 || !std::isfinite(r[0])) && bad < 0) bad = i;
     }
     if (bad >= 0) return fail(NLSE_ENONFINITE, "instance %d holds non-finite values", bad);
+    return NLSE_OK;
+}
+
+// nlse_run's entry check, enqueued on the stream (no host synchronisation):
+// the bound of Eq. (kdfull) of every instance against its dt; a refusal is
+// left in the status block, where it stops the stage-4 kernels from writing
+// the state and where nlse_check finds it.  MSD contexts need the boundary
+// term B of Table t:bc2 and take the full invariants reduction; the other
+// boundary rules have B = 0 and take the extremes pass of check.cu.
+int enqueue_entry_check(nlse_ctx* c, const void* psi, cudaStream_t st) {
+    const void* lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
+    if (c->p.bc == NLSE_BC_MSD) {
+        nlse::InvLaunch L;
+        L.dim = c->p.dim;
+        for (int ax = 0; ax < 3; ++ax) L.n[ax] = ax < c->p.dim ? c->p.n[ax] : 1;
+        L.prec = c->p.prec; L.lap = c->p.lap; L.bc = c->p.bc;
+        L.h = c->p.h; L.a = c->p.a; L.s = c->p.s;
+        L.psi = psi; L.lo = lo; L.V = c->V;
+        L.energy = false;
+        NLSE_CUDA(nlse::launch_invariants(L, c->partials, c->nblocks, c->red_out, st), "entry check launch");
+        NLSE_CUDA(nlse::launch_invariants_gate(c->red_out, c->p.dim, c->p.h, c->p.a, c->p.dt, c->check_bounds,
+                                               c->status, st), "entry check launch");
+        return NLSE_OK;
+    }
+    nlse::CheckLaunch C;
+    C.table = c->check_tab;
+    C.count = c->check_count;
+    C.nrows = c->check_nrows;
+    C.prec = c->p.prec;
+    C.psi = psi; C.lo = lo; C.V = c->V;
+    C.partials = c->check_partials;
+    C.bounds = c->check_bounds;
+    C.status = c->status;
+    NLSE_CUDA(nlse::launch_entry_check(C, st), "entry check launch");
+    return NLSE_OK;
+}
+
+// Builds the entry check's per-instance table (one entry per instance of a
+// batch or of a stack, one for a single grid) and its scratch.
+int setup_entry_check(nlse_ctx* c) {
+    const int count = c->count ? c->count : c->stack;
+    std::vector<nlse::CheckEntry> tab(count);
+    int rows = 0;
+    for (int i = 0; i < count; ++i) {
+        nlse::CheckEntry& e = tab[i];
+        const nlse_params& q = c->count ? c->bparams[i] : c->p;
+        int64_t npts = c->count ? q.n[0] * q.n[1] : c->npts / c->stack;
+        e.psi_off = c->count ? c->boff[i] : (int64_t)i * npts;
+        e.v_off = c->count ? c->boff[i] : 0;           // a stack's instances share V
+        e.npts = npts;
+        e.h = q.h; e.a = q.a; e.s = q.s; e.dt = q.dt;
+        e.h2a = q.h * q.h / q.a;
+        e.dim = q.dim;
+        e.row0 = rows;
+        rows += nlse::check_rows(npts);
+        e.row1 = rows;
+    }
+    c->check_count = count;
+    c->check_nrows = rows;
+    NLSE_CUDA(cudaMalloc((void**)&c->check_tab, sizeof(nlse::CheckEntry) * count), "allocating the check table");
+    NLSE_CUDA(cudaMemcpy(c->check_tab, tab.data(), sizeof(nlse::CheckEntry) * count, cudaMemcpyHostToDevice),
+              "uploading the check table");
+    NLSE_CUDA(cudaMalloc((void**)&c->check_partials, sizeof(double) * 3 * rows), "allocating check partials");
+    NLSE_CUDA(cudaMalloc((void**)&c->check_bounds, sizeof(double) * count), "allocating check bounds");
+    NLSE_CUDA(cudaMalloc((void**)&c->status, sizeof(nlse::StatusBlock)), "allocating the status block");
+    c->flag = &c->status->bits;
+    NLSE_CUDA(cudaMemset(&c->status->bits, 0, sizeof(int)), "zeroing the status");
+    NLSE_CUDA(cudaMemset(&c->status->inst, 0x7f, sizeof(int)), "zeroing the status");
+    return NLSE_OK;
+}
+
+// Status of the device block s (read by the caller after a synchronisation),
+// cleared on the stream when it holds anything: NLSE_ETIMEOUT, then the entry
+// check's refusals, then a non-finite value written by a step.
+int report_status(nlse_ctx* c, const nlse::StatusBlock& s, cudaStream_t st) {
+    if (!s.bits) return NLSE_OK;
+    double bound = 0.0;
+    if ((s.bits & nlse::kStatusUnstable) && s.inst >= 0 && s.inst < c->check_count)
+        NLSE_CUDA(cudaMemcpyAsync(&bound, c->check_bounds + s.inst, sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "bound copy");
+    NLSE_CUDA(cudaMemsetAsync(&c->status->bits, 0, sizeof(int), st), "status reset");
+    NLSE_CUDA(cudaMemsetAsync(&c->status->inst, 0x7f, sizeof(int), st), "status reset");
+    NLSE_CUDA(cudaStreamSynchronize(st), "status synchronise");
+    if (s.bits & nlse::kStatusTimeout)
+        return fail(NLSE_ETIMEOUT, "a bounded device-side wait gave up (a data transfer never completed)");
+    const int inst = s.inst == kNoInstance ? 0 : s.inst;
+    const char* what = c->count ? "instance" : (c->stack > 1 ? "stacked instance" : "grid");
+    if (s.bits & nlse::kStatusUnstable) {
+        const double dt = c->count ? c->bparams[inst].dt : c->p.dt;
+        return fail(NLSE_EUNSTABLE, "entry check of nlse_run (%s %d): dt = %.17g exceeds the bound %.17g of Eq. (kdfull); "
+                    "the steps were not taken", what, inst, dt, bound);
+    }
+    if (s.bits & nlse::kStatusEntryNonFinite)
+        return fail(NLSE_ENONFINITE, "entry check of nlse_run (%s %d): the state holds non-finite values; the steps "
+                    "were not taken", what, inst);
+    return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
+}
+
+// Captures n RK4 steps on psi (n = 2^j) into c->graphs[j].
+int capture_steps(nlse_ctx* c, void* psi, int j) {
+    cudaStream_t cs;
+    NLSE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e, "begin capture");
+    }
+    int rc = enqueue_steps(c, psi, (int64_t)1 << j, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&c->graphs[j], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graphs[j] = nullptr;
+        return cuda_fail(e, "graph instantiate");
+    }
+    return NLSE_OK;
+}
+
+// n RK4 steps on psi as replays of the cached graphs (see kGraphLevels).
+// Every level is captured together on the first run for a state pointer, so
+// that no later step count pays for a capture.
+int run_graphs(nlse_ctx* c, void* psi, int64_t n, cudaStream_t st) {
+    if (c->graph_psi != psi || !c->graphs[0]) {
+        drop_graph(c);
+        for (int j = 0; j < kGraphLevels; ++j) {
+            int rc = capture_steps(c, psi, j);
+            if (rc) {
+                drop_graph(c);
+                return rc;
+            }
+        }
+        c->graph_psi = psi;
+    }
+    for (int64_t i = 0; i < n / kGraphSteps; ++i)
+        NLSE_CUDA(cudaGraphLaunch(c->graphs[kGraphLevels - 1], st), "graph launch");
+    for (int j = kGraphLevels - 2; j >= 0; --j)
+        if ((n >> j) & 1) NLSE_CUDA(cudaGraphLaunch(c->graphs[j], st), "graph launch");
     return NLSE_OK;
 }
 
@@ -398,7 +540,11 @@ void release(nlse_ctx* c) {
     cudaFree(c->adj_buf);
     cudaFree(c->host_state);
     cudaFree(c->inv_table);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto& g : c->graphs)
+        if (g) cudaGraphExecDestroy(g);
+    cudaFree(c->check_tab);
+    cudaFree(c->check_partials);
+    cudaFree(c->check_bounds);
     nlse::batch2d_destroy(c->batch);
     delete[] c->bparams;
     delete[] c->boff;
@@ -408,7 +554,7 @@ void release(nlse_ctx* c) {
     cudaFree(c->acc);
     cudaFree(c->lo);
     for (int i = 0; i < 4; ++i) cudaFree(c->plain[i]);
-    cudaFree(c->flag);
+    cudaFree(c->status);
     cudaFree(c->partials);
     cudaFree(c->red_out);
     cudaFreeHost(c->host_out);
@@ -459,8 +605,6 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
         TRY(cudaMalloc(&c->lo, c->cbytes), "allocating compensated part");
         TRY(cudaMemset(c->lo, 0, c->cbytes), "zeroing compensated part");
     }
-    TRY(cudaMalloc((void**)&c->flag, sizeof(int)), "allocating flag");
-    TRY(cudaMemset(c->flag, 0, sizeof(int)), "zeroing flag");
     {
         nlse::InvLaunch L;
         L.dim = p->dim;
@@ -471,6 +615,10 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
     TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth), "allocating result");
     TRY(cudaMallocHost((void**)&c->host_out, sizeof(double) * nlse::kPartialWidth), "allocating pinned result");
 #undef TRY
+    if ((rc = setup_entry_check(c))) {
+        release(c);
+        return rc;
+    }
     *out = c;
     return NLSE_OK;
 }
@@ -534,8 +682,6 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
         TRY(cudaMalloc(&c->lo, c->cbytes), "allocating compensated part");
         TRY(cudaMemset(c->lo, 0, c->cbytes), "zeroing compensated part");
     }
-    TRY(cudaMalloc((void**)&c->flag, sizeof(int)), "allocating flag");
-    TRY(cudaMemset(c->flag, 0, sizeof(int)), "zeroing flag");
     c->nblocks = c->brow[count];
     TRY(cudaMalloc((void**)&c->partials, sizeof(double) * nlse::kPartialWidth * c->nblocks), "allocating partials");
     TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth * count), "allocating results");
@@ -557,6 +703,10 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
     }
     TRY(nlse::batch2d_create(count, p, V_dev, c->Y[0], c->Y[1], c->acc, c->lo, &c->batch), "building the batch plan");
 #undef TRY
+    if ((rc = setup_entry_check(c))) {
+        release(c);
+        return rc;
+    }
     *out = c;
     return NLSE_OK;
 }
@@ -681,9 +831,15 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     if (c->stack > 1)
         NLSE_CUDA(nlse::launch_stack_sum(gvs, c->stack, vpts, static_cast<double*>(dV), st), "summing dV over the stack");
     double h_loss = 0.0;
+    nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);
     NLSE_CUDA(cudaMemcpyAsync(&h_loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, st), "loss copy");
+    NLSE_CUDA(cudaMemcpyAsync(hs, c->status, sizeof(nlse::StatusBlock), cudaMemcpyDeviceToHost, st), "status copy");
     NLSE_CUDA(cudaStreamSynchronize(st), "adjoint synchronise");
     c->state_psi = nullptr;          // the compensated part no longer belongs to any caller state
+    // A refusal of an earlier nlse_run that nobody read kept the stage-4
+    // kernels from stepping: the forward pass did not run.
+    const nlse::StatusBlock sb = *hs;
+    if (sb.bits & nlse::kStatusRefused) return report_status(c, sb, st);
     if (loss) *loss = h_loss;
     return NLSE_OK;
 }
@@ -795,63 +951,14 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
     int rc = bind_state(c, psi, st);
     if (rc) return rc;
     if (nsteps == 0) return NLSE_OK;
-    if (!(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK)) {
-        if (c->batch) {
-            double* dtmax = new (std::nothrow) double[c->count];
-            if (!dtmax) return fail(NLSE_ENOMEM, "host allocation failed");
-            rc = invariants_batch_impl(c, psi, nullptr, nullptr, dtmax, st);
-            int worst = -1;
-            for (int i = 0; rc == NLSE_OK && i < c->count; ++i)
-                if (c->bparams[i].dt > dtmax[i]) { worst = i; break; }
-            double b = worst >= 0 ? dtmax[worst] : 0.0;
-            delete[] dtmax;
-            if (rc) return rc;
-            if (worst >= 0)
-                return fail(NLSE_EUNSTABLE, "instance %d: dt = %g exceeds the bound %g of Eq. (kdfull)", worst,
-                            c->bparams[worst].dt, b);
-        } else {
-            double dtmax = 0;
-            rc = invariants_impl(c, psi, nullptr, nullptr, &dtmax, st);
-            if (rc) return rc;
-            if (c->p.dt > dtmax)
-                return fail(NLSE_EUNSTABLE, "dt = %g exceeds the bound %g of Eq. (kdfull)", c->p.dt, dtmax);
-        }
-    }
+    if (!(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK) && (rc = enqueue_entry_check(c, psi, st))) return rc;
     if (resident_1d(c)) return enqueue_resident(c, psi, nsteps, st);
-    if (nsteps >= kGraphSteps && (!c->graph || c->graph_psi != psi)) {
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
-        }
-        cudaStream_t cs;
-        NLSE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) {
-            cudaStreamDestroy(cs);
-            return cuda_fail(e, "begin capture");
-        }
-        rc = enqueue_steps(c, psi, kGraphSteps, cs);
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(cs, &g);
-        cudaStreamDestroy(cs);
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&c->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            c->graph = nullptr;
-            return cuda_fail(e, "graph instantiate");
-        }
-        c->graph_psi = psi;
-    }
-    int64_t done = 0;
-    if (c->graph && c->graph_psi == psi)
-        for (; done + kGraphSteps <= nsteps; done += kGraphSteps)
-            NLSE_CUDA(cudaGraphLaunch(c->graph, st), "graph launch");
-    return enqueue_steps(c, psi, nsteps - done, st);
+    // Inside a caller's stream capture the steps are enqueued as they are
+    // (they become part of the caller's graph); otherwise cached graphs.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NLSE_CUDA(cudaStreamIsCapturing(st, &cap), "stream capture query");
+    if (cap != cudaStreamCaptureStatusNone) return enqueue_steps(c, psi, nsteps, st);
+    return run_graphs(c, psi, nsteps, st);
 }
 
 int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
@@ -864,9 +971,12 @@ int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
     if (c->state_psi == c->host_state) c->state_psi = nullptr;    // a new state: no compensated part yet
     int rc = nlse_run(c, c->host_state, nsteps, stream);
     if (rc) return rc;
+    nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);
+    NLSE_CUDA(cudaMemcpyAsync(hs, c->status, sizeof(nlse::StatusBlock), cudaMemcpyDeviceToHost, st), "status copy");
     NLSE_CUDA(cudaMemcpyAsync(psi_host, c->host_state, c->cbytes, cudaMemcpyDeviceToHost, st), "state copy out");
     NLSE_CUDA(cudaStreamSynchronize(st), "synchronise");
-    return NLSE_OK;
+    const nlse::StatusBlock s = *hs;
+    return report_status(c, s, st);
 }
 
 int nlse_invariants(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
@@ -887,16 +997,11 @@ int nlse_check(nlse_ctx* c, void* stream) {
     g_err[0] = 0;
     if (!c) return fail(NLSE_EINVAL, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    int h = 0;
-    NLSE_CUDA(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
-    NLSE_CUDA(cudaStreamSynchronize(st), "flag synchronise");
-    if (h) {
-        NLSE_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), st), "flag reset");
-        NLSE_CUDA(cudaStreamSynchronize(st), "flag synchronise");
-        if (h & 2) return fail(NLSE_ETIMEOUT, "a bounded device-side wait gave up (a data transfer never completed)");
-        return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
-    }
-    return NLSE_OK;
+    nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);
+    NLSE_CUDA(cudaMemcpyAsync(hs, c->status, sizeof(nlse::StatusBlock), cudaMemcpyDeviceToHost, st), "status copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "status synchronise");
+    const nlse::StatusBlock s = *hs;
+    return report_status(c, s, st);
 }
 
 }  // extern "C"

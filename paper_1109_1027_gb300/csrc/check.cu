@@ -1,0 +1,251 @@
+// check.cu -- the entry check of nlse_run on the device: the time-step bound
+// of Eq. (kdfull) of every instance is evaluated from its state and compared
+// with its dt, and the verdict is left in the context's status block, so that
+// nlse_run never waits for the host.  When the check refuses (dt above the
+// bound, or a NaN or Inf in the state), the status block carries the refusal
+// and every RK4 stage-4 kernel leaves the state as it is until nlse_check
+// reads and clears it.
+//
+// Only the extremes of u_i = s|Psi_i|^2 - V_i are needed (L_i = (h^2/a) u_i,
+// and rounding is monotone, so max_i fl(h^2/a u_i) = fl(h^2/a max_i u_i)); the
+// boundary term B of Table t:bc2 is 0 for the boundary rules this check
+// serves (Dirichlet, periodic, Laplacian-zero; MSD contexts take the full
+// invariants path).  The extremes are FP64 values.  For a complex64 state
+// (hi + compensated lo) the FP64 evaluation of every point would make this an
+// FP64-rate-bound pass on a GPU whose FP64 rate is 1/64 of its FP32 rate, so
+// each point is first evaluated in FP32 together with a rigorous bound E_i on
+// |u32_i - u64_i|; the FP64 value is computed only for points that can still
+// be an extreme of their thread's points (u32_i + E_i >= the largest
+// u32_j - E_j seen, and the mirror rule for the minimum).  The result is the
+// exact FP64 extreme, at the cost of a memory pass.
+#include <cfloat>
+#include <climits>
+
+#include "nlse_device.cuh"
+#include "stability.cuh"
+
+namespace nlse {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+struct Ext {
+    double umin, umax, bad;
+};
+
+__device__ __forceinline__ Ext ext_identity() { return {DBL_MAX, -DBL_MAX, 0.0}; }
+
+__device__ __forceinline__ void ext_combine(Ext& a, const Ext& b) {
+    a.umin = fmin(a.umin, b.umin);
+    a.umax = fmax(a.umax, b.umax);
+    a.bad += b.bad;
+}
+
+__device__ Ext ext_block_reduce(Ext a) {
+    __shared__ Ext warp_tot[kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+        Ext b{__shfl_down_sync(0xffffffffu, a.umin, off), __shfl_down_sync(0xffffffffu, a.umax, off),
+              __shfl_down_sync(0xffffffffu, a.bad, off)};
+        ext_combine(a, b);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        a = lane < kThreads / 32 ? warp_tot[lane] : ext_identity();
+        for (int off = 16; off > 0; off >>= 1) {
+            Ext b{__shfl_down_sync(0xffffffffu, a.umin, off), __shfl_down_sync(0xffffffffu, a.umax, off),
+                  __shfl_down_sync(0xffffffffu, a.bad, off)};
+            ext_combine(a, b);
+        }
+    }
+    return a;
+}
+
+// Per-thread state of the filtered FP64 extremes (complex64 states).
+struct Filter {
+    Ext e;
+    float lb_max;     // largest u32_j - E_j seen: a lower bound of the thread's FP64 maximum
+    float ub_min;     // smallest u32_j + E_j seen: an upper bound of the thread's FP64 minimum
+};
+
+// u = s|Psi|^2 - V of one complex64 point (hi + lo) in FP64, with explicit
+// roundings (the same expression nlse_invariants evaluates pointwise).
+__device__ __forceinline__ double u_fp64(float2 h, float2 l, float v, double s) {
+    const double x = __dadd_rn((double)h.x, (double)l.x), y = __dadd_rn((double)h.y, (double)l.y);
+    return __fma_rn(s, __fma_rn(x, x, __dmul_rn(y, y)), -(double)v);
+}
+
+// One complex64 point.  Error bound of the FP32 evaluation u32 of u (with
+// rho_hi = hi.x^2 + hi.y^2): the compensated part changes rho by
+// |2 hi.x lo.x + lo.x^2 + 2 hi.y lo.y + lo.y^2| <= t = (2|hi.x| + |lo.x|)|lo.x|
+// + (2|hi.y| + |lo.y|)|lo.y|; the two FP32 roundings of rho32 add 2^-23 rho,
+// the FMA of u32 2^-24 |u32|, and s rounded to FP32 2^-24 |s| rho.
+// E = 2^-18 (|u32| + |s| rho32) + 2 |s| t + (|s| + 1) 2^-120 covers these
+// with a margin of at least 2 and absorbs FP32 underflow; an overflowed u32
+// (or an infinite E) is always evaluated in FP64.  A non-finite input point
+// counts as bad (its FP64 value would be non-finite too).
+__device__ __forceinline__ void point32(Filter& f, float2 h, float2 l, float v, float s32, float abs_s,
+                                        double s) {
+    if (!(isfinite(h.x) && isfinite(h.y) && isfinite(l.x) && isfinite(l.y))) {
+        f.e.bad += 1.0;
+        return;
+    }
+    const float rho = __fmaf_rn(h.x, h.x, __fmul_rn(h.y, h.y));
+    const float u = __fmaf_rn(s32, rho, -v);
+    const float ax = fabsf(l.x), ay = fabsf(l.y);
+    const float t = __fmaf_rn(__fmaf_rn(2.0f, fabsf(h.x), ax), ax, __fmul_rn(__fmaf_rn(2.0f, fabsf(h.y), ay), ay));
+    const float E = __fmaf_rn(2.0f * abs_s, t,
+                              __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
+    const bool cmax = !(u + E < f.lb_max);     // also true when u or E is infinite or NaN
+    const bool cmin = !(u - E > f.ub_min);
+    if (cmax || cmin) {
+        const double u64 = u_fp64(h, l, v, s);
+        if (cmax) {
+            f.e.umax = fmax(f.e.umax, u64);
+            f.lb_max = fmaxf(f.lb_max, u - E);
+        }
+        if (cmin) {
+            f.e.umin = fmin(f.e.umin, u64);
+            f.ub_min = fminf(f.ub_min, u + E);
+        }
+    }
+}
+
+// One complex128 point: FP64 throughout.
+__device__ __forceinline__ void point64(Ext& e, double2 p, double v, double s) {
+    const double rho = __fma_rn(p.x, p.x, __dmul_rn(p.y, p.y));
+    if (!isfinite(rho)) {
+        e.bad += 1.0;
+        return;
+    }
+    const double u = __fma_rn(s, rho, -v);
+    e.umin = fmin(e.umin, u);
+    e.umax = fmax(e.umax, u);
+}
+
+// Index of the last entry whose first row is <= b.
+__device__ __forceinline__ int entry_of(const CheckEntry* tab, int count, int b) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (tab[mid].row0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block b covers one contiguous chunk of the points of one entry (the entry
+// whose rows [row0, row1) contain b) and writes one row of partials.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __restrict__ tab, int count,
+                                                           const cplx<R>* __restrict__ psi,
+                                                           const cplx<R>* __restrict__ lo, const R* __restrict__ V,
+                                                           double* __restrict__ partials) {
+    const int b = blockIdx.x;
+    const CheckEntry e = tab[entry_of(tab, count, b)];
+    const int64_t nblk = e.row1 - e.row0;
+    const int64_t per = (e.npts + nblk - 1) / nblk;
+    const int64_t p0 = (b - e.row0) * per, p1 = min(e.npts, p0 + per);
+    const cplx<R>* ps = psi + e.psi_off;
+    const cplx<R>* ls = lo ? lo + e.psi_off : nullptr;
+    const R* vs = V + e.v_off;
+    Ext acc = ext_identity();
+    if constexpr (sizeof(R) == 4) {
+        Filter f{ext_identity(), -FLT_MAX, FLT_MAX};
+        const float s32 = (float)e.s, abs_s = fabsf(s32);
+        const float2 zero = make_float2(0.f, 0.f);
+        int64_t p = p0 + threadIdx.x;
+        for (; p + (kUnroll - 1) * kThreads < p1; p += kUnroll * kThreads) {
+            float2 h[kUnroll], l[kUnroll];
+            float v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                h[u] = ps[p + u * kThreads];
+                l[u] = ls ? ls[p + u * kThreads] : zero;
+                v[u] = vs[p + u * kThreads];
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) point32(f, h[u], l[u], v[u], s32, abs_s, e.s);
+        }
+        for (; p < p1; p += kThreads) point32(f, ps[p], ls ? ls[p] : zero, vs[p], s32, abs_s, e.s);
+        acc = f.e;
+    } else {
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) point64(acc, ps[p], vs[p], e.s);
+    }
+    acc = ext_block_reduce(acc);
+    if (threadIdx.x == 0) {
+        double* row = partials + (int64_t)b * 3;
+        row[0] = acc.umin; row[1] = acc.umax; row[2] = acc.bad;
+    }
+}
+
+// One block per entry: its rows in a fixed order, then the bound of
+// Eq. (kdfull) against the entry's dt.  A refusal sets its status bit; the
+// smallest refused entry index is kept for the message, and every entry's
+// bound is written to bounds[].
+__global__ void __launch_bounds__(kThreads) check_final(const CheckEntry* __restrict__ tab,
+                                                         const double* __restrict__ partials,
+                                                         double* __restrict__ bounds, StatusBlock* status) {
+    const CheckEntry e = tab[blockIdx.x];
+    Ext a = ext_identity();
+    for (int r = e.row0 + threadIdx.x; r < e.row1; r += kThreads) {
+        const double* row = partials + (int64_t)r * 3;
+        ext_combine(a, Ext{row[0], row[1], row[2]});
+    }
+    a = ext_block_reduce(a);
+    if (threadIdx.x != 0) return;
+    const double bound = dt_bound(e.dim, e.h, e.a, e.h2a * a.umin, e.h2a * a.umax, 0.0);
+    bounds[blockIdx.x] = bound;
+    int bit = 0;
+    if (a.bad != 0.0) bit = kStatusEntryNonFinite;
+    else if (!(e.dt <= bound)) bit = kStatusUnstable;
+    if (bit) {
+        atomicOr(&status->bits, bit);
+        atomicMin(&status->inst, (int)blockIdx.x);
+    }
+}
+
+// The same verdict from the reduced row of the full invariants reduction
+// (mass, energy, min L, max L, max |B|, non-finite count), for MSD contexts.
+__global__ void invariants_gate(const double* __restrict__ r, int dim, double h, double a, double dt,
+                                double* __restrict__ bound_out, StatusBlock* status) {
+    const double bound = dt_bound(dim, h, a, r[2], r[3], r[4]);
+    *bound_out = bound;
+    int bit = 0;
+    if (r[5] != 0.0 || !isfinite(r[0])) bit = kStatusEntryNonFinite;
+    else if (!(dt <= bound)) bit = kStatusUnstable;
+    if (bit) {
+        atomicOr(&status->bits, bit);
+        atomicMin(&status->inst, 0);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_invariants_gate(const double* reduced, int dim, double h, double a, double dt, double* bound_out,
+                                   StatusBlock* status, cudaStream_t st) {
+    invariants_gate<<<1, 1, 0, st>>>(reduced, dim, h, a, dt, bound_out, status);
+    return cudaGetLastError();
+}
+
+int check_rows(int64_t npts) {
+    const int64_t want = (npts + kPointsPerCheckRow - 1) / kPointsPerCheckRow;
+    return (int)(want < 1 ? 1 : (want > kMaxCheckRowsPerEntry ? kMaxCheckRowsPerEntry : want));
+}
+
+cudaError_t launch_entry_check(const CheckLaunch& C, cudaStream_t st) {
+    if (C.prec == 0)
+        check_partial<float><<<C.nrows, kThreads, 0, st>>>(C.table, C.count, (const float2*)C.psi,
+                                                           (const float2*)C.lo, (const float*)C.V, C.partials);
+    else
+        check_partial<double><<<C.nrows, kThreads, 0, st>>>(C.table, C.count, (const double2*)C.psi,
+                                                            (const double2*)C.lo, (const double*)C.V, C.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    check_final<<<C.count, kThreads, 0, st>>>(C.table, C.partials, C.bounds, C.status);
+    return cudaGetLastError();
+}
+
+}  // namespace nlse

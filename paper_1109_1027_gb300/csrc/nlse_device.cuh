@@ -32,6 +32,15 @@ template <typename C> __device__ __forceinline__ decltype(C::x) cabs2(C a) { ret
 // i * a
 template <typename C> __device__ __forceinline__ C ctimesi(C a) { return cmake<C>(-a.y, a.x); }
 
+// Whether nlse_run's entry check refused the steps now being run (a refusal
+// bit in the context's status block, set on the device before the steps were
+// enqueued behind it and cleared only by nlse_check): the stage-4 kernels then
+// leave the state as it is.  Read once per CTA; no kernel of a step changes
+// these bits.
+__device__ __forceinline__ bool refused(const int* flag) {
+    return (*(const volatile int*)flag & kStatusRefused) != 0;
+}
+
 // Row within its stacked instance of grid row r >= 0 (instances of rows1 rows;
 // without a stack rows1 is the grid's row count and r is returned undivided).
 __device__ __forceinline__ int inst_row(int r, int rows1) { return r < rows1 ? r : r % rows1; }

@@ -10,6 +10,19 @@
 
 namespace nlse {
 
+// The context's status block.  bits collects what the device reports to
+// nlse_check; the stage-4 kernels (the only ones that write the state) leave
+// the state unchanged while a refusal bit of nlse_run's entry check is set.
+constexpr int kStatusNonFinite = 1;        // an RK4 step wrote a NaN or Inf
+constexpr int kStatusTimeout = 2;          // a bounded device-side wait gave up
+constexpr int kStatusUnstable = 4;         // entry check: dt above the bound of Eq. (kdfull)
+constexpr int kStatusEntryNonFinite = 8;   // entry check: the state held a NaN or Inf
+constexpr int kStatusRefused = kStatusUnstable | kStatusEntryNonFinite;
+struct StatusBlock {
+    int bits;
+    int inst;               // smallest instance the entry check refused (0x7f7f7f7f: none)
+};
+
 // One launch of a fused RK4 stage (stage 1..4) or of the standalone
 // Laplacian (stage 0).  Pointers are device pointers; their element types
 // follow prec (complex64 / float or complex128 / double).
@@ -27,8 +40,7 @@ struct StageLaunch {
     void* yout;             // next stage input
     void* lap_out;          // stage 0 output
     const void* V;
-    int* flag;              // status bits: 1 = non-finite result (stage 4),
-                            // 2 = a bounded device-side wait timed out
+    int* flag;              // status bits of the context's StatusBlock (kStatus*)
     int tile_rows;          // 2D TMA kernel: rows per CTA (8, 16, 32)
     int tile_planes;        // 3D TMA kernel: z planes per CTA (32, 64, 128)
     int keep_v;             // TMA kernels: load V with an L2 evict-last hint (V small enough
@@ -175,6 +187,41 @@ struct InvBatchLaunch {
     double* out;            // count x kPartialWidth
 };
 cudaError_t launch_invariants_batch(const InvBatchLaunch& B, cudaStream_t st);
+
+// nlse_run's entry check on the device (check.cu): one entry per instance
+// (a single grid: one; a stack: one per stacked instance; a batch: one per
+// instance), each with its own points, dt and coefficients.
+struct CheckEntry {
+    int64_t psi_off;        // first element of the instance in Psi (and lo)
+    int64_t v_off;          // first element of its V
+    int64_t npts;
+    double h, a, s, dt;
+    double h2a;             // h^2 / a
+    int dim;
+    int row0, row1;         // its rows of partials
+};
+constexpr int64_t kPointsPerCheckRow = 16384;
+constexpr int kMaxCheckRowsPerEntry = 2048;
+// Rows of partials (blocks of the check) for an instance of npts points.
+int check_rows(int64_t npts);
+struct CheckLaunch {
+    const CheckEntry* table;    // device, count entries, row0 ascending
+    int count, nrows, prec;
+    const void* psi;
+    const void* lo;             // FP32 compensated part or nullptr
+    const void* V;
+    double* partials;           // nrows x 3
+    double* bounds;             // count: each instance's bound of Eq. (kdfull)
+    StatusBlock* status;
+};
+// Enqueues the check: partial extremes, then per instance the bound and the
+// refusal bits.  No host synchronisation.
+cudaError_t launch_entry_check(const CheckLaunch& C, cudaStream_t st);
+// The same verdict from the reduced row (kPartialWidth doubles, on the
+// device) of launch_invariants without energy: for MSD contexts, whose bound
+// needs the boundary term.
+cudaError_t launch_invariants_gate(const double* reduced, int dim, double h, double a, double dt, double* bound_out,
+                                   StatusBlock* status, cudaStream_t st);
 
 // Records msg as the calling thread's nlse_last_error() and returns code.
 int report_error(int code, const char* msg);

@@ -24,6 +24,7 @@
 
 #include "nlse.h"
 #include "nlse_internal.h"
+#include "stability.cuh"
 
 namespace {
 
@@ -129,15 +130,7 @@ extern "C" int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev
     const double h = p->h, hd = std::pow(h, (double)p->dim);
     if (mass) *mass = hd * r[0];
     if (energy) *energy = hd * r[1];
-    if (dt_max) {
-        // Extreme entries of G (Table t:sumresults) in units of 1/12; |L - g|
-        // is convex in L, so its maximum is at an extreme of L and of G.
-        const double gmax = 64.0 * p->dim / 12.0, gmin = -4.0 * p->dim / 12.0;
-        double worst = std::fmax(std::fmax(std::fabs(r[3] - gmin), std::fabs(r[2] - gmax)),
-                                 std::fmax(std::fabs(r[2] - gmin), std::fabs(r[3] - gmax)));
-        worst = std::fmax(worst, r[4]);
-        *dt_max = std::sqrt(8.0) * h * h / (p->a * worst);
-    }
+    if (dt_max) *dt_max = nlse::dt_bound(p->dim, h, p->a, r[2], r[3], r[4]);
     if (r[5] != 0.0 || !std::isfinite(r[0]))
         return nlse::report_error(NLSE_ENONFINITE, "state holds non-finite values");
     return NLSE_OK;

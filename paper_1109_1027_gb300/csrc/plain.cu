@@ -160,7 +160,7 @@ template <typename R>
 __global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, cplx<R>* lo, R w, const cplx<R>* a,
                                                   const cplx<R>* b, int64_t n, int* flag) {
     int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
-    if (p >= n) return;
+    if (p >= n || refused(flag)) return;
     cplx<R> v;
     if constexpr (sizeof(R) == 4) {
         if (lo) {

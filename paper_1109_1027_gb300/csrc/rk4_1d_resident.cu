@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
                                                                 Coef<R> c, Weights<R> w, int n, int m,
                                                                 int64_t nsteps, int* flag) {
     using C = cplx<R>;
+    if (refused(flag)) return;                             // every CTA of the cluster, before any cluster barrier
     cg::cluster_group cl = cg::this_cluster();
     const int CS = (int)cl.num_blocks();
     const int r = (int)cl.block_rank();

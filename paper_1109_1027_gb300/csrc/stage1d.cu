@@ -30,6 +30,9 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
     C* sF = sD + ND;                          // x0-1 .. x0+T
     const int x0 = blockIdx.x * T;
     const int tid = threadIdx.x;
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;
+    }
 
     for (int j = tid; j < NP; j += NT) {
         int g = x0 - 3 + j;

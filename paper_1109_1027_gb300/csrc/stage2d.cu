@@ -42,6 +42,9 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
     const int x0 = blockIdx.x * TX;
     const int y0 = blockIdx.y * TY;
     const int tid = threadIdx.x;
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;
+    }
 
     // Stage input tile with halo; points outside the grid read as zero (never used).
     for (int i = tid; i < PX * PY; i += NT) {

@@ -153,6 +153,9 @@ rk4_2d_fused_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_const
                     const FusedIO io, const Coef<float> c, const int nx, const int ny, const int ty,
                     const int dir) {
     using L = Lay<PAIR>;
+    if constexpr (PAIR == 1) {
+        if (refused(io.flag)) return;              // stages 3+4 write the state; before any barrier or copy
+    }
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     const uint32_t sbase = smem_u32(smem);

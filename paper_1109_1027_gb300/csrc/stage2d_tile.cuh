@@ -422,6 +422,9 @@ __device__ __forceinline__ void stage2d_tile(const CUtensorMap* m_in, const CUte
                                              const CUtensorMap* m_acc, const CUtensorMap* m_lo,
                                              const StageIO<R>& io, const Coef<R>& c, const int nx, const int ny,
                                              const int x0, const int y0, const int dir) {
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;              // before any barrier or copy
+    }
     if constexpr (sizeof(R) == 4) {
         stage2d_walk<R, LP, STAGE, NT, TY, false>(m_in, m_in2, m_V, m_psi, m_acc, m_lo, io, c, nx, ny, x0, y0, dir);
     } else {

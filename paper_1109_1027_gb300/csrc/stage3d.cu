@@ -40,6 +40,9 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     const int z1 = min(z0 + TZ, nz);
     const int tid = threadIdx.x;
     const int64_t plane = (int64_t)nx * ny;
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;
+    }
 
     auto load_plane = [&](int gz) {
         C* dst = sP + pslot(gz) * PP;
@@ -159,6 +162,9 @@ stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     const int z1 = min(z0 + TZ, nz);
     const int tid = threadIdx.x;
     const int64_t plane = (int64_t)nx * ny;
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;
+    }
 
     auto load_plane = [&](int gz) {
         C* dst = sP + pslot(gz) * PP;

@@ -101,6 +101,9 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
 
+    if constexpr (STAGE == 4) {
+        if (refused(io.flag)) return;              // before any barrier or copy
+    }
     const int t = threadIdx.x;
     const int tx = t % TXP, ty = t / TXP;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;

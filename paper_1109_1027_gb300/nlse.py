@@ -397,6 +397,9 @@ class BatchSolver:
     def get_tiling(self, key: int) -> int:
         return nlse_get_tiling(self.ctx, key)
 
+    def reset_compensation(self):
+        nlse_reset_compensation(self.ctx)
+
     def check(self):
         nlse_check(self.ctx)
 

@@ -5,7 +5,8 @@ takes a few warm-up steps, then a few more, and exits.
     python -m paper_1109_1027_gb300.profile_case --workload ring3d --n 256 --steps 3
 
 Workloads: vortex2d (2D dark vortex), ring3d (3D vortex ring), soliton1d
-(1D bright soliton), batch2d (512 uneven 2D instances).  FP32 unless --fp64.
+(1D bright soliton), batch2d (the first --count of the 512 uneven 2D
+instances).  FP32 unless --fp64.
 --fuse runs the 2D steps as two launches of two RK4 stages each.
 """
 from __future__ import annotations
@@ -22,6 +23,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="vortex2d", choices=["vortex2d", "ring3d", "soliton1d", "batch2d"])
     ap.add_argument("--n", type=int, default=0, help="points per axis (default: the workload's)")
+    ap.add_argument("--count", type=int, default=512, help="batch2d: instances (the first ones of the batch)")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64", action="store_true")
@@ -31,7 +33,7 @@ def main():
     rdt, cdt = (torch.float64, torch.complex128) if args.fp64 else (torch.float32, torch.complex64)
     dev = "cuda:0"
     if args.workload == "batch2d":
-        insts = wl.gaussian_batch_2d(count=512, steps=0)
+        insts = wl.gaussian_batch_2d(count=512, steps=0, only=set(range(args.count)))
         V = nlse.BatchSolver.pack([q.V for q in insts], rdt, dev)
         x = nlse.BatchSolver.pack([q.psi0 for q in insts], cdt, dev)
         shapes = [q.shape for q in insts]

@@ -113,10 +113,12 @@ def vortex_ring_3d(n: int = 512, lo: float = -30.0, hi: float = 30.0, seed: int 
 
 
 def gaussian_batch_2d(count: int = 512, seed: int = 4, sides=range(64, 1025, 64),
-                      lo: float = -32.0, hi: float = 32.0, steps: int = 5000):
+                      lo: float = -32.0, hi: float = 32.0, steps: int = 5000, only=None):
     """Independent 2D problems of uneven size: side ~ U(sides), a ~ U[0.3, 1],
     s = +-1, V = w^2 r^2 with w ~ U[0, 0.1], psi0 a Gaussian of width U[2, 8]
-    with a random phase gradient (wavenumbers U[-1, 1])."""
+    with a random phase gradient (wavenumbers U[-1, 1]).  With ``only`` (a
+    set of indices) just those instances are built -- the same ones, since
+    every instance's draws are still taken in order -- and returned in order."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sides = np.asarray(list(sides))
     out = []
@@ -127,6 +129,8 @@ def gaussian_batch_2d(count: int = 512, seed: int = 4, sides=range(64, 1025, 64)
         w = float(rng.uniform(0.0, 0.1))
         width = float(rng.uniform(2.0, 8.0))
         kx, ky = rng.uniform(-1.0, 1.0, 2)
+        if only is not None and i not in only:
+            continue
         x, y = mesh((n, n), lo, hi)
         V = w * w * (x * x + y * y)
         psi0 = np.exp(-(x * x + y * y) / (2.0 * width * width)) * np.exp(1j * (kx * x + ky * y))

@@ -119,9 +119,12 @@ def test_batch_refuses_an_unstable_instance():
     bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
                           [q["a"] for q in insts], [q["s"] for q in insts], prec="fp64")
     psi = nlse.BatchSolver.pack([q["psi"] for q in insts], torch.complex128, DEV)
+    psi0 = psi.clone()
+    bs.run(psi, 5)                                  # the check runs on the device
     with pytest.raises(nlse.NLSEError) as ei:
-        bs.run(psi, 5)
+        bs.check()
     assert ei.value.code == nlse.EUNSTABLE and "instance 1" in str(ei.value)
+    assert torch.equal(psi, psi0)                   # no instance was stepped
 
 
 def test_batch_workload_sample_equals_single_grid():

@@ -15,8 +15,8 @@ SCRIPT = r'''
 import sys
 sys.path.insert(0, {root!r})
 import oracle
-oracle._lib = None
-oracle.build = lambda: {lib!r}
+oracle._libs.clear()
+oracle.build = lambda threaded=False: {lib!r}
 from paper_1109_1027_gb300 import workloads as wl
 for shape in [(3,), (4,), (37,), (3, 3), (17, 12), (3, 3, 3), (6, 7, 8)]:
     psi = wl.random_field(shape, seed=1) + 2.5

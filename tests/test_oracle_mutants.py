@@ -43,8 +43,16 @@ MUTANTS = [
      "return P->s * c_abs2(psi) + V;",
      PINS, "general_a"),
     ("RK4: K_2 weighted 1 instead of 2",
-     C, "for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* 4 */",
-     "for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(1.0, get(Ktmp, p))));    /* 4 */",
+     C, "    rhs(P, ptmp, V, Ktmp, work);                                              /* K_tmp = F(psi_tmp) */\n"
+        "#pragma omp parallel for schedule(static)\n"
+        "    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(2.0, get(Ktmp, p))));    /* K_tot += 2 K_tmp */\n"
+        "#pragma omp parallel for schedule(static)\n"
+        "    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktmp, p))));",
+     "    rhs(P, ptmp, V, Ktmp, work);                                              /* K_tmp = F(psi_tmp) */\n"
+        "#pragma omp parallel for schedule(static)\n"
+        "    for (p = 0; p < N; ++p) put(Ktot, p, c_add(get(Ktot, p), c_scale(1.0, get(Ktmp, p))));    /* K_tot += 2 K_tmp */\n"
+        "#pragma omp parallel for schedule(static)\n"
+        "    for (p = 0; p < N; ++p) put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktmp, p))));",
      PINS, "stability_polynomial"),
     ("MSD inward point one too far on the upper side",
      C, "if (v > n - 2) return n - 2;",
@@ -71,8 +79,8 @@ MUTANTS = [
      "rest = c_add(rest, d);",
      PINS, "multi_storage_boundary_split"),
     ("RK4: second stage input at k instead of k/2",
-     C, "put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktot, p))));  /* 2 */",
-     "put(ptmp, p, c_add(get(psi, p), c_scale(k, get(Ktot, p))));  /* 2 */",
+     C, "put(ptmp, p, c_add(get(psi, p), c_scale(k / 2.0, get(Ktot, p))));  /* psi_tmp */",
+     "put(ptmp, p, c_add(get(psi, p), c_scale(k, get(Ktot, p))));  /* psi_tmp */",
      PINS, "stability_polynomial"),
     ("RK4: final weight k/6 -> k/3",
      C, "put(psi, p, c_add(get(psi, p), c_scale(k / 6.0, c_add(get(Ktot, p), get(Ktmp, p)))));",

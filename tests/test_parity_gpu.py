@@ -231,8 +231,8 @@ def test_unfused_schedule_matches_oracle(shape, lap):
 @pytest.mark.parametrize("shape,prec", [((3001,), "fp64"), ((67, 200), "fp32"), ((67, 200), "fp64"),
                                         ((35, 18, 40), "fp32"), ((40, 131), "fp32")])
 def test_run_replays_the_same_steps(shape, prec):
-    """nlse_run (CUDA graph of 32 steps + direct remainder) is bit-identical to
-    repeated nlse_rk4_step."""
+    """nlse_run (replays of the cached 32-, 16-, ... 1-step graphs) is
+    bit-identical to repeated nlse_rk4_step."""
     psi, V = _problem(shape, 55)
     h, a, s = 0.5, 0.9, 1.0
     prob = oracle.Problem(shape, h, a, s)
@@ -497,6 +497,9 @@ def test_nonfinite_state_is_reported():
 
 
 def test_unstable_time_step_is_refused():
+    """The entry check of nlse_run runs on the device: the call itself
+    returns, the state is left as it was, and nlse_check reports the refusal
+    (then clears it)."""
     shape = (64,)
     psi, V = _problem(shape, 6)
     prob = oracle.Problem(shape, 0.25, 1.0, 0.0)
@@ -504,10 +507,12 @@ def test_unstable_time_step_is_refused():
     solver = nlse.Solver(to_dev(np.zeros(shape), "fp64"), 0.25, 1.2 * dtmax, 1.0, 0.0, prec="fp64")
     x = to_dev(psi, "fp64")
     x0 = x.clone()
+    solver.run(x, 10)
     with pytest.raises(nlse.NLSEError) as ei:
-        solver.run(x, 10)
+        solver.check()
     assert ei.value.code == nlse.EUNSTABLE
     assert torch.equal(x, x0)
+    solver.check()                                  # cleared
 
 
 def test_bad_tensors_are_rejected():
