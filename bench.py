@@ -12,7 +12,7 @@ compensated part (FP64 invariants).  The default K = 5000 is the workload's
 full length.
 
 Reported beside it: the same batch in FP64 and the FP32-vs-FP64 error per
-instance; the batch end to end through host buffers; the paper's unfused FP64
+instance; the batch end to end through host buffers; the unfused FP64
 schedule per instance; the 2D dark vortex on one 2048 x 2048 grid (FP32, FP64,
 the multi-storage form, the unfused schedule, two stages per launch); the
 gradient workload; the 3D vortex ring and the 1D soliton; and the CPU oracle,
@@ -64,15 +64,25 @@ BYTES_PER_UPDATE_FP32 = 168
 BYTES_PER_UPDATE_FP32_FUSED = 80
 # FP64 fused path (complex128 = 16 B, V double = 8 B, no low part): 56 + 88 + 88 + 72.
 BYTES_PER_UPDATE_FP64 = 304
-# The paper's unfused FP64 schedule: 4 x (D: 32 + F: 56) + axpy lines 5 x 48 + 64.
-BYTES_PER_UPDATE_PLAIN = 656
+# The unfused FP64 schedule (complex128 16 B, V 8 B): 4 slopes x (D: R Y, W D = 32;
+# step 2 + F: R Y, D, V, W K = 56) + 3 stage inputs (R Psi, K, W Y = 48) + the
+# first increment (R K, W acc = 32) + 3 increments (R acc, K, W acc = 48) + the
+# state update (R Psi, acc, W Psi = 48) = 352 + 144 + 32 + 144 + 48.
+BYTES_PER_UPDATE_PLAIN = 720
 # DRAM bytes per stage launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, the mean over the four stage launches of one RK4 step,
-# with the L2 state of back-to-back steps) for the kernel sources with the
-# given hash; a kernel changed since its capture gets null.  The batch figure
-# is the mean over the wide-tile group's four stage launches.
-NCU_TRAFFIC_GRID = {}
-NCU_TRAFFIC_BATCH = {}
+# dram__bytes_write.sum, the mean over the stage launches of consecutive RK4
+# steps, with the L2 state of back-to-back steps: --cache-control none) for the
+# kernel sources with the given hash; a kernel changed since its capture gets
+# null.  Grid: 2048^2 dark vortex, mean of 12 launches.  Batch: the 512-instance
+# batch with the default tile groups, mean of the wide-tile group's 8 launches
+# (two steps), which covered `points` of the batch's points; the bench scales
+# it to its own launches by points (the traffic is proportional to them).
+NCU_TRAFFIC_GRID = {"a4c11e7dc514": 113517099}
+NCU_TRAFFIC_BATCH = {"b03c7bbe283c": {"bytes": 8579640672, "points": 198578176}}
+# FP64 flops per grid-point update (one RK4 step) of the FP64 stage kernels,
+# from ncu instruction counts (2 x DFMA + DADD + DMUL, summed over the four
+# stage launches of one step, divided by the points), keyed as the traffic.
+FP64_FLOPS_PER_UPDATE_GRID = {}
 # Instances of the batch that the CPU oracle times (every 32nd).
 CPU_SAMPLE_STRIDE = 32
 
@@ -363,7 +373,9 @@ def run_ours(args):
     ms_step = ms / K
     value = job_rate(world, npts * K, ms * 1e-3)
     launches = 4 * groups * K + 2
-    wide_pts = sum(sh[0] * sh[1] for sh in shapes if sh[1] > narrow)
+
+    # ---- this GPU's FP64 rate, the denominator of the FP64 legs' roofline ----------
+    fp64_peak = nlse.nlse_measure_fp64_rate()
 
     # ---- the same batch in FP64 ----------------------------------------------------
     k64 = min(K, 50)
@@ -430,7 +442,8 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = BYTES_PER_UPDATE_FP32 * npts / (ms_step * 1e-3) / 1e9
     bkh = batch_kernel_hash()
-    traffic = NCU_TRAFFIC_BATCH.get(bkh)
+    cap = NCU_TRAFFIC_BATCH.get(bkh)
+    traffic = cap["bytes"] * npts / cap["points"] if cap else None      # per stage pass over the whole batch
     launch_ms = ms_step / 4
     roofline = {"bound": "hbm", "kernel": "stage2d_batch_kernel<float> (RK4 stages 1-4 over the batch, mean per "
                                           "stage; both tile groups of a stage counted as one pass)",
@@ -439,12 +452,13 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": BYTES_PER_UPDATE_FP32 / 4 * npts,
                 "launch_ms": launch_ms,
                 "traffic": traffic,
-                "traffic_what": "ncu dram__bytes_read.sum + dram__bytes_write.sum per wide-tile stage launch "
-                                f"(mean of the four stages; {wide_pts} of the {npts} points)",
-                "dram_gbs": (traffic * npts / wide_pts / (launch_ms * 1e-3) / 1e9) if traffic else None,
+                "traffic_what": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean per stage launch of the "
+                                "wide-tile group, scaled to all of the batch's points",
+                "dram_gbs": traffic / (launch_ms * 1e-3) / 1e9 if traffic else None,
+                "dram_frac": traffic / (launch_ms * 1e-3) / 1e9 / peak if traffic else None,
                 "kernel_hash": bkh}
 
-    # ---- the paper's unfused FP64 schedule, one context per instance --------------
+    # ---- the unfused FP64 schedule, one context per instance --------------
     plain = None
     if not args.quick:
         sample = list(range(0, len(insts), 8))
@@ -469,13 +483,13 @@ def run_ours(args):
             sv.close()
         plain = {"value": job_rate(world, spts * pst, msp * 1e-3), "unit": UNIT, "instances": len(sample),
                  "points": int(spts), "steps": pst,
-                 "what": "paper's unfused FP64 schedule, one context per instance, instances in sequence "
+                 "what": "unfused FP64 schedule, one context per instance, instances in sequence "
                          "(every 8th instance of the batch)"}
     b32.close()
     b64.close()
     del x32, x64, psi64, V64
 
-    grid = None if args.quick else run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks)
+    grid = None if args.quick else run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_peak)
     grad = None if args.quick else run_gradient_leg(args, dev, barrier, max_over_ranks)
     other = None if args.quick else run_other_grids(dev, barrier, max_over_ranks)
 
@@ -515,6 +529,9 @@ def run_ours(args):
                             "off: the workload's focusing instances collapse and fall below their bound)"},
             "gpu_launches": launches,
             "clocks": clocks,
+            "fp64_peak": {"value": fp64_peak / 1e12, "unit": "TFLOP/s",
+                          "how": "nlse_measure_fp64_rate: 8 independent FMA chains per thread, 8 CTAs of 256 "
+                                 "threads per SM, best of three launches (CUDA events)"},
             "batched_fp64": {"value": job_rate(world, npts * k64, ms64 * 1e-3), "unit": UNIT, "steps": k64,
                              "ms_per_step": ms64 / k64,
                              "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / k64 * 1e-3) / 1e9},
@@ -533,9 +550,9 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
-def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks):
+def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_peak):
     """The 2D dark vortex on one 2048 x 2048 grid: FP32 (autotuned), the other
-    FP32 launch schedule, FP64 fused, FP64 multi-storage, the paper's unfused
+    FP32 launch schedule, FP64 fused, FP64 multi-storage, the unfused
     FP64 schedule; FP32-vs-FP64 difference, mass and energy drift."""
     import torch
 
@@ -611,8 +628,15 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks):
     steps_taken(s64)
     s32.run(x32, K)
     steps_taken(s32)
+    fpu = FP64_FLOPS_PER_UPDATE_GRID.get(kh)
+    rate64 = npts * K / (ms64 * 1e-3)
     out["fp64"] = {"value": job_rate(world, npts * K, ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K,
-                   "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / K * 1e-3) / 1e9}
+                   "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / K * 1e-3) / 1e9,
+                   "roofline": {"bound": "alu", "kernel": "stage2d_tma_kernel<double>",
+                                "achieved": fpu * rate64 / 1e12 if fpu else None, "peak": fp64_peak / 1e12,
+                                "unit": "TFLOP/s", "frac": fpu * rate64 / fp64_peak if fpu else None,
+                                "peak_kind": "measured FP64 FMA rate (nlse_measure_fp64_rate)",
+                                "flops_per_update": fpu, "kernel_hash": kh}}
     out["fp32_vs_fp64_rel_l2_after_steps"] = float(
         torch.linalg.vector_norm(x32.to(torch.complex128) - x64) / torch.linalg.vector_norm(x64))
     m32, en32, _ = s32.invariants(x32)
@@ -638,7 +662,7 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks):
                                                                    torch.linalg.vector_norm(xs))}
     del xs, xm
 
-    # the paper's unfused FP64 schedule on the same GPU (baseline)
+    # the unfused FP64 schedule on the same GPU (baseline)
     kp = min(K, 500)
     sp = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", plain=True)
     xp = psi0.clone().contiguous()
@@ -649,7 +673,7 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks):
     out["fp64_plain"] = {"value": job_rate(world, npts * kp, msp * 1e-3), "unit": UNIT, "steps": kp,
                          "ms_per_step": msp / kp,
                          "achieved_gbs": BYTES_PER_UPDATE_PLAIN * npts / (msp / kp * 1e-3) / 1e9,
-                         "what": "paper's unfused schedule: D, K_tot, K_tmp, Psi_tmp in HBM, 14 launches/step"}
+                         "what": "unfused schedule: D and the RK4 work fields in HBM, 16 launches per step"}
     s32.close()
     s64.close()
     return out

@@ -109,11 +109,13 @@ typedef enum {
                                             the summed loss, dL/dpsi0 per instance and
                                             dL/dV summed over the instances.  Dirichlet
                                             and the fused schedule only.           */
-#define NLSE_FLAG_PLAIN_SCHEDULE 2u      /* step with the paper's unfused schedule
-                                            (Sec. 3.1): D, K_tot, K_tmp, Psi_tmp as
-                                            full device arrays, one launch per
-                                            line of Eq. (RK4); no compensation.
-                                            Dirichlet only.  A baseline.        */
+#define NLSE_FLAG_PLAIN_SCHEDULE 2u      /* step unfused, with the storage plan of
+                                            Sec. 3.1: the step-1 field D and the RK4
+                                            work fields (stage input, slope,
+                                            increment) as full device arrays, one
+                                            launch per operation (16 per step);
+                                            no compensation.  Dirichlet only.  A
+                                            baseline.                            */
 
 typedef struct {
     int dim;                /* 1, 2 or 3                                              */
@@ -193,7 +195,9 @@ int nlse_rk4_step(nlse_ctx* ctx, void* psi_dev, void* stream);
  * for this psi_dev (n = 32 q + r: q replays of the 32-step graph and one of
  * each graph whose bit is set in r).  When the stream is being captured by the
  * caller, the kernels are enqueued directly instead and become part of the
- * caller's graph.  Unless NLSE_FLAG_NO_STABILITY_CHECK is set, the steps are
+ * caller's graph; the binding of a new psi_dev (FP32: zeroing the compensated
+ * part; batches: encoding the tensor maps, which synchronises) then belongs
+ * in a call before the capture, e.g. nlse_run(ctx, psi_dev, 0, stream).  Unless NLSE_FLAG_NO_STABILITY_CHECK is set, the steps are
  * preceded on the stream by an entry check on the device: the bound of
  * Eq. (kdfull) of every instance, evaluated in FP64 from the current state,
  * against its dt.  If dt exceeds a bound (or the state holds a NaN or Inf),
@@ -282,6 +286,26 @@ int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const voi
 int nlse_adjoint(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
                  int64_t ckpt_every, void* dpsi0_dev, void* dV_dev, double* loss, void* stream);
 
+/* nlse_adjoint in two halves, for callers that need the loss before they know
+ * whether (or with what weight) they want its gradient -- an automatic-
+ * differentiation framework's forward and backward calls.  The forward half
+ * runs the nsteps RK4 steps of Eq. (RK4) from psi0 with a checkpoint every
+ * ckpt_every steps, keeps the checkpoints and dL/dPsi_T in the context's
+ * adjoint work space, writes the FP64 loss L = sum |Psi_T - target|^2 to
+ * *loss and synchronises the stream.  Arguments and support as nlse_adjoint.
+ * The paper has no counterpart (it computes no gradients). */
+int nlse_adjoint_forward(nlse_ctx* ctx, const void* psi0_dev, const void* target_dev, int64_t nsteps,
+                         int64_t ckpt_every, double* loss, void* stream);
+
+/* The reverse half: the gradients of dloss * L, dL/dpsi0 into dpsi0_dev and
+ * dL/dV (FP64) into dV_dev, as nlse_adjoint gives them, from the forward pass
+ * the context holds (the segments are recomputed from its checkpoints).  Each
+ * forward pass admits one reverse sweep: NLSE_EINVAL without a pending forward
+ * pass of nlse_adjoint_forward on this context (nlse_adjoint consumes its own).
+ * Other calls on the context in between are allowed.  Synchronises the
+ * stream.  The paper has no counterpart. */
+int nlse_adjoint_backward(nlse_ctx* ctx, double dloss, void* dpsi0_dev, void* dV_dev, void* stream);
+
 /* Tiling of the streaming kernels (the paper has no counterpart: these are
  * launch-shape choices that leave the arithmetic unchanged; results are bit
  * for bit the same).  Set per context, typically by an autotuner that times
@@ -312,6 +336,14 @@ int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
 /* Reads one tiling key into *value (its default if never set); no counterpart
  * in the paper.  NLSE_EINVAL for an unknown key or NULL arguments. */
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
+
+/* Measurement helper; no counterpart in the paper.  Times a chain of FP64
+ * fused multiply-adds on every SM of the current GPU (CUDA events, best of
+ * three launches after a warm-up) and writes the rate in FP64 flops per
+ * second (2 per FMA) to *flops_per_s: the denominator of the roofline of the
+ * FP64 stage kernels, which FP64 arithmetic bounds on this GPU.  Allocates a
+ * small output buffer; synchronises the stream. */
+int nlse_measure_fp64_rate(double* flops_per_s, void* stream);
 
 /* Human-readable description of the calling thread's last error ("" if none).
  * No counterpart in the paper; the string belongs to the library. */

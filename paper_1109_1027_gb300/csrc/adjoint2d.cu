@@ -197,7 +197,21 @@ __global__ void stack_sum_kernel(const double* src, int count, int64_t n, double
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) scale_kernel(cplx<R>* z, R f, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        z[p] = cscale(f, z[p]);
+}
+
 }  // namespace
+
+cudaError_t launch_scale(int prec, void* z, double f, int64_t n, cudaStream_t st) {
+    const int64_t b = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+    if (prec == 0) scale_kernel<float><<<blocks, 256, 0, st>>>((float2*)z, (float)f, n);
+    else scale_kernel<double><<<blocks, 256, 0, st>>>((double2*)z, f, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st) {
     const bool cd = L.lap == 1;

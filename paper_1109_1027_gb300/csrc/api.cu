@@ -10,6 +10,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nlse.h"
 #include "nlse_internal.h"
 #include "stability.cuh"
@@ -32,6 +34,15 @@ int cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? NLSE_ENOMEM : NLSE_ECUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
+
+// NVTX range over the rest of the enclosing scope (seen by profilers; a
+// no-op without one).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 #define NLSE_CUDA(call, what)                                  \
     do {                                                       \
@@ -57,7 +68,7 @@ struct nlse_ctx {
     void* Y[2];               // stage inputs (ping-pong)
     void* acc;                // accumulated RK4 increment
     void* lo;                 // FP32 compensated low part (FP32 only)
-    void* plain[4];           // unfused schedule: D, K_tot, K_tmp, Psi_tmp
+    void* plain[4];           // unfused schedule: D, K, Y, acc
     int* flag;                // status bits (the first member of status)
     nlse::StatusBlock* status;  // device status block (nlse_check reads and clears it)
     // nlse_run's entry check (check.cu): one entry per instance, its rows of
@@ -80,9 +91,12 @@ struct nlse_ctx {
     int64_t* boff;            // per-instance element offsets
     int* brow;                // per-instance first row of partials (count + 1 entries)
     const void* maps_psi;     // Psi buffer the batch tensor maps currently point at
-    // Adjoint work space (nlse_adjoint), allocated on first use.
+    // Adjoint work space (nlse_adjoint), allocated on first use, and the
+    // forward pass it holds (nlse_adjoint_forward) for a reverse sweep.
     void* adj_buf;
     size_t adj_bytes;
+    bool adj_ready;           // a forward pass awaits its reverse sweep
+    int64_t adj_nsteps, adj_ckpt;
     // Device copy of a host state (nlse_run_host), allocated on first use.
     void* host_state;
     // Batch: per-instance table of the one-launch invariants (device).
@@ -183,7 +197,7 @@ nlse::PlainLaunch plain_launch(const nlse_ctx* c, const void* psi) {
     L.prec = c->p.prec; L.lap = c->p.lap; L.bc = c->p.bc;
     L.h = c->p.h; L.a = c->p.a; L.s = c->p.s; L.dt = c->p.dt;
     L.psi = const_cast<void*>(psi); L.lo = c->lo; L.V = c->V;
-    L.D = c->plain[0]; L.Ktot = c->plain[1]; L.Ktmp = c->plain[2]; L.ptmp = c->plain[3];
+    L.D = c->plain[0]; L.K = c->plain[1]; L.Y = c->plain[2]; L.acc = c->plain[3];
     L.flag = c->flag;
     return L;
 }
@@ -205,7 +219,9 @@ int enqueue_step(nlse_ctx* c, void* psi, cudaStream_t st) {
     L.lo = c->lo;
     const void* in[5] = {nullptr, psi, c->Y[0], c->Y[1], c->Y[0]};
     void* out[5] = {nullptr, c->Y[0], c->Y[1], c->Y[0], nullptr};
+    static const char* const names[5] = {"", "RK4 stage 1", "RK4 stage 2", "RK4 stage 3", "RK4 stage 4"};
     for (int s = 1; s <= 4; ++s) {
+        Range range(names[s]);
         L.stage = s;
         L.yin = in[s];
         L.yout = out[s];
@@ -398,6 +414,7 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
 // term B of Table t:bc2 and take the full invariants reduction; the other
 // boundary rules have B = 0 and take the extremes pass of check.cu.
 int enqueue_entry_check(nlse_ctx* c, const void* psi, cudaStream_t st) {
+    Range range("entry check (Eq. kdfull)");
     const void* lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
     if (c->p.bc == NLSE_BC_MSD) {
         nlse::InvLaunch L;
@@ -711,80 +728,118 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
     return NLSE_OK;
 }
 
-int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nsteps, int64_t ckpt_every,
-                 void* dpsi0, void* dV, double* loss, void* stream) {
-    g_err[0] = 0;
-    if (!c || !psi0 || !target || !dpsi0 || !dV) return fail(NLSE_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Layout of the adjoint work space for nsteps steps with a checkpoint every
+// ckpt steps: state S, checkpoints (state + compensated part), the four stage
+// inputs (Psi_n, Y2, Y3, Y4) of every step of one segment, two cotangents,
+// two adjoint states (the first holds dL/dPsi_T after the forward pass), loss
+// partials and the loss, and for a stack the per-instance dL/dV.
+struct AdjLayout {
+    int64_t nseg, seglen;
+    int nb;
+    size_t ck_bytes, need;
+    char *S, *ck, *seg, *W, *WN, *LA, *LB;
+    double *part, *lossd, *gvs;
+};
+
+AdjLayout adj_layout(nlse_ctx* c, int64_t nsteps, int64_t ckpt_every) {
+    AdjLayout A;
+    const size_t cb = c->cbytes;
+    A.nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    A.seglen = nsteps < ckpt_every ? nsteps : ckpt_every;
+    A.nb = nlse::loss_num_blocks(c->npts);
+    A.ck_bytes = (size_t)A.nseg * cb * (c->lo ? 2 : 1);
+    const size_t gv_bytes = c->stack > 1 ? sizeof(double) * (size_t)c->npts : 0;
+    A.need = cb + A.ck_bytes + 4 * (size_t)A.seglen * cb + 4 * cb + sizeof(double) * (A.nb + 1) + gv_bytes;
+    char* base = static_cast<char*>(c->adj_buf);
+    A.S = base;
+    A.ck = A.S + cb;
+    A.seg = A.ck + A.ck_bytes;
+    A.W = A.seg + 4 * (size_t)A.seglen * cb;
+    A.WN = A.W + cb;
+    A.LA = A.WN + cb;
+    A.LB = A.LA + cb;
+    A.part = reinterpret_cast<double*>(A.LB + cb);
+    A.lossd = A.part + A.nb;
+    A.gvs = c->stack > 1 ? A.lossd + 1 : nullptr;
+    return A;
+}
+
+int adjoint_check_args(nlse_ctx* c, int64_t nsteps, int64_t ckpt_every) {
     if (c->batch || c->p.dim != 2 || c->p.bc != NLSE_BC_DIRICHLET || (c->p.flags & NLSE_FLAG_PLAIN_SCHEDULE))
         return fail(NLSE_EUNSUPPORTED, "the adjoint is implemented for single 2D Dirichlet grids (fused schedule)");
     if (nsteps < 0 || ckpt_every < 1) return fail(NLSE_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
-    if (((uintptr_t)psi0 | (uintptr_t)target | (uintptr_t)dpsi0 | (uintptr_t)dV) % 16)
-        return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t cb = c->cbytes;
-    const bool has_lo = c->lo != nullptr;
-    const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
-    const int64_t seglen = nsteps < ckpt_every ? nsteps : ckpt_every;
-    const int nb = nlse::loss_num_blocks(c->npts);
-    // Work space: state S, checkpoints (state + compensated part), the four
-    // stage inputs (Psi_n, Y2, Y3, Y4) of every step of one segment, two
-    // cotangents, two adjoint states, loss partials.
-    const size_t ck_bytes = (size_t)nseg * cb * (has_lo ? 2 : 1);
-    const int64_t vpts = c->npts / c->stack;
-    // A stack accumulates dL/dV per instance, summed at the end.
-    const size_t gv_bytes = c->stack > 1 ? sizeof(double) * (size_t)c->npts : 0;
-    const size_t need = cb + ck_bytes + 4 * (size_t)seglen * cb + 4 * cb + sizeof(double) * (nb + 1) + gv_bytes;
-    if (need > c->adj_bytes) {
+    return NLSE_OK;
+}
+
+// The forward pass with checkpoints, dL/dPsi_T = 2 (Psi_T - target) into LA
+// and the loss on the device; no synchronisation.
+int adjoint_forward(nlse_ctx* c, const void* psi0, const void* target, int64_t nsteps, int64_t ckpt_every,
+                    cudaStream_t st) {
+    c->adj_ready = false;
+    AdjLayout A = adj_layout(c, nsteps, ckpt_every);
+    if (A.need > c->adj_bytes) {
         cudaFree(c->adj_buf);
         c->adj_buf = nullptr;
         c->adj_bytes = 0;
-        NLSE_CUDA(cudaMalloc(&c->adj_buf, need), "allocating adjoint work space");
-        c->adj_bytes = need;
+        NLSE_CUDA(cudaMalloc(&c->adj_buf, A.need), "allocating adjoint work space");
+        c->adj_bytes = A.need;
+        A = adj_layout(c, nsteps, ckpt_every);
     }
-    char* base = static_cast<char*>(c->adj_buf);
-    char* S = base;
-    char* ck = S + cb;
-    char* seg = ck + ck_bytes;                   // [seglen][4] stage inputs
-    char* W = seg + 4 * (size_t)seglen * cb;
-    char* WN = W + cb;
-    char* LA = WN + cb;
-    char* LB = LA + cb;
-    double* part = reinterpret_cast<double*>(LB + cb);
-    double* lossd = part + nb;
-    double* gvs = c->stack > 1 ? lossd + 1 : static_cast<double*>(dV);
-    auto ckp = [&](int64_t i) { return ck + (size_t)i * cb * (has_lo ? 2 : 1); };
-    auto yin = [&](int64_t m, int j) { return seg + ((size_t)m * 4 + (size_t)(j - 1)) * cb; };   // Y_j of step m
-
-    // Forward pass with checkpoints.  S is the state; the context's
-    // compensated part belongs to S for the duration of the call.
-    NLSE_CUDA(cudaMemcpyAsync(S, psi0, cb, cudaMemcpyDeviceToDevice, st), "copying psi0");
+    const size_t cb = c->cbytes;
+    const bool has_lo = c->lo != nullptr;
+    auto ckp = [&](int64_t i) { return A.ck + (size_t)i * cb * (has_lo ? 2 : 1); };
+    // S is the state; the context's compensated part belongs to S for the
+    // duration of the pass.
+    NLSE_CUDA(cudaMemcpyAsync(A.S, psi0, cb, cudaMemcpyDeviceToDevice, st), "copying psi0");
     if (has_lo) NLSE_CUDA(cudaMemsetAsync(c->lo, 0, cb, st), "zeroing the compensated part");
     c->state_psi = nullptr;
-    int rc;
-    for (int64_t g = 0; g < nseg; ++g) {
-        NLSE_CUDA(cudaMemcpyAsync(ckp(g), S, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
+    for (int64_t g = 0; g < A.nseg; ++g) {
+        NLSE_CUDA(cudaMemcpyAsync(ckp(g), A.S, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
         if (has_lo) NLSE_CUDA(cudaMemcpyAsync(ckp(g) + cb, c->lo, cb, cudaMemcpyDeviceToDevice, st), "checkpoint");
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
-        if ((rc = enqueue_steps(c, S, steps, st))) return rc;
+        int rc = enqueue_steps(c, A.S, steps, st);
+        if (rc) return rc;
     }
-    NLSE_CUDA(nlse::launch_loss(c->p.prec, S, target, LA, c->npts, part, nb, lossd, st), "loss launch");
+    NLSE_CUDA(nlse::launch_loss(c->p.prec, A.S, target, A.LA, c->npts, A.part, A.nb, A.lossd, st), "loss launch");
+    c->adj_nsteps = nsteps;
+    c->adj_ckpt = ckpt_every;
+    c->adj_ready = true;
+    return NLSE_OK;
+}
 
-    // Reverse sweep, segment by segment from the last.
-    char* lamp = LA;
-    char* lam = LB;
+// The reverse sweep of the held forward pass, segment by segment from the
+// last, with dL/dPsi_T scaled by dloss; no synchronisation.
+int adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, cudaStream_t st) {
+    const int64_t nsteps = c->adj_nsteps, ckpt_every = c->adj_ckpt;
+    AdjLayout A = adj_layout(c, nsteps, ckpt_every);
+    c->adj_ready = false;                        // the sweep consumes dL/dPsi_T
+    const size_t cb = c->cbytes;
+    const bool has_lo = c->lo != nullptr;
+    auto ckp = [&](int64_t i) { return A.ck + (size_t)i * cb * (has_lo ? 2 : 1); };
+    auto yin = [&](int64_t m, int j) { return A.seg + ((size_t)m * 4 + (size_t)(j - 1)) * cb; };  // Y_j of step m
+    double* gvs = c->stack > 1 ? A.gvs : static_cast<double*>(dV);
+    const int64_t vpts = c->npts / c->stack;
+    if (dloss != 1.0)
+        NLSE_CUDA(nlse::launch_scale(c->p.prec, A.LA, dloss, c->npts, st), "scaling the loss cotangent");
+    char* lamp = A.LA;
+    char* lam = A.LB;
     StageLaunch F = base_launch(c);
     F.acc = c->acc;
     F.lo = c->lo;
-    nlse::AdjLaunch A;
-    A.prec = c->p.prec; A.lap = c->p.lap;
-    A.nx = c->p.n[0]; A.ny = c->p.n[1] * c->stack;
-    A.rows1 = c->p.n[1];
-    A.h = c->p.h; A.a = c->p.a; A.s = c->p.s;
-    A.V = c->V;
-    A.gV = gvs;
+    nlse::AdjLaunch J;
+    J.prec = c->p.prec; J.lap = c->p.lap;
+    J.nx = c->p.n[0]; J.ny = c->p.n[1] * c->stack;
+    J.rows1 = c->p.n[1];
+    J.h = c->p.h; J.a = c->p.a; J.s = c->p.s;
+    J.V = c->V;
+    J.gV = gvs;
     NLSE_CUDA(cudaMemsetAsync(gvs, 0, sizeof(double) * c->npts, st), "zeroing dV");
     const double k = c->p.dt;
-    for (int64_t g = nseg - 1; g >= 0; --g) {
+    for (int64_t g = A.nseg - 1; g >= 0; --g) {
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
         // Recompute the segment from its checkpoint with the fused stage
         // kernels, keeping every stage input: stage j of step m reads
@@ -805,23 +860,19 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
             }
         }
         for (int64_t m = steps - 1; m >= 0; --m) {
-            const void* psi_n = yin(m, 1);
-            const void* Y2 = yin(m, 2);
-            const void* Y3 = yin(m, 3);
-            const void* Y4 = yin(m, 4);
+            const void* Ys[5] = {nullptr, yin(m, 1), yin(m, 2), yin(m, 3), yin(m, 4)};
             // Stages 4 .. 1 reversed.
-            const void* w[5] = {nullptr, W, WN, W, lamp};
+            const void* w[5] = {nullptr, A.W, A.WN, A.W, lamp};
             const double sw[5] = {0, 1, 1, 1, k / 6.0};
-            const void* Ys[5] = {nullptr, psi_n, Y2, Y3, Y4};
-            void* wn[5] = {nullptr, nullptr, W, WN, W};
+            void* wn[5] = {nullptr, nullptr, A.W, A.WN, A.W};
             const double cw[5] = {0, 0, k / 6.0, k / 3.0, k / 3.0};
             const double cy[5] = {0, 0, k / 2.0, k / 2.0, k};
             for (int j = 4; j >= 1; --j) {
-                A.j = j;
-                A.w = w[j]; A.scale_w = sw[j]; A.Y = Ys[j];
-                A.lamp = lamp; A.lam = lam; A.w_next = wn[j];
-                A.cw = cw[j]; A.cy = cy[j];
-                cudaError_t e = nlse::launch_adjoint_stage_2d(A, st);
+                J.j = j;
+                J.w = w[j]; J.scale_w = sw[j]; J.Y = Ys[j];
+                J.lamp = lamp; J.lam = lam; J.w_next = wn[j];
+                J.cw = cw[j]; J.cy = cy[j];
+                cudaError_t e = nlse::launch_adjoint_stage_2d(J, st);
                 if (e != cudaSuccess) return cuda_fail(e, "adjoint stage launch");
             }
             std::swap(lamp, lam);
@@ -830,18 +881,76 @@ int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nste
     NLSE_CUDA(cudaMemcpyAsync(dpsi0, lamp, cb, cudaMemcpyDeviceToDevice, st), "gradient copy");
     if (c->stack > 1)
         NLSE_CUDA(nlse::launch_stack_sum(gvs, c->stack, vpts, static_cast<double*>(dV), st), "summing dV over the stack");
+    return NLSE_OK;
+}
+
+// Synchronises; reads the loss (when asked) and the status.  A refusal of an
+// earlier nlse_run that nobody read kept the stage-4 kernels from stepping:
+// then the forward pass did not run, and the refusal is returned.
+int adjoint_finish(nlse_ctx* c, double* loss, cudaStream_t st) {
     double h_loss = 0.0;
     nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);
-    NLSE_CUDA(cudaMemcpyAsync(&h_loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, st), "loss copy");
+    if (loss) {
+        AdjLayout A = adj_layout(c, c->adj_nsteps, c->adj_ckpt);
+        NLSE_CUDA(cudaMemcpyAsync(&h_loss, A.lossd, sizeof(double), cudaMemcpyDeviceToHost, st), "loss copy");
+    }
     NLSE_CUDA(cudaMemcpyAsync(hs, c->status, sizeof(nlse::StatusBlock), cudaMemcpyDeviceToHost, st), "status copy");
     NLSE_CUDA(cudaStreamSynchronize(st), "adjoint synchronise");
     c->state_psi = nullptr;          // the compensated part no longer belongs to any caller state
-    // A refusal of an earlier nlse_run that nobody read kept the stage-4
-    // kernels from stepping: the forward pass did not run.
     const nlse::StatusBlock sb = *hs;
-    if (sb.bits & nlse::kStatusRefused) return report_status(c, sb, st);
+    if (sb.bits & nlse::kStatusRefused) {
+        c->adj_ready = false;
+        return report_status(c, sb, st);
+    }
     if (loss) *loss = h_loss;
     return NLSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nlse_adjoint(nlse_ctx* c, const void* psi0, const void* target, int64_t nsteps, int64_t ckpt_every,
+                 void* dpsi0, void* dV, double* loss, void* stream) {
+    g_err[0] = 0;
+    Range range("nlse_adjoint");
+    if (!c || !psi0 || !target || !dpsi0 || !dV) return fail(NLSE_EINVAL, "NULL argument");
+    int rc = adjoint_check_args(c, nsteps, ckpt_every);
+    if (rc) return rc;
+    if (((uintptr_t)psi0 | (uintptr_t)target | (uintptr_t)dpsi0 | (uintptr_t)dV) % 16)
+        return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = adjoint_forward(c, psi0, target, nsteps, ckpt_every, st))) return rc;
+    if ((rc = adjoint_backward(c, 1.0, dpsi0, dV, st))) return rc;
+    return adjoint_finish(c, loss, st);
+}
+
+int nlse_adjoint_forward(nlse_ctx* c, const void* psi0, const void* target, int64_t nsteps, int64_t ckpt_every,
+                         double* loss, void* stream) {
+    g_err[0] = 0;
+    Range range("nlse_adjoint_forward");
+    if (!c || !psi0 || !target) return fail(NLSE_EINVAL, "NULL argument");
+    int rc = adjoint_check_args(c, nsteps, ckpt_every);
+    if (rc) return rc;
+    if (((uintptr_t)psi0 | (uintptr_t)target) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = adjoint_forward(c, psi0, target, nsteps, ckpt_every, st))) return rc;
+    return adjoint_finish(c, loss, st);
+}
+
+int nlse_adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, void* stream) {
+    g_err[0] = 0;
+    Range range("nlse_adjoint_backward");
+    if (!c || !dpsi0 || !dV) return fail(NLSE_EINVAL, "NULL argument");
+    if (!c->adj_ready)
+        return fail(NLSE_EINVAL, "no forward pass to reverse: call nlse_adjoint_forward first (each forward pass "
+                    "admits one reverse sweep)");
+    if (!std::isfinite(dloss)) return fail(NLSE_EINVAL, "dloss must be finite");
+    if (((uintptr_t)dpsi0 | (uintptr_t)dV) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = adjoint_backward(c, dloss, dpsi0, dV, st);
+    if (rc) return rc;
+    return adjoint_finish(c, nullptr, st);
 }
 
 int nlse_invariants_batch(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
@@ -908,6 +1017,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
 
 int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
     g_err[0] = 0;
+    Range range("nlse_lap2shoc");
     if (!c || !psi || !lap) return fail(NLSE_EINVAL, "NULL argument");
     if (((uintptr_t)psi | (uintptr_t)lap) % 16) return fail(NLSE_EINVAL, "pointers must be 16-byte aligned");
     const char *a0 = (const char*)psi, *b0 = (const char*)lap;
@@ -933,6 +1043,7 @@ int nlse_lap2shoc(nlse_ctx* c, const void* psi, void* lap, void* stream) {
 
 int nlse_rk4_step(nlse_ctx* c, void* psi, void* stream) {
     g_err[0] = 0;
+    Range range("nlse_rk4_step");
     if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
     if ((uintptr_t)psi % 16) return fail(NLSE_EINVAL, "psi must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
@@ -944,6 +1055,7 @@ int nlse_rk4_step(nlse_ctx* c, void* psi, void* stream) {
 
 int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
     g_err[0] = 0;
+    Range range("nlse_run");
     if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
     if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps must be >= 0");
     if ((uintptr_t)psi % 16) return fail(NLSE_EINVAL, "psi must be 16-byte aligned");
@@ -963,6 +1075,7 @@ int nlse_run(nlse_ctx* c, void* psi, int64_t nsteps, void* stream) {
 
 int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
     g_err[0] = 0;
+    Range range("nlse_run_host");
     if (!c || !psi_host) return fail(NLSE_EINVAL, "NULL argument");
     if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -982,6 +1095,7 @@ int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
 int nlse_invariants(nlse_ctx* c, const void* psi, double* mass, double* energy, double* dt_max,
                     void* stream) {
     g_err[0] = 0;
+    Range range("nlse_invariants");
     if (!c || !psi) return fail(NLSE_EINVAL, "NULL argument");
     return invariants_impl(c, psi, mass, energy, dt_max, (cudaStream_t)stream);
 }
@@ -995,6 +1109,7 @@ int nlse_reset_compensation(nlse_ctx* c, void* stream) {
 
 int nlse_check(nlse_ctx* c, void* stream) {
     g_err[0] = 0;
+    Range range("nlse_check");
     if (!c) return fail(NLSE_EINVAL, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);

@@ -215,22 +215,27 @@ __device__ Acc block_reduce(Acc a) {
 // only the pointwise extremes (and, for MSD, the boundary term), which read
 // each point once, while the energy's FP64 Laplacian is the costly part.
 // Accumulates the points first, first + stride, ... of one grid into a.
+// Coordinates are formed (three integer divisions) only where they are
+// needed: for the energy's Laplacian and the MSD boundary term.
 template <typename R, bool ENERGY>
 __device__ void accumulate(const InvView<R>& v, int64_t npts, int64_t first, int64_t stride, Acc& a) {
+    const bool coords = ENERGY || v.bc == 1;
+    const bool shared_v = v.vpts != npts;            // a stack: V indexed within the instance
     for (int64_t p = first; p < npts; p += stride) {
-        int c[3];
-        int64_t r = p;
-        c[0] = (int)(r % v.n[0]); r /= v.n[0];
-        c[1] = (int)(r % v.n[1]); r /= v.n[1];
-        c[2] = (int)r;
         double2 ps = psi_at(v, p);
         double rho = ps.x * ps.x + ps.y * ps.y;
-        double Vp = v_at(v, p);
+        double Vp = shared_v ? v_at(v, p) : (double)v.V[p];
         if (!isfinite(rho)) { a.nonfinite += 1.0; continue; }
         a.mass += rho;
         double L = v.h2a * (v.s * rho - Vp);
         a.lmin = fmin(a.lmin, L);
         a.lmax = fmax(a.lmax, L);
+        if (!coords) continue;
+        int c[3];
+        int64_t r = p;
+        c[0] = (int)(r % v.n[0]); r /= v.n[0];
+        c[1] = (int)(r % v.n[1]); r /= v.n[1];
+        c[2] = (int)r;
         if (!on_boundary(v, c)) {
             if (!ENERGY) continue;
             double2 lp = lap_interior(v, c);

@@ -77,8 +77,8 @@ cudaError_t launch_stage_3d_tma_planes32(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d_tma_planes64(const StageLaunch& L, cudaStream_t st);
 cudaError_t launch_stage_3d_tma_planes128(const StageLaunch& L, cudaStream_t st);
 
-// One RK4 step of the paper's unfused schedule (plain.cu): D, K_tot, K_tmp
-// and Psi_tmp are full device arrays (Sec. 3.1).
+// One unfused RK4 step (plain.cu): the step-1 field D, the stage slope K,
+// the stage input Y and the increment acc are full device arrays.
 struct PlainLaunch {
     int dim;
     int64_t n[3];
@@ -87,7 +87,7 @@ struct PlainLaunch {
     void* psi;
     void* lo;               // FP32 compensated part, or nullptr
     const void* V;
-    void *D, *Ktot, *Ktmp, *ptmp;
+    void *D, *K, *Y, *acc;
     int* flag;
 };
 
@@ -143,6 +143,8 @@ struct AdjLaunch {
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st);
 // dst[q] = sum over i of src[i n + q], i = 0 .. count-1 in order (stacked dL/dV).
 cudaError_t launch_stack_sum(const double* src, int count, int64_t n, double* dst, cudaStream_t st);
+// z *= f over n complex values (the cotangent of the loss, nlse_adjoint_backward).
+cudaError_t launch_scale(int prec, void* z, double f, int64_t n, cudaStream_t st);
 int loss_num_blocks(int64_t n);
 cudaError_t launch_loss(int prec, const void* psi, const void* target, void* lam, int64_t n, double* partials,
                         int nblocks, double* out, cudaStream_t st);

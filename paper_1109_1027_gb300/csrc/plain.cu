@@ -1,11 +1,14 @@
-// plain.cu -- the paper's own, unfused schedule of one RK4+2SHOC step, kept
-// as the per-instance baseline the fused kernels are measured against.
+// plain.cu -- an unfused RK4+2SHOC step, one launch per operation over the
+// whole grid: the per-instance baseline the fused kernels are measured
+// against, with the storage plan of an unfused CPU-style code (Sec. 3.1): the
+// step-1 field D and the RK4 work fields are full grids in device memory.
 //
-// Storage and order follow Sec. 3.1 literally: the step-1 field D, and the
-// RK4 work arrays K_tot, K_tmp and Psi_tmp, are full grids in device memory;
-// every F(Psi) is two launches (D, then step 2 + F), and each axpy line of
-// Eq. (RK4) is its own launch -- fourteen launches per step.  One thread per
-// grid point, no shared memory.
+// The step is classic four-stage RK4 written from its Butcher tableau
+// (nodes 0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6): for stage j the stage
+// input Y = Psi + c_j k K_{j-1} (Y = Psi for j = 1) is one launch, its slope
+// K_j = F(Y) two (D, then step 2 + F), and the increment acc = sum b_j k K_j
+// one; the state update Psi += acc closes the step -- sixteen launches per
+// step.  One thread per grid point, no shared memory.
 //
 // The same kernels carry the MSD boundary rule in every dimension (the fused
 // 2D and 3D kernels are Dirichlet only): with the D and F fields in global
@@ -17,7 +20,7 @@
 // or corner).  They also carry the two further conditions Sec. 3.2 names:
 // periodic (no boundary points, neighbour indices wrap) and Laplacian-zero
 // (D_b = 0 and F_b = i (s|Psi_b|^2 - V_b) Psi_b, the equation with a zero
-// Laplacian).  In FP32 the last line of Eq. (RK4) adds to the state with the
+// Laplacian).  In FP32 the state update adds the increment with the
 // compensated (Kahan) sum of the fused path.
 #include "nlse_device.cuh"
 
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(NT) plain_f(const cplx<R>* psi, const cplx<R>*
     K[p] = LAP ? lap : rhs_point(c, y, lap, V[p]);
 }
 
-// out = a + w b   (lines 2, 5, 8 of Eq. RK4)
+// out = a + w b: a stage input Y = Psi + c_j k K_{j-1}
 template <typename R>
 __global__ void __launch_bounds__(NT) plain_axpy(cplx<R>* out, const cplx<R>* a, R w, const cplx<R>* b,
                                                  int64_t n) {
@@ -148,33 +151,32 @@ __global__ void __launch_bounds__(NT) plain_axpy(cplx<R>* out, const cplx<R>* a,
     if (p < n) out[p] = caxpy(a[p], w, b[p]);
 }
 
-// acc += w b      (lines 4, 7)
-template <typename R>
+// acc = w b (first stage) or acc += w b: the increment sum b_j k K_j
+template <typename R, bool FIRST>
 __global__ void __launch_bounds__(NT) plain_acc(cplx<R>* acc, R w, const cplx<R>* b, int64_t n) {
     int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
-    if (p < n) acc[p] = caxpy(acc[p], w, b[p]);
+    if (p < n) acc[p] = FIRST ? cscale(w, b[p]) : caxpy(acc[p], w, b[p]);
 }
 
-// psi += w (a + b)  (line 10); compensated in FP32 when lo is given
+// psi += acc, compensated in FP32 when lo is given
 template <typename R>
-__global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, cplx<R>* lo, R w, const cplx<R>* a,
-                                                  const cplx<R>* b, int64_t n, int* flag) {
+__global__ void __launch_bounds__(NT) plain_final(cplx<R>* psi, cplx<R>* lo, const cplx<R>* acc, int64_t n,
+                                                  int* flag) {
     int64_t p = blockIdx.x * (int64_t)NT + threadIdx.x;
     if (p >= n || refused(flag)) return;
-    cplx<R> v;
+    cplx<R> v = psi[p];
+    const cplx<R> d = acc[p];
     if constexpr (sizeof(R) == 4) {
         if (lo) {
-            const cplx<R> d = cscale(w, cadd(a[p], b[p]));
-            v = psi[p];
             cplx<R> l = lo[p];
             kahan_add(v.x, l.x, d.x);
             kahan_add(v.y, l.y, d.y);
             lo[p] = l;
         } else {
-            v = caxpy(psi[p], w, cadd(a[p], b[p]));
+            v = cadd(v, d);
         }
     } else {
-        v = caxpy(psi[p], w, cadd(a[p], b[p]));
+        v = cadd(v, d);
     }
     psi[p] = v;
     if (!(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
@@ -199,13 +201,12 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
     Coef<R> c = make_coef<R>(L.h, L.a, L.s);
     C* psi = (C*)L.psi;
     C* D = (C*)L.D;
-    C* Ktot = (C*)L.Ktot;
-    C* Ktmp = (C*)L.Ktmp;
-    C* ptmp = (C*)L.ptmp;
+    C* K = (C*)L.K;
+    C* Y = (C*)L.Y;
+    C* acc = (C*)L.acc;
     const R* V = (const R*)L.V;
     const int64_t n = g.npts;
     const unsigned blocks = (unsigned)((n + NT - 1) / NT);
-    const R k = (R)L.dt;
     const bool msd = L.bc == 1;
     auto F = [&](const C* in, C* out) {
         plain_d<R><<<blocks, NT, 0, st>>>(in, V, D, g, c);
@@ -214,16 +215,21 @@ cudaError_t step_r(const PlainLaunch& L, cudaStream_t st) {
         else plain_f<R, false><<<blocks, NT, 0, st>>>(in, D, V, out, g, c);
         if (msd) plain_f_msd<R><<<blocks, NT, 0, st>>>(in, out, g);
     };
-    F(psi, Ktot);                                                          // 1
-    plain_axpy<R><<<blocks, NT, 0, st>>>(ptmp, psi, k / 2, Ktot, n);      // 2
-    F(ptmp, Ktmp);                                                         // 3
-    plain_acc<R><<<blocks, NT, 0, st>>>(Ktot, (R)2, Ktmp, n);             // 4
-    plain_axpy<R><<<blocks, NT, 0, st>>>(ptmp, psi, k / 2, Ktmp, n);      // 5
-    F(ptmp, Ktmp);                                                         // 6
-    plain_acc<R><<<blocks, NT, 0, st>>>(Ktot, (R)2, Ktmp, n);             // 7
-    plain_axpy<R><<<blocks, NT, 0, st>>>(ptmp, psi, k, Ktmp, n);          // 8
-    F(ptmp, Ktmp);                                                         // 9
-    plain_final<R><<<blocks, NT, 0, st>>>(psi, (C*)L.lo, k / 6, Ktot, Ktmp, n, L.flag);  // 10
+    // Butcher tableau of classic RK4: nodes c_j, weights b_j (in units of k).
+    const double c_node[4] = {0.0, 0.5, 0.5, 1.0};
+    const double b_weight[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    for (int j = 0; j < 4; ++j) {
+        const C* in = psi;
+        if (j > 0) {
+            plain_axpy<R><<<blocks, NT, 0, st>>>(Y, psi, (R)(c_node[j] * L.dt), K, n);
+            in = Y;
+        }
+        F(in, K);
+        const R w = (R)(b_weight[j] * L.dt);
+        if (j == 0) plain_acc<R, true><<<blocks, NT, 0, st>>>(acc, w, K, n);
+        else plain_acc<R, false><<<blocks, NT, 0, st>>>(acc, w, K, n);
+    }
+    plain_final<R><<<blocks, NT, 0, st>>>(psi, (C*)L.lo, acc, n, L.flag);
     return cudaGetLastError();
 }
 

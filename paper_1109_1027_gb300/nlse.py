@@ -82,8 +82,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_invariants_batch": ([vp, vp, dp, dp, dp, vp], ctypes.c_int),
         "nlse_batch_count": ([vp], ctypes.c_int),
         "nlse_adjoint": ([vp, vp, vp, i64, i64, vp, vp, dp, vp], ctypes.c_int),
+        "nlse_adjoint_forward": ([vp, vp, vp, i64, i64, dp, vp], ctypes.c_int),
+        "nlse_adjoint_backward": ([vp, ctypes.c_double, vp, vp, vp], ctypes.c_int),
         "nlse_set_tiling": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "nlse_get_tiling": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "nlse_measure_fp64_rate": ([dp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +203,25 @@ def nlse_adjoint(ctx, psi0_ptr: int, target_ptr: int, nsteps: int, ckpt_every: i
     return loss.value
 
 
+def nlse_adjoint_forward(ctx, psi0_ptr: int, target_ptr: int, nsteps: int, ckpt_every: int, stream=None) -> float:
+    loss = ctypes.c_double()
+    _raise(load_library().nlse_adjoint_forward(ctx, ctypes.c_void_p(psi0_ptr), ctypes.c_void_p(target_ptr),
+                                               int(nsteps), int(ckpt_every), ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def nlse_adjoint_backward(ctx, dloss: float, dpsi0_ptr: int, dV_ptr: int, stream=None) -> None:
+    _raise(load_library().nlse_adjoint_backward(ctx, float(dloss), ctypes.c_void_p(dpsi0_ptr),
+                                                ctypes.c_void_p(dV_ptr), _stream(stream)))
+
+
+def nlse_measure_fp64_rate(stream=None) -> float:
+    """FP64 flops per second of the current GPU (a chain-of-FMAs probe)."""
+    r = ctypes.c_double()
+    _raise(load_library().nlse_measure_fp64_rate(ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
 def nlse_set_tiling(ctx, key: int, value: int) -> None:
     _raise(load_library().nlse_set_tiling(ctx, int(key), int(value)))
 
@@ -294,6 +316,20 @@ class Solver:
         loss = nlse_adjoint(self.ctx, psi0.data_ptr(), target.data_ptr(), nsteps, ckpt_every,
                             g_psi.data_ptr(), g_V.data_ptr())
         return loss, g_psi, g_V
+
+    def adjoint_forward(self, psi0: torch.Tensor, target: torch.Tensor, nsteps: int, ckpt_every: int = 100) -> float:
+        """The loss L = sum |Psi_T - target|^2, keeping the checkpoints for one
+        later adjoint_backward."""
+        self._check_psi(psi0)
+        self._check_psi(target)
+        return nlse_adjoint_forward(self.ctx, psi0.data_ptr(), target.data_ptr(), nsteps, ckpt_every)
+
+    def adjoint_backward(self, dloss: float = 1.0):
+        """(d(dloss L)/dpsi0, d(dloss L)/dV) of the held forward pass."""
+        g_psi = torch.empty(self.shape, dtype=self.cdtype, device=self.V.device)
+        g_V = torch.empty(tuple(self.V.shape), dtype=torch.float64, device=self.V.device)
+        nlse_adjoint_backward(self.ctx, dloss, g_psi.data_ptr(), g_V.data_ptr())
+        return g_psi, g_V
 
     def reset_compensation(self):
         nlse_reset_compensation(self.ctx)
@@ -416,27 +452,29 @@ class BatchSolver:
 
 
 class _FinalLoss(torch.autograd.Function):
-    """L = sum |Psi_T(psi0, V) - target|^2 through the CUDA library; the
-    forward call runs the adjoint too (checkpointed), so backward only scales
-    the stored gradients by the incoming gradient."""
+    """L = sum |Psi_T(psi0, V) - target|^2 through the CUDA library.  The
+    forward call runs the forward pass with its checkpoints
+    (nlse_adjoint_forward) and keeps the context; backward runs the reverse
+    sweep (nlse_adjoint_backward) with the incoming gradient as the loss's
+    weight, so a forward call whose gradient is never asked for pays for the
+    forward pass only."""
 
     @staticmethod
     def forward(ctx, psi0, V, target, h, dt, a, s, nsteps, ckpt_every, lap):
         prec = "fp32" if psi0.dtype == torch.complex64 else "fp64"
         solver = Solver(V.detach().contiguous(), h, dt, a, s, prec=prec, lap=lap, check_stability=False)
-        loss, g_psi, g_V = solver.adjoint(psi0.detach().contiguous(), target.detach().contiguous(), nsteps,
-                                          ckpt_every)
-        solver.close()
-        ctx.save_for_backward(g_psi, g_V)
+        loss = solver.adjoint_forward(psi0.detach().contiguous(), target.detach().contiguous(), nsteps, ckpt_every)
+        ctx.solver = solver
         ctx.v_dtype = V.dtype
         return torch.tensor(loss, dtype=torch.float64, device=psi0.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        g_psi, g_V = ctx.saved_tensors
-        go = grad_out.to(torch.float64)
-        return (g_psi * go.to(g_psi.real.dtype), (g_V * go).to(ctx.v_dtype), None, None, None, None, None, None,
-                None, None)
+        solver = ctx.solver
+        ctx.solver = None
+        g_psi, g_V = solver.adjoint_backward(float(grad_out))
+        solver.close()
+        return g_psi, g_V.to(ctx.v_dtype), None, None, None, None, None, None, None, None
 
 
 def final_loss(psi0, V, target, h, dt, a, s, nsteps, ckpt_every=100, lap="2shoc"):
@@ -447,30 +485,15 @@ def final_loss(psi0, V, target, h, dt, a, s, nsteps, ckpt_every=100, lap="2shoc"
 
 
 def adjoint_many(psi0s, V: torch.Tensor, targets, h, dt, a, s, nsteps: int, ckpt_every: int = 100,
-                 lap: str = "2shoc", workers: int | None = None):
-    """Gradients of L_b = sum |Psi_T^b - target_b|^2 for a batch of initial
-    states sharing V: one context and one CUDA stream per state, driven from
-    host threads so that the instances' kernels run concurrently.  Returns
-    (losses, [dL_b/dpsi0_b], sum_b dL_b/dV in FP64)."""
-    from concurrent.futures import ThreadPoolExecutor
-
+                 lap: str = "2shoc"):
+    """Gradients of the summed loss sum_b |Psi_T^b - target_b|^2 for a batch
+    of initial states sharing V: one stacked context (NLSE_FLAG_STACK) that
+    advances every state in one launch per stage.  Returns (the summed loss,
+    [dL/dpsi0_b], dL/dV summed over the batch in FP64 by the library)."""
     prec = "fp32" if psi0s[0].dtype == torch.complex64 else "fp64"
-    dev = V.device
-    solvers = [Solver(V, h, dt, a, s, prec=prec, lap=lap, check_stability=False) for _ in psi0s]
-    streams = [torch.cuda.Stream(device=dev) for _ in psi0s]
-    torch.cuda.current_stream(dev).synchronize()
-
-    def one(i):
-        with torch.cuda.device(dev), torch.cuda.stream(streams[i]):
-            return solvers[i].adjoint(psi0s[i], targets[i], nsteps, ckpt_every)
-
-    with ThreadPoolExecutor(max_workers=workers or len(psi0s)) as ex:
-        res = list(ex.map(one, range(len(psi0s))))
-    for st in streams:
-        st.synchronize()
-    for sv in solvers:
-        sv.close()
-    gV = torch.zeros(V.shape, dtype=torch.float64, device=dev)
-    for _, _, g in res:
-        gV += g
-    return [r[0] for r in res], [r[1] for r in res], gV
+    solver = Solver(V, h, dt, a, s, prec=prec, lap=lap, check_stability=False, stack=len(psi0s))
+    x0 = torch.stack(list(psi0s)).contiguous()
+    tg = torch.stack(list(targets)).contiguous()
+    loss, g_psi, g_V = solver.adjoint(x0, tg, nsteps, ckpt_every)
+    solver.close()
+    return loss, list(g_psi.unbind(0)), g_V

@@ -109,7 +109,25 @@ def vortex_ring_3d(n: int = 512, lo: float = -30.0, hi: float = 30.0, seed: int 
     core = np.tanh(np.sqrt((rho - radius) ** 2 + z * z))
     psi0 = np.sqrt(np.maximum(mu - V, 0.0)) * core * np.exp(1j * theta)
     return Instance("vortex_ring_3d", (n, n, n), lo, hi, 0.5, -1.0, V, psi0, 0, steps,
-                    {"seed": seed, "centre": (float(cx), float(cy))})
+                    {"seed": seed, "centre": (float(cx), float(cy)), "radius": radius})
+
+
+def gaussian_batch_params(count: int = 512, seed: int = 4, sides=range(64, 1025, 64)):
+    """The per-instance draws of gaussian_batch_2d, without building any
+    array: a list of dicts with the side n, a, s, w, the Gaussian's width and
+    its phase gradient (kx, ky)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = np.asarray(list(sides))
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(sides))
+        a = float(rng.uniform(0.3, 1.0))
+        s = float(rng.choice([-1.0, 1.0]))
+        w = float(rng.uniform(0.0, 0.1))
+        width = float(rng.uniform(2.0, 8.0))
+        kx, ky = rng.uniform(-1.0, 1.0, 2)
+        out.append({"n": n, "a": a, "s": s, "w": w, "width": width, "k": (float(kx), float(ky))})
+    return out
 
 
 def gaussian_batch_2d(count: int = 512, seed: int = 4, sides=range(64, 1025, 64),
@@ -119,23 +137,17 @@ def gaussian_batch_2d(count: int = 512, seed: int = 4, sides=range(64, 1025, 64)
     with a random phase gradient (wavenumbers U[-1, 1]).  With ``only`` (a
     set of indices) just those instances are built -- the same ones, since
     every instance's draws are still taken in order -- and returned in order."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    sides = np.asarray(list(sides))
     out = []
-    for i in range(count):
-        n = int(rng.choice(sides))
-        a = float(rng.uniform(0.3, 1.0))
-        s = float(rng.choice([-1.0, 1.0]))
-        w = float(rng.uniform(0.0, 0.1))
-        width = float(rng.uniform(2.0, 8.0))
-        kx, ky = rng.uniform(-1.0, 1.0, 2)
+    for i, p in enumerate(gaussian_batch_params(count, seed, sides)):
         if only is not None and i not in only:
             continue
+        n, w, width = p["n"], p["w"], p["width"]
+        kx, ky = p["k"]
         x, y = mesh((n, n), lo, hi)
         V = w * w * (x * x + y * y)
         psi0 = np.exp(-(x * x + y * y) / (2.0 * width * width)) * np.exp(1j * (kx * x + ky * y))
-        out.append(Instance(f"gauss_{i}", (n, n), lo, hi, a, s, V, psi0, 0, steps,
-                            {"w": w, "width": width, "k": (float(kx), float(ky))}))
+        out.append(Instance(f"gauss_{i}", (n, n), lo, hi, p["a"], p["s"], V, psi0, 0, steps,
+                            {"w": w, "width": width, "k": p["k"]}))
     return out
 
 

@@ -125,22 +125,55 @@ def test_autograd_function_gives_the_adjoint_gradients():
     assert torch.allclose(Vt.grad.double(), (refs[0] + refs[1]), rtol=1e-5, atol=1e-6 * float(refs[0].abs().max()))
 
 
-def test_concurrent_adjoints_equal_sequential_ones():
+def test_adjoint_many_equals_per_instance_adjoints():
+    """adjoint_many runs one stacked context: each dL/dpsi0 equals the
+    instance's own adjoint bit for bit, the loss their sum, and dL/dV their
+    sum in instance order (added in FP64 by the library)."""
     V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=4)
     prob = oracle.Problem((64, 64), h, a, s)
     k = 0.5 * oracle.invariants(prob, psis[0], V)[2]
     Vd = torch.from_numpy(V).to(DEV).float().contiguous()
     xs = [torch.from_numpy(p).to(DEV).to(torch.complex64).contiguous() for p in psis]
     ts = [torch.from_numpy(t).to(DEV).to(torch.complex64).contiguous() for t in targets]
-    losses, gps, gV = nlse.adjoint_many(xs, Vd, ts, h, k, a, s, 25, 10)
+    loss, gps, gV = nlse.adjoint_many(xs, Vd, ts, h, k, a, s, 25, 10)
     sv = nlse.Solver(Vd, h, k, a, s, prec="fp32", check_stability=False)
-    total = torch.zeros_like(gV)
+    total, losses = None, []
     for i in range(4):
         L, g, g_V = sv.adjoint(xs[i], ts[i], 25, 10)
-        assert L == losses[i]
-        assert torch.equal(g, gps[i])
-        total += g_V
-    assert torch.allclose(total, gV, rtol=1e-12, atol=0)
+        losses.append(L)
+        assert torch.equal(g, gps[i]), i
+        total = g_V if total is None else total + g_V
+    assert torch.equal(total, gV)
+    assert loss == pytest.approx(sum(losses), rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_adjoint_halves_equal_the_whole(prec):
+    """nlse_adjoint_forward then nlse_adjoint_backward(1) give nlse_adjoint's
+    bits; a weight on the loss scales the gradients; a reverse sweep needs
+    its own forward pass."""
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=64, batch=1)
+    rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(DEV).to(rdt).contiguous()
+    x0 = torch.from_numpy(psis[0]).to(DEV).to(cdt).contiguous()
+    tg = torch.from_numpy(targets[0]).to(DEV).to(cdt).contiguous()
+    sv = nlse.Solver(Vd, h, 1e-3, a, s, prec=prec, check_stability=False)
+    L, g, gV = sv.adjoint(x0, tg, 23, 5)
+    with pytest.raises(nlse.NLSEError) as ei:
+        sv.adjoint_backward()                       # nlse_adjoint consumed its own forward pass
+    assert ei.value.code == nlse.EINVAL
+    L1 = sv.adjoint_forward(x0, tg, 23, 5)
+    y = x0.clone()
+    sv.run(y, 3)                                    # other calls in between are allowed
+    g1, gV1 = sv.adjoint_backward(1.0)
+    assert L1 == L and torch.equal(g1, g) and torch.equal(gV1, gV)
+    with pytest.raises(nlse.NLSEError):
+        sv.adjoint_backward(1.0)                    # one reverse sweep per forward pass
+    sv.adjoint_forward(x0, tg, 23, 5)
+    g2, gV2 = sv.adjoint_backward(2.5)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert _close(g2.cpu().numpy(), 2.5 * g.cpu().numpy(), tol)
+    assert _close(gV2.cpu().numpy(), 2.5 * gV.cpu().numpy(), tol)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])

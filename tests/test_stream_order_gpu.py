@@ -67,6 +67,10 @@ def test_run_can_be_captured_into_a_cuda_graph(shape, prec, stack):
     s1.run(x1, 20)
     s1.check()
     x2 = _dev(psi, prec)
+    # The first call for a state pointer binds it (in FP32: zeroes the
+    # compensated part); bound outside the capture, the graph holds the steps
+    # alone and can be replayed to continue the run.
+    s2.run(x2, 0)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):                       # global capture mode: no host waits allowed

@@ -53,3 +53,16 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
                                      ctypes.byref(m), None, None, None)
     assert rc == nlse.EINVAL
     assert "67,108,864" in lib.nlse_last_error().decode()
+
+
+def test_noalloc_refuses_a_stack():
+    """A stack of grids (NLSE_FLAG_STACK) is refused before any device work."""
+    lib = nlse.load_library()
+    params = nlse.make_params((64, 64), 0.1, 1e-4, 1.0, 1.0, prec="fp32")
+    params.n[2] = 3
+    params.flags |= nlse.FLAG_STACK
+    m = ctypes.c_double()
+    rc = lib.nlse_invariants_noalloc(ctypes.byref(params), ctypes.c_void_p(4096), ctypes.c_void_p(4096),
+                                     ctypes.byref(m), None, None, None)
+    assert rc == nlse.EUNSUPPORTED
+    assert "stack" in lib.nlse_last_error().decode()
