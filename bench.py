@@ -79,10 +79,13 @@ BYTES_PER_UPDATE_PLAIN = 720
 # it to its own launches by points (the traffic is proportional to them).
 NCU_TRAFFIC_GRID = {"a4c11e7dc514": 113517099}
 NCU_TRAFFIC_BATCH = {"b03c7bbe283c": {"bytes": 8579640672, "points": 198578176}}
-# FP64 flops per grid-point update (one RK4 step) of the FP64 stage kernels,
-# from ncu instruction counts (2 x DFMA + DADD + DMUL, summed over the four
-# stage launches of one step, divided by the points), keyed as the traffic.
-FP64_FLOPS_PER_UPDATE_GRID = {}
+# FP64 work per grid-point update (one RK4 step) of the FP64 stage kernels,
+# from ncu instruction counts summed over the four stage launches of a step
+# and divided by the points: flops = 2 x DFMA + DADD + DMUL, and instructions
+# = DFMA + DADD + DMUL (each takes one FP64 issue slot).  Keyed by the source
+# hash like the traffic.  2D: 2048^2 dark vortex; 3D: 256^3 vortex ring.
+FP64_WORK_GRID = {"a4c11e7dc514": {"flops": 211.47, "instructions": 150.5}}
+FP64_WORK_3D = {"938607a896a7": {"flops": 333.28, "instructions": 270.3}}
 # Instances of the batch that the CPU oracle times (every 32nd).
 CPU_SAMPLE_STRIDE = 32
 
@@ -491,7 +494,7 @@ def run_ours(args):
 
     grid = None if args.quick else run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_peak)
     grad = None if args.quick else run_gradient_leg(args, dev, barrier, max_over_ranks)
-    other = None if args.quick else run_other_grids(dev, barrier, max_over_ranks)
+    other = None if args.quick else run_other_grids(dev, barrier, max_over_ranks, fp64_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -628,15 +631,11 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_
     steps_taken(s64)
     s32.run(x32, K)
     steps_taken(s32)
-    fpu = FP64_FLOPS_PER_UPDATE_GRID.get(kh)
     rate64 = npts * K / (ms64 * 1e-3)
     out["fp64"] = {"value": job_rate(world, npts * K, ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / K,
                    "achieved_gbs": BYTES_PER_UPDATE_FP64 * npts / (ms64 / K * 1e-3) / 1e9,
-                   "roofline": {"bound": "alu", "kernel": "stage2d_tma_kernel<double>",
-                                "achieved": fpu * rate64 / 1e12 if fpu else None, "peak": fp64_peak / 1e12,
-                                "unit": "TFLOP/s", "frac": fpu * rate64 / fp64_peak if fpu else None,
-                                "peak_kind": "measured FP64 FMA rate (nlse_measure_fp64_rate)",
-                                "flops_per_update": fpu, "kernel_hash": kh}}
+                   "roofline": fp64_roofline(FP64_WORK_GRID.get(kh), rate64, fp64_peak, "stage2d_tma_kernel<double>",
+                                             kh)}
     out["fp32_vs_fp64_rel_l2_after_steps"] = float(
         torch.linalg.vector_norm(x32.to(torch.complex128) - x64) / torch.linalg.vector_norm(x64))
     m32, en32, _ = s32.invariants(x32)
@@ -679,7 +678,20 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_
     return out
 
 
-def run_other_grids(dev, barrier, max_over_ranks):
+def fp64_roofline(work, rate, fp64_peak, kernel, kh):
+    """ALU roofline of an FP64 stage kernel: achieved FP64 flops against the
+    measured FMA rate, and the FP64 issue slots used (one per DFMA, DADD or
+    DMUL) against the slots that rate implies (half the flop rate)."""
+    out = {"bound": "alu", "kernel": kernel, "achieved": None, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+           "frac": None, "peak_kind": "measured FP64 FMA rate (nlse_measure_fp64_rate)", "kernel_hash": kh}
+    if work:
+        out.update(achieved=work["flops"] * rate / 1e12, frac=work["flops"] * rate / fp64_peak,
+                   flops_per_update=work["flops"], fp64_instructions_per_update=work["instructions"],
+                   fp64_issue_frac=work["instructions"] * rate / (fp64_peak / 2))
+    return out
+
+
+def run_other_grids(dev, barrier, max_over_ranks, fp64_peak):
     """Step rates of the 3D vortex ring (512^3) and the 1D bright soliton
     (2048 points, the whole 2000-step run) in FP32 and FP64."""
     import torch
@@ -709,6 +721,10 @@ def run_other_grids(dev, barrier, max_over_ranks):
         else:
             bpu = BYTES_PER_UPDATE_FP32 if prec == "fp32" else BYTES_PER_UPDATE_FP64
             res["achieved_gbs"] = bpu * npts / (ms * 1e-3) / 1e9
+        if len(inst.shape) == 3 and prec == "fp64" and lap == "2shoc":
+            kh3 = _hash(("stage3d.cu", "nlse_device.cuh"))
+            res["roofline"] = fp64_roofline(FP64_WORK_3D.get(kh3), npts / (ms * 1e-3), fp64_peak,
+                                            "stage3d_kernel<double>", kh3)
         sv.close()
         return res
 
