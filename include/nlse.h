@@ -48,7 +48,9 @@ typedef enum {
     NLSE_EUNSTABLE = 4,     /* dt exceeds the stability bound of Eq. (kdfull)        */
     NLSE_ENONFINITE = 5,    /* a NaN or Inf appeared in the state                    */
     NLSE_ETIMEOUT = 6,      /* a bounded device-side wait gave up                    */
-    NLSE_EUNSUPPORTED = 7   /* valid request that this build does not implement      */
+    NLSE_EUNSUPPORTED = 7,  /* valid request that this build does not implement      */
+    NLSE_EBOUNDS = 8        /* bounds-check build (-DNLSE_BOUNDS_CHECK): a kernel met an
+                               index outside its array and skipped the access        */
 } nlse_status;
 
 /* Boundary conditions of Sec. 3.2. */
@@ -216,7 +218,14 @@ int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
  * compensated part: each call starts from psi_host with it zero.  As it
  * synchronises anyway, it returns the context's status as nlse_check does
  * (and clears it): a refusal of the entry check (psi_host unchanged), a
- * non-finite value produced by the steps (psi_host holds the result). */
+ * non-finite value produced by the steps (psi_host holds the result).
+ * A batch context moves the state in up to 8 chunks of consecutive instances
+ * of about equal size, on three internal streams ordered after the caller's:
+ * a chunk's copy in, its steps and its copy out overlap the neighbouring
+ * chunks' (the results are the bits of nlse_run).  Its entry check then runs
+ * per chunk: a refusal leaves the refused chunk's instances unchanged, the
+ * other chunks are stepped, and the refusal (naming the first refused
+ * instance) is returned. */
 int nlse_run_host(nlse_ctx* ctx, void* psi_host, int64_t nsteps, void* stream);
 
 /* Mass M = h^d sum |Psi|^2, energy
@@ -240,7 +249,8 @@ int nlse_reset_compensation(nlse_ctx* ctx, void* stream);
 
 /* No counterpart in the paper.
  * Synchronises the stream, reads the context's device status and clears it.
- * Returns, in this order of precedence: NLSE_ETIMEOUT if a kernel gave up a
+ * Returns, in this order of precedence: NLSE_EBOUNDS (bounds-check build
+ * only) if a kernel met an index outside its array; NLSE_ETIMEOUT if a kernel gave up a
  * bounded wait for its own data transfers; NLSE_EUNSTABLE if an entry check
  * of nlse_run found dt above the bound of Eq. (kdfull) (the message names the
  * instance, its dt and its bound); NLSE_ENONFINITE if an entry check found a

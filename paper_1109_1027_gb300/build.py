@@ -4,6 +4,12 @@ Each translation unit under ``csrc/`` is compiled by nvcc in parallel and the
 objects are linked into ``paper_1109_1027_gb300/lib/libnlse.so`` (static CUDA
 runtime, so the library needs nothing beyond the driver at load time).  A
 stamp of the sources and flags skips the build when nothing changed.
+
+``build(checked=True)`` builds the bounds-check variant ``libnlse_checked.so``
+from the same sources with -DNLSE_BOUNDS_CHECK: every kernel tests its
+indices before the access and reports NLSE_EBOUNDS instead of accessing out
+of range.  Loaded in place of the library through the NLSE_LIBRARY
+environment variable (tests run it in a child process).
 """
 from __future__ import annotations
 
@@ -19,6 +25,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libnlse.so")
+CHECKED_LIB = os.path.join(LIBDIR, "libnlse_checked.so")
 OBJDIR = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,7 +44,7 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stamp() -> str:
+def _stamp(flags) -> str:
     h = hashlib.sha1()
     files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
                                if f.endswith((".h", ".cuh")))
@@ -46,25 +53,29 @@ def _stamp() -> str:
         h.update(f.encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(NVCC_FLAGS).encode())
+    h.update(" ".join(flags).encode())
     return h.hexdigest()
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile (if needed) and return the path of libnlse.so."""
-    stamp = _stamp()
-    stamp_file = LIB + ".stamp"
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Compile (if needed) and return the path of libnlse.so, or with checked
+    of the bounds-check variant libnlse_checked.so."""
+    lib = CHECKED_LIB if checked else LIB
+    objdir = OBJDIR + ("_checked" if checked else "")
+    flags = NVCC_FLAGS + (["-DNLSE_BOUNDS_CHECK"] if checked else [])
+    stamp = _stamp(flags)
+    stamp_file = lib + ".stamp"
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         with open(stamp_file) as f:
             if f.read().strip() == stamp:
-                return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+                return lib
+    os.makedirs(objdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -75,15 +86,15 @@ def build(verbose: bool = False, force: bool = False) -> str:
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

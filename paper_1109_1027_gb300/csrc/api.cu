@@ -101,6 +101,15 @@ struct nlse_ctx {
     void* host_state;
     // Batch: per-instance table of the one-launch invariants (device).
     nlse::InvBatchEntry* inv_table;
+    // Pipelined host runs of a batch (nlse_run_host): chunks of consecutive
+    // instances whose copy in, steps and copy out overlap on three streams.
+    int hp_chunks;
+    std::vector<int> hp_first;          // first instance of each chunk (+ the count)
+    std::vector<int> check_row0;        // entry check: first row of each entry (+ the total)
+    cudaStream_t hp_stream[3];          // copy in, steps, copy out
+    cudaEvent_t hp_start, hp_done;
+    std::vector<cudaEvent_t> hp_ev;     // per chunk: copied in, stepped
+    nlse::StatusBlock* hp_status;       // per chunk (device): a chunk's refusal stops that chunk only
     // Instances of a stack (NLSE_FLAG_STACK), else 1.
     int stack;
     // Tiling choices (nlse_set_tiling); 0 = the default.
@@ -463,6 +472,9 @@ int setup_entry_check(nlse_ctx* c) {
         e.row1 = rows;
     }
     c->check_count = count;
+    c->check_row0.resize(count + 1);
+    for (int i = 0; i < count; ++i) c->check_row0[i] = tab[i].row0;
+    c->check_row0[count] = rows;
     c->check_nrows = rows;
     NLSE_CUDA(cudaMalloc((void**)&c->check_tab, sizeof(nlse::CheckEntry) * count), "allocating the check table");
     NLSE_CUDA(cudaMemcpy(c->check_tab, tab.data(), sizeof(nlse::CheckEntry) * count, cudaMemcpyHostToDevice),
@@ -472,7 +484,7 @@ int setup_entry_check(nlse_ctx* c) {
     NLSE_CUDA(cudaMalloc((void**)&c->status, sizeof(nlse::StatusBlock)), "allocating the status block");
     c->flag = &c->status->bits;
     NLSE_CUDA(cudaMemset(&c->status->bits, 0, sizeof(int)), "zeroing the status");
-    NLSE_CUDA(cudaMemset(&c->status->inst, 0x7f, sizeof(int)), "zeroing the status");
+    NLSE_CUDA(cudaMemset(&c->status->inst, 0x7f, 2 * sizeof(int)), "zeroing the status");
     return NLSE_OK;
 }
 
@@ -486,8 +498,11 @@ int report_status(nlse_ctx* c, const nlse::StatusBlock& s, cudaStream_t st) {
         NLSE_CUDA(cudaMemcpyAsync(&bound, c->check_bounds + s.inst, sizeof(double), cudaMemcpyDeviceToHost, st),
                   "bound copy");
     NLSE_CUDA(cudaMemsetAsync(&c->status->bits, 0, sizeof(int), st), "status reset");
-    NLSE_CUDA(cudaMemsetAsync(&c->status->inst, 0x7f, sizeof(int), st), "status reset");
+    NLSE_CUDA(cudaMemsetAsync(&c->status->inst, 0x7f, 2 * sizeof(int), st), "status reset");
     NLSE_CUDA(cudaStreamSynchronize(st), "status synchronise");
+    if (s.bits & nlse::kStatusBounds)
+        return fail(NLSE_EBOUNDS, "bounds-check build: an index outside its array at site %d (file %d, line %d); "
+                    "the access was skipped", s.site, s.site / 100000, s.site % 100000);
     if (s.bits & nlse::kStatusTimeout)
         return fail(NLSE_ETIMEOUT, "a bounded device-side wait gave up (a data transfer never completed)");
     const int inst = s.inst == kNoInstance ? 0 : s.inst;
@@ -501,6 +516,134 @@ int report_status(nlse_ctx* c, const nlse::StatusBlock& s, cudaStream_t st) {
         return fail(NLSE_ENONFINITE, "entry check of nlse_run (%s %d): the state holds non-finite values; the steps "
                     "were not taken", what, inst);
     return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
+}
+
+// Sets up the pipelined host run of a batch: up to 8 chunks of consecutive
+// instances of about equal points, their work lists, streams, events and
+// per-chunk status blocks.
+int setup_host_pipe(nlse_ctx* c) {
+    const int n = std::min(8, c->count);
+    std::vector<int> first(1, 0);
+    int64_t done = 0;
+    for (int i = 0; i < c->count; ++i) {
+        done += c->bparams[i].n[0] * c->bparams[i].n[1];
+        const int k = (int)first.size();                 // chunk being filled
+        if (k < n && done * n >= (int64_t)k * c->npts && i + 1 < c->count && c->count - (i + 1) >= n - k)
+            first.push_back(i + 1);
+    }
+    first.push_back(c->count);
+    const int nch = (int)first.size() - 1;
+    NLSE_CUDA(nlse::batch2d_set_chunks(c->batch, first), "building the chunk work lists");
+    for (cudaStream_t& sp : c->hp_stream) NLSE_CUDA(cudaStreamCreateWithFlags(&sp, cudaStreamNonBlocking), "stream");
+    NLSE_CUDA(cudaEventCreateWithFlags(&c->hp_start, cudaEventDisableTiming), "event");
+    NLSE_CUDA(cudaEventCreateWithFlags(&c->hp_done, cudaEventDisableTiming), "event");
+    c->hp_ev.assign(2 * nch, nullptr);
+    for (cudaEvent_t& ev : c->hp_ev) NLSE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    NLSE_CUDA(cudaMalloc((void**)&c->hp_status, sizeof(nlse::StatusBlock) * nch), "allocating chunk status");
+    c->hp_first = first;
+    c->hp_chunks = nch;
+    return NLSE_OK;
+}
+
+// The four fused stages of n RK4 steps on the instances of chunk k only,
+// with that chunk's status word (its refusal stops only its stage 4).
+int enqueue_chunk_steps(nlse_ctx* c, void* psi, int k, int64_t n, int* flag, cudaStream_t st) {
+    StageLaunch L = base_launch(c);
+    L.psi = psi;
+    L.psi_out = psi;
+    L.acc = c->acc;
+    L.lo = c->lo;
+    L.flag = flag;
+    const void* in[5] = {nullptr, psi, c->Y[0], c->Y[1], c->Y[0]};
+    void* out[5] = {nullptr, c->Y[0], c->Y[1], c->Y[0], nullptr};
+    for (int64_t i = 0; i < n; ++i)
+        for (int s = 1; s <= 4; ++s) {
+            L.stage = s;
+            L.yin = in[s];
+            L.yout = out[s];
+            cudaError_t e = nlse::batch2d_launch_chunk(c->batch, L, k, st);
+            if (e != cudaSuccess) return cuda_fail(e, "RK4 stage launch");
+        }
+    return NLSE_OK;
+}
+
+// nlse_run_host of a batch: per chunk, the copy in (stream 0), the entry check
+// and the steps (stream 1) and the copy out (stream 2), so that the copies of
+// one chunk overlap the steps of its neighbours.  The caller's stream orders
+// the whole and is synchronised at the end.
+int run_host_pipelined(nlse_ctx* c, void* psi_host, int64_t nsteps, cudaStream_t st) {
+    Range range("pipelined host run");
+    if (!c->hp_chunks) {
+        int rc = setup_host_pipe(c);
+        if (rc) return rc;
+    }
+    int rc = bind_maps(c, c->host_state, st);
+    if (rc) return rc;
+    c->state_psi = c->host_state;                 // its compensated part is zeroed per chunk below
+    const int nch = c->hp_chunks;
+    const size_t eb = c->p.prec == NLSE_FP32 ? 8 : 16;
+    cudaStream_t sin = c->hp_stream[0], scomp = c->hp_stream[1], sout = c->hp_stream[2];
+    NLSE_CUDA(cudaMemsetAsync(c->hp_status, 0, sizeof(nlse::StatusBlock) * nch, st), "chunk status reset");
+    NLSE_CUDA(cudaMemset2DAsync(&c->hp_status[0].inst, sizeof(nlse::StatusBlock), 0x7f, 2 * sizeof(int), nch, st),
+              "chunk status reset");
+    NLSE_CUDA(cudaEventRecord(c->hp_start, st), "event");
+    for (cudaStream_t sp : c->hp_stream) NLSE_CUDA(cudaStreamWaitEvent(sp, c->hp_start, 0), "stream wait");
+    char* dev = static_cast<char*>(c->host_state);
+    char* host = static_cast<char*>(psi_host);
+    for (int k = 0; k < nch; ++k) {
+        const int64_t o0 = c->boff[c->hp_first[k]];
+        const int64_t o1 = c->hp_first[k + 1] < c->count ? c->boff[c->hp_first[k + 1]] : c->npts;
+        NLSE_CUDA(cudaMemcpyAsync(dev + o0 * eb, host + o0 * eb, (o1 - o0) * eb, cudaMemcpyHostToDevice, sin),
+                  "state copy in");
+        NLSE_CUDA(cudaEventRecord(c->hp_ev[2 * k], sin), "event");
+    }
+    for (int k = 0; k < nch; ++k) {
+        const int i0 = c->hp_first[k], i1 = c->hp_first[k + 1];
+        const int64_t o0 = c->boff[i0], o1 = i1 < c->count ? c->boff[i1] : c->npts;
+        NLSE_CUDA(cudaStreamWaitEvent(scomp, c->hp_ev[2 * k], 0), "stream wait");
+        if (c->lo)
+            NLSE_CUDA(cudaMemsetAsync(static_cast<char*>(c->lo) + o0 * eb, 0, (o1 - o0) * eb, scomp),
+                      "zeroing the compensated part");
+        if (nsteps > 0 && !(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK)) {
+            nlse::CheckLaunch C;
+            C.table = c->check_tab;
+            C.inst_base = i0;
+            C.count = i1 - i0;
+            C.row_base = c->check_row0[i0];
+            C.nrows = c->check_row0[i1] - c->check_row0[i0];
+            C.prec = c->p.prec;
+            C.psi = c->host_state; C.lo = c->lo; C.V = c->V;
+            C.partials = c->check_partials;
+            C.bounds = c->check_bounds;
+            C.status = &c->hp_status[k];
+            NLSE_CUDA(nlse::launch_entry_check(C, scomp), "entry check launch");
+        }
+        if ((rc = enqueue_chunk_steps(c, c->host_state, k, nsteps, &c->hp_status[k].bits, scomp))) return rc;
+        NLSE_CUDA(cudaEventRecord(c->hp_ev[2 * k + 1], scomp), "event");
+    }
+    for (int k = 0; k < nch; ++k) {
+        const int64_t o0 = c->boff[c->hp_first[k]];
+        const int64_t o1 = c->hp_first[k + 1] < c->count ? c->boff[c->hp_first[k + 1]] : c->npts;
+        NLSE_CUDA(cudaStreamWaitEvent(sout, c->hp_ev[2 * k + 1], 0), "stream wait");
+        NLSE_CUDA(cudaMemcpyAsync(host + o0 * eb, dev + o0 * eb, (o1 - o0) * eb, cudaMemcpyDeviceToHost, sout),
+                  "state copy out");
+    }
+    NLSE_CUDA(cudaEventRecord(c->hp_done, sout), "event");
+    NLSE_CUDA(cudaStreamWaitEvent(st, c->hp_done, 0), "stream wait");
+    // The chunks' status blocks and the context's, merged.
+    std::vector<nlse::StatusBlock> hs(nch + 1);
+    NLSE_CUDA(cudaMemcpyAsync(hs.data(), c->hp_status, sizeof(nlse::StatusBlock) * nch, cudaMemcpyDeviceToHost, st),
+              "status copy");
+    NLSE_CUDA(cudaMemcpyAsync(&hs[nch], c->status, sizeof(nlse::StatusBlock), cudaMemcpyDeviceToHost, st),
+              "status copy");
+    NLSE_CUDA(cudaStreamSynchronize(st), "synchronise");
+    nlse::StatusBlock m = hs[nch];
+    for (int k = 0; k < nch; ++k) {
+        m.bits |= hs[k].bits;
+        m.inst = std::min(m.inst, hs[k].inst);
+        m.site = std::min(m.site, hs[k].site);
+    }
+    return report_status(c, m, st);
 }
 
 // Captures n RK4 steps on psi (n = 2^j) into c->graphs[j].
@@ -554,6 +697,13 @@ int run_graphs(nlse_ctx* c, void* psi, int64_t n, cudaStream_t st) {
 
 void release(nlse_ctx* c) {
     if (!c) return;
+    for (cudaStream_t& sp : c->hp_stream)
+        if (sp) cudaStreamDestroy(sp);
+    for (cudaEvent_t ev : c->hp_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->hp_start) cudaEventDestroy(c->hp_start);
+    if (c->hp_done) cudaEventDestroy(c->hp_done);
+    cudaFree(c->hp_status);
     cudaFree(c->adj_buf);
     cudaFree(c->host_state);
     cudaFree(c->inv_table);
@@ -1080,6 +1230,7 @@ int nlse_run_host(nlse_ctx* c, void* psi_host, int64_t nsteps, void* stream) {
     if (nsteps < 0) return fail(NLSE_EINVAL, "nsteps must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (!c->host_state) NLSE_CUDA(cudaMalloc(&c->host_state, c->cbytes), "allocating the device state");
+    if (c->batch && c->count > 1) return run_host_pipelined(c, psi_host, nsteps, st);
     NLSE_CUDA(cudaMemcpyAsync(c->host_state, psi_host, c->cbytes, cudaMemcpyHostToDevice, st), "state copy in");
     if (c->state_psi == c->host_state) c->state_psi = nullptr;    // a new state: no compensated part yet
     int rc = nlse_run(c, c->host_state, nsteps, stream);

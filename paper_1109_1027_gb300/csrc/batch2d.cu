@@ -138,6 +138,12 @@ struct BatchPlan {
     int nt[2] = {32, 128};
     int narrow = 64;
     const void* bases[6] = {};                // psi, Y0, Y1, acc, lo, V
+    // Work lists of consecutive instance ranges (chunks) for a pipelined host
+    // run: chunk k covers instances [chunk_first[k], chunk_first[k+1]).
+    std::vector<int> chunk_first;
+    int4* chunk_tiles = nullptr;              // per chunk: group 0 then group 1
+    std::vector<int> chunk_off;               // first tile of chunk k's group g: chunk_off[2k + g]
+    std::vector<int> chunk_n;                 // tiles of chunk k's group g: chunk_n[2k + g]
 };
 
 bool batch2d_instance_ok(const nlse_params& p) {
@@ -145,6 +151,8 @@ bool batch2d_instance_ok(const nlse_params& p) {
 }
 
 int64_t batch2d_points(const nlse_params& p) { return p.n[0] * p.n[1]; }
+
+cudaError_t build_chunk_tiles(BatchPlan* b);
 
 // Tile lists: instances with n[0] <= narrow get 64-column tiles (one warp),
 // the rest 256-column tiles; largest instances first.
@@ -177,6 +185,40 @@ cudaError_t build_tiles(BatchPlan* b, int narrow) {
         e = cudaMemcpy(b->tiles + lists[0].size(), lists[1].data(), sizeof(int4) * lists[1].size(),
                        cudaMemcpyHostToDevice);
     b->narrow = narrow;
+    if (e == cudaSuccess && !b->chunk_first.empty()) e = build_chunk_tiles(b);
+    return e;
+}
+
+// The work lists of every chunk, built like the full lists (largest instance
+// of the chunk first) from the current tile groups.
+cudaError_t build_chunk_tiles(BatchPlan* b) {
+    const int nch = (int)b->chunk_first.size() - 1;
+    std::vector<int4> all;
+    b->chunk_off.assign(2 * nch, 0);
+    b->chunk_n.assign(2 * nch, 0);
+    for (int k = 0; k < nch; ++k) {
+        std::vector<int> order;
+        for (int i = b->chunk_first[k]; i < b->chunk_first[k + 1]; ++i) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (int64_t)b->host[x].nx * b->host[x].ny > (int64_t)b->host[y].nx * b->host[y].ny;
+        });
+        for (int g = 0; g < 2; ++g) {
+            b->chunk_off[2 * k + g] = (int)all.size();
+            for (int i : order) {
+                const BatchDesc& d = b->host[i];
+                if ((d.nt == 32 ? 0 : 1) != g) continue;
+                const int txc = 2 * d.nt;
+                for (int y0 = 0; y0 < d.ny; y0 += TYB)
+                    for (int x0 = 0; x0 < d.nx; x0 += txc) all.push_back(make_int4(i, x0, y0, 0));
+            }
+            b->chunk_n[2 * k + g] = (int)all.size() - b->chunk_off[2 * k + g];
+        }
+    }
+    cudaFree(b->chunk_tiles);
+    b->chunk_tiles = nullptr;
+    cudaError_t e = cudaMalloc((void**)&b->chunk_tiles, sizeof(int4) * (all.empty() ? 1 : all.size()));
+    if (e != cudaSuccess) return e;
+    if (!all.empty()) e = cudaMemcpy(b->chunk_tiles, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice);
     return e;
 }
 
@@ -187,6 +229,13 @@ cudaError_t batch2d_retile(BatchPlan* b, int narrow) {
 }
 
 int batch2d_narrow(const BatchPlan* b) { return b->narrow; }
+
+cudaError_t batch2d_set_chunks(BatchPlan* b, const std::vector<int>& first) {
+    b->chunk_first = first;
+    return build_chunk_tiles(b);
+}
+
+int batch2d_chunks(const BatchPlan* b) { return b->chunk_first.empty() ? 0 : (int)b->chunk_first.size() - 1; }
 
 cudaError_t batch2d_create(int count, const nlse_params* p, const void* V, void* Y0, void* Y1, void* acc,
                            void* lo, BatchPlan** out) {
@@ -244,20 +293,33 @@ cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st) {
     return cudaMemcpyAsync(b->dev, b->host, sizeof(BatchDesc) * b->count, cudaMemcpyHostToDevice, st);
 }
 
-cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st) {
+namespace {
+cudaError_t launch_lists(BatchPlan* b, const StageLaunch& L, const int4* const lists[2], const int n[2],
+                         cudaStream_t st) {
     // Same walk-direction alternation between stages as the single-grid kernel.
     const int dir = (L.stage % 2 == 0 && L.stage != 0) ? -1 : 1;
-    const int4* lists[2] = {b->tiles, b->tiles + b->ntiles[0]};
     for (int g = 0; g < 2; ++g) {
-        if (!b->ntiles[g]) continue;
+        if (!n[g]) continue;
         cudaError_t e;
-        if (b->prec == 0) e = launch_stage_r<float>(L.stage, b->lap, b->nt[g], b->dev, lists[g], b->ntiles[g],
+        if (b->prec == 0) e = launch_stage_r<float>(L.stage, b->lap, b->nt[g], b->dev, lists[g], n[g],
                                                     make_io<float>(L), dir, st);
-        else e = launch_stage_r<double>(L.stage, b->lap, b->nt[g], b->dev, lists[g], b->ntiles[g],
+        else e = launch_stage_r<double>(L.stage, b->lap, b->nt[g], b->dev, lists[g], n[g],
                                         make_io<double>(L), dir, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st) {
+    const int4* lists[2] = {b->tiles, b->tiles + b->ntiles[0]};
+    return launch_lists(b, L, lists, b->ntiles, st);
+}
+
+cudaError_t batch2d_launch_chunk(BatchPlan* b, const StageLaunch& L, int k, cudaStream_t st) {
+    const int4* lists[2] = {b->chunk_tiles + b->chunk_off[2 * k], b->chunk_tiles + b->chunk_off[2 * k + 1]};
+    const int n[2] = {b->chunk_n[2 * k], b->chunk_n[2 * k + 1]};
+    return launch_lists(b, L, lists, n, st);
 }
 
 void batch2d_destroy(BatchPlan* b) {
@@ -265,6 +327,7 @@ void batch2d_destroy(BatchPlan* b) {
     cudaFreeHost(b->host);
     cudaFree(b->dev);
     cudaFree(b->tiles);
+    cudaFree(b->chunk_tiles);
     delete b;
 }
 

@@ -142,8 +142,8 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __restrict__ tab, int count,
                                                            const cplx<R>* __restrict__ psi,
                                                            const cplx<R>* __restrict__ lo, const R* __restrict__ V,
-                                                           double* __restrict__ partials) {
-    const int b = blockIdx.x;
+                                                           double* __restrict__ partials, int row_base) {
+    const int b = row_base + blockIdx.x;
     const CheckEntry e = tab[entry_of(tab, count, b)];
     const int64_t nblk = e.row1 - e.row0;
     const int64_t per = (e.npts + nblk - 1) / nblk;
@@ -187,8 +187,10 @@ __global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __re
 // bound is written to bounds[].
 __global__ void __launch_bounds__(kThreads) check_final(const CheckEntry* __restrict__ tab,
                                                          const double* __restrict__ partials,
-                                                         double* __restrict__ bounds, StatusBlock* status) {
-    const CheckEntry e = tab[blockIdx.x];
+                                                         double* __restrict__ bounds, StatusBlock* status,
+                                                         int inst_base) {
+    const int inst = inst_base + (int)blockIdx.x;
+    const CheckEntry e = tab[inst];
     Ext a = ext_identity();
     for (int r = e.row0 + threadIdx.x; r < e.row1; r += kThreads) {
         const double* row = partials + (int64_t)r * 3;
@@ -197,13 +199,13 @@ __global__ void __launch_bounds__(kThreads) check_final(const CheckEntry* __rest
     a = ext_block_reduce(a);
     if (threadIdx.x != 0) return;
     const double bound = dt_bound(e.dim, e.h, e.a, e.h2a * a.umin, e.h2a * a.umax, 0.0);
-    bounds[blockIdx.x] = bound;
+    bounds[inst] = bound;
     int bit = 0;
     if (a.bad != 0.0) bit = kStatusEntryNonFinite;
     else if (!(e.dt <= bound)) bit = kStatusUnstable;
     if (bit) {
         atomicOr(&status->bits, bit);
-        atomicMin(&status->inst, (int)blockIdx.x);
+        atomicMin(&status->inst, inst);
     }
 }
 
@@ -236,15 +238,19 @@ int check_rows(int64_t npts) {
 }
 
 cudaError_t launch_entry_check(const CheckLaunch& C, cudaStream_t st) {
+    // The entries [inst_base, inst_base + count) and their rows [row_base, row_base + nrows).
+    const int total = C.inst_base + C.count;
     if (C.prec == 0)
-        check_partial<float><<<C.nrows, kThreads, 0, st>>>(C.table, C.count, (const float2*)C.psi,
-                                                           (const float2*)C.lo, (const float*)C.V, C.partials);
+        check_partial<float><<<C.nrows, kThreads, 0, st>>>(C.table, total, (const float2*)C.psi,
+                                                           (const float2*)C.lo, (const float*)C.V, C.partials,
+                                                           C.row_base);
     else
-        check_partial<double><<<C.nrows, kThreads, 0, st>>>(C.table, C.count, (const double2*)C.psi,
-                                                            (const double2*)C.lo, (const double*)C.V, C.partials);
+        check_partial<double><<<C.nrows, kThreads, 0, st>>>(C.table, total, (const double2*)C.psi,
+                                                            (const double2*)C.lo, (const double*)C.V, C.partials,
+                                                            C.row_base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    check_final<<<C.count, kThreads, 0, st>>>(C.table, C.partials, C.bounds, C.status);
+    check_final<<<C.count, kThreads, 0, st>>>(C.table, C.partials, C.bounds, C.status, C.inst_base);
     return cudaGetLastError();
 }
 

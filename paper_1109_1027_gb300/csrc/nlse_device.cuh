@@ -41,6 +41,33 @@ __device__ __forceinline__ bool refused(const int* flag) {
     return (*(const volatile int*)flag & kStatusRefused) != 0;
 }
 
+// Bounds-check build (compiled with -DNLSE_BOUNDS_CHECK): the kernels test
+// their shared-memory and global indices (and the 16-byte alignment of their
+// TMA coordinates) before the access.  An index outside its array sets
+// kStatusBounds in the status word and records the smallest failing site
+// (file id * 100000 + source line), and the access is skipped: nothing traps.
+// nlse_check then returns NLSE_EBOUNDS.  In the normal build every check is
+// the constant true and compiles away.
+#ifdef NLSE_BOUNDS_CHECK
+static __device__ __noinline__ bool bounds_fail(int* flag, int site) {
+    atomicOr(flag, kStatusBounds);
+    atomicMin(flag + 2, site);              // StatusBlock::site
+    return false;
+}
+__device__ __forceinline__ bool idx_ok(int* flag, int64_t i, int64_t n, int site) {
+    return (i >= 0 && i < n) ? true : bounds_fail(flag, site);
+}
+#define NLSE_IDX(flag, i, n, file) ::nlse::idx_ok((flag), (int64_t)(i), (int64_t)(n), (file) * 100000 + __LINE__)
+#define NLSE_ALIGN16(flag, bytes, file) \
+    ::nlse::idx_ok((flag), ((int64_t)(bytes)) % 16 == 0 ? 0 : -1, 1, (file) * 100000 + __LINE__)
+#else
+#define NLSE_IDX(flag, i, n, file) true
+#define NLSE_ALIGN16(flag, bytes, file) true
+#endif
+// File ids of the check sites.
+constexpr int kSiteTile2d = 1, kSiteTma3d = 2, kSiteStage1d = 3, kSiteStage2d = 4, kSiteStage3d = 5,
+              kSiteFused = 6, kSiteResident1d = 7, kSitePlain = 8, kSiteCheck = 9;
+
 // Row within its stacked instance of grid row r >= 0 (instances of rows1 rows;
 // without a stack rows1 is the grid's row count and r is returned undivided).
 __device__ __forceinline__ int inst_row(int r, int rows1) { return r < rows1 ? r : r % rows1; }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nlse.h"
 
 namespace nlse {
@@ -18,9 +20,13 @@ constexpr int kStatusTimeout = 2;          // a bounded device-side wait gave up
 constexpr int kStatusUnstable = 4;         // entry check: dt above the bound of Eq. (kdfull)
 constexpr int kStatusEntryNonFinite = 8;   // entry check: the state held a NaN or Inf
 constexpr int kStatusRefused = kStatusUnstable | kStatusEntryNonFinite;
+constexpr int kStatusBounds = 16;          // bounds-check build: an index outside its array
 struct StatusBlock {
     int bits;
     int inst;               // smallest instance the entry check refused (0x7f7f7f7f: none)
+    int site;               // bounds-check build: smallest failing site, file * 100000 + line
+                            // (0x7f7f7f7f: none)
+    int pad;
 };
 
 // One launch of a fused RK4 stage (stage 1..4) or of the standalone
@@ -122,6 +128,13 @@ cudaError_t batch2d_bind(BatchPlan* b, const void* psi, cudaStream_t st);
 cudaError_t batch2d_retile(BatchPlan* b, int narrow);   // synchronises the device
 int batch2d_narrow(const BatchPlan* b);
 cudaError_t batch2d_launch(BatchPlan* b, const StageLaunch& L, cudaStream_t st);
+// Chunks of consecutive instances for a pipelined host run: first[k] is the
+// first instance of chunk k, first.back() the instance count.  Their work
+// lists follow the tile groups (rebuilt with them).
+cudaError_t batch2d_set_chunks(BatchPlan* b, const std::vector<int>& first);
+int batch2d_chunks(const BatchPlan* b);
+// One RK4 stage (or the Laplacian) of chunk k's instances only.
+cudaError_t batch2d_launch_chunk(BatchPlan* b, const StageLaunch& L, int k, cudaStream_t st);
 void batch2d_destroy(BatchPlan* b);
 
 // Adjoint of one RK4 stage on a 2D grid (adjoint2d.cu).
@@ -207,8 +220,10 @@ constexpr int kMaxCheckRowsPerEntry = 2048;
 // Rows of partials (blocks of the check) for an instance of npts points.
 int check_rows(int64_t npts);
 struct CheckLaunch {
-    const CheckEntry* table;    // device, count entries, row0 ascending
-    int count, nrows, prec;
+    const CheckEntry* table;    // device, all entries, row0 ascending
+    int count, nrows, prec;     // checks entries inst_base .. inst_base + count - 1, whose rows
+    int inst_base = 0;          // are row_base .. row_base + nrows - 1
+    int row_base = 0;
     const void* psi;
     const void* lo;             // FP32 compensated part or nullptr
     const void* V;

@@ -45,7 +45,8 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
         int g = x0 - 2 + j;
         const C* q = sP + j + 1;
         C d = czero<C>();
-        if (g == 0 || g == n - 1) d = dirichlet_D(c, q[0], io.V[g]);
+        if (!NLSE_IDX(io.flag, j + 2, NP, kSiteStage1d)) continue;
+        if ((g == 0 || g == n - 1) && NLSE_IDX(io.flag, g, n, kSiteStage1d)) d = dirichlet_D(c, q[0], io.V[g]);
         else if (g > 0 && g < n - 1)
             d = cscale(c.inv_h2, csub(cadd(q[1], q[-1]), cscale((R)2, q[0])));
         sD[j] = d;
@@ -59,7 +60,9 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
             int j = g - (x0 - 2);
             if (j >= 0 && j < ND) {
                 int jq = qg - (x0 - 2);
-                sD[j] = msd_D(c, sP[j + 1], io.V[g], sP[jq + 1], io.V[qg], sD[jq]);
+                if (NLSE_IDX(io.flag, jq, ND, kSiteStage1d) && NLSE_IDX(io.flag, j + 1, NP, kSiteStage1d) &&
+                    NLSE_IDX(io.flag, jq + 1, NP, kSiteStage1d))
+                    sD[j] = msd_D(c, sP[j + 1], io.V[g], sP[jq + 1], io.V[qg], sD[jq]);
             }
         }
         __syncthreads();
@@ -70,6 +73,7 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
         int g = x0 - 1 + j;
         const C* e = sD + j + 1;
         C out = czero<C>();
+        if (!(NLSE_IDX(io.flag, j + 2, ND, kSiteStage1d) && NLSE_IDX(io.flag, j + 2, NP, kSiteStage1d))) continue;
         if (g >= 0 && g < n) {
             bool bnd = (g == 0 || g == n - 1);
             C lap = (bnd || CD) ? e[0]
@@ -86,6 +90,7 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
     for (int j = tid; j < T; j += NT) {
         int g = x0 + j;
         if (g >= n) break;
+        if (!(NLSE_IDX(io.flag, j + 1, NF, kSiteStage1d) && NLSE_IDX(io.flag, j + 3, NP, kSiteStage1d))) continue;
         C v = sF[j + 1];
         if constexpr (STAGE == 0) {
             io.lap[g] = v;
@@ -93,7 +98,8 @@ stage1d_kernel(StageIO<R> io, Coef<R> c, int n) {
             const C y = sP[j + 3];
             if (MSD && (g == 0 || g == n - 1)) {
                 int qg = g == 0 ? 1 : n - 2;
-                v = msd_F(y, sP[qg - (x0 - 3)], sF[qg - (x0 - 1)]);
+                if (NLSE_IDX(io.flag, qg - (x0 - 3), NP, kSiteStage1d) && NLSE_IDX(io.flag, qg - (x0 - 1), NF, kSiteStage1d))
+                    v = msd_F(y, sP[qg - (x0 - 3)], sF[qg - (x0 - 1)]);
             }
             bad |= stage_epilogue<STAGE>(io, g, y, v);
         }

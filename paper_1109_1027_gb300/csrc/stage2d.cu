@@ -61,6 +61,10 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         int ly = i / DX, lx = i - ly * DX;
         int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const C* q = sP + (ly + 1) * PX + (lx + 1);
+        // (the five-point window q -+ 1, q -+ PX inside the staged tile)
+        if (!(NLSE_IDX(io.flag, (ly + 1) * PX + lx + 1 - PX, PX * PY, kSiteStage2d) &&
+              NLSE_IDX(io.flag, (ly + 1) * PX + lx + 1 + PX, PX * PY, kSiteStage2d)))
+            continue;
         C d = czero<C>();
         if constexpr (MS) {
             C dx = czero<C>(), dy = czero<C>();
@@ -70,7 +74,7 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
                 dy = cscale(c.inv_h2, csub(cadd(q[-PX], q[PX]), cscale((R)2, pc)));
                 const int gyl = inst_row(gy, io.rows1);
                 const bool bx = gx == 0 || gx == nx - 1, by = gyl == 0 || gyl == io.rows1 - 1;
-                if (bx || by) {
+                if ((bx || by) && NLSE_IDX(io.flag, (int64_t)gyl * nx + gx, (int64_t)io.rows1 * nx, kSiteStage2d)) {
                     const C lb = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
                     if (bx && by) dx = dy = czero<C>();
                     else if (bx) dx = csub(lb, dy);
@@ -85,7 +89,8 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
             C pc = q[0];
             const int gyl = inst_row(gy, io.rows1);
             if (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1) {
-                d = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
+                if (NLSE_IDX(io.flag, (int64_t)gyl * nx + gx, (int64_t)io.rows1 * nx, kSiteStage2d))
+                    d = dirichlet_D(c, pc, io.V[(int64_t)gyl * nx + gx]);
             } else {
                 C sum = cadd(cadd(q[1], q[-1]), cadd(q[PX], q[-PX]));
                 d = cscale(c.inv_h2, csub(sum, cscale((R)4, pc)));
@@ -107,6 +112,14 @@ stage2d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny) {
         const C y = q[0];
         const int gyl = inst_row(gy, io.rows1);
         const int64_t pv = (int64_t)gyl * nx + gx;     // V is shared by stacked instances
+        // (the windows in the staged tile and in D, the output and V indices)
+        if (!(NLSE_IDX(io.flag, (ly + 2) * PX + lx + 2 - PX - 1, PX * PY, kSiteStage2d) &&
+              NLSE_IDX(io.flag, (ly + 2) * PX + lx + 2 + PX + 1, PX * PY, kSiteStage2d) &&
+              NLSE_IDX(io.flag, (ly + 1) * DX + lx + 1 - DX, DX * DY, kSiteStage2d) &&
+              NLSE_IDX(io.flag, (ly + 1) * DX + lx + 1 + DX, DX * DY, kSiteStage2d) &&
+              NLSE_IDX(io.flag, p, (int64_t)nx * ny, kSiteStage2d) &&
+              NLSE_IDX(io.flag, pv, (int64_t)io.rows1 * nx, kSiteStage2d)))
+            continue;
         const bool bnd = (gx == 0 || gx == nx - 1 || gyl == 0 || gyl == io.rows1 - 1);
         C lap;
         if (MS) {

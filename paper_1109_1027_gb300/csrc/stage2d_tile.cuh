@@ -131,6 +131,27 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
     };
     const int rl_base = ybase % io.rows1;
 
+#ifdef NLSE_BOUNDS_CHECK
+    {
+        // This thread's column window k-1 .. k+2 and the CTA's halo columns in
+        // the row buffers, its epilogue slots, the tile origin, the TMA x
+        // coordinates' 16-byte alignment, and the dynamic shared memory the
+        // launch gave against the layout.
+        const int kk = 2 * t + 2;
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const bool okb = NLSE_IDX(io.flag, kk - 1, L::ROW, kSiteTile2d) && NLSE_IDX(io.flag, kk + 2, L::ROW, kSiteTile2d) &&
+                         NLSE_IDX(io.flag, TXC + 3, L::ROW, kSiteTile2d) && NLSE_IDX(io.flag, 2 * t + 1, TXC, kSiteTile2d) &&
+                         NLSE_IDX(io.flag, x0, nx, kSiteTile2d) && NLSE_IDX(io.flag, y0, ny, kSiteTile2d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)(x0 - 2) * L::CB, kSiteTile2d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)(x0 - 2 + HB) * L::CB, kSiteTile2d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)x0 * L::CB, kSiteTile2d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)x0 * (int64_t)sizeof(R), kSiteTile2d) &&
+                         NLSE_IDX(io.flag, L::TOTAL - 1, dyn, kSiteTile2d);
+        if (__syncthreads_or(!okb)) return;
+    }
+#endif
+
     if (t == 0) {
         tma_prefetch_desc(m_in);
         tma_prefetch_desc(m_in2);
@@ -154,6 +175,8 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         const uint32_t dst = sbase + L::E_OFF + (e & 1) * L::E_SLOT;
         const uint32_t bar = ebar0 + 8 * (e & 1);
         const int r = ybase + dir * e;
+        // (TMA loads outside the grid read the fill value; the rows are checked for the record only.)
+        (void)(NLSE_IDX(io.flag, r, ny, kSiteTile2d) && NLSE_IDX(io.flag, erl, io.rows1, kSiteTile2d));
         uint32_t bytes = L::V_BYTES;
         if (NEED_PA) bytes += 2 * L::T_BYTES;
         if (NEED_LO) bytes += L::T_BYTES;
@@ -204,11 +227,16 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
     // D at grid point (x, r), rl its row within its instance, from its five
     // stencil values (boundary: Eq. dbc_lap, V read from global memory;
     // outside the grid: 0, never used).
+    // V at (x, row rl of its instance), read from global memory at boundary points.
+    auto vat = [&](int rl, int x) -> R {
+        const int64_t q = (int64_t)rl * nx + x;
+        return NLSE_IDX(io.flag, q, (int64_t)io.rows1 * nx, kSiteTile2d) ? io.V[q] : R(0);
+    };
     auto dpoint = [&](int x, int r, int rl, C ctr, C up, C dn, C lf, C rt) -> C {
         if constexpr (!INNER) {
             if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
             if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
-                return bnd_D(ctr, io.V[(int64_t)rl * nx + x]);
+                return bnd_D(ctr, vat(rl, x));
         }
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
@@ -221,7 +249,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         if constexpr (INNER) return d;
         const bool bx = x == 0 || x == nx - 1, by = rl == 0 || rl == io.rows1 - 1;
         if (bx || by) {
-            const C lb = bnd_D(ctr, io.V[(int64_t)rl * nx + x]);
+            const C lb = bnd_D(ctr, vat(rl, x));
             if (bx && by) d = {czero<C>(), czero<C>()};
             else if (bx) d.a = sub2(lb, d.b);
             else d.b = sub2(lb, d.a);
@@ -320,7 +348,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         // carries ok = false to that barrier, where the CTA stops together.
         if (NEED_E) wait_e(i);
 
-        if (xin) {
+        if (xin && NLSE_IDX(io.flag, (int64_t)y * nx + xa + 1, (int64_t)nx * ny, kSiteTile2d)) {
             const C* dr = dring + (j & 1) * L::ROW;          // dr[k-1] = D(xa-1, y), dr[k+2] = D(xa+2, y)
             const bool rowb = !INNER && (yl == 0 || yl == io.rows1 - 1);
             const bool ba = !INNER && (rowb || xa == 0), bb = !INNER && (rowb || xa + 1 == nx - 1);
@@ -332,8 +360,8 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
                 lap.a = fma2(c76, add2(dx0.a, d0.a), mul2(m12, sa));
                 lap.b = fma2(c76, add2(dx0.b, d0.b), mul2(m12, sb));
                 if (STAGE == 0) {
-                    if (ba) lap.a = dirichlet_D(c, c0.a, io.V[(int64_t)yl * nx + xa]);
-                    if (bb) lap.b = dirichlet_D(c, c0.b, io.V[(int64_t)yl * nx + xa + 1]);
+                    if (ba) lap.a = dirichlet_D(c, c0.a, vat(yl, xa));
+                    if (bb) lap.b = dirichlet_D(c, c0.b, vat(yl, xa + 1));
                 }
             } else if (!CD) {
                 const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));

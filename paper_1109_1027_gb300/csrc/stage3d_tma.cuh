@@ -113,6 +113,34 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
     const uint32_t sbase = smem_u32(smem);
     const uint32_t ibar0 = sbase + L::BAR_OFF, ebar0 = ibar0 + 8 * S;
 
+#ifdef NLSE_BOUNDS_CHECK
+    {
+        // This thread's window in a plane buffer (k -+ PW -+ 1 .. 2) and its
+        // halo slot, its epilogue slots, the tile origin, the TMA x
+        // coordinates' 16-byte alignment and the dynamic shared memory given.
+        const int kk = (ty + 2) * PW + 2 * tx + 2;
+        int hkk = -1;
+        if (t < TY) hkk = (t + 2) * PW + 1;
+        else if (t < 2 * TY) hkk = (t - TY + 2) * PW + TX + 2;
+        else if (t < 2 * TY + TX) hkk = PW + (t - 2 * TY) + 2;
+        else if (t < 2 * TY + 2 * TX) hkk = (TY + 2) * PW + (t - 2 * TY - TX) + 2;
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const bool okb = NLSE_IDX(io.flag, kk - PW - 1, PW * PH, kSiteTma3d) &&
+                         NLSE_IDX(io.flag, kk + PW + 2, PW * PH, kSiteTma3d) &&
+                         (hkk < 0 || (NLSE_IDX(io.flag, hkk - PW, PW * PH, kSiteTma3d) &&
+                                      NLSE_IDX(io.flag, hkk + PW, PW * PH, kSiteTma3d))) &&
+                         NLSE_IDX(io.flag, ty * TX + 2 * tx + 1, TX * TY, kSiteTma3d) &&
+                         NLSE_IDX(io.flag, x0, nx, kSiteTma3d) && NLSE_IDX(io.flag, y0, ny, kSiteTma3d) &&
+                         NLSE_IDX(io.flag, z0, nz, kSiteTma3d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)(x0 - 2) * L::CB, kSiteTma3d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)x0 * L::CB, kSiteTma3d) &&
+                         NLSE_ALIGN16(io.flag, (int64_t)x0 * 4, kSiteTma3d) &&
+                         NLSE_IDX(io.flag, L::TOTAL - 1, dyn, kSiteTma3d);
+        if (__syncthreads_or(!okb)) return;
+    }
+#endif
+
     if (t == 0) {
         tma_prefetch_desc(&m_in);
         for (int s = 0; s < S + 2; ++s) mbar_init(ibar0 + 8 * s, 1);
@@ -183,9 +211,11 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
 
     // D at (x, y, z) from its seven stencil values; the caller passes whether
     // the point is outside the grid or on its boundary (Eq. dbc_lap).
+    [[maybe_unused]] const int64_t npts = (int64_t)nx * ny * nz;
+    auto vat = [&](int64_t gp) -> float { return NLSE_IDX(io.flag, gp, npts, kSiteTma3d) ? io.V[gp] : 0.f; };
     auto dval = [&](bool out, bool bnd, int64_t gp, C ctr, C s6) -> C {
         if (out) return czero<C>();
-        if (bnd) return dirichlet_D(c, ctr, io.V[gp]);
+        if (bnd) return dirichlet_D(c, ctr, vat(gp));
         return mul2(fma2(m6, ctr, s6), ih2);
     };
     // Multi-storage step 1 at one point, (D^x, D^y, D^z), from the centre and
@@ -198,7 +228,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         D3 d{mul2(fma2(m2, ctr, xs), ih2), mul2(fma2(m2, ctr, ys), ih2), mul2(fma2(m2, ctr, zs), ih2)};
         const int nb = (int)bx + (int)by + (int)bz;
         if (nb) {
-            const C lb = dirichlet_D(c, ctr, io.V[gp]);
+            const C lb = dirichlet_D(c, ctr, vat(gp));
             if (nb > 1) d = {czero<C>(), czero<C>(), czero<C>()};
             else if (bx) d.x = sub2(sub2(lb, d.y), d.z);
             else if (by) d.y = sub2(sub2(lb, d.x), d.z);
@@ -350,7 +380,7 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
         // carries ok = false to that barrier, where the CTA stops together.
         if (NEED_E) wait_e(i);
 
-        if (pin) {
+        if (pin && NLSE_IDX(io.flag, ((int64_t)z * ny + y) * nx + xa + 1, npts, kSiteTma3d)) {
             const C* pz = iplane(j);
             const C* dz = dring + (j & 1) * (PW * PH);
             const bool zb = zbnd(z);
@@ -367,8 +397,8 @@ stage3d_tma_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_consta
                 lap.b = fma2(c76, add2(add2(dx0.b, dy0.b), d0.b), mul2(m12, sb));
                 if (STAGE == 0) {
                     const int64_t pg = ((int64_t)z * ny + y) * nx + xa;
-                    if (bA) lap.a = dirichlet_D(c, c0.a, io.V[pg]);
-                    if (bB) lap.b = dirichlet_D(c, c0.b, io.V[pg + 1]);
+                    if (bA) lap.a = dirichlet_D(c, c0.a, vat(pg));
+                    if (bB) lap.b = dirichlet_D(c, c0.b, vat(pg + 1));
                 }
             } else if (!CD) {
                 // six axial D

@@ -21,7 +21,7 @@ import torch
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED = range(8)
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ENONFINITE, ETIMEOUT, EUNSUPPORTED, EBOUNDS = range(9)
 BC = {"dirichlet": 0, "msd": 1, "periodic": 2, "lapzero": 3}
 PREC = {"fp32": 0, "fp64": 1}
 LAP = {"2shoc": 0, "cd": 1, "2shoc_ms": 2}
@@ -31,7 +31,7 @@ FLAG_STACK = 4
 TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW, TILE_1D_RESIDENT, TILE_2D_FUSE = 1, 2, 3, 4, 5
 
 _STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
-                 "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
+                 "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED", "NLSE_EBOUNDS"]
 
 
 class NLSEError(RuntimeError):
@@ -60,7 +60,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_missing else _build.LIB
+    override = os.environ.get("NLSE_LIBRARY")       # e.g. the bounds-check build (build.build(checked=True))
+    if override:
+        path = override
+    else:
+        path = _build.build() if build_if_missing else _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libnlse.so not found at {path}; build it with "
                            "paper_1109_1027_gb300.build.build()")

@@ -132,9 +132,9 @@ def test_binding_constants_match_the_header():
     boundary, precision or schedule to the library)."""
     h = _header_constants()
     statuses = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE", "NLSE_ENONFINITE",
-                "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED"]
+                "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED", "NLSE_EBOUNDS"]
     assert [h[n] for n in statuses] == [nlse.OK, nlse.EINVAL, nlse.ENOMEM, nlse.ECUDA, nlse.EUNSTABLE,
-                                        nlse.ENONFINITE, nlse.ETIMEOUT, nlse.EUNSUPPORTED]
+                                        nlse.ENONFINITE, nlse.ETIMEOUT, nlse.EUNSUPPORTED, nlse.EBOUNDS]
     assert {k: h["NLSE_BC_" + {"lapzero": "LAPZERO"}.get(k, k.upper())] for k in nlse.BC} == nlse.BC
     assert {k: h["NLSE_" + k.upper()] for k in nlse.PREC} == nlse.PREC
     assert {k: h["NLSE_LAP_" + k.upper()] for k in nlse.LAP} == nlse.LAP

@@ -191,3 +191,46 @@ def test_batch_invariants_equal_the_single_grid_ones(prec):
                          prec=prec)
         mi, ei, di = sv.invariants(torch.from_numpy(q["psi"]).to(DEV).to(cdt).contiguous())
         assert (m[i], e[i], d[i]) == (mi, ei, di), (i, q["shape"])
+
+
+@pytest.mark.parametrize("prec,check", [("fp32", True), ("fp32", False), ("fp64", True)])
+def test_batch_run_host_equals_a_device_run(prec, check):
+    """nlse_run_host of a batch moves the state in chunks of instances whose
+    copies overlap the other chunks' steps; the result is the bits of
+    nlse_run on the device, for 1, 2 and 33 steps."""
+    sides = [(64, 64), (130, 256), (40, 68), (96, 128), (200, 200), (64, 64), (33, 132), (128, 384), (70, 100),
+             (256, 256), (48, 64)]
+    insts = _batch(sides, seed=31)
+    rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+    dts = _dts(insts, prec)
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], rdt, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec=prec, check_stability=check)
+    for steps in (1, 2, 33):
+        x = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, DEV)
+        bs.run(x, steps)
+        bs.check()
+        host = nlse.BatchSolver.pack([q["psi"] for q in insts], cdt, "cpu").pin_memory()
+        bs.run_host(host, steps)
+        assert torch.equal(host, x.cpu()), steps
+
+
+def test_batch_run_host_refuses_chunk_by_chunk():
+    """A refusal of the entry check inside a pipelined host run leaves the
+    refused instance's chunk unchanged and is returned."""
+    sides = [(64, 64)] * 6 + [(128, 128)] * 6
+    insts = _batch(sides, seed=33)
+    dts = _dts(insts, "fp64")
+    dts[9] *= 3.0                                   # 1.5x its bound
+    V = nlse.BatchSolver.pack([q["V"] for q in insts], torch.float64, DEV)
+    bs = nlse.BatchSolver(V, [q["shape"] for q in insts], [q["h"] for q in insts], dts,
+                          [q["a"] for q in insts], [q["s"] for q in insts], prec="fp64")
+    host = nlse.BatchSolver.pack([q["psi"] for q in insts], torch.complex128, "cpu").pin_memory()
+    h0 = host.clone()
+    with pytest.raises(nlse.NLSEError) as ei:
+        bs.run_host(host, 4)
+    assert ei.value.code == nlse.EUNSTABLE and "instance 9" in str(ei.value)
+    parts0, parts = bs.unpack(h0), bs.unpack(host)
+    assert torch.equal(parts[9], parts0[9])         # the refused instance is not stepped
+    assert not torch.equal(parts[0], parts0[0])     # an instance of an earlier chunk is
+    bs.check()                                      # run_host cleared the status
