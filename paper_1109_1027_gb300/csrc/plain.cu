@@ -35,6 +35,7 @@ struct Grid3 {
     int bc;                 // 0 Dirichlet, 1 MSD, 2 periodic, 3 Laplacian-zero
     int64_t stride[3];
     int64_t npts;
+    int* flag;              // status word (bounds-check build: out-of-range neighbour indices)
 };
 
 __device__ __forceinline__ bool decompose(const Grid3& g, int64_t p, int* c) {
@@ -51,10 +52,15 @@ __device__ __forceinline__ bool decompose(const Grid3& g, int64_t p, int* c) {
 // Index of the neighbour of point p (coordinates x) at offset d along axis
 // ax; on a periodic grid the coordinate wraps.
 __device__ __forceinline__ int64_t nbr(const Grid3& g, const int* x, int64_t p, int ax, int d) {
-    if (g.bc != 2) return p + d * g.stride[ax];
-    int c = x[ax] + d;
-    c = c < 0 ? c + g.n[ax] : (c >= g.n[ax] ? c - g.n[ax] : c);
-    return p + (int64_t)(c - x[ax]) * g.stride[ax];
+    int64_t q;
+    if (g.bc != 2) {
+        q = p + d * g.stride[ax];
+    } else {
+        int c = x[ax] + d;
+        c = c < 0 ? c + g.n[ax] : (c >= g.n[ax] ? c - g.n[ax] : c);
+        q = p + (int64_t)(c - x[ax]) * g.stride[ax];
+    }
+    return NLSE_IDX(g.flag, q, g.npts, kSitePlain) ? q : p;    // (out of range: recorded, the point itself read)
 }
 
 __device__ __forceinline__ int64_t inward(const Grid3& g, const int* x) {
@@ -191,6 +197,7 @@ Grid3 make_grid(const PlainLaunch& L) {
     g.stride[1] = g.n[0];
     g.stride[2] = (int64_t)g.n[0] * g.n[1];
     g.npts = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    g.flag = L.flag;
     return g;
 }
 

@@ -77,6 +77,18 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
         else __syncthreads();
     };
 
+#ifdef NLSE_BOUNDS_CHECK
+    {
+        // The chunk inside the grid and the three shared buffers inside the
+        // launch's dynamic shared memory (recorded only: a CTA may not leave
+        // before the cluster barriers its neighbours wait at).
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const int64_t need = (int64_t)(nbuf * (m + 4) + (m + 2) + (MSD ? m : 0)) * (int64_t)sizeof(C);
+        (void)(NLSE_IDX(flag, p0 + mr - 1, n, kSiteResident1d) && NLSE_IDX(flag, mr - 2, m - 1, kSiteResident1d) &&
+               NLSE_IDX(flag, need - 1, dyn, kSiteResident1d));
+    }
+#endif
     // Every CTA of the cluster must be running before any writes its shared memory.
     if (CS > 1) cl.sync();
     C psi[PPT], lo[PPT], acc[PPT];
@@ -84,7 +96,7 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int j = tid + k * T;
-        if (j < mr) {
+        if (j < mr && NLSE_IDX(flag, p0 + j, n, kSiteResident1d)) {
             psi[k] = psi_g[p0 + j];
             lo[k] = lo_g ? lo_g[p0 + j] : czero<C>();
             V[k] = V_g[p0 + j];
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(MAX_T) rk4_1d_resident_kernel(cplx<R>* psi_g, 
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int j = tid + k * T;
-        if (j < mr) {
+        if (j < mr && NLSE_IDX(flag, p0 + j, n, kSiteResident1d)) {
             psi_g[p0 + j] = psi[k];
             if (lo_g) lo_g[p0 + j] = lo[k];
         }

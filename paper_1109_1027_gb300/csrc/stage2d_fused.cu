@@ -108,7 +108,8 @@ __device__ __forceinline__ C dpt(const Coef<float>& c, const FusedIO& io, int nx
                                  C ctr, C up, C dn, C lf, C rt) {
     if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
     if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
-        return dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]);
+        return NLSE_IDX(io.flag, (int64_t)rl * nx + x, (int64_t)io.rows1 * nx, kSiteFused)
+                   ? dirichlet_D(c, ctr, io.V[(int64_t)rl * nx + x]) : czero<C>();
     return mul2(fma2(pair<C>(-4, -4), ctr, add2(add2(lf, rt), add2(up, dn))), pair<C>(c.inv_h2, c.inv_h2));
 }
 
@@ -415,7 +416,7 @@ rk4_2d_fused_kernel(const __grid_constant__ CUtensorMap m_in, const __grid_const
                 d1.b = dpt(c, io, nx, ny, xa + 1, ya, rlya, bC1.b, bC0.b, c2.b, bC1.a, r1);
                 st2(dbrow(j + 1) + k, d1);
                 wait_eb(ib);
-                if (xin) {
+                if (xin && NLSE_IDX(io.flag, (int64_t)y * nx + xa + 1, (int64_t)nx * ny, kSiteFused)) {
                     const C* dr = dbrow(j);
                     const bool rowb = rly == 0 || rly == rows1 - 1;
                     const bool ba = rowb || xa == 0, bb = rowb || xa + 1 == nx - 1;

@@ -68,10 +68,12 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
             int k = (ly + 1) * PX + (lx + 1);
             C d = czero<C>();
+            if (!(NLSE_IDX(io.flag, k - PX, PP, kSiteStage3d) && NLSE_IDX(io.flag, k + PX, PP, kSiteStage3d))) continue;
             if (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 C ctr = pc[k];
                 if (zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
-                    d = dirichlet_D(c, ctr, io.V[gz * plane + (int64_t)gy * nx + gx]);
+                    if (NLSE_IDX(io.flag, gz * plane + (int64_t)gy * nx + gx, plane * nz, kSiteStage3d))
+                        d = dirichlet_D(c, ctr, io.V[gz * plane + (int64_t)gy * nx + gx]);
                 } else {
                     C sum = cadd(cadd(cadd(pc[k + 1], pc[k - 1]), cadd(pc[k + PX], pc[k - PX])),
                                  cadd(pp[k], pm[k]));
@@ -109,6 +111,10 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             const int64_t p = gz * plane + (int64_t)gy * nx + gx;
             const int k = (ly + 2) * PX + (lx + 2);
             const int kd = (ly + 1) * DX + (lx + 1);
+            if (!(NLSE_IDX(io.flag, k - PX - 1, PP, kSiteStage3d) && NLSE_IDX(io.flag, k + PX + 1, PP, kSiteStage3d) &&
+                  NLSE_IDX(io.flag, kd - DX, DP, kSiteStage3d) && NLSE_IDX(io.flag, kd + DX, DP, kSiteStage3d) &&
+                  NLSE_IDX(io.flag, p, plane * nz, kSiteStage3d)))
+                continue;
             const C y = pc[k];
             const bool bnd = zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1;
             C lap;
@@ -258,7 +264,10 @@ stage3d_ms_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             const int i = tid + m * NT, ly = i / TX, lx = i - ly * TX;
             const int gx = x0 + lx, gy = y0 + ly;
             const C dz1 = dz_own(m, gz + 1);
-            if (gx < nx && gy < ny) {
+            if (gx < nx && gy < ny &&
+                NLSE_IDX(io.flag, gz * plane + (int64_t)gy * nx + gx, plane * nz, kSiteStage3d) &&
+                NLSE_IDX(io.flag, (ly + 1) * DX + lx + 1 + DX, DP, kSiteStage3d) &&
+                NLSE_IDX(io.flag, (ly + 2) * PX + lx + 2, PP, kSiteStage3d)) {
                 const int64_t p = gz * plane + (int64_t)gy * nx + gx;
                 const int k = (ly + 2) * PX + (lx + 2);
                 const int kd = (ly + 1) * DX + (lx + 1);
