@@ -347,6 +347,17 @@ int nlse_set_tiling(nlse_ctx* ctx, int key, int value);
  * in the paper.  NLSE_EINVAL for an unknown key or NULL arguments. */
 int nlse_get_tiling(const nlse_ctx* ctx, int key, int* value);
 
+/* Self-test of the failure path of the bounded waits; no counterpart in the
+ * paper.  Every mbarrier wait of the TMA-fed kernels gives up after a time
+ * limit, records NLSE_ETIMEOUT in the context's status and lets the kernel
+ * return, so a transfer that never lands cannot hang the GPU.  This enqueues
+ * a one-warp kernel that runs exactly that path: it waits, with the same
+ * bounded wait, on an mbarrier that nothing completes, gives up after
+ * limit_ms (0 < limit_ms <= 1000) and sets the timeout bit; the next
+ * nlse_check returns NLSE_ETIMEOUT and clears it.  No copy is issued and
+ * nothing traps; the context stays usable. */
+int nlse_selftest_timeout(nlse_ctx* ctx, double limit_ms, void* stream);
+
 /* Measurement helper; no counterpart in the paper.  Times a chain of FP64
  * fused multiply-adds on every SM of the current GPU (CUDA events, best of
  * three launches after a warm-up) and writes the rate in FP64 flops per

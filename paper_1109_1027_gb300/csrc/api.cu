@@ -1258,6 +1258,14 @@ int nlse_reset_compensation(nlse_ctx* c, void* stream) {
     return NLSE_OK;
 }
 
+int nlse_selftest_timeout(nlse_ctx* c, double limit_ms, void* stream) {
+    g_err[0] = 0;
+    if (!c) return fail(NLSE_EINVAL, "NULL context");
+    if (!(limit_ms > 0 && limit_ms <= 1000)) return fail(NLSE_EINVAL, "limit_ms must be in (0, 1000]");
+    NLSE_CUDA(nlse::launch_bounded_wait_probe(c->flag, limit_ms, (cudaStream_t)stream), "probe launch");
+    return NLSE_OK;
+}
+
 int nlse_check(nlse_ctx* c, void* stream) {
     g_err[0] = 0;
     Range range("nlse_check");

@@ -240,6 +240,11 @@ cudaError_t launch_entry_check(const CheckLaunch& C, cudaStream_t st);
 cudaError_t launch_invariants_gate(const double* reduced, int dim, double h, double a, double dt, double* bound_out,
                                    StatusBlock* status, cudaStream_t st);
 
+// The failure path of the bounded waits, run on purpose (selftest.cu): one
+// warp waits on an mbarrier nothing completes, gives up after limit_ms and
+// sets kStatusTimeout in *flag.
+cudaError_t launch_bounded_wait_probe(int* flag, double limit_ms, cudaStream_t st);
+
 // Records msg as the calling thread's nlse_last_error() and returns code.
 int report_error(int code, const char* msg);
 cudaError_t launch_invariants(const InvLaunch& L, double* partials, int nblocks, double* out,

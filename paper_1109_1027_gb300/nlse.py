@@ -91,6 +91,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "nlse_set_tiling": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "nlse_get_tiling": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "nlse_measure_fp64_rate": ([dp, vp], ctypes.c_int),
+        "nlse_selftest_timeout": ([vp, ctypes.c_double, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +239,10 @@ def nlse_get_tiling(ctx, key: int) -> int:
 
 def nlse_reset_compensation(ctx, stream=None) -> None:
     _raise(load_library().nlse_reset_compensation(ctx, _stream(stream)))
+
+
+def nlse_selftest_timeout(ctx, limit_ms: float, stream=None) -> None:
+    _raise(load_library().nlse_selftest_timeout(ctx, float(limit_ms), _stream(stream)))
 
 
 def nlse_check(ctx, stream=None) -> None:

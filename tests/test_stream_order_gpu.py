@@ -267,3 +267,26 @@ def test_run_host_and_adjoint_report_a_pending_refusal():
         sv.adjoint(x, x, 4, 2)
     assert ei.value.code == nlse.EUNSTABLE
     sv.check()
+
+
+def test_a_bounded_wait_that_runs_out_is_reported_and_the_context_stays_usable():
+    """The failure path of the kernels' bounded mbarrier waits, on purpose: a
+    wait on a barrier nothing completes gives up after 20 ms, the status
+    carries NLSE_ETIMEOUT, nlse_check reports and clears it, and the context
+    keeps working (the GPU is not hung and nothing trapped)."""
+    sv, psi, Vd, _ = _solver((70, 128), "fp32", 830)
+    nlse.nlse_selftest_timeout(sv.ctx, 20.0)
+    with pytest.raises(nlse.NLSEError) as ei:
+        sv.check()
+    assert ei.value.code == nlse.ETIMEOUT
+    sv.check()                                      # cleared
+    x, y = _dev(psi, "fp32"), _dev(psi, "fp32")
+    sv.run(x, 7)
+    sv.check()
+    s2, _, _, _ = _solver((70, 128), "fp32", 830)
+    s2.run(y, 7)
+    s2.check()
+    assert torch.equal(x, y)
+    with pytest.raises(nlse.NLSEError) as ei:
+        nlse.nlse_selftest_timeout(sv.ctx, 5000.0)   # limits above a second are refused
+    assert ei.value.code == nlse.EINVAL
