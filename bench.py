@@ -77,8 +77,8 @@ BYTES_PER_UPDATE_PLAIN = 720
 # batch with the default tile groups, mean of the wide-tile group's 8 launches
 # (two steps), which covered `points` of the batch's points; the bench scales
 # it to its own launches by points (the traffic is proportional to them).
-NCU_TRAFFIC_GRID = {"a4c11e7dc514": 113517099}
-NCU_TRAFFIC_BATCH = {"b03c7bbe283c": {"bytes": 8579640672, "points": 198578176}}
+NCU_TRAFFIC_GRID = {"3c40de3cc10f": 113541333}
+NCU_TRAFFIC_BATCH = {"9b9d4abea560": {"bytes": 8578984480, "points": 198578176}}
 # FP64 work per grid-point update (one RK4 step) of the FP64 stage kernels,
 # from ncu instruction counts summed over the four stage launches of a step
 # and divided by the points: flops = 2 x DFMA + DADD + DMUL, and instructions

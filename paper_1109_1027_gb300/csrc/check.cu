@@ -14,10 +14,13 @@
 // (hi + compensated lo) the FP64 evaluation of every point would make this an
 // FP64-rate-bound pass on a GPU whose FP64 rate is 1/64 of its FP32 rate, so
 // each point is first evaluated in FP32 together with a rigorous bound E_i on
-// |u32_i - u64_i|; the FP64 value is computed only for points that can still
-// be an extreme of their thread's points (u32_i + E_i >= the largest
-// u32_j - E_j seen, and the mirror rule for the minimum).  The result is the
-// exact FP64 extreme, at the cost of a memory pass.
+// |u32_i - u64_i|.  A warp takes 256 points at a time (8 per lane, each load
+// instruction covering 32 consecutive points), bounds their FP32 values,
+// reduces max(u32 - E) and min(u32 + E) over the warp with shuffles, and forms
+// the FP64 value only of the points that can still be an extreme of the 256
+// (u32_i + E_i >= max_j(u32_j - E_j), and the mirror rule for the minimum):
+// on smooth fields a few points per warp.  The result is the exact FP64
+// extreme, at the cost of one memory pass.
 #include <cfloat>
 #include <climits>
 
@@ -28,7 +31,6 @@ namespace nlse {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
 
 struct Ext {
     double umin, umax, bad;
@@ -63,13 +65,6 @@ __device__ Ext ext_block_reduce(Ext a) {
     return a;
 }
 
-// Per-thread state of the filtered FP64 extremes (complex64 states).
-struct Filter {
-    Ext e;
-    float lb_max;     // largest u32_j - E_j seen: a lower bound of the thread's FP64 maximum
-    float ub_min;     // smallest u32_j + E_j seen: an upper bound of the thread's FP64 minimum
-};
-
 // u = s|Psi|^2 - V of one complex64 point (hi + lo) in FP64, with explicit
 // roundings (the same expression nlse_invariants evaluates pointwise).
 __device__ __forceinline__ double u_fp64(float2 h, float2 l, float v, double s) {
@@ -77,40 +72,73 @@ __device__ __forceinline__ double u_fp64(float2 h, float2 l, float v, double s) 
     return __fma_rn(s, __fma_rn(x, x, __dmul_rn(y, y)), -(double)v);
 }
 
-// One complex64 point.  Error bound of the FP32 evaluation u32 of u (with
-// rho_hi = hi.x^2 + hi.y^2): the compensated part changes rho by
+// FP32 value u32 of u at one complex64 point and a bound E on |u32 - u64|
+// (with rho_hi = hi.x^2 + hi.y^2): the compensated part changes rho by
 // |2 hi.x lo.x + lo.x^2 + 2 hi.y lo.y + lo.y^2| <= t = (2|hi.x| + |lo.x|)|lo.x|
 // + (2|hi.y| + |lo.y|)|lo.y|; the two FP32 roundings of rho32 add 2^-23 rho,
 // the FMA of u32 2^-24 |u32|, and s rounded to FP32 2^-24 |s| rho.
 // E = 2^-18 (|u32| + |s| rho32) + 2 |s| t + (|s| + 1) 2^-120 covers these
 // with a margin of at least 2 and absorbs FP32 underflow; an overflowed u32
-// (or an infinite E) is always evaluated in FP64.  A non-finite input point
-// counts as bad (its FP64 value would be non-finite too).
-__device__ __forceinline__ void point32(Filter& f, float2 h, float2 l, float v, float s32, float abs_s,
-                                        double s) {
-    if (!(isfinite(h.x) && isfinite(h.y) && isfinite(l.x) && isfinite(l.y))) {
-        f.e.bad += 1.0;
-        return;
-    }
+// (or an infinite E) makes the point a candidate for both extremes.
+__device__ __forceinline__ void u_fp32(float2 h, float2 l, float v, float s32, float abs_s, float& u, float& E) {
     const float rho = __fmaf_rn(h.x, h.x, __fmul_rn(h.y, h.y));
-    const float u = __fmaf_rn(s32, rho, -v);
+    u = __fmaf_rn(s32, rho, -v);
     const float ax = fabsf(l.x), ay = fabsf(l.y);
     const float t = __fmaf_rn(__fmaf_rn(2.0f, fabsf(h.x), ax), ax, __fmul_rn(__fmaf_rn(2.0f, fabsf(h.y), ay), ay));
-    const float E = __fmaf_rn(2.0f * abs_s, t,
-                              __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
-    const bool cmax = !(u + E < f.lb_max);     // also true when u or E is infinite or NaN
-    const bool cmin = !(u - E > f.ub_min);
-    if (cmax || cmin) {
-        const double u64 = u_fp64(h, l, v, s);
-        if (cmax) {
-            f.e.umax = fmax(f.e.umax, u64);
-            f.lb_max = fmaxf(f.lb_max, u - E);
+    E = __fmaf_rn(2.0f * abs_s, t, __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
+}
+
+constexpr int kWarpPts = 8;                 // points per lane in one warp tile (256 points)
+
+// The points [p0, p1) of one instance (complex64 state + compensated part),
+// by the block's warps in tiles of 256 points.  A non-finite input point
+// counts as bad (its FP64 value would be non-finite too) and is no candidate.
+__device__ __forceinline__ Ext extremes32(const float2* __restrict__ ps, const float2* __restrict__ ls,
+                                          const float* __restrict__ vs, int64_t p0, int64_t p1, double s) {
+    Ext e = ext_identity();
+    const float s32 = (float)s, abs_s = fabsf(s32);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t tb = p0 + (int64_t)warp * 32 * kWarpPts; tb < p1; tb += (int64_t)nwarps * 32 * kWarpPts) {
+        float2 h[kWarpPts], l[kWarpPts];
+        float v[kWarpPts], u[kWarpPts], E[kWarpPts];
+        bool use[kWarpPts];
+#pragma unroll
+        for (int k = 0; k < kWarpPts; ++k) {
+            const int64_t p = tb + k * 32 + lane;
+            use[k] = p < p1;
+            h[k] = use[k] ? ps[p] : make_float2(0.f, 0.f);
+            l[k] = (use[k] && ls) ? ls[p] : make_float2(0.f, 0.f);
+            v[k] = use[k] ? vs[p] : 0.f;
         }
-        if (cmin) {
-            f.e.umin = fmin(f.e.umin, u64);
-            f.ub_min = fminf(f.ub_min, u + E);
+        float lb = -FLT_MAX, ub = FLT_MAX;   // the tile's max(u32 - E), min(u32 + E)
+#pragma unroll
+        for (int k = 0; k < kWarpPts; ++k) {
+            if (use[k] && !(isfinite(h[k].x) && isfinite(h[k].y) && isfinite(l[k].x) && isfinite(l[k].y))) {
+                e.bad += 1.0;
+                use[k] = false;
+            }
+            u_fp32(h[k], l[k], v[k], s32, abs_s, u[k], E[k]);
+            if (use[k]) {
+                lb = fmaxf(lb, u[k] - E[k]);     // a NaN (inf - inf) is ignored by fmaxf / fminf
+                ub = fminf(ub, u[k] + E[k]);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            lb = fmaxf(lb, __shfl_xor_sync(0xffffffffu, lb, off));
+            ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, off));
+        }
+#pragma unroll
+        for (int k = 0; k < kWarpPts; ++k) {
+            if (!use[k]) continue;
+            const bool cmax = !(u[k] + E[k] < lb), cmin = !(u[k] - E[k] > ub);   // true for inf / NaN
+            if (cmax || cmin) {
+                const double u64 = u_fp64(h[k], l[k], v[k], s);
+                if (cmax) e.umax = fmax(e.umax, u64);
+                if (cmin) e.umin = fmin(e.umin, u64);
+            }
         }
     }
+    return e;
 }
 
 // One complex128 point: FP64 throughout.
@@ -153,24 +181,7 @@ __global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __re
     const R* vs = V + e.v_off;
     Ext acc = ext_identity();
     if constexpr (sizeof(R) == 4) {
-        Filter f{ext_identity(), -FLT_MAX, FLT_MAX};
-        const float s32 = (float)e.s, abs_s = fabsf(s32);
-        const float2 zero = make_float2(0.f, 0.f);
-        int64_t p = p0 + threadIdx.x;
-        for (; p + (kUnroll - 1) * kThreads < p1; p += kUnroll * kThreads) {
-            float2 h[kUnroll], l[kUnroll];
-            float v[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                h[u] = ps[p + u * kThreads];
-                l[u] = ls ? ls[p + u * kThreads] : zero;
-                v[u] = vs[p + u * kThreads];
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) point32(f, h[u], l[u], v[u], s32, abs_s, e.s);
-        }
-        for (; p < p1; p += kThreads) point32(f, ps[p], ls ? ls[p] : zero, vs[p], s32, abs_s, e.s);
-        acc = f.e;
+        acc = extremes32(ps, ls, vs, p0, p1, e.s);
     } else {
         for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) point64(acc, ps[p], vs[p], e.s);
     }
