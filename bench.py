@@ -86,6 +86,14 @@ NCU_TRAFFIC_BATCH = {"9b9d4abea560": {"bytes": 8578984480, "points": 198578176}}
 # hash like the traffic.  2D: 2048^2 dark vortex; 3D: 256^3 vortex ring.
 FP64_WORK_GRID = {"a4c11e7dc514": {"flops": 211.47, "instructions": 150.5}}
 FP64_WORK_3D = {"938607a896a7": {"flops": 333.28, "instructions": 270.3}}
+# The gradient (FP32 state, FP64 dL/dV): per point and RK4 step the forward
+# pass (168 B), the segment recompute (168 B: the same four stages, the stage
+# inputs kept) and the four adjoint stages, each reading its cotangent w (8),
+# the stage input Y (8), V (4), lam' (8) and dL/dV (8, FP64) and writing lam
+# (8), dL/dV (8) and, for stages 4..2, the next cotangent (8); stages 3 and 2
+# also read lam (8): 60 + 68 + 68 + 60 = 256 B.  Checkpoints (state and
+# compensated part every 100 steps) add 0.6 B.
+BYTES_PER_UPDATE_GRADIENT = 168 + 168 + 256
 # Instances of the batch that the CPU oracle times (every 32nd).
 CPU_SAMPLE_STRIDE = 32
 
@@ -769,6 +777,11 @@ def run_gradient_leg(args, dev, barrier, max_over_ranks):
             "how": "one stacked context (NLSE_FLAG_STACK): the 16 instances share V and advance in one launch "
                    "per stage; dL/dV summed over the instances in FP64",
             "forward_equivalent_updates_per_s": 16 * 512 * 512 * steps / el,
+            "roofline": {"bound": "hbm", "kernel": "forward + recompute stages and adj2d_kernel, whole gradient",
+                         "bytes_per_update": BYTES_PER_UPDATE_GRADIENT,
+                         "achieved": BYTES_PER_UPDATE_GRADIENT * 16 * 512 * 512 * steps / el / 1e9,
+                         "peak": load_peaks()[0], "unit": "GB/s",
+                         "frac": BYTES_PER_UPDATE_GRADIENT * 16 * 512 * 512 * steps / el / 1e9 / load_peaks()[0]},
             "loss_sum": float(loss), "dV_norm": float(torch.linalg.vector_norm(gV))}
 
 

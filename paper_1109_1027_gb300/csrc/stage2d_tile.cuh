@@ -33,7 +33,7 @@
 //   F = i[a Lap + (s|Psi|^2 - V) Psi] (Sec. 3.1), F_b = 0 (Eq. dbc_ut);
 //   the RK4 stage epilogue (Eq. RK4, accumulated-increment form).
 // Complex64 arithmetic uses the packed f32x2 instructions.  Every mbarrier
-// wait is bounded (1 s); on timeout the CTA sets bit 2 of the status flag,
+// wait is bounded (1 s); on timeout the CTA sets the timeout bit of the status,
 // lets its own copies in flight land and returns.
 #pragma once
 
@@ -160,7 +160,13 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
     }
     __syncthreads();
 
-    // Producer side (thread 0): input row j, epilogue row e.
+    // Producer side: input rows are issued by the first lane of warp 1 (PIN),
+    // epilogue rows by the first lane of warp 2 (PE), while warp 0 forms the
+    // left halo D and the last warp the right one: with four warps each
+    // carries one extra task per row, and no warp waits at the row barrier for
+    // another's two.
+    constexpr int PIN = NT >= 64 ? 32 : 0;
+    constexpr int PE = NT >= 96 ? 64 : 0;
     auto issue_in = [&](int j) {
         const int s = j % S;
         const uint32_t dst = sbase + L::IN_OFF + s * L::IN_SLOT;
@@ -190,11 +196,10 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         }
         if (NEED_LO) load_cplx_box<R>(dst + L::E_LO, m_lo, x0, r, bar);
     };
-    int next = 0, enext = 0;                     // rows issued so far (thread 0)
-    if (t == 0) {
+    int next = 0, enext = 0;                     // rows issued so far (by PIN, by PE)
+    if (t == PIN)
         for (; next < S && next < jmax; ++next) issue_in(next);
-        if (NEED_E) issue_e(enext++);
-    }
+    if (NEED_E && t == PE) issue_e(enext++);
 
     auto irow = [&](int j) { return reinterpret_cast<const C*>(smem + L::IN_OFF + (j % S) * L::IN_SLOT); };
     auto erow = [&](int e) { return smem + L::E_OFF + (e & 1) * L::E_SLOT; };
@@ -315,10 +320,8 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         const int yla = rstep(yl, dir);
         wait_in(j + 2);
         if (!__syncthreads_and(ok)) { alive = false; break; }
-        if (t == 0) {
-            if (next < jmax) issue_in(next++);
-            if (NEED_E && enext < nrows) issue_e(enext++);
-        }
+        if (t == PIN && next < jmax) issue_in(next++);
+        if (NEED_E && t == PE && enext < nrows) issue_e(enext++);
 
         // D(., ya), one row ahead.
         const C* q1 = irow(j + 1);
@@ -424,13 +427,13 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
 
     if (!alive) {
         // A transfer never arrived: report, let this CTA's copies in flight land, leave.
-        if (t == 0) {
-            atomicOr(io.flag, 2);
+        if (t == 0) atomicOr(io.flag, 2);
+        if (t == PIN)
             for (int j = next > S ? next - S : 0; j < next; ++j)
                 mbar_wait(ibar0 + 8 * (j % S), (uint32_t)((j / S) & 1), kDrainNs);
+        if (t == PE)
             for (int e = enext > 2 ? enext - 2 : 0; e < enext; ++e)
                 mbar_wait(ebar0 + 8 * (e & 1), (uint32_t)((e >> 1) & 1), kDrainNs);
-        }
         return;
     }
     if constexpr (STAGE == 4) {

@@ -31,7 +31,7 @@
 // plane, so a 4-slot input ring suffices and the two D rings fit.
 // Consecutive stages walk z in opposite directions so that each starts on
 // planes the previous one wrote last.  Every mbarrier wait is bounded (1 s);
-// on timeout the CTA sets bit 2 of the status flag, lets its copies land and
+// on timeout the CTA sets the timeout bit of the status, lets its copies land and
 // returns.
 #pragma once
 

@@ -6,7 +6,8 @@ takes a few warm-up steps, then a few more, and exits.
 
 Workloads: vortex2d (2D dark vortex), ring3d (3D vortex ring), soliton1d
 (1D bright soliton), batch2d (the first --count of the 512 uneven 2D
-instances).  FP32 unless --fp64.
+instances), gradient (the gradient workload's 16 x 512^2 stack: --steps RK4
+steps forward and back, checkpoints every 10).  FP32 unless --fp64.
 --fuse runs the 2D steps as two launches of two RK4 stages each.
 """
 from __future__ import annotations
@@ -21,7 +22,8 @@ from . import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="vortex2d", choices=["vortex2d", "ring3d", "soliton1d", "batch2d"])
+    ap.add_argument("--workload", default="vortex2d",
+                    choices=["vortex2d", "ring3d", "soliton1d", "batch2d", "gradient"])
     ap.add_argument("--n", type=int, default=0, help="points per axis (default: the workload's)")
     ap.add_argument("--count", type=int, default=512, help="batch2d: instances (the first ones of the batch)")
     ap.add_argument("--steps", type=int, default=3)
@@ -32,6 +34,18 @@ def main():
     prec = "fp64" if args.fp64 else "fp32"
     rdt, cdt = (torch.float64, torch.complex128) if args.fp64 else (torch.float32, torch.complex64)
     dev = "cuda:0"
+    if args.workload == "gradient":
+        V, psis, targets, h, a, s = wl.gradient_problem_2d(n=512, batch=16)
+        Vd = torch.from_numpy(V).to(dev).to(rdt).contiguous()
+        x0 = torch.stack([torch.from_numpy(p_).to(cdt) for p_ in psis]).to(dev).contiguous()
+        tg = torch.stack([torch.from_numpy(t_).to(cdt) for t_ in targets]).to(dev).contiguous()
+        solver = nlse.Solver(Vd, h, 1e-3, a, s, prec=prec, check_stability=False, stack=len(psis))
+        for _ in range(args.warmup):
+            solver.adjoint(x0, tg, 2, 1)
+        solver.adjoint(x0, tg, args.steps, 10)
+        torch.cuda.synchronize()
+        print("profile_case: ok")
+        return
     if args.workload == "batch2d":
         insts = wl.gaussian_batch_2d(count=512, steps=0, only=set(range(args.count)))
         V = nlse.BatchSolver.pack([q.V for q in insts], rdt, dev)
