@@ -88,12 +88,14 @@ FP64_WORK_GRID = {"a4c11e7dc514": {"flops": 211.47, "instructions": 150.5}}
 FP64_WORK_3D = {"938607a896a7": {"flops": 333.28, "instructions": 270.3}}
 # The gradient (FP32 state, FP64 dL/dV): per point and RK4 step the forward
 # pass (168 B), the segment recompute (168 B: the same four stages, the stage
-# inputs kept) and the four adjoint stages, each reading its cotangent w (8),
-# the stage input Y (8), V (4), lam' (8) and dL/dV (8, FP64) and writing lam
-# (8), dL/dV (8) and, for stages 4..2, the next cotangent (8); stages 3 and 2
-# also read lam (8): 60 + 68 + 68 + 60 = 256 B.  Checkpoints (state and
-# compensated part every 100 steps) add 0.6 B.
-BYTES_PER_UPDATE_GRADIENT = 168 + 168 + 256
+# inputs kept) and the four reversed stages.  Each reads its cotangent w (8),
+# the stage input Y (8) and V (4) and writes lam (8); stages 4..2 write the
+# next cotangent (8) and their dL/dV contribution (4); stages 3 and 2 read
+# lam' (8; stage 4's w is lam' itself) and stages 3..1 the running lam (8);
+# stage 1 reads the three contributions (12) and dL/dV (8, FP64) and writes
+# dL/dV (8): 40 + 56 + 56 + 64 = 216 B.  Checkpoints (state and compensated
+# part every 100 steps) add 0.6 B.
+BYTES_PER_UPDATE_GRADIENT = 168 + 168 + 216
 # Instances of the batch that the CPU oracle times (every 32nd).
 CPU_SAMPLE_STRIDE = 32
 

@@ -219,7 +219,7 @@ int nlse_run(nlse_ctx* ctx, void* psi_dev, int64_t nsteps, void* stream);
  * synchronises anyway, it returns the context's status as nlse_check does
  * (and clears it): a refusal of the entry check (psi_host unchanged), a
  * non-finite value produced by the steps (psi_host holds the result).
- * A batch context moves the state in up to 8 chunks of consecutive instances
+ * A batch context moves the state in up to 16 chunks of consecutive instances
  * of about equal size, on three internal streams ordered after the caller's:
  * a chunk's copy in, its steps and its copy out overlap the neighbouring
  * chunks' (the results are the bits of nlse_run).  Its entry check then runs
@@ -284,8 +284,9 @@ int nlse_invariants_noalloc(const nlse_params* p, const void* psi_dev, const voi
  * sweep recomputes each segment from its checkpoint).  Single-grid 2D
  * Dirichlet contexts.  psi0_dev and target_dev are complex fields of the
  * context's precision (not modified); dpsi0_dev (same type) receives
- * dL/dRe(psi0) + i dL/dIm(psi0); dV_dev receives dL/dV as FP64 (double,
- * accumulated in FP64); *loss the FP64 loss.  The context allocates its work
+ * dL/dRe(psi0) + i dL/dIm(psi0); dV_dev receives dL/dV as FP64 (double;
+ * accumulated in FP64, or for FP32 contexts as an FP32 double-float of about
+ * 48 significant bits); *loss the FP64 loss.  The context allocates its work
  * space on first use: (5 + 4 ckpt_every + c nsteps/ckpt_every) fields of the
  * state's size (c = 2 in FP32, 1 in FP64), as the reverse sweep keeps the four
  * stage inputs of every step of a segment.  Uses the context's compensated
@@ -339,6 +340,11 @@ int nlse_adjoint_backward(nlse_ctx* ctx, double dloss, void* dpsi0_dev, void* dV
                                      168 bytes moved per point and step), 0 as four
                                      single-stage launches (default).  Other
                                      contexts accept the key and ignore it.        */
+#define NLSE_TILE_ADJ_ROWS 6      /* the adjoint's reversed stages (2D): 8
+                                     (default), 16 or 32 rows per CTA of the TMA row
+                                     walk, 0 the shared-memory tile kernel (which
+                                     also serves rows that are not 16-byte
+                                     aligned)                                      */
 /* Sets one tiling key of the context (no counterpart in the paper).  Returns
  * NLSE_EINVAL for an unknown key or a value outside its range (the context is
  * then unchanged). */

@@ -19,11 +19,17 @@
 //        + boundary: alpha E + beta conj(E), alpha = -(2s|Y|^2 - V)/a, beta = -s Y^2/a   (Eq. dbc_lap)
 //        + interior: -i (2s|Y|^2 - V) w + i s Y^2 conj(w)
 //   dL/dV += interior: Im(conj(w) Y);  boundary: Re(conj(E) Y) / a.
-// (With the CD Laplacian: E = u and no corner terms.)  The stage kernels
-// accumulate dL/dV in FP64.
+// (With the CD Laplacian: E = u and no corner terms.)  Stages 4, 3, 2 store
+// their dL/dV contribution; stage 1 adds the four to the running dL/dV in the
+// order 4, 3, 2, 1 (one read-modify-write per step; FP64, or in FP32 runs a
+// double-float converted to FP64 when the sweep ends).  The
+// per-point arithmetic is in adjoint2d.cuh, shared with the TMA row walk of
+// adjoint2d_tma.cuh, which runs the stage wherever its rows are 16-byte
+// aligned; the shared-memory tile kernel below serves the rest.
 #include <cfloat>
 
-#include "nlse_device.cuh"
+#include "adjoint2d.cuh"
+#include "tmap.cuh"
 
 namespace nlse {
 namespace {
@@ -34,48 +40,48 @@ constexpr int DX = TX + 2, DY = TY + 2;   // E with a 1-point halo
 
 template <typename R>
 struct AdjIO {
-    const cplx<R>* w;      // cotangent of this stage's K (scaled by scale_w)
-    R scale_w;
+    const cplx<R>* w;      // stored cotangent of this stage's K (w = scale * stored)
     const cplx<R>* Y;      // this stage's input Y_j
     const R* V;
     const cplx<R>* lamp;   // lam' = dL/dPsi_{n+1}
     cplx<R>* lam;          // running dL/dPsi_n
     cplx<R>* w_next;       // cotangent of the previous stage's K
-    double* gV;            // dL/dV, accumulated in FP64
-    R cw, cy;              // w_next = cw lam' + cy Ybar
+    R* g_out;              // stages 4..2: this stage's dL/dV contribution
+    const R* g4;           // stage 1: the contributions of stages 4, 3, 2
+    const R* g3;
+    const R* g2;
+    adj::gacc<R>* gV;      // stage 1: the running dL/dV
 };
 
 template <typename R, bool CD, int J>
-__global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int nx, int ny, int rows1) {
+__global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, adj::Coef<R> c, int nx, int ny, int rows1) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sU = reinterpret_cast<C*>(smem_raw);   // [PY][PX]
     C* sE = sU + PX * PY;                     // [DY][DX]
+    __shared__ bool rin[PY];                  // grid rows y0-2 .. y0+TY+1: interior of their instance
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, tid = threadIdx.x;
-    // Interior of its stacked instance (rows1 rows each; one instance when rows1 = ny).
-    auto interior = [&](int x, int y) {
-        if (x <= 0 || x >= nx - 1 || y < 0 || y >= ny) return false;
-        const int yl = inst_row(y, rows1);
-        return yl > 0 && yl < rows1 - 1;
-    };
+    if (tid < PY) {
+        const int gy = y0 - 2 + tid;
+        const int yl = gy >= 0 ? inst_row(gy, rows1) : -1;
+        rin[tid] = gy >= 0 && gy < ny && yl > 0 && yl < rows1 - 1;
+    }
+    __syncthreads();
+    // Interior of its stacked instance, by row offset ly from y0 - 2.
+    auto interior = [&](int x, int ly) { return x > 0 && x < nx - 1 && rin[ly]; };
 
     for (int i = tid; i < PX * PY; i += NT) {
         const int ly = i / PX, lx = i - ly * PX;
         const int gx = x0 - 2 + lx, gy = y0 - 2 + ly;
         C u = czero<C>();
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && interior(gx, gy)) {
-            const C w = cscale(io.scale_w, io.w[(int64_t)gy * nx + gx]);
-            u = cmake<C>(c.a * w.y, -c.a * w.x);                    // -i a w
-        }
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) u = adj::u_of(c, io.w[(int64_t)gy * nx + gx], interior(gx, ly));
         sU[i] = u;
     }
     __syncthreads();
     for (int i = tid; i < DX * DY; i += NT) {
         const int ly = i / DX, lx = i - ly * DX;
         const C* q = sU + (ly + 1) * PX + (lx + 1);
-        C e = q[0];
-        if (!CD) e = csub(e, cscale((R)(1.0 / 12.0), cadd(cadd(q[1], q[-1]), cadd(q[PX], q[-PX]))));
-        sE[i] = e;
+        sE[i] = adj::e_of<CD>(q[0], q[1], q[-1], q[PX], q[-PX]);
     }
     __syncthreads();
 
@@ -86,40 +92,21 @@ __global__ void __launch_bounds__(NT) adj2d_kernel(AdjIO<R> io, Coef<R> c, int n
         const int64_t p = (int64_t)gy * nx + gx;
         const C* e = sE + (ly + 1) * DX + (lx + 1);
         const C* u = sU + (ly + 2) * PX + (lx + 2);
-        auto ein = [&](int dx, int dy) {
-            return interior(gx + dx, gy + dy) ? e[dy * DX + dx] : czero<C>();
-        };
-        const bool inner = interior(gx, gy);
-        const C esum = cadd(cadd(ein(1, 0), ein(-1, 0)), cadd(ein(0, 1), ein(0, -1)));
-        C ybar = cscale(c.inv_h2, csub(esum, cscale((R)4, inner ? e[0] : czero<C>())));
-        if (!CD) {
-            const C corners = cadd(cadd(u[PX + 1], u[PX - 1]), cadd(u[-PX + 1], u[-PX - 1]));
-            ybar = cadd(ybar, cscale(c.inv_6h2, csub(corners, cscale((R)4, u[0]))));
-        }
-        const C Y = io.Y[p];
+        auto ein = [&](int dx, int dy) { return interior(gx + dx, ly + 2 + dy) ? e[dy * DX + dx] : czero<C>(); };
+        const bool inner = interior(gx, ly + 2);
+        C ybar = adj::ybar_stencil<CD>(c, inner ? e[0] : czero<C>(), ein(1, 0), ein(-1, 0), ein(0, 1), ein(0, -1),
+                                       u[0], u[PX + 1], u[PX - 1], u[-PX + 1], u[-PX - 1]);
         const R v = io.V[(int64_t)inst_row(gy, rows1) * nx + gx];     // V is shared by stacked instances
-        const R rho = Y.x * Y.x + Y.y * Y.y;
-        const C Y2 = cmake<C>(Y.x * Y.x - Y.y * Y.y, 2 * Y.x * Y.y);   // Y^2
-        R gv;
-        if (inner) {
-            const C w = cscale(io.scale_w, io.w[p]);
-            const R g = 2 * c.s * rho - v;
-            // -i g w + i s Y^2 conj(w)
-            const C sy = cmake<C>(Y2.x * w.x + Y2.y * w.y, Y2.y * w.x - Y2.x * w.y);   // Y^2 conj(w)
-            ybar = cadd(ybar, cmake<C>(g * w.y - c.s * sy.y, -g * w.x + c.s * sy.x));
-            gv = w.x * Y.y - w.y * Y.x;                                             // Im(conj(w) Y)
+        const R gv = adj::pointwise(c, inner, adj::wscale(c, io.w[p]), e[0], io.Y[p], v, ybar);
+        if constexpr (J == 1) {
+            io.lam[p] = add2(io.lam[p], ybar);
+            io.gV[p] = adj::gv_total(io.gV[p], io.g4[p], io.g3[p], io.g2[p], gv);
         } else {
-            const C E = e[0];
-            const R alpha = -(2 * c.s * rho - v) * c.inv_a;
-            const C ce = cmake<C>(Y2.x * E.x + Y2.y * E.y, Y2.y * E.x - Y2.x * E.y); // Y^2 conj(E)
-            ybar = cadd(ybar, cadd(cscale(alpha, E), cscale(-c.s * c.inv_a, ce)));
-            gv = (E.x * Y.x + E.y * Y.y) * c.inv_a;                                 // Re(conj(E) Y) / a
+            const C lp = io.lamp[p];
+            io.lam[p] = add2(J == 4 ? lp : io.lam[p], ybar);
+            io.w_next[p] = adj::w_next(c, lp, ybar);
+            io.g_out[p] = gv;
         }
-        io.gV[p] += (double)gv;
-        const C lp = io.lamp[p];
-        if constexpr (J == 4) io.lam[p] = cadd(lp, ybar);
-        else io.lam[p] = cadd(io.lam[p], ybar);
-        if constexpr (J > 1) io.w_next[p] = cadd(cscale(io.cw, lp), cscale(io.cy, ybar));
     }
 }
 
@@ -127,15 +114,16 @@ template <typename R, bool CD, int J>
 cudaError_t launch_j(const AdjLaunch& L, cudaStream_t st) {
     AdjIO<R> io;
     io.w = (const cplx<R>*)L.w;
-    io.scale_w = (R)L.scale_w;
     io.Y = (const cplx<R>*)L.Y;
     io.V = (const R*)L.V;
     io.lamp = (const cplx<R>*)L.lamp;
     io.lam = (cplx<R>*)L.lam;
     io.w_next = (cplx<R>*)L.w_next;
-    io.gV = L.gV;
-    io.cw = (R)L.cw;
-    io.cy = (R)L.cy;
+    io.g_out = (R*)L.g_out;
+    io.g4 = (const R*)L.g_in[0];
+    io.g3 = (const R*)L.g_in[1];
+    io.g2 = (const R*)L.g_in[2];
+    io.gV = (adj::gacc<R>*)L.gV;
     const int nx = (int)L.nx, ny = (int)L.ny;
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY);
     const size_t smem = sizeof(cplx<R>) * (PX * PY + DX * DY);
@@ -144,7 +132,8 @@ cudaError_t launch_j(const AdjLaunch& L, cudaStream_t st) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, NT, smem, st>>>(io, make_coef<R>(L.h, L.a, L.s), nx, ny, (int)(L.rows1 ? L.rows1 : L.ny));
+    kern<<<grid, NT, smem, st>>>(io, adj::make_coef<R>(L.h, L.a, L.s, L.scale_w, L.cw, L.cy), nx, ny,
+                                 (int)(L.rows1 ? L.rows1 : L.ny));
     return cudaGetLastError();
 }
 
@@ -189,6 +178,11 @@ __global__ void sum_kernel(const double* partials, int n, double* out) {
     }
 }
 
+__global__ void __launch_bounds__(256) gv_double_kernel(const float2* acc, double* out, int64_t n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = adj::gv_double(acc[p]);
+}
+
 __global__ void stack_sum_kernel(const double* src, int count, int64_t n, double* dst) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -213,10 +207,31 @@ cudaError_t launch_scale(int prec, void* z, double f, int64_t n, cudaStream_t st
     return cudaGetLastError();
 }
 
+bool adjoint_2d_tma_eligible(const AdjLaunch& L) {
+    if (L.nx % (L.prec == 0 ? 4 : 2) != 0) return false;
+    const void* ptrs[10] = {L.w, L.Y, L.V, L.lamp, L.lam, L.w_next, L.g_out, L.g_in[0], L.g_in[1], L.gV};
+    for (const void* p : ptrs)
+        if ((uintptr_t)p % 16) return false;
+    return (uintptr_t)L.g_in[2] % 16 == 0 && encoder() != nullptr;
+}
+
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st) {
+    if (L.walk_rows && adjoint_2d_tma_eligible(L)) {
+        switch (L.walk_rows) {
+            case 8: return launch_adjoint_2d_tma_rows8(L, st);
+            case 32: return launch_adjoint_2d_tma_rows32(L, st);
+            default: return launch_adjoint_2d_tma_rows16(L, st);
+        }
+    }
     const bool cd = L.lap == 1;
     if (L.prec == 0) return cd ? launch_r<float, true>(L, st) : launch_r<float, false>(L, st);
     return cd ? launch_r<double, true>(L, st) : launch_r<double, false>(L, st);
+}
+
+cudaError_t launch_gv_double(const void* acc, double* out, int64_t n, cudaStream_t st) {
+    const int64_t b = (n + 255) / 256;
+    gv_double_kernel<<<(unsigned)(b < 4096 ? (b < 1 ? 1 : b) : 4096), 256, 0, st>>>((const float2*)acc, out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stack_sum(const double* src, int count, int64_t n, double* dst, cudaStream_t st) {

@@ -116,6 +116,7 @@ struct nlse_ctx {
     int tile_rows, tile_planes;
     int resident;             // 1D time loop: 0 default, -1 tiled kernels, else largest cluster
     int fuse2;                // 2D FP32: two stages per launch (NLSE_TILE_2D_FUSE)
+    int adj_rows;             // adjoint: rows per CTA of the TMA walk; -1 the tile kernel; 0 default
 };
 
 namespace {
@@ -518,11 +519,11 @@ int report_status(nlse_ctx* c, const nlse::StatusBlock& s, cudaStream_t st) {
     return fail(NLSE_ENONFINITE, "a non-finite value appeared in the state");
 }
 
-// Sets up the pipelined host run of a batch: up to 8 chunks of consecutive
+// Sets up the pipelined host run of a batch: up to 16 chunks of consecutive
 // instances of about equal points, their work lists, streams, events and
 // per-chunk status blocks.
 int setup_host_pipe(nlse_ctx* c) {
-    const int n = std::min(8, c->count);
+    const int n = std::min(16, c->count);
     std::vector<int> first(1, 0);
     int64_t done = 0;
     for (int i = 0; i < c->count; ++i) {
@@ -885,13 +886,15 @@ namespace {
 // Layout of the adjoint work space for nsteps steps with a checkpoint every
 // ckpt steps: state S, checkpoints (state + compensated part), the four stage
 // inputs (Psi_n, Y2, Y3, Y4) of every step of one segment, two cotangents,
-// two adjoint states (the first holds dL/dPsi_T after the forward pass), loss
-// partials and the loss, and for a stack the per-instance dL/dV.
+// two adjoint states (the first holds dL/dPsi_T after the forward pass), the
+// dL/dV contributions of reversed stages 4, 3, 2, in FP32 the double-float
+// running dL/dV, for a stack the per-instance dL/dV, loss partials and the
+// loss.
 struct AdjLayout {
     int64_t nseg, seglen;
     int nb;
     size_t ck_bytes, need;
-    char *S, *ck, *seg, *W, *WN, *LA, *LB;
+    char *S, *ck, *seg, *W, *WN, *LA, *LB, *G, *GA;
     double *part, *lossd, *gvs;
 };
 
@@ -903,7 +906,10 @@ AdjLayout adj_layout(nlse_ctx* c, int64_t nsteps, int64_t ckpt_every) {
     A.nb = nlse::loss_num_blocks(c->npts);
     A.ck_bytes = (size_t)A.nseg * cb * (c->lo ? 2 : 1);
     const size_t gv_bytes = c->stack > 1 ? sizeof(double) * (size_t)c->npts : 0;
-    A.need = cb + A.ck_bytes + 4 * (size_t)A.seglen * cb + 4 * cb + sizeof(double) * (A.nb + 1) + gv_bytes;
+    const size_t g_bytes = 3 * (cb / 2);          // three real arrays
+    const size_t ga_bytes = c->p.prec == NLSE_FP32 ? 8 * (size_t)c->npts : 0;
+    A.need = cb + A.ck_bytes + 4 * (size_t)A.seglen * cb + 4 * cb + g_bytes + ga_bytes + gv_bytes +
+             sizeof(double) * (A.nb + 1);
     char* base = static_cast<char*>(c->adj_buf);
     A.S = base;
     A.ck = A.S + cb;
@@ -912,9 +918,14 @@ AdjLayout adj_layout(nlse_ctx* c, int64_t nsteps, int64_t ckpt_every) {
     A.WN = A.W + cb;
     A.LA = A.WN + cb;
     A.LB = A.LA + cb;
-    A.part = reinterpret_cast<double*>(A.LB + cb);
+    A.G = A.LB + cb;
+    // The running and per-instance dL/dV before the loss scalars, so that they
+    // stay as aligned as the arrays before them (the TMA walk of the reversed
+    // stages reads the running dL/dV by rows).
+    A.GA = ga_bytes ? A.G + g_bytes : nullptr;
+    A.gvs = c->stack > 1 ? reinterpret_cast<double*>(A.G + g_bytes + ga_bytes) : nullptr;
+    A.part = reinterpret_cast<double*>(A.G + g_bytes + ga_bytes + gv_bytes);
     A.lossd = A.part + A.nb;
-    A.gvs = c->stack > 1 ? A.lossd + 1 : nullptr;
     return A;
 }
 
@@ -986,8 +997,14 @@ int adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, cudaStrea
     J.rows1 = c->p.n[1];
     J.h = c->p.h; J.a = c->p.a; J.s = c->p.s;
     J.V = c->V;
-    J.gV = gvs;
-    NLSE_CUDA(cudaMemsetAsync(gvs, 0, sizeof(double) * c->npts, st), "zeroing dV");
+    // The running dL/dV: FP64 in place, or in FP32 the double-float work array
+    // converted at the end.
+    J.gV = A.GA ? static_cast<void*>(A.GA) : static_cast<void*>(gvs);
+    J.flag = &c->status->bits;
+    J.walk_rows = c->adj_rows < 0 ? 0 : (c->adj_rows ? c->adj_rows : 8);
+    char* G[3] = {A.G, A.G + cb / 2, A.G + cb};   // contributions of reversed stages 4, 3, 2
+    for (int i = 0; i < 3; ++i) J.g_in[i] = G[i];
+    NLSE_CUDA(cudaMemsetAsync(J.gV, 0, sizeof(double) * c->npts, st), "zeroing dV");
     const double k = c->p.dt;
     for (int64_t g = A.nseg - 1; g >= 0; --g) {
         const int64_t steps = std::min<int64_t>(ckpt_every, nsteps - g * ckpt_every);
@@ -1022,6 +1039,7 @@ int adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, cudaStrea
                 J.w = w[j]; J.scale_w = sw[j]; J.Y = Ys[j];
                 J.lamp = lamp; J.lam = lam; J.w_next = wn[j];
                 J.cw = cw[j]; J.cy = cy[j];
+                J.g_out = j > 1 ? G[4 - j] : nullptr;
                 cudaError_t e = nlse::launch_adjoint_stage_2d(J, st);
                 if (e != cudaSuccess) return cuda_fail(e, "adjoint stage launch");
             }
@@ -1029,6 +1047,7 @@ int adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, cudaStrea
         }
     }
     NLSE_CUDA(cudaMemcpyAsync(dpsi0, lamp, cb, cudaMemcpyDeviceToDevice, st), "gradient copy");
+    if (A.GA) NLSE_CUDA(nlse::launch_gv_double(A.GA, gvs, c->npts, st), "dV to FP64");
     if (c->stack > 1)
         NLSE_CUDA(nlse::launch_stack_sum(gvs, c->stack, vpts, static_cast<double*>(dV), st), "summing dV over the stack");
     return NLSE_OK;
@@ -1036,7 +1055,9 @@ int adjoint_backward(nlse_ctx* c, double dloss, void* dpsi0, void* dV, cudaStrea
 
 // Synchronises; reads the loss (when asked) and the status.  A refusal of an
 // earlier nlse_run that nobody read kept the stage-4 kernels from stepping:
-// then the forward pass did not run, and the refusal is returned.
+// then the forward pass did not run, and the refusal is returned; so is a
+// bounded wait of the adjoint walk that gave up, or (bounds-check build) an
+// index outside its array.
 int adjoint_finish(nlse_ctx* c, double* loss, cudaStream_t st) {
     double h_loss = 0.0;
     nlse::StatusBlock* hs = reinterpret_cast<nlse::StatusBlock*>(c->host_out);
@@ -1048,7 +1069,7 @@ int adjoint_finish(nlse_ctx* c, double* loss, cudaStream_t st) {
     NLSE_CUDA(cudaStreamSynchronize(st), "adjoint synchronise");
     c->state_psi = nullptr;          // the compensated part no longer belongs to any caller state
     const nlse::StatusBlock sb = *hs;
-    if (sb.bits & nlse::kStatusRefused) {
+    if (sb.bits & (nlse::kStatusRefused | nlse::kStatusTimeout | nlse::kStatusBounds)) {
         c->adj_ready = false;
         return report_status(c, sb, st);
     }
@@ -1134,6 +1155,11 @@ int nlse_set_tiling(nlse_ctx* c, int key, int value) {
             if (value != 0 && value != 1) return fail(NLSE_EINVAL, "two stages per launch: 0 or 1");
             c->fuse2 = value;
             break;
+        case NLSE_TILE_ADJ_ROWS:
+            if (value != 0 && value != 8 && value != 16 && value != 32)
+                return fail(NLSE_EINVAL, "adjoint rows per CTA: 0, 8, 16 or 32");
+            c->adj_rows = value ? value : -1;
+            break;
         case NLSE_TILE_BATCH_NARROW: {
             if (!c->batch) return fail(NLSE_EINVAL, "not a batch context");
             if (value < 0) return fail(NLSE_EINVAL, "the narrow-tile width bound must be >= 0");
@@ -1161,6 +1187,7 @@ int nlse_get_tiling(const nlse_ctx* c, int key, int* value) {
             return NLSE_OK;
         case NLSE_TILE_1D_RESIDENT: *value = resident_cluster(c); return NLSE_OK;
         case NLSE_TILE_2D_FUSE: *value = c->fuse2; return NLSE_OK;
+        case NLSE_TILE_ADJ_ROWS: *value = c->adj_rows < 0 ? 0 : (c->adj_rows ? c->adj_rows : 8); return NLSE_OK;
     }
     return fail(NLSE_EINVAL, "unknown tiling key %d", key);
 }

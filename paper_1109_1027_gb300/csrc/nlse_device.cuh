@@ -66,7 +66,7 @@ __device__ __forceinline__ bool idx_ok(int* flag, int64_t i, int64_t n, int site
 #endif
 // File ids of the check sites.
 constexpr int kSiteTile2d = 1, kSiteTma3d = 2, kSiteStage1d = 3, kSiteStage2d = 4, kSiteStage3d = 5,
-              kSiteFused = 6, kSiteResident1d = 7, kSitePlain = 8, kSiteCheck = 9;
+              kSiteFused = 6, kSiteResident1d = 7, kSitePlain = 8, kSiteCheck = 9, kSiteAdj2d = 10;
 
 // Row within its stacked instance of grid row r >= 0 (instances of rows1 rows;
 // without a stack rows1 is the grid's row count and r is returned undivided).

@@ -149,11 +149,23 @@ struct AdjLaunch {
     const void* lamp;       // dL/dPsi_{n+1}
     void* lam;              // dL/dPsi_n being accumulated
     void* w_next;           // cotangent of K_{j-1} = cw lam' + cy Ybar_j
-    double* gV;             // dL/dV (FP64, accumulated), one value per point of the state
+    void* g_out;            // stages 4..2: this stage's dL/dV contribution (R), one per point
+    const void* g_in[3];    // stage 1: the contributions of stages 4, 3, 2
+    void* gV;               // stage 1: the running dL/dV, 8 bytes a point: FP64, or in FP32 runs a
+                            // double-float (float hi, lo) that launch_gv_double converts
     double cw, cy;
     int64_t rows1;          // rows per stacked instance (ny when not stacked); V has rows1 rows
+    int* flag;              // status bits (the TMA walk's timeout bit)
+    int walk_rows;          // 8, 16, 32: the TMA row walk with that many rows per CTA; 0: the tile kernel
 };
 cudaError_t launch_adjoint_stage_2d(const AdjLaunch& L, cudaStream_t st);
+// out[p] = hi + lo in FP64 for the n double-float pairs at acc.
+cudaError_t launch_gv_double(const void* acc, double* out, int64_t n, cudaStream_t st);
+// Whether the TMA row walk can run the stage (16-byte aligned rows and arrays).
+bool adjoint_2d_tma_eligible(const AdjLaunch& L);
+cudaError_t launch_adjoint_2d_tma_rows8(const AdjLaunch& L, cudaStream_t st);
+cudaError_t launch_adjoint_2d_tma_rows16(const AdjLaunch& L, cudaStream_t st);
+cudaError_t launch_adjoint_2d_tma_rows32(const AdjLaunch& L, cudaStream_t st);
 // dst[q] = sum over i of src[i n + q], i = 0 .. count-1 in order (stacked dL/dV).
 cudaError_t launch_stack_sum(const double* src, int count, int64_t n, double* dst, cudaStream_t st);
 // z *= f over n complex values (the cotangent of the loss, nlse_adjoint_backward).

@@ -28,7 +28,7 @@ LAP = {"2shoc": 0, "cd": 1, "2shoc_ms": 2}
 FLAG_NO_STABILITY_CHECK = 1
 FLAG_PLAIN_SCHEDULE = 2
 FLAG_STACK = 4
-TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW, TILE_1D_RESIDENT, TILE_2D_FUSE = 1, 2, 3, 4, 5
+TILE_ROWS, TILE_PLANES, TILE_BATCH_NARROW, TILE_1D_RESIDENT, TILE_2D_FUSE, TILE_ADJ_ROWS = 1, 2, 3, 4, 5, 6
 
 _STATUS_NAMES = ["NLSE_OK", "NLSE_EINVAL", "NLSE_ENOMEM", "NLSE_ECUDA", "NLSE_EUNSTABLE",
                  "NLSE_ENONFINITE", "NLSE_ETIMEOUT", "NLSE_EUNSUPPORTED", "NLSE_EBOUNDS"]

@@ -141,7 +141,7 @@ def test_binding_constants_match_the_header():
     assert h["NLSE_FLAG_NO_STABILITY_CHECK"] == nlse.FLAG_NO_STABILITY_CHECK
     assert h["NLSE_FLAG_PLAIN_SCHEDULE"] == nlse.FLAG_PLAIN_SCHEDULE
     assert h["NLSE_FLAG_STACK"] == nlse.FLAG_STACK
-    for key in ("ROWS", "PLANES", "BATCH_NARROW", "1D_RESIDENT", "2D_FUSE"):
+    for key in ("ROWS", "PLANES", "BATCH_NARROW", "1D_RESIDENT", "2D_FUSE", "ADJ_ROWS"):
         assert h["NLSE_TILE_" + key] == getattr(nlse, "TILE_" + key), key
 
 

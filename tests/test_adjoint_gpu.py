@@ -225,3 +225,40 @@ def test_adjoint_with_two_stages_per_launch(stack):
     assert out[0][0] == out[1][0]
     assert torch.equal(out[0][1], out[1][1])
     assert torch.equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape,lap,stack", [((37, 68), "2shoc", 0), ((64, 260), "2shoc", 0), ((40, 132), "cd", 0),
+                                             ((21, 36), "2shoc", 3), ((19, 516), "2shoc_ms", 0),
+                                             ((30, 70), "2shoc", 0)])
+def test_adjoint_walk_equals_tile_kernel(prec, shape, lap, stack):
+    """The TMA row walk of the reversed stages (8, 16 or 32 rows per CTA)
+    gives the shared-memory tile kernel's bits: the loss, dL/dpsi0 and dL/dV
+    are identical, with row counts that are not a multiple of the walk's rows,
+    column counts that are not a multiple of its 256 columns, stacks, and
+    (FP32, 70 columns) rows the walk cannot address, where both keys run the
+    tile kernel."""
+    psi0, V, target, h = _problem(shape, 5)
+    rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(DEV).to(rdt).contiguous()
+    if stack:
+        x0 = torch.stack([torch.from_numpy(psi0 * (1 + 0.1 * i)).to(DEV).to(cdt) for i in range(stack)]).contiguous()
+        tg = torch.stack([torch.from_numpy(target * (1 - 0.1 * i)).to(DEV).to(cdt) for i in range(stack)]).contiguous()
+    else:
+        x0 = torch.from_numpy(psi0).to(DEV).to(cdt).contiguous()
+        tg = torch.from_numpy(target).to(DEV).to(cdt).contiguous()
+    prob = oracle.Problem(shape, h, 0.6, -1.0, lap={"2shoc": 0, "cd": oracle.LAP_CD, "2shoc_ms": 2}[lap])
+    k = 0.5 * oracle.invariants(prob, psi0 * (1 + 0.1 * max(stack - 1, 0)), V)[2]
+    sv = nlse.Solver(Vd, h, k, 0.6, -1.0, prec=prec, lap=lap, check_stability=False, stack=stack)
+    out = {}
+    for rows in (0, 8, 16, 32):
+        sv.set_tiling(nlse.TILE_ADJ_ROWS, rows)
+        assert sv.get_tiling(nlse.TILE_ADJ_ROWS) == rows
+        out[rows] = sv.adjoint(x0, tg, 11, 4)
+    ref = out[0]
+    assert np.isfinite(ref[0]) and float(ref[1].abs().max()) > 0 and float(ref[2].abs().max()) > 0
+    for rows in (8, 16, 32):
+        assert out[rows][0] == ref[0], rows
+        assert torch.equal(out[rows][1], ref[1]), rows
+        assert torch.equal(out[rows][2], ref[2]), rows
+

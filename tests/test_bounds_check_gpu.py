@@ -5,7 +5,8 @@ nlse_check instead of accessing out of range.  A child process loads the
 checked library (NLSE_LIBRARY) and runs each kernel family -- 1D tiled and
 resident, 2D TMA walk and generic tile, 3D TMA walk and generic 2.5D,
 multi-storage, CD, MSD, periodic and Laplacian-zero through the unfused
-kernels, stacks, batches, two stages per launch, the entry check -- on grids
+kernels, stacks, batches, two stages per launch, the entry check, the
+adjoint's TMA row walk and tile kernel -- on grids
 of 3 to 9 points per axis, odd widths and tiles with ragged edges, checking
 the status after every call and the results against the FP64 oracle.  This
 stands in for a race/bounds checker, which is closed on this machine."""
@@ -128,6 +129,28 @@ for prec in ("fp32", "fp64"):
     host = x.cpu().pin_memory()
     bs.run_host(host, 2)
     bs.close()
+# the reversed stages of the adjoint: TMA row walk (8, 16, 32 rows) and tile kernel
+for prec in ("fp32", "fp64"):
+    rdt = torch.float32 if prec == "fp32" else torch.float64
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    for shape, stack in (((5, 8), 0), ((19, 68), 0), ((9, 260), 0), ((7, 12), 3), ((6, 10), 0)):
+        V = wl.random_potential(shape, seed=61, scale=1.0)
+        Vd = torch.from_numpy(V).to(DEV).to(rdt).contiguous()
+        n = max(stack, 1)
+        x0 = torch.stack([torch.from_numpy(wl.random_field(shape, seed=70 + i)) for i in range(n)]).to(DEV).to(cdt)
+        tg = torch.stack([torch.from_numpy(wl.random_field(shape, seed=80 + i)) for i in range(n)]).to(DEV).to(cdt)
+        if not stack:
+            x0, tg = x0[0], tg[0]
+        sv = nlse.Solver(Vd, 0.4, 1e-3, 0.7, -1.0, prec=prec, check_stability=False, stack=stack)
+        outs = []
+        for rows in (0, 8, 16, 32):
+            sv.set_tiling(nlse.TILE_ADJ_ROWS, rows)
+            outs.append(sv.adjoint(x0.contiguous(), tg.contiguous(), 3, 2))
+            sv.check()
+        for o in outs[1:]:
+            assert o[0] == outs[0][0] and torch.equal(o[1], outs[0][1]) and torch.equal(o[2], outs[0][2]), shape
+        sv.close()
+        count += 1
 print("checked cases:", count)
 print("BOUNDS_CLEAN")
 '''
