@@ -74,6 +74,7 @@ struct nlse_ctx {
     // nlse_run's entry check (check.cu): one entry per instance, its rows of
     // partial extremes and each instance's bound.
     nlse::CheckEntry* check_tab;
+    int* check_row_entry;     // per row of partials, its entry
     int check_count, check_nrows;
     double* check_partials;
     double* check_bounds;
@@ -441,6 +442,7 @@ int enqueue_entry_check(nlse_ctx* c, const void* psi, cudaStream_t st) {
     }
     nlse::CheckLaunch C;
     C.table = c->check_tab;
+    C.row_entry = c->check_row_entry;
     C.count = c->check_count;
     C.nrows = c->check_nrows;
     C.prec = c->p.prec;
@@ -481,6 +483,12 @@ int setup_entry_check(nlse_ctx* c) {
     NLSE_CUDA(cudaMemcpy(c->check_tab, tab.data(), sizeof(nlse::CheckEntry) * count, cudaMemcpyHostToDevice),
               "uploading the check table");
     NLSE_CUDA(cudaMalloc((void**)&c->check_partials, sizeof(double) * 3 * rows), "allocating check partials");
+    std::vector<int> row_entry(rows);
+    for (int i = 0; i < count; ++i)
+        for (int r = tab[i].row0; r < tab[i].row1; ++r) row_entry[r] = i;
+    NLSE_CUDA(cudaMalloc((void**)&c->check_row_entry, sizeof(int) * rows), "allocating the check row map");
+    NLSE_CUDA(cudaMemcpy(c->check_row_entry, row_entry.data(), sizeof(int) * rows, cudaMemcpyHostToDevice),
+              "uploading the check row map");
     NLSE_CUDA(cudaMalloc((void**)&c->check_bounds, sizeof(double) * count), "allocating check bounds");
     NLSE_CUDA(cudaMalloc((void**)&c->status, sizeof(nlse::StatusBlock)), "allocating the status block");
     c->flag = &c->status->bits;
@@ -528,9 +536,10 @@ int setup_host_pipe(nlse_ctx* c) {
     int64_t done = 0;
     for (int i = 0; i < c->count; ++i) {
         done += c->bparams[i].n[0] * c->bparams[i].n[1];
-        const int k = (int)first.size();                 // chunk being filled
-        if (k < n && done * n >= (int64_t)k * c->npts && i + 1 < c->count && c->count - (i + 1) >= n - k)
-            first.push_back(i + 1);
+        // Chunk k - 1 ends after instance i once it reaches k / n of the points
+        // (fewer chunks when large instances overshoot; none is empty).
+        const int k = (int)first.size();
+        if (k < n && done * n >= (int64_t)k * c->npts && i + 1 < c->count) first.push_back(i + 1);
     }
     first.push_back(c->count);
     const int nch = (int)first.size() - 1;
@@ -608,6 +617,7 @@ int run_host_pipelined(nlse_ctx* c, void* psi_host, int64_t nsteps, cudaStream_t
         if (nsteps > 0 && !(c->p.flags & NLSE_FLAG_NO_STABILITY_CHECK)) {
             nlse::CheckLaunch C;
             C.table = c->check_tab;
+            C.row_entry = c->check_row_entry;
             C.inst_base = i0;
             C.count = i1 - i0;
             C.row_base = c->check_row0[i0];
@@ -711,6 +721,7 @@ void release(nlse_ctx* c) {
     for (auto& g : c->graphs)
         if (g) cudaGraphExecDestroy(g);
     cudaFree(c->check_tab);
+    cudaFree(c->check_row_entry);
     cudaFree(c->check_partials);
     cudaFree(c->check_bounds);
     nlse::batch2d_destroy(c->batch);

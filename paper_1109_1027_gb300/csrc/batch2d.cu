@@ -69,7 +69,7 @@ template <typename R, int LP, int STAGE, int NT>
 cudaError_t launch_group(const BatchDesc* descs, const int4* tiles, int ntiles, const StageIO<R>& io, int dir,
                          cudaStream_t st) {
     auto kern = stage2d_batch_kernel<R, LP, STAGE, NT>;
-    const int smem = tile2d::Lay<R, NT>::TOTAL;
+    const int smem = tile2d::Lay<R, NT, STAGE>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

@@ -14,10 +14,10 @@
 // (hi + compensated lo) the FP64 evaluation of every point would make this an
 // FP64-rate-bound pass on a GPU whose FP64 rate is 1/64 of its FP32 rate, so
 // each point is first evaluated in FP32 together with a rigorous bound E_i on
-// |u32_i - u64_i|.  A warp takes 256 points at a time (8 per lane, each load
+// |u32_i - u64_i|.  A warp takes 128 points at a time (4 per lane, each load
 // instruction covering 32 consecutive points), bounds their FP32 values,
 // reduces max(u32 - E) and min(u32 + E) over the warp with shuffles, and forms
-// the FP64 value only of the points that can still be an extreme of the 256
+// the FP64 value only of the points that can still be an extreme of the 128
 // (u32_i + E_i >= max_j(u32_j - E_j), and the mirror rule for the minimum):
 // on smooth fields a few points per warp.  The result is the exact FP64
 // extreme, at the cost of one memory pass.
@@ -88,7 +88,8 @@ __device__ __forceinline__ void u_fp32(float2 h, float2 l, float v, float s32, f
     E = __fmaf_rn(2.0f * abs_s, t, __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
 }
 
-constexpr int kWarpPts = 8;                 // points per lane in one warp tile (256 points)
+constexpr int kWarpPts = 4;                 // points per lane in one warp tile (128 points; 64
+                                            // registers, four blocks per SM)
 
 // The points [p0, p1) of one instance (complex64 state + compensated part),
 // by the block's warps in tiles of 256 points.  A non-finite input point
@@ -153,26 +154,17 @@ __device__ __forceinline__ void point64(Ext& e, double2 p, double v, double s) {
     e.umax = fmax(e.umax, u);
 }
 
-// Index of the last entry whose first row is <= b.
-__device__ __forceinline__ int entry_of(const CheckEntry* tab, int count, int b) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (tab[mid].row0 <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Block b covers one contiguous chunk of the points of one entry (the entry
-// whose rows [row0, row1) contain b) and writes one row of partials.
+// whose rows [row0, row1) contain b, row_entry[b]) and writes one row of
+// partials.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __restrict__ tab, int count,
+__global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __restrict__ tab,
+                                                           const int* __restrict__ row_entry,
                                                            const cplx<R>* __restrict__ psi,
                                                            const cplx<R>* __restrict__ lo, const R* __restrict__ V,
                                                            double* __restrict__ partials, int row_base) {
     const int b = row_base + blockIdx.x;
-    const CheckEntry e = tab[entry_of(tab, count, b)];
+    const CheckEntry e = tab[row_entry[b]];
     const int64_t nblk = e.row1 - e.row0;
     const int64_t per = (e.npts + nblk - 1) / nblk;
     const int64_t p0 = (b - e.row0) * per, p1 = min(e.npts, p0 + per);
@@ -250,13 +242,12 @@ int check_rows(int64_t npts) {
 
 cudaError_t launch_entry_check(const CheckLaunch& C, cudaStream_t st) {
     // The entries [inst_base, inst_base + count) and their rows [row_base, row_base + nrows).
-    const int total = C.inst_base + C.count;
     if (C.prec == 0)
-        check_partial<float><<<C.nrows, kThreads, 0, st>>>(C.table, total, (const float2*)C.psi,
+        check_partial<float><<<C.nrows, kThreads, 0, st>>>(C.table, C.row_entry, (const float2*)C.psi,
                                                            (const float2*)C.lo, (const float*)C.V, C.partials,
                                                            C.row_base);
     else
-        check_partial<double><<<C.nrows, kThreads, 0, st>>>(C.table, total, (const double2*)C.psi,
+        check_partial<double><<<C.nrows, kThreads, 0, st>>>(C.table, C.row_entry, (const double2*)C.psi,
                                                             (const double2*)C.lo, (const double*)C.V, C.partials,
                                                             C.row_base);
     cudaError_t e = cudaGetLastError();

@@ -233,6 +233,7 @@ constexpr int kMaxCheckRowsPerEntry = 2048;
 int check_rows(int64_t npts);
 struct CheckLaunch {
     const CheckEntry* table;    // device, all entries, row0 ascending
+    const int* row_entry;       // device, per row: the entry it belongs to
     int count, nrows, prec;     // checks entries inst_base .. inst_base + count - 1, whose rows
     int inst_base = 0;          // are row_base .. row_base + nrows - 1
     int row_base = 0;

@@ -51,8 +51,11 @@ constexpr int al128(int v) { return (v + 127) / 128 * 128; }
 
 // Shared-memory layout.  Input rows and D rows are indexed by column
 // x - (x0 - 2), so a thread's column pair (xa, xa+1) sits at the 16-byte
-// aligned index 2t + 2.  Every TMA destination is 128-byte aligned.
-template <typename R, int NT>
+// aligned index 2t + 2.  Every TMA destination is 128-byte aligned.  The
+// epilogue slots hold only what the stage reads (stage 1: V; stages 2, 3:
+// Psi^n, the accumulator and V; stage 4 in FP32 also the compensated part), so
+// the earlier stages need less shared memory and fit one more CTA per SM.
+template <typename R, int NT, int STAGE>
 struct Lay {
     static constexpr int TXC = 2 * NT;
     static constexpr int CB = (int)sizeof(cplx<R>);
@@ -61,9 +64,11 @@ struct Lay {
     static constexpr int IN_SLOT = al128(IN_BYTES);
     static constexpr int T_BYTES = TXC * CB;                  // one complex output row
     static constexpr int V_BYTES = TXC * (int)sizeof(R);
+    static constexpr bool PA = STAGE >= 2;                    // Psi^n and the accumulator
+    static constexpr bool LO = STAGE == 4 && sizeof(R) == 4;  // the compensated part
     static constexpr int E_PSI = 0, E_ACC = T_BYTES, E_LO = 2 * T_BYTES;
-    static constexpr int E_V = E_LO + (sizeof(R) == 4 ? T_BYTES : 0);
-    static constexpr int E_SLOT = al128(E_V + V_BYTES);
+    static constexpr int E_V = (PA ? 2 * T_BYTES : 0) + (LO ? T_BYTES : 0);
+    static constexpr int E_SLOT = STAGE >= 1 ? al128(E_V + V_BYTES) : 0;
     static constexpr int IN_OFF = 0;
     static constexpr int E_OFF = S * IN_SLOT;
     static constexpr int D_OFF = E_OFF + 2 * E_SLOT;
@@ -106,7 +111,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
     constexpr int TXC = 2 * NT;          // columns per CTA
     constexpr int HB = TXC;              // first input TMA box: x0-2 .. x0+TXC-3; the second: 4 points
     using C = cplx<R>;
-    using L = Lay<R, NT>;
+    using L = Lay<R, NT, STAGE>;
     using T2 = Two<C>;
     constexpr bool NEED_E = STAGE >= 1;          // V on the output row
     constexpr bool NEED_PA = STAGE >= 2;

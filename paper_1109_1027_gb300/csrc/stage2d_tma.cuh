@@ -46,7 +46,7 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     }
     if (STAGE == 4 && sizeof(R) == 4 && !complex_map<R>(&m_lo, L.lo, nx, ny, TXC)) return cudaErrorInvalidValue;
     auto kern = stage2d_tma_kernel<R, LP, STAGE, TY>;
-    const int smem = Lay<R, NT>::TOTAL;
+    const int smem = Lay<R, NT, STAGE>::TOTAL;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
