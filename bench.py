@@ -85,7 +85,7 @@ NCU_TRAFFIC_BATCH = {"9b9d4abea560": {"bytes": 8578984480, "points": 198578176}}
 # = DFMA + DADD + DMUL (each takes one FP64 issue slot).  Keyed by the source
 # hash like the traffic.  2D: 2048^2 dark vortex; 3D: 256^3 vortex ring.
 FP64_WORK_GRID = {"a4c11e7dc514": {"flops": 211.47, "instructions": 150.5}}
-FP64_WORK_3D = {"938607a896a7": {"flops": 333.28, "instructions": 270.3}}
+FP64_WORK_3D = {"acafec411981": {"flops": 287.70, "instructions": 226.68}}
 # The gradient (FP32 state, FP64 dL/dV): per point and RK4 step the forward
 # pass (168 B), the segment recompute (168 B: the same four stages, the stage
 # inputs kept) and the four reversed stages.  Each reads its cotangent w (8),

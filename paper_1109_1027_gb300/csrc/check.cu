@@ -14,13 +14,17 @@
 // (hi + compensated lo) the FP64 evaluation of every point would make this an
 // FP64-rate-bound pass on a GPU whose FP64 rate is 1/64 of its FP32 rate, so
 // each point is first evaluated in FP32 together with a rigorous bound E_i on
-// |u32_i - u64_i|.  A warp takes 128 points at a time (4 per lane, each load
+// |u32_i - u64_i|.  A warp takes 256 points at a time (8 per lane, each load
 // instruction covering 32 consecutive points), bounds their FP32 values,
-// reduces max(u32 - E) and min(u32 + E) over the warp with shuffles, and forms
-// the FP64 value only of the points that can still be an extreme of the 128
-// (u32_i + E_i >= max_j(u32_j - E_j), and the mirror rule for the minimum):
-// on smooth fields a few points per warp.  The result is the exact FP64
-// extreme, at the cost of one memory pass.
+// reduces max(u32 - E) and min(u32 + E) over the warp with shuffles, and keeps
+// only the points that can still be an extreme of the 256 (u32_i + E_i >=
+// max_j(u32_j - E_j), and the mirror rule for the minimum): on smooth fields a
+// few points per tile.  The warp collects those candidates in a shared buffer
+// and forms their FP64 values 32 at a time, every lane busy: an FP64
+// instruction issued for a warp with one useful lane costs as much as one
+// with 32, and at 1/64 of the FP32 rate per-tile evaluation made the check
+// FP64-bound.  The result is the exact FP64 extreme, at the cost of one
+// memory pass.
 #include <cfloat>
 #include <climits>
 
@@ -88,17 +92,37 @@ __device__ __forceinline__ void u_fp32(float2 h, float2 l, float v, float s32, f
     E = __fmaf_rn(2.0f * abs_s, t, __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
 }
 
-constexpr int kWarpPts = 4;                 // points per lane in one warp tile (128 points; 64
-                                            // registers, four blocks per SM)
+constexpr int kWarpPts = 8;                 // points per lane in one warp tile (256 points)
+constexpr int kCand = 64;                   // a warp's candidate buffer: one batch of 32 and an overflow
+
+// The candidates of one warp waiting for their FP64 value: the point's
+// inputs and which extreme it may be (bit 0: maximum, bit 1: minimum).
+struct CandBuf {
+    float2 h[kCand], l[kCand];
+    float v[kCand];
+    int f[kCand];
+};
 
 // The points [p0, p1) of one instance (complex64 state + compensated part),
 // by the block's warps in tiles of 256 points.  A non-finite input point
 // counts as bad (its FP64 value would be non-finite too) and is no candidate.
 __device__ __forceinline__ Ext extremes32(const float2* __restrict__ ps, const float2* __restrict__ ls,
-                                          const float* __restrict__ vs, int64_t p0, int64_t p1, double s) {
+                                          const float* __restrict__ vs, int64_t p0, int64_t p1, double s,
+                                          CandBuf* cb) {
     Ext e = ext_identity();
     const float s32 = (float)s, abs_s = fabsf(s32);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int nc = 0;                                 // buffered candidates (the same in every lane)
+    // FP64 values of the buffered candidates [0, n), n <= 32, one per lane.
+    auto flush = [&](int n) {
+        __syncwarp();
+        if (lane < n) {
+            const double u64 = u_fp64(cb->h[lane], cb->l[lane], cb->v[lane], s);
+            if (cb->f[lane] & 1) e.umax = fmax(e.umax, u64);
+            if (cb->f[lane] & 2) e.umin = fmin(e.umin, u64);
+        }
+        __syncwarp();
+    };
     for (int64_t tb = p0 + (int64_t)warp * 32 * kWarpPts; tb < p1; tb += (int64_t)nwarps * 32 * kWarpPts) {
         float2 h[kWarpPts], l[kWarpPts];
         float v[kWarpPts], u[kWarpPts], E[kWarpPts];
@@ -130,15 +154,27 @@ __device__ __forceinline__ Ext extremes32(const float2* __restrict__ ps, const f
         }
 #pragma unroll
         for (int k = 0; k < kWarpPts; ++k) {
-            if (!use[k]) continue;
-            const bool cmax = !(u[k] + E[k] < lb), cmin = !(u[k] - E[k] > ub);   // true for inf / NaN
+            const bool cmax = use[k] && !(u[k] + E[k] < lb);   // true for an infinite or NaN u32
+            const bool cmin = use[k] && !(u[k] - E[k] > ub);
+            const unsigned m = __ballot_sync(0xffffffffu, cmax || cmin);
             if (cmax || cmin) {
-                const double u64 = u_fp64(h[k], l[k], v[k], s);
-                if (cmax) e.umax = fmax(e.umax, u64);
-                if (cmin) e.umin = fmin(e.umin, u64);
+                const int q = nc + __popc(m & ((1u << lane) - 1u));
+                cb->h[q] = h[k]; cb->l[q] = l[k]; cb->v[q] = v[k];
+                cb->f[q] = (cmax ? 1 : 0) | (cmin ? 2 : 0);
+            }
+            nc += __popc(m);
+            if (nc >= 32) {                     // one full batch; the rest moves to the front
+                flush(32);
+                if (lane < nc - 32) {
+                    cb->h[lane] = cb->h[32 + lane]; cb->l[lane] = cb->l[32 + lane];
+                    cb->v[lane] = cb->v[32 + lane]; cb->f[lane] = cb->f[32 + lane];
+                }
+                __syncwarp();
+                nc -= 32;
             }
         }
     }
+    if (nc) flush(nc);
     return e;
 }
 
@@ -173,7 +209,8 @@ __global__ void __launch_bounds__(kThreads) check_partial(const CheckEntry* __re
     const R* vs = V + e.v_off;
     Ext acc = ext_identity();
     if constexpr (sizeof(R) == 4) {
-        acc = extremes32(ps, ls, vs, p0, p1, e.s);
+        __shared__ CandBuf cand[kThreads / 32];
+        acc = extremes32(ps, ls, vs, p0, p1, e.s, &cand[threadIdx.x >> 5]);
     } else {
         for (int64_t p = p0 + threadIdx.x; p < p1; p += kThreads) point64(acc, ps[p], vs[p], e.s);
     }

@@ -23,6 +23,10 @@
 //                           boundary points D_b of Eq. (dbc_lap);
 //   step 2 (Eq. 2d2shocs2): Lap = D_c - (1/12) sum of the four axial D
 //                           + (1/(6h^2)) (four corner Psi - 4 Psi_c);
+// in FP64 the corner sum of row y is hx(y-1) + hx(y+1), with hx the sum of a
+// point's two x neighbours that step 1 formed for D on those rows, kept in
+// the register window (the same additions, two fewer per point; FP32 forms
+// them again, which keeps its walk within 64 registers);
 // With the multi-storage form (LP = 2) step 1 keeps the two second
 // differences apart, Eq. (2d2shocMs1), D^y in the register window and D^x in
 // the shared ring, and step 2 is Eq. (2d2shocMs2):
@@ -250,6 +254,17 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         }
         return mul2(fma2(m4, ctr, add2(add2(lf, rt), add2(up, dn))), ih2);
     };
+    // The same from the sum hx of the two x neighbours (FP64, which keeps hx).
+    auto dpoint_h = [&](int x, int r, int rl, C ctr, C up, C dn, C hx) -> C {
+        if constexpr (!INNER) {
+            if (x < 0 || x >= nx || r < 0 || r >= ny) return czero<C>();
+            if (x == 0 || x == nx - 1 || rl == 0 || rl == io.rows1 - 1)
+                return bnd_D(ctr, vat(rl, x));
+        }
+        return mul2(fma2(m4, ctr, add2(hx, add2(up, dn))), ih2);
+    };
+    // The x-neighbour sums of this thread's pair on a row (its values, the outer left and right ones).
+    auto hpair = [&](const T2& cc, C l, C r) { return T2{add2(l, cc.b), add2(cc.a, r)}; };
 
     // Multi-storage step 1 at grid point (x, r): (D^x, D^y).  Outside the grid:
     // 0; on the boundary of both axes: 0 (never used).
@@ -275,6 +290,9 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
     wait_in(0); wait_in(1); wait_in(2); wait_in(3);
     bool alive = __syncthreads_and(ok);
     T2 cm, c0, c1, dm, d0;
+    // FP64 single-storage 2SHOC keeps the x-neighbour sums of rows y - 1, y.
+    constexpr bool KEEPH = sizeof(R) == 8 && !MS && !CD;
+    T2 hm, h0;
     C lm, rm, l0, r0;
     T2 dx0;                                      // multi storage: D^x of row y (D^y is in dm, d0, d1)
     if (alive && MS) {
@@ -301,10 +319,19 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         lm = q1[k - 1]; rm = q1[k + 2];
         l0 = q2[k - 1]; r0 = q2[k + 2];
         const int yb = ybase - dir, rlb = rstep(rl_base, -dir);   // the row before the first output row
-        dm.a = dpoint(xa, yb, rlb, cm.a, cmm.a, c0.a, lm, cm.b);
-        dm.b = dpoint(xa + 1, yb, rlb, cm.b, cmm.b, c0.b, cm.a, rm);
-        d0.a = dpoint(xa, ybase, rl_base, c0.a, cm.a, c1.a, l0, c0.b);
-        d0.b = dpoint(xa + 1, ybase, rl_base, c0.b, cm.b, c1.b, c0.a, r0);
+        if constexpr (KEEPH) {
+            hm = hpair(cm, lm, rm);
+            h0 = hpair(c0, l0, r0);
+            dm.a = dpoint_h(xa, yb, rlb, cm.a, cmm.a, c0.a, hm.a);
+            dm.b = dpoint_h(xa + 1, yb, rlb, cm.b, cmm.b, c0.b, hm.b);
+            d0.a = dpoint_h(xa, ybase, rl_base, c0.a, cm.a, c1.a, h0.a);
+            d0.b = dpoint_h(xa + 1, ybase, rl_base, c0.b, cm.b, c1.b, h0.b);
+        } else {
+            dm.a = dpoint(xa, yb, rlb, cm.a, cmm.a, c0.a, lm, cm.b);
+            dm.b = dpoint(xa + 1, yb, rlb, cm.b, cmm.b, c0.b, cm.a, rm);
+            d0.a = dpoint(xa, ybase, rl_base, c0.a, cm.a, c1.a, l0, c0.b);
+            d0.b = dpoint(xa + 1, ybase, rl_base, c0.b, cm.b, c1.b, c0.a, r0);
+        }
         C* drow = dring;                                   // input row 2 -> D ring row 0
         st2(drow + k, d0);
         if (t == 0) drow[1] = dpoint(x0 - 1, ybase, rl_base, l0, q1[1], q3[1], q2[0], c0.a);
@@ -333,7 +360,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         const C* q2 = irow(j + 2);
         const T2 c2 = ld2(q2 + k);
         const C l1 = q1[k - 1], r1 = q1[k + 2];
-        T2 d1, dx1;
+        T2 d1, dx1, h1;
         C* dn = dring + ((j + 1) & 1) * L::ROW;
         if constexpr (MS) {
             const Two<C> pa = ms_point(xa, ya, yla, c1.a, c0.a, c2.a, l1, c1.b);
@@ -344,8 +371,14 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
             if (t == 0) dn[1] = ms_point(x0 - 1, ya, yla, l1, l0, q2[1], q1[0], c1.a).a;
             if (t == NT - 1) dn[TXC + 2] = ms_point(x0 + TXC, ya, yla, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]).a;
         } else {
-            d1.a = dpoint(xa, ya, yla, c1.a, c0.a, c2.a, l1, c1.b);
-            d1.b = dpoint(xa + 1, ya, yla, c1.b, c0.b, c2.b, c1.a, r1);
+            if constexpr (KEEPH) {
+                h1 = hpair(c1, l1, r1);
+                d1.a = dpoint_h(xa, ya, yla, c1.a, c0.a, c2.a, h1.a);
+                d1.b = dpoint_h(xa + 1, ya, yla, c1.b, c0.b, c2.b, h1.b);
+            } else {
+                d1.a = dpoint(xa, ya, yla, c1.a, c0.a, c2.a, l1, c1.b);
+                d1.b = dpoint(xa + 1, ya, yla, c1.b, c0.b, c2.b, c1.a, r1);
+            }
             st2(dn + k, d1);
             if (t == 0) dn[1] = dpoint(x0 - 1, ya, yla, l1, l0, q2[1], q1[0], c1.a);
             if (t == NT - 1) dn[TXC + 2] = dpoint(x0 + TXC, ya, yla, r1, r0, q2[TXC + 2], c1.b, q1[TXC + 3]);
@@ -374,8 +407,15 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
             } else if (!CD) {
                 const C dsa = add2(add2(dr[k - 1], d0.b), add2(dm.a, d1.a));
                 const C dsb = add2(add2(d0.a, dr[k + 2]), add2(dm.b, d1.b));
-                const C cna = add2(add2(lm, cm.b), add2(l1, c1.b));
-                const C cnb = add2(add2(cm.a, rm), add2(c1.a, r1));
+                // corners: the x-neighbour sums of rows y -+ 1
+                C cna, cnb;
+                if constexpr (KEEPH) {
+                    cna = add2(hm.a, h1.a);
+                    cnb = add2(hm.b, h1.b);
+                } else {
+                    cna = add2(add2(lm, cm.b), add2(l1, c1.b));
+                    cnb = add2(add2(cm.a, rm), add2(c1.a, r1));
+                }
                 if (!ba) lap.a = fma2(i6h2, fma2(m4, c0.a, cna), fma2(m12, dsa, d0.a));
                 if (!bb) lap.b = fma2(i6h2, fma2(m4, c0.b, cnb), fma2(m12, dsb, d0.b));
             }
@@ -426,6 +466,7 @@ __device__ __forceinline__ void stage2d_walk(const CUtensorMap* m_in, const CUte
         lm = l0; rm = r0; l0 = l1; r0 = r1;
         cm = c0; c0 = c1; c1 = c2;
         dm = d0; d0 = d1;
+        if constexpr (KEEPH) { hm = h0; h0 = h1; }
         if constexpr (MS) dx0 = dx1;
         yl = yla;
     }
