@@ -77,14 +77,14 @@ BYTES_PER_UPDATE_PLAIN = 720
 # batch with the default tile groups, mean of the wide-tile group's 8 launches
 # (two steps), which covered `points` of the batch's points; the bench scales
 # it to its own launches by points (the traffic is proportional to them).
-NCU_TRAFFIC_GRID = {"3c40de3cc10f": 113541333}
+NCU_TRAFFIC_GRID = {"93cfabc02338": 114148864}
 NCU_TRAFFIC_BATCH = {"9b9d4abea560": {"bytes": 8578984480, "points": 198578176}}
 # FP64 work per grid-point update (one RK4 step) of the FP64 stage kernels,
 # from ncu instruction counts summed over the four stage launches of a step
 # and divided by the points: flops = 2 x DFMA + DADD + DMUL, and instructions
 # = DFMA + DADD + DMUL (each takes one FP64 issue slot).  Keyed by the source
 # hash like the traffic.  2D: 2048^2 dark vortex; 3D: 256^3 vortex ring.
-FP64_WORK_GRID = {"a4c11e7dc514": {"flops": 211.47, "instructions": 150.5}}
+FP64_WORK_GRID = {"93cfabc02338": {"flops": 202.89, "instructions": 141.91}}
 FP64_WORK_3D = {"acafec411981": {"flops": 287.70, "instructions": 226.68}}
 # The gradient (FP32 state, FP64 dL/dV): per point and RK4 step the forward
 # pass (168 B), the segment recompute (168 B: the same four stages, the stage
