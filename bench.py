@@ -78,7 +78,7 @@ BYTES_PER_UPDATE_PLAIN = 720
 # (two steps), which covered `points` of the batch's points; the bench scales
 # it to its own launches by points (the traffic is proportional to them).
 NCU_TRAFFIC_GRID = {"93cfabc02338": 114148864}
-NCU_TRAFFIC_BATCH = {"9b9d4abea560": {"bytes": 8578984480, "points": 198578176}}
+NCU_TRAFFIC_BATCH = {"d8632e21fd29": {"bytes": 8571187616, "points": 198578176}}
 # FP64 work per grid-point update (one RK4 step) of the FP64 stage kernels,
 # from ncu instruction counts summed over the four stage launches of a step
 # and divided by the points: flops = 2 x DFMA + DADD + DMUL, and instructions

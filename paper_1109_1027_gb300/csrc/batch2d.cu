@@ -27,7 +27,7 @@
 namespace nlse {
 namespace {
 
-constexpr int TYB = 16;                       // rows per tile
+constexpr int TYB = 32;                       // rows per tile
 
 // One instance's tensor maps and scalars (device-resident; CUtensorMap's own
 // alignment keeps every map 64-byte aligned, as TMA descriptors in global
