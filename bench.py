@@ -85,7 +85,7 @@ NCU_TRAFFIC_BATCH = {"d8632e21fd29": {"bytes": 8571187616, "points": 198578176}}
 # = DFMA + DADD + DMUL (each takes one FP64 issue slot).  Keyed by the source
 # hash like the traffic.  2D: 2048^2 dark vortex; 3D: 256^3 vortex ring.
 FP64_WORK_GRID = {"93cfabc02338": {"flops": 202.89, "instructions": 141.91}}
-FP64_WORK_3D = {"acafec411981": {"flops": 287.70, "instructions": 226.68}}
+FP64_WORK_3D = {"05d6af1dabeb": {"flops": 264.27, "instructions": 203.26}}
 # The gradient (FP32 state, FP64 dL/dV): per point and RK4 step the forward
 # pass (168 B), the segment recompute (168 B: the same four stages, the stage
 # inputs kept) and the four reversed stages.  Each reads its cotangent w (8),

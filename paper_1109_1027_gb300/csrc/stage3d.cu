@@ -3,8 +3,8 @@
 // the TMA-fed FP32 kernel is in stage3d_tma.cu.
 //
 // One CTA owns a TX x TY column of the grid over TZ consecutive z planes and
-// streams through them (2.5D blocking): shared memory holds a ring of four
-// stage-input planes (z-1 .. z+2, each with a 2-point xy halo) and three D
+// streams through them (2.5D blocking): shared memory holds a ring of three
+// stage-input planes (z .. z+2, each with a 2-point xy halo) and three D
 // planes (z-1 .. z+1, 1-point xy halo).  Per plane it loads input plane z+2,
 // computes step 1, the seven-point D of Eq. (3d2shocs), for plane z+1
 // (boundary points take D_b of Eq. dbc_lap), and evaluates step 2,
@@ -13,11 +13,14 @@
 //           + (1/(6h^2))[sum of the twelve edge neighbours of Psi - 12 Psi_c],
 // then F, the Dirichlet rule F_b = 0 and the RK4 stage epilogue for plane z.
 // Each input plane is read once per CTA, so the halo overhead is only the xy
-// ring plus four planes per TZ.  Step 1 forms, at every point of the tile, the
-// sum q of its four in-plane axial neighbours; a three-plane ring keeps it,
-// and step 2 takes the x-z and y-z edge terms of plane z as q(z-1) + q(z+1)
-// instead of adding the eight values again (12 fewer FP64 additions per point
-// and stage, which bound the FP64 kernel on this GPU).
+// ring plus four planes per TZ.  Step 1 forms, at every point, the sum hx of
+// its two x neighbours and the sum q of its four in-plane axial neighbours;
+// rings keep them, and step 2 takes the x-z and y-z edge terms of plane z as
+// q(z-1) + q(z+1) and the four in-plane diagonals as hx(y-1) + hx(y+1)
+// instead of adding the values again (16 fewer FP64 additions per point and
+// stage; FP64 arithmetic bounds the FP64 kernel on this GPU).  The FP64
+// stages also carry a Lap: the a of F goes into the difference weights and the
+// boundary value a D_b = -N_b Psi_b (Eq. dbc_lap), two multiplies fewer.
 #include "nlse_device.cuh"
 #include "tmap.cuh"
 
@@ -37,9 +40,14 @@ __global__ void __launch_bounds__(NT)
 stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sP = reinterpret_cast<C*>(smem_raw);   // [4][PY][PX]
-    C* sD = sP + 4 * PP;                      // [3][DY][DX]
+    C* sP = reinterpret_cast<C*>(smem_raw);   // [3][PY][PX]
+    C* sD = sP + 3 * PP;                      // [3][DY][DX]
     C* sQ = sD + 3 * DP;                      // [3][TY][TX]: in-plane axial sums of the tile's points
+    C* sH = sQ + 3 * TX * TY;                 // [2][TY+2][TX]: x-neighbour sums, tile columns, rows y0-1 .. y0+TY
+    // FP64 stages fold a into the weights (a Lap instead of Lap); FP32 and the
+    // standalone Laplacian keep the unscaled form.
+    constexpr bool SC = sizeof(R) == 8 && STAGE >= 1;
+    const R wd = SC ? c.a * c.inv_h2 : c.inv_h2, we = SC ? c.a * c.inv_6h2 : c.inv_6h2;
 
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const int z1 = min(z0 + TZ, nz);
@@ -50,7 +58,7 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     }
 
     auto load_plane = [&](int gz) {
-        C* dst = sP + pslot(gz) * PP;
+        C* dst = sP + dslot(gz) * PP;
         const bool zin = gz >= 0 && gz < nz;
         for (int i = tid; i < PP; i += NT) {
             int ly = i / PX, lx = i - ly * PX;
@@ -64,9 +72,10 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
     auto d_plane = [&](int gz) {
         C* dst = sD + dslot(gz) * DP;
         C* qdst = sQ + dslot(gz) * (TX * TY);
-        const C* pm = sP + pslot(gz - 1) * PP;
-        const C* pc = sP + pslot(gz) * PP;
-        const C* pp = sP + pslot(gz + 1) * PP;
+        C* hdst = sH + ((gz + 2) & 1) * (TX * (TY + 2));
+        const C* pm = sP + dslot(gz - 1) * PP;
+        const C* pc = sP + dslot(gz) * PP;
+        const C* pp = sP + dslot(gz + 1) * PP;
         const bool zin = gz >= 0 && gz < nz;
         const bool zb = gz == 0 || gz == nz - 1;
         for (int i = tid; i < DP; i += NT) {
@@ -75,41 +84,48 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             int k = (ly + 1) * PX + (lx + 1);
             C d = czero<C>();
             if (!(NLSE_IDX(io.flag, k - PX, PP, kSiteStage3d) && NLSE_IDX(io.flag, k + PX, PP, kSiteStage3d))) continue;
-            // in-plane axial sum (the values outside the grid read as zero)
-            const C q = cadd(cadd(pc[k + 1], pc[k - 1]), cadd(pc[k + PX], pc[k - PX]));
+            // in-plane neighbour sums (the values outside the grid read as zero)
+            const C hx = cadd(pc[k + 1], pc[k - 1]);
+            const C q = cadd(hx, cadd(pc[k + PX], pc[k - PX]));
+            if (lx >= 1 && lx <= TX && NLSE_IDX(io.flag, ly * TX + lx - 1, TX * (TY + 2), kSiteStage3d))
+                hdst[ly * TX + (lx - 1)] = hx;
             if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY &&
                 NLSE_IDX(io.flag, (ly - 1) * TX + lx - 1, TX * TY, kSiteStage3d))
                 qdst[(ly - 1) * TX + (lx - 1)] = q;
             if (zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
                 C ctr = pc[k];
                 if (zb || gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
-                    if (NLSE_IDX(io.flag, gz * plane + (int64_t)gy * nx + gx, plane * nz, kSiteStage3d))
-                        d = dirichlet_D(c, ctr, io.V[gz * plane + (int64_t)gy * nx + gx]);
+                    if (NLSE_IDX(io.flag, gz * plane + (int64_t)gy * nx + gx, plane * nz, kSiteStage3d)) {
+                        const R vb = io.V[gz * plane + (int64_t)gy * nx + gx];
+                        d = SC ? cscale(-nonlin(c.s, ctr, vb), ctr) : dirichlet_D(c, ctr, vb);
+                    }
                 } else {
                     C sum = cadd(q, cadd(pp[k], pm[k]));
-                    d = cscale(c.inv_h2, csub(sum, cscale((R)6, ctr)));
+                    d = cscale(wd, csub(sum, cscale((R)6, ctr)));
                 }
             }
             dst[i] = d;
         }
     };
 
-    for (int gz = z0 - 2; gz <= z0 + 1; ++gz) load_plane(gz);
+    for (int gz = z0 - 2; gz <= z0; ++gz) load_plane(gz);
     __syncthreads();
     d_plane(z0 - 1);
+    __syncthreads();
+    load_plane(z0 + 1);                       // into the slot of plane z0 - 2
+    __syncthreads();
     d_plane(z0);
     __syncthreads();
 
     bool bad = false;
     for (int gz = z0; gz < z1; ++gz) {
-        load_plane(gz + 2);
+        load_plane(gz + 2);                   // into the slot of plane gz - 1
         __syncthreads();
         d_plane(gz + 1);
         __syncthreads();
 
-        const C* pm = sP + pslot(gz - 1) * PP;
-        const C* pc = sP + pslot(gz) * PP;
-        const C* pp = sP + pslot(gz + 1) * PP;
+        const C* pc = sP + dslot(gz) * PP;    // step 2 reads input plane gz only
+        const C* hc = sH + ((gz + 2) & 1) * (TX * (TY + 2));
         const C* dm = sD + dslot(gz - 1) * DP;
         const C* dc = sD + dslot(gz) * DP;
         const C* dp = sD + dslot(gz + 1) * DP;
@@ -125,6 +141,7 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             const int kd = (ly + 1) * DX + (lx + 1);
             if (!(NLSE_IDX(io.flag, k - PX - 1, PP, kSiteStage3d) && NLSE_IDX(io.flag, k + PX + 1, PP, kSiteStage3d) &&
                   NLSE_IDX(io.flag, kd - DX, DP, kSiteStage3d) && NLSE_IDX(io.flag, kd + DX, DP, kSiteStage3d) &&
+                  NLSE_IDX(io.flag, (ly + 2) * TX + lx, TX * (TY + 2), kSiteStage3d) &&
                   NLSE_IDX(io.flag, p, plane * nz, kSiteStage3d)))
                 continue;
             const C y = pc[k];
@@ -135,18 +152,27 @@ stage3d_kernel(StageIO<R> io, Coef<R> c, int nx, int ny, int nz) {
             } else {
                 C dsum = cadd(cadd(cadd(dc[kd + 1], dc[kd - 1]), cadd(dc[kd + DX], dc[kd - DX])),
                               cadd(dp[kd], dm[kd]));
-                // the twelve edge neighbours: the four in-plane diagonals, and the
-                // in-plane axial sums of planes z -+ 1 kept by step 1
-                C exy = cadd(cadd(pc[k + PX + 1], pc[k + PX - 1]), cadd(pc[k - PX + 1], pc[k - PX - 1]));
+                // the twelve edge neighbours, from the sums step 1 kept: the four
+                // in-plane diagonals as hx(y+1) + hx(y-1), and the in-plane axial
+                // sums of planes z -+ 1
+                C exy = cadd(hc[(ly + 2) * TX + lx], hc[ly * TX + lx]);
                 C edges = cadd(exy, cadd(qm[i], qp[i]));
                 C dpart = cscale((R)(-1.0 / 12.0), csub(dsum, cscale((R)10, dc[kd])));
-                C ppart = cscale(c.inv_6h2, csub(edges, cscale((R)12, y)));
+                C ppart = cscale(we, csub(edges, cscale((R)12, y)));
                 lap = cadd(dpart, ppart);
             }
             if constexpr (STAGE == 0) {
                 io.lap[p] = lap;
             } else {
-                C F = bnd ? czero<C>() : rhs_point(c, y, lap, io.V[p]);
+                C F = czero<C>();
+                if (!bnd) {
+                    if constexpr (SC) {
+                        const R N = nonlin(c.s, y, io.V[p]);           // F = i [a Lap + N y]
+                        F = ctimesi(cmake<C>(lap.x + N * y.x, lap.y + N * y.y));
+                    } else {
+                        F = rhs_point(c, y, lap, io.V[p]);
+                    }
+                }
                 bad |= stage_epilogue<STAGE>(io, p, y, F);
             }
         }
@@ -330,7 +356,7 @@ cudaError_t launch_t(const StageLaunch& L, cudaStream_t st) {
     if (!CD && L.lap == 2) return launch_ms<R, STAGE>(L, st);
     const int nx = (int)L.n[0], ny = (int)L.n[1], nz = (int)L.n[2];
     dim3 grid((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ);
-    size_t smem = sizeof(cplx<R>) * (4 * PP + 3 * DP + 3 * TX * TY);
+    size_t smem = sizeof(cplx<R>) * (3 * PP + 3 * DP + 3 * TX * TY + 2 * TX * (TY + 2));
     auto kern = stage3d_kernel<R, CD, STAGE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
