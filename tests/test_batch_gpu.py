@@ -128,34 +128,41 @@ def test_batch_refuses_an_unstable_instance():
 
 
 def test_batch_workload_sample_equals_single_grid():
-    """The 512-instance batch workload (sides 64..1024): 3 steps of the whole
-    batch, sampled instances compared with their single-grid runs."""
+    """The 512-instance batch workload (sides 64..1024) at full size, in the
+    launch configuration the benchmark times: 3 steps of the whole batch;
+    sampled instances compared with their single-grid runs and with the FP64
+    oracle (FP32 inputs, relative L2 <= 1e-5).  The sampled instances' dt is
+    the oracle's bound; the others take the library's."""
     insts = wl.gaussian_batch_2d(count=512, steps=0)
-    dts = []
-    Vs, psis = [], []
-    for q in insts:
-        Vs.append(q.V)
-        psis.append(q.psi0)
-    # dt from the library's own FP64 bound, instance by instance (no oracle on 2e8 points)
-    Vf = nlse.BatchSolver.pack(Vs, torch.float32, DEV)
+    sample = [0, 1, 17, 100, 255, 256, 400, 511]
+    r32 = lambda z: z.astype(np.complex64).astype(np.complex128) if np.iscomplexobj(z) \
+        else z.astype(np.float32).astype(np.float64)
+    Vf = nlse.BatchSolver.pack([q.V for q in insts], torch.float32, DEV)
     probe = nlse.BatchSolver(Vf, [q.shape for q in insts], [q.h for q in insts], 1e-9,
                              [q.a for q in insts], [q.s for q in insts], prec="fp32", check_stability=False)
-    psi = nlse.BatchSolver.pack(psis, torch.complex64, DEV)
+    psi = nlse.BatchSolver.pack([q.psi0 for q in insts], torch.complex64, DEV)
     _, _, dtmax = probe.invariants(psi)
     probe.close()
     dts = [0.5 * d for d in dtmax]
+    probs = {i: oracle.Problem(insts[i].shape, insts[i].h, insts[i].a, insts[i].s) for i in sample}
+    for i in sample:
+        dts[i] = 0.5 * oracle.invariants(probs[i], r32(insts[i].psi0), r32(insts[i].V))[2]
     bs = nlse.BatchSolver(Vf, [q.shape for q in insts], [q.h for q in insts], dts,
                           [q.a for q in insts], [q.s for q in insts], prec="fp32")
     bs.run(psi, 3)
     bs.check()
     out = bs.unpack(psi)
-    for i in [0, 1, 17, 100, 255, 256, 400, 511]:
+    for i in sample:
         q = insts[i]
         sv = nlse.Solver(torch.from_numpy(q.V).to(DEV).float().contiguous(), q.h, dts[i], q.a, q.s)
         x = torch.from_numpy(q.psi0).to(DEV).to(torch.complex64).contiguous()
         sv.run(x, 3)
         diff = (out[i] - x).abs().max().item()
         assert diff <= 1e-6 * x.abs().max().item(), (i, q.shape, diff)
+        ref = oracle.run(probs[i], r32(q.psi0), r32(q.V), dts[i], 3)
+        got = out[i].cpu().numpy().astype(np.complex128)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-5, (i, q.shape, err)
 
 
 def test_batch_tiling_variants_give_identical_results():
