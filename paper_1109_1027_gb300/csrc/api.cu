@@ -533,13 +533,15 @@ int report_status(nlse_ctx* c, const nlse::StatusBlock& s, cudaStream_t st) {
 int setup_host_pipe(nlse_ctx* c) {
     const int n = std::min(16, c->count);
     std::vector<int> first(1, 0);
+    // Chunk targets: the first and the last chunk a quarter of the others, so
+    // that the pipeline fills and drains sooner.
+    std::vector<double> cum(n + 1, 0.0);
+    for (int k = 0; k < n; ++k) cum[k + 1] = cum[k] + ((k == 0 || k == n - 1) && n > 2 ? 0.25 : 1.0);
     int64_t done = 0;
     for (int i = 0; i < c->count; ++i) {
         done += c->bparams[i].n[0] * c->bparams[i].n[1];
-        // Chunk k - 1 ends after instance i once it reaches k / n of the points
-        // (fewer chunks when large instances overshoot; none is empty).
         const int k = (int)first.size();
-        if (k < n && done * n >= (int64_t)k * c->npts && i + 1 < c->count) first.push_back(i + 1);
+        if (k < n && (double)done >= cum[k] / cum[n] * (double)c->npts && i + 1 < c->count) first.push_back(i + 1);
     }
     first.push_back(c->count);
     const int nch = (int)first.size() - 1;
