@@ -80,6 +80,9 @@ struct nlse_ctx {
     double* check_bounds;
     double* partials;         // reduction scratch, nblocks x kPartialWidth
     int nblocks;
+    double* epartials;        // 2D Dirichlet: rows of the tiled energy pass (etiles)
+    int* emap;                // batch: per energy tile its instance
+    int etiles;
     double* red_out;          // reduced values on the device
     double* host_out;         // pinned copy of red_out
     const void* state_psi;    // psi whose compensated part lo currently holds
@@ -370,6 +373,7 @@ int invariants_impl(nlse_ctx* c, const void* psi, double* mass, double* energy, 
     L.lo = (c->lo && psi == c->state_psi) ? c->lo : nullptr;
     L.V = c->V;
     L.energy = energy != nullptr;
+    L.epartials = c->epartials;
     NLSE_CUDA(nlse::launch_invariants(L, c->partials, c->nblocks, c->red_out, st), "invariants launch");
     NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth,
                               cudaMemcpyDeviceToHost, st), "invariants copy");
@@ -400,6 +404,9 @@ int invariants_batch_impl(nlse_ctx* c, const void* psi, double* mass, double* en
     B.energy = energy != nullptr;
     B.partials = c->partials;
     B.out = c->red_out;
+    B.emap = c->emap;
+    B.etiles = c->etiles;
+    B.epartials = c->epartials;
     NLSE_CUDA(nlse::launch_invariants_batch(B, st), "invariants launch");
     NLSE_CUDA(cudaMemcpyAsync(c->host_out, c->red_out, sizeof(double) * nlse::kPartialWidth * c->count,
                               cudaMemcpyDeviceToHost, st), "invariants copy");
@@ -737,6 +744,8 @@ void release(nlse_ctx* c) {
     for (int i = 0; i < 4; ++i) cudaFree(c->plain[i]);
     cudaFree(c->status);
     cudaFree(c->partials);
+    cudaFree(c->epartials);
+    cudaFree(c->emap);
     cudaFree(c->red_out);
     cudaFreeHost(c->host_out);
     delete c;
@@ -793,6 +802,10 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
         c->nblocks = nlse::inv_num_blocks(L, nsm);
     }
     TRY(cudaMalloc((void**)&c->partials, sizeof(double) * nlse::kPartialWidth * c->nblocks), "allocating partials");
+    if (p->dim == 2 && p->bc == NLSE_BC_DIRICHLET) {
+        c->etiles = nlse::energy2d_tiles(p->n[0], p->n[1] * c->stack);
+        TRY(cudaMalloc((void**)&c->epartials, sizeof(double) * c->etiles), "allocating energy partials");
+    }
     TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth), "allocating result");
     TRY(cudaMallocHost((void**)&c->host_out, sizeof(double) * nlse::kPartialWidth), "allocating pinned result");
 #undef TRY
@@ -870,6 +883,7 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
         "allocating pinned results");
     {
         std::vector<nlse::InvBatchEntry> tab(count);
+        std::vector<int> emap;
         for (int i = 0; i < count; ++i) {
             tab[i].off = c->boff[i];
             tab[i].nx = (int)p[i].n[0];
@@ -877,6 +891,16 @@ int nlse_create_batch(int count, const nlse_params* p, const void* V_dev, nlse_c
             tab[i].h = p[i].h; tab[i].a = p[i].a; tab[i].s = p[i].s;
             tab[i].row0 = c->brow[i];
             tab[i].row1 = c->brow[i + 1];
+            tab[i].erow0 = (int)emap.size();
+            if (p[0].bc == NLSE_BC_DIRICHLET) emap.resize(emap.size() + nlse::energy2d_tiles(p[i].n[0], p[i].n[1]), i);
+            tab[i].erow1 = (int)emap.size();
+        }
+        if (!emap.empty()) {
+            c->etiles = (int)emap.size();
+            TRY(cudaMalloc((void**)&c->epartials, sizeof(double) * c->etiles), "allocating energy partials");
+            TRY(cudaMalloc((void**)&c->emap, sizeof(int) * c->etiles), "allocating the energy tile map");
+            TRY(cudaMemcpy(c->emap, emap.data(), sizeof(int) * c->etiles, cudaMemcpyHostToDevice),
+                "uploading the energy tile map");
         }
         TRY(cudaMalloc((void**)&c->inv_table, sizeof(nlse::InvBatchEntry) * count), "allocating the instance table");
         TRY(cudaMemcpy(c->inv_table, tab.data(), sizeof(nlse::InvBatchEntry) * count, cudaMemcpyHostToDevice),

@@ -10,6 +10,14 @@
 // it, and the block reduces with warp shuffles.  Every block writes one row
 // of partials to scratch; a single-block kernel then reduces the rows in a
 // fixed order, so the result is deterministic for a given launch shape.
+//
+// 2D Dirichlet grids (single, stacked or batched) take the energy from a
+// tiled pass instead: a block converts its 36 x 12 window of the state to
+// FP64 once into shared memory, forms D on the 34 x 10 ring around its
+// 32 x 8 tile there, and the Laplacian and the energy density of its points
+// from those; the grid-stride pass then skips the energy.  Evaluating the
+// Laplacian point by point from global memory converted every value to FP64
+// some thirty times, at an FP64 rate 1/64 of the FP32 rate.
 #include <cfloat>
 
 #include "nlse_device.cuh"
@@ -256,6 +264,168 @@ __device__ void accumulate(const InvView<R>& v, int64_t npts, int64_t first, int
     }
 }
 
+// ---- the tiled energy pass (2D, Dirichlet) ------------------------------
+
+constexpr int kETX = 32, kETY = 8;                    // a block's tile: one point per thread
+constexpr int kEPX = kETX + 4, kEPY = kETY + 4;       // the state with a 2-point halo
+constexpr int kEDX = kETX + 2, kEDY = kETY + 2;       // D with a 1-point halo
+static_assert(kETX * kETY == kInvThreads, "one point per thread");
+
+template <typename R>
+struct EGrid {
+    const cplx<R>* psi;
+    const cplx<R>* lo;
+    const R* V;                 // rows1 rows (shared by a stack's instances)
+    int nx, ny, rows1;          // ny: all rows of a stack; the Dirichlet rows are 0 and rows1-1 of each
+    int lap;
+    double a, s, inv_a, inv_h2, inv_6h2;
+};
+
+// Sum over the block of one double per thread, in a fixed order; thread 0
+// returns it.
+__device__ double block_sum(double x) {
+    __shared__ double warp_tot[kInvThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();                                   // warp_tot may still be read by a previous call
+    if (lane == 0) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        x = lane < kInvThreads / 32 ? warp_tot[lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    }
+    return x;
+}
+
+// The energy density -a Re(conj(Psi) Lap Psi) + V |Psi|^2 - (s/2) |Psi|^4
+// summed over the interior points of the tile at (x0, y0); thread 0 returns
+// the block's sum.  D, the Laplacian and the density follow d_interior,
+// d_any (Dirichlet) and lap_interior above, term by term.
+template <typename R>
+__device__ double energy_tile(const EGrid<R>& g, int x0, int y0) {
+    __shared__ double2 sP[kEPY * kEPX];
+    __shared__ double2 sD[kEDY * kEDX];
+    const int t = threadIdx.x;
+    auto vat = [&](int y, int x) { return (double)g.V[(int64_t)(y % g.rows1) * g.nx + x]; };
+    for (int i = t; i < kEPY * kEPX; i += kInvThreads) {
+        const int ly = i / kEPX, lx = i - ly * kEPX;
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly;
+        double2 v = make_double2(0.0, 0.0);
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+            const int64_t p = (int64_t)y * g.nx + x;
+            const cplx<R> z = g.psi[p];
+            v = make_double2((double)z.x, (double)z.y);
+            if (g.lo) {
+                const cplx<R> l = g.lo[p];
+                v.x += (double)l.x;
+                v.y += (double)l.y;
+            }
+        }
+        sP[i] = v;
+    }
+    __syncthreads();
+    for (int i = t; i < kEDY * kEDX; i += kInvThreads) {
+        const int ly = i / kEDX, lx = i - ly * kEDX;
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+        const double2* c = sP + (ly + 1) * kEPX + (lx + 1);
+        double2 d = make_double2(0.0, 0.0);
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+            const int yl = y % g.rows1;
+            if (x == 0 || x == g.nx - 1 || yl == 0 || yl == g.rows1 - 1) {
+                const double Nb = g.s * (c[0].x * c[0].x + c[0].y * c[0].y) - vat(y, x);
+                d = make_double2(-Nb * g.inv_a * c[0].x, -Nb * g.inv_a * c[0].y);
+            } else {
+                double2 sum = make_double2(0.0, 0.0);
+                sum.x += c[1].x + c[-1].x;
+                sum.y += c[1].y + c[-1].y;
+                sum.x += c[kEPX].x + c[-kEPX].x;
+                sum.y += c[kEPX].y + c[-kEPX].y;
+                d = make_double2((sum.x - 4.0 * c[0].x) * g.inv_h2, (sum.y - 4.0 * c[0].y) * g.inv_h2);
+            }
+        }
+        sD[i] = d;
+    }
+    __syncthreads();
+    double e = 0.0;
+    const int lx = t % kETX, ly = t / kETX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x > 0 && x < g.nx - 1 && y < g.ny) {
+        const int yl = y % g.rows1;
+        if (yl > 0 && yl < g.rows1 - 1) {
+            const double2* c = sP + (ly + 2) * kEPX + (lx + 2);
+            const double2* dd = sD + (ly + 1) * kEDX + (lx + 1);
+            double2 lp = dd[0];
+            if (g.lap != 1) {
+                double2 dsum = make_double2(0.0, 0.0);
+                const double2 dn[4] = {dd[-1], dd[1], dd[-kEDX], dd[kEDX]};
+                for (int q = 0; q < 4; ++q) {
+                    dsum.x += dn[q].x;
+                    dsum.y += dn[q].y;
+                }
+                double2 edges = make_double2(0.0, 0.0);
+                const double2 en[4] = {c[-kEPX - 1], c[kEPX - 1], c[-kEPX + 1], c[kEPX + 1]};
+                for (int q = 0; q < 4; ++q) {
+                    edges.x += en[q].x;
+                    edges.y += en[q].y;
+                }
+                lp = make_double2(1.0 * dd[0].x - dsum.x / 12.0 + (edges.x - 4.0 * c[0].x) * g.inv_6h2,
+                                  1.0 * dd[0].y - dsum.y / 12.0 + (edges.y - 4.0 * c[0].y) * g.inv_6h2);
+            }
+            const double rho = c[0].x * c[0].x + c[0].y * c[0].y;
+            e = -g.a * (c[0].x * lp.x + c[0].y * lp.y) + vat(y, x) * rho - 0.5 * g.s * rho * rho;
+        }
+    }
+    return block_sum(e);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) energy2d_partial(EGrid<R> g, double* epartials) {
+    const int ntx = (g.nx + kETX - 1) / kETX;
+    const int b = blockIdx.x;
+    const double e = energy_tile(g, (b % ntx) * kETX, (b / ntx) * kETY);
+    if (threadIdx.x == 0) epartials[b] = e;
+}
+
+// A batch: block b belongs to instance emap[b], whose tiles are numbered as
+// in a launch for that instance alone, so the rows equal those of one launch
+// per instance.
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) energy2d_batch_partial(const InvBatchEntry* __restrict__ tab,
+                                                                      const int* __restrict__ emap,
+                                                                      const cplx<R>* psi, const cplx<R>* lo,
+                                                                      const R* V, int lap, double* epartials) {
+    const int b = blockIdx.x;
+    const InvBatchEntry e = tab[emap[b]];
+    EGrid<R> g;
+    g.psi = psi + e.off;
+    g.lo = lo ? lo + e.off : nullptr;
+    g.V = V + e.off;
+    g.nx = e.nx; g.ny = e.ny; g.rows1 = e.ny;
+    g.lap = lap;
+    g.a = e.a; g.s = e.s; g.inv_a = 1.0 / e.a;
+    g.inv_h2 = 1.0 / (e.h * e.h); g.inv_6h2 = 1.0 / (6.0 * e.h * e.h);
+    const int ntx = (e.nx + kETX - 1) / kETX, tl = b - e.erow0;
+    const double s = energy_tile(g, (tl % ntx) * kETX, (tl / ntx) * kETY);
+    if (threadIdx.x == 0) epartials[b] = s;
+}
+
+// The rows [0, n) in a fixed order into *out (the energy slot of a result row).
+__global__ void __launch_bounds__(kInvThreads) energy_final(const double* __restrict__ rows, int n, double* out) {
+    double x = 0.0;
+    for (int i = threadIdx.x; i < n; i += kInvThreads) x += rows[i];
+    x = block_sum(x);
+    if (threadIdx.x == 0) *out = x;
+}
+
+__global__ void __launch_bounds__(kInvThreads) energy_batch_final(const InvBatchEntry* __restrict__ tab,
+                                                                  const double* __restrict__ rows, double* out) {
+    const InvBatchEntry e = tab[blockIdx.x];
+    double x = 0.0;
+    for (int i = e.erow0 + threadIdx.x; i < e.erow1; i += kInvThreads) x += rows[i];
+    x = block_sum(x);
+    if (threadIdx.x == 0) out[(int64_t)blockIdx.x * kPartialWidth + 1] = x;
+}
+
 __device__ __forceinline__ void write_row(double* row, const Acc& a) {
     row[0] = a.mass; row[1] = a.energy; row[2] = a.lmin;
     row[3] = a.lmax; row[4] = a.bmax; row[5] = a.nonfinite;
@@ -361,15 +531,30 @@ cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* 
     int64_t npts = (int64_t)v.n[0] * v.n[1] * v.n[2];
     v.rows1 = (int)(L.rows1 ? L.rows1 : v.n[1]);
     v.vpts = (int64_t)v.n[0] * v.rows1 * v.n[2];
-    if (L.energy) invariants_partial<R, true><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
+    const bool tiled = L.energy && L.dim == 2 && L.bc == 0 && L.epartials;
+    if (L.energy && !tiled) invariants_partial<R, true><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     else invariants_partial<R, false><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     invariants_final<<<1, kInvThreads, 0, st>>>(partials, nblocks, out);
+    if ((e = cudaGetLastError()) != cudaSuccess || !tiled) return e;
+    EGrid<R> g;
+    g.psi = v.psi; g.lo = v.lo; g.V = v.V;
+    g.nx = v.n[0]; g.ny = v.n[1]; g.rows1 = v.rows1;
+    g.lap = L.lap;
+    g.a = v.a; g.s = v.s; g.inv_a = v.inv_a; g.inv_h2 = v.inv_h2; g.inv_6h2 = v.inv_6h2;
+    const int ntiles = energy2d_tiles(v.n[0], v.n[1]);
+    energy2d_partial<R><<<ntiles, kInvThreads, 0, st>>>(g, L.epartials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    energy_final<<<1, kInvThreads, 0, st>>>(L.epartials, ntiles, out + 1);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int energy2d_tiles(int64_t nx, int64_t ny) {
+    return (int)(((nx + kETX - 1) / kETX) * ((ny + kETY - 1) / kETY));
+}
 
 int inv_num_blocks(const InvLaunch& L, int num_sms) {
     int64_t npts = 1;
@@ -391,7 +576,8 @@ cudaError_t launch_batch_r(const InvBatchLaunch& B, cudaStream_t st) {
     const cplx<R>* psi = (const cplx<R>*)B.psi;
     const cplx<R>* lo = (const cplx<R>*)B.lo;
     const R* V = (const R*)B.V;
-    if (B.energy)
+    const bool tiled = B.energy && B.bc == 0 && B.emap;
+    if (B.energy && !tiled)
         invariants_batch_partial<R, true><<<B.nrows, kInvThreads, 0, st>>>(B.table, B.count, psi, lo, V, B.bc, B.lap,
                                                                            B.partials);
     else
@@ -400,6 +586,10 @@ cudaError_t launch_batch_r(const InvBatchLaunch& B, cudaStream_t st) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     invariants_batch_final<<<B.count, kInvThreads, 0, st>>>(B.table, B.partials, B.out);
+    if ((e = cudaGetLastError()) != cudaSuccess || !tiled) return e;
+    energy2d_batch_partial<R><<<B.etiles, kInvThreads, 0, st>>>(B.table, B.emap, psi, lo, V, B.lap, B.epartials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    energy_batch_final<<<B.count, kInvThreads, 0, st>>>(B.table, B.epartials, B.out);
     return cudaGetLastError();
 }
 }  // namespace

@@ -190,9 +190,12 @@ struct InvLaunch {
     const void* V;
     bool energy = true;     // false: skip the energy sum (mass, extremes and count only)
     int64_t rows1 = 0;      // 2D stack: rows per instance (0: not stacked)
+    double* epartials = nullptr;   // 2D Dirichlet: energy2d_tiles rows for the tiled energy pass
 };
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);
+// Tiles (blocks) of the tiled energy pass over an nx x ny grid.
+int energy2d_tiles(int64_t nx, int64_t ny);
 
 // Invariants of every instance of a batch in one launch (plus one for the
 // per-instance reduction), with the partial rows a launch per instance gives.
@@ -201,6 +204,7 @@ struct InvBatchEntry {
     int nx, ny;
     double h, a, s;
     int row0, row1;         // its rows of partials
+    int erow0, erow1;       // its tiles of the tiled energy pass
 };
 struct InvBatchLaunch {
     const InvBatchEntry* table;   // device, count entries, row0 ascending
@@ -212,6 +216,9 @@ struct InvBatchLaunch {
     bool energy;
     double* partials;       // nrows x kPartialWidth
     double* out;            // count x kPartialWidth
+    const int* emap = nullptr;     // Dirichlet: per energy tile its instance (nullptr: no tiled pass)
+    int etiles = 0;
+    double* epartials = nullptr;   // etiles
 };
 cudaError_t launch_invariants_batch(const InvBatchLaunch& B, cudaStream_t st);
 
