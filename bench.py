@@ -654,6 +654,18 @@ def run_grid_legs(args, dev, rank, world, stream, barrier, max_over_ranks, fp64_
     out["mass_drift"] = {"fp32": m32 / m0 - 1, "fp64": m64 / m0 - 1}
     out["energy_drift"] = {"fp32": en32 / en0 - 1, "fp64": en64 / en0 - 1}
 
+    # the cost of a look at the invariants (FP64 reductions, one synchronising call each)
+    def inv_ms(solver, x, energy):
+        solver.invariants(x, energy=energy)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            solver.invariants(x, energy=energy)
+        return (time.perf_counter() - t0) / 5 * 1e3
+    out["invariants_ms_per_call"] = {"fp32": inv_ms(s32, x32, True), "fp32_without_energy": inv_ms(s32, x32, False),
+                                     "fp64": inv_ms(s64, x64, True),
+                                     "what": "nlse_invariants on the grid (mass, energy, dt_max; host clock "
+                                             "around the synchronising call)"}
+
     # FP64 with the multi-storage 2SHOC form (Eqs. 2d2shocMs1-2)
     kms = min(K, 500)
     sm = nlse.Solver(V64, inst.h, k, inst.a, inst.s, prec="fp64", lap="2shoc_ms")
