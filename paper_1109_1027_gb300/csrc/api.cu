@@ -802,8 +802,9 @@ int nlse_create(const nlse_params* p, const void* V_dev, nlse_ctx** out) {
         c->nblocks = nlse::inv_num_blocks(L, nsm);
     }
     TRY(cudaMalloc((void**)&c->partials, sizeof(double) * nlse::kPartialWidth * c->nblocks), "allocating partials");
-    if (p->dim == 2 && p->bc == NLSE_BC_DIRICHLET) {
-        c->etiles = nlse::energy2d_tiles(p->n[0], p->n[1] * c->stack);
+    if ((p->dim == 2 || p->dim == 3) && p->bc == NLSE_BC_DIRICHLET) {
+        c->etiles = p->dim == 2 ? nlse::energy2d_tiles(p->n[0], p->n[1] * c->stack)
+                                : nlse::energy3d_tiles(p->n[0], p->n[1], p->n[2]);
         TRY(cudaMalloc((void**)&c->epartials, sizeof(double) * c->etiles), "allocating energy partials");
     }
     TRY(cudaMalloc((void**)&c->red_out, sizeof(double) * nlse::kPartialWidth), "allocating result");

@@ -15,7 +15,9 @@
 // tiled pass instead: a block converts its 36 x 12 window of the state to
 // FP64 once into shared memory, forms D on the 34 x 10 ring around its
 // 32 x 8 tile there, and the Laplacian and the energy density of its points
-// from those; the grid-stride pass then skips the energy.  Evaluating the
+// from those; the grid-stride pass then skips the energy.  3D Dirichlet
+// grids do the same on a 32 x 8 column walking 16 planes (rings of four
+// state planes and three D planes).  Evaluating the
 // Laplacian point by point from global memory converted every value to FP64
 // some thirty times, at an FP64 rate 1/64 of the FP32 rate.
 #include <cfloat>
@@ -409,6 +411,138 @@ __global__ void __launch_bounds__(kInvThreads) energy2d_batch_partial(const InvB
     if (threadIdx.x == 0) epartials[b] = s;
 }
 
+// ---- 3D: a 32 x 8 column walking kEZ planes ------------------------------
+
+constexpr int kEZ = 16;
+constexpr int kEP3 = kEPX * kEPY;                     // a state plane with a 2-point xy halo
+constexpr int kED3 = kEDX * kEDY;                     // a D plane with a 1-point xy halo
+
+template <typename R>
+struct EGrid3 {
+    const cplx<R>* psi;
+    const cplx<R>* lo;
+    const R* V;
+    int nx, ny, nz;
+    int lap;
+    double a, s, inv_a, inv_h2, inv_6h2;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kInvThreads) energy3d_partial(EGrid3<R> g, double* epartials) {
+    extern __shared__ __align__(16) unsigned char esm[];
+    double2* sP = reinterpret_cast<double2*>(esm);    // [4][kEPY][kEPX], plane z in slot z & 3
+    double2* sD = sP + 4 * kEP3;                       // [3][kEDY][kEDX], plane z in slot (z + 3) % 3
+    const int ntx = (g.nx + kETX - 1) / kETX, nty = (g.ny + kETY - 1) / kETY;
+    const int b = blockIdx.x;
+    const int x0 = (b % ntx) * kETX, y0 = ((b / ntx) % nty) * kETY, z0 = (b / (ntx * nty)) * kEZ;
+    const int z1 = min(z0 + kEZ, g.nz);
+    const int t = threadIdx.x;
+    const int64_t plane = (int64_t)g.nx * g.ny;
+    auto pslot = [](int z) { return (z + 4) & 3; };
+    auto dslot = [](int z) { return (z + 3) % 3; };
+    auto load = [&](int z) {
+        double2* dst = sP + pslot(z) * kEP3;
+        for (int i = t; i < kEP3; i += kInvThreads) {
+            const int ly = i / kEPX, lx = i - ly * kEPX;
+            const int x = x0 - 2 + lx, y = y0 - 2 + ly;
+            double2 v = make_double2(0.0, 0.0);
+            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+                const int64_t p = z * plane + (int64_t)y * g.nx + x;
+                const cplx<R> q = g.psi[p];
+                v = make_double2((double)q.x, (double)q.y);
+                if (g.lo) {
+                    const cplx<R> l = g.lo[p];
+                    v.x += (double)l.x;
+                    v.y += (double)l.y;
+                }
+            }
+            dst[i] = v;
+        }
+    };
+    auto dplane = [&](int z) {
+        double2* dst = sD + dslot(z) * kED3;
+        const double2* pm = sP + pslot(z - 1) * kEP3;
+        const double2* pc = sP + pslot(z) * kEP3;
+        const double2* pp = sP + pslot(z + 1) * kEP3;
+        for (int i = t; i < kED3; i += kInvThreads) {
+            const int ly = i / kEDX, lx = i - ly * kEDX;
+            const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+            const int k = (ly + 1) * kEPX + (lx + 1);
+            double2 d = make_double2(0.0, 0.0);
+            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
+                const double2 c = pc[k];
+                if (x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 || z == 0 || z == g.nz - 1) {
+                    const double Nb = g.s * (c.x * c.x + c.y * c.y) - (double)g.V[z * plane + (int64_t)y * g.nx + x];
+                    d = make_double2(-Nb * g.inv_a * c.x, -Nb * g.inv_a * c.y);
+                } else {
+                    double2 sum = make_double2(0.0, 0.0);
+                    sum.x += pc[k + 1].x + pc[k - 1].x;
+                    sum.y += pc[k + 1].y + pc[k - 1].y;
+                    sum.x += pc[k + kEPX].x + pc[k - kEPX].x;
+                    sum.y += pc[k + kEPX].y + pc[k - kEPX].y;
+                    sum.x += pp[k].x + pm[k].x;
+                    sum.y += pp[k].y + pm[k].y;
+                    d = make_double2((sum.x - 6.0 * c.x) * g.inv_h2, (sum.y - 6.0 * c.y) * g.inv_h2);
+                }
+            }
+            dst[i] = d;
+        }
+    };
+    for (int z = z0 - 2; z <= z0 + 1; ++z) load(z);
+    __syncthreads();
+    dplane(z0 - 1);
+    dplane(z0);
+    __syncthreads();
+    double e = 0.0;
+    const int lx = t % kETX, ly = t / kETX;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool inxy = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
+    for (int z = z0; z < z1; ++z) {
+        load(z + 2);                                   // into the slot of plane z - 2
+        __syncthreads();
+        dplane(z + 1);
+        __syncthreads();
+        if (inxy && z > 0 && z < g.nz - 1) {
+            const int k = (ly + 2) * kEPX + (lx + 2), kd = (ly + 1) * kEDX + (lx + 1);
+            const double2* pm = sP + pslot(z - 1) * kEP3;
+            const double2* pc = sP + pslot(z) * kEP3;
+            const double2* pp = sP + pslot(z + 1) * kEP3;
+            const double2* dm = sD + dslot(z - 1) * kED3;
+            const double2* dc = sD + dslot(z) * kED3;
+            const double2* dp = sD + dslot(z + 1) * kED3;
+            double2 lp = dc[kd];
+            if (g.lap != 1) {
+                // axial D in the order x -+ 1, y -+ 1, z -+ 1; edges in the order of the
+                // axis pairs (x, y), (x, z), (y, z), each at (-,-), (-,+), (+,-), (+,+)
+                const double2 dn[6] = {dc[kd - 1], dc[kd + 1], dc[kd - kEDX], dc[kd + kEDX], dm[kd], dp[kd]};
+                double2 dsum = make_double2(0.0, 0.0);
+                for (int q = 0; q < 6; ++q) {
+                    dsum.x += dn[q].x;
+                    dsum.y += dn[q].y;
+                }
+                const double2 en[12] = {pc[k - kEPX - 1], pc[k + kEPX - 1], pc[k - kEPX + 1], pc[k + kEPX + 1],
+                                        pm[k - 1], pp[k - 1], pm[k + 1], pp[k + 1],
+                                        pm[k - kEPX], pp[k - kEPX], pm[k + kEPX], pp[k + kEPX]};
+                double2 edges = make_double2(0.0, 0.0);
+                for (int q = 0; q < 12; ++q) {
+                    edges.x += en[q].x;
+                    edges.y += en[q].y;
+                }
+                const double2 c = pc[k];
+                lp = make_double2((10.0 / 12.0) * dc[kd].x - dsum.x / 12.0 + (edges.x - 12.0 * c.x) * g.inv_6h2,
+                                  (10.0 / 12.0) * dc[kd].y - dsum.y / 12.0 + (edges.y - 12.0 * c.y) * g.inv_6h2);
+            }
+            const double2 c = pc[k];
+            const double rho = c.x * c.x + c.y * c.y;
+            const double v = (double)g.V[z * plane + (int64_t)y * g.nx + x];
+            e += -g.a * (c.x * lp.x + c.y * lp.y) + v * rho - 0.5 * g.s * rho * rho;
+        }
+        __syncthreads();
+    }
+    e = block_sum(e);
+    if (t == 0) epartials[b] = e;
+}
+
 // The rows [0, n) in a fixed order into *out (the energy slot of a result row).
 __global__ void __launch_bounds__(kInvThreads) energy_final(const double* __restrict__ rows, int n, double* out) {
     double x = 0.0;
@@ -531,20 +665,32 @@ cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* 
     int64_t npts = (int64_t)v.n[0] * v.n[1] * v.n[2];
     v.rows1 = (int)(L.rows1 ? L.rows1 : v.n[1]);
     v.vpts = (int64_t)v.n[0] * v.rows1 * v.n[2];
-    const bool tiled = L.energy && L.dim == 2 && L.bc == 0 && L.epartials;
+    const bool tiled = L.energy && (L.dim == 2 || L.dim == 3) && L.bc == 0 && L.epartials;
     if (L.energy && !tiled) invariants_partial<R, true><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     else invariants_partial<R, false><<<nblocks, kInvThreads, 0, st>>>(v, npts, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     invariants_final<<<1, kInvThreads, 0, st>>>(partials, nblocks, out);
     if ((e = cudaGetLastError()) != cudaSuccess || !tiled) return e;
-    EGrid<R> g;
-    g.psi = v.psi; g.lo = v.lo; g.V = v.V;
-    g.nx = v.n[0]; g.ny = v.n[1]; g.rows1 = v.rows1;
-    g.lap = L.lap;
-    g.a = v.a; g.s = v.s; g.inv_a = v.inv_a; g.inv_h2 = v.inv_h2; g.inv_6h2 = v.inv_6h2;
-    const int ntiles = energy2d_tiles(v.n[0], v.n[1]);
-    energy2d_partial<R><<<ntiles, kInvThreads, 0, st>>>(g, L.epartials);
+    int ntiles;
+    if (L.dim == 3) {
+        EGrid3<R> g;
+        g.psi = v.psi; g.lo = v.lo; g.V = v.V;
+        g.nx = v.n[0]; g.ny = v.n[1]; g.nz = v.n[2];
+        g.lap = L.lap;
+        g.a = v.a; g.s = v.s; g.inv_a = v.inv_a; g.inv_h2 = v.inv_h2; g.inv_6h2 = v.inv_6h2;
+        ntiles = energy3d_tiles(v.n[0], v.n[1], v.n[2]);
+        const size_t smem = sizeof(double2) * (4 * kEP3 + 3 * kED3);
+        energy3d_partial<R><<<ntiles, kInvThreads, smem, st>>>(g, L.epartials);
+    } else {
+        EGrid<R> g;
+        g.psi = v.psi; g.lo = v.lo; g.V = v.V;
+        g.nx = v.n[0]; g.ny = v.n[1]; g.rows1 = v.rows1;
+        g.lap = L.lap;
+        g.a = v.a; g.s = v.s; g.inv_a = v.inv_a; g.inv_h2 = v.inv_h2; g.inv_6h2 = v.inv_6h2;
+        ntiles = energy2d_tiles(v.n[0], v.n[1]);
+        energy2d_partial<R><<<ntiles, kInvThreads, 0, st>>>(g, L.epartials);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     energy_final<<<1, kInvThreads, 0, st>>>(L.epartials, ntiles, out + 1);
     return cudaGetLastError();
@@ -554,6 +700,10 @@ cudaError_t launch_r(const InvLaunch& L, double* partials, int nblocks, double* 
 
 int energy2d_tiles(int64_t nx, int64_t ny) {
     return (int)(((nx + kETX - 1) / kETX) * ((ny + kETY - 1) / kETY));
+}
+
+int energy3d_tiles(int64_t nx, int64_t ny, int64_t nz) {
+    return (int)(((nx + kETX - 1) / kETX) * ((ny + kETY - 1) / kETY) * ((nz + kEZ - 1) / kEZ));
 }
 
 int inv_num_blocks(const InvLaunch& L, int num_sms) {

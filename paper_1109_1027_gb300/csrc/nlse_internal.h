@@ -190,12 +190,13 @@ struct InvLaunch {
     const void* V;
     bool energy = true;     // false: skip the energy sum (mass, extremes and count only)
     int64_t rows1 = 0;      // 2D stack: rows per instance (0: not stacked)
-    double* epartials = nullptr;   // 2D Dirichlet: energy2d_tiles rows for the tiled energy pass
+    double* epartials = nullptr;   // 2D / 3D Dirichlet: rows for the tiled energy pass
 };
 
 int inv_num_blocks(const InvLaunch& L, int num_sms);
-// Tiles (blocks) of the tiled energy pass over an nx x ny grid.
+// Tiles (blocks) of the tiled energy pass over an nx x ny grid / an nx x ny x nz grid.
 int energy2d_tiles(int64_t nx, int64_t ny);
+int energy3d_tiles(int64_t nx, int64_t ny, int64_t nz);
 
 // Invariants of every instance of a batch in one launch (plus one for the
 // per-instance reduction), with the partial rows a launch per instance gives.

@@ -261,6 +261,25 @@ def test_invariants_match_oracle(shape, prec):
     assert d == pytest.approx(d0, rel=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(67, 200), (17, 33), (35, 18, 40), (9, 33, 70)])
+@pytest.mark.parametrize("lap", ["2shoc", "cd"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiled_energy_matches_oracle(shape, lap, prec):
+    """The tiled energy pass of 2D and 3D Dirichlet grids (32 x 8 tiles; in 3D
+    walks of 16 planes), on shapes with ragged tiles in every direction, both
+    Laplacian forms, against the oracle's energy."""
+    psi, V = _problem(shape, 81)
+    h, a, s = 0.45, 0.7, -1.2
+    psi_r, V_r = rounded(psi, prec), rounded(V, prec)
+    ol = oracle.LAP_CD if lap == "cd" else 0
+    m0, e0, d0 = oracle.invariants(oracle.Problem(shape, h, a, s, lap=ol), psi_r, V_r)
+    solver = nlse.Solver(to_dev(V, prec), h, 1e-4, a, s, prec=prec, lap=lap)
+    m, e, d = solver.invariants(to_dev(psi, prec))
+    assert e == pytest.approx(e0, rel=1e-11, abs=1e-12 * abs(m0))
+    assert m == pytest.approx(m0, rel=1e-12)
+    assert d == pytest.approx(d0, rel=1e-12)
+
+
 def test_invariants_msd_1d_match_oracle():
     n = 1030
     psi, V = _problem((n,), 78)
