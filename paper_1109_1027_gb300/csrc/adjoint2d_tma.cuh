@@ -200,8 +200,7 @@ adj2d_walk_kernel(const __grid_constant__ CUtensorMap m_w, const __grid_constant
     // Prologue: input rows y-2 .. y+1 (y = ybase) give E(., y-1) and E(., y).
     wait_in(0); wait_in(1); wait_in(2); wait_in(3);
     bool alive = __syncthreads_and(ok);
-    int yl = rl_base;                            // instance rows of y, y + dir
-    int yla = rstep(rl_base, dir);
+    int yla = rstep(rl_base, dir);               // instance row of y + dir
     bool fm, f0, f1;                             // rows y - dir, y, y + dir interior
     T2 um, u0, u1, em, e0;
     C lm, rm, l0, r0;
@@ -295,9 +294,8 @@ adj2d_walk_kernel(const __grid_constant__ CUtensorMap m_w, const __grid_constant
         um = u0; u0 = u1; u1 = u2;
         em = e0; e0 = e1;
         fm = f0; f0 = f1; f1 = f2;
-        yl = yla; yla = ylb;
+        yla = ylb;
     }
-    (void)yl;
 
     if (!alive) {
         // A transfer never arrived: report, let this CTA's copies in flight land, leave.
