@@ -14,10 +14,10 @@
 // (hi + compensated lo) the FP64 evaluation of every point would make this an
 // FP64-rate-bound pass on a GPU whose FP64 rate is 1/64 of its FP32 rate, so
 // each point is first evaluated in FP32 together with a rigorous bound E_i on
-// |u32_i - u64_i|.  A warp takes 256 points at a time (8 per lane, each load
+// |u32_i - u64_i|.  A warp takes 128 points at a time (4 per lane, each load
 // instruction covering 32 consecutive points), bounds their FP32 values,
 // reduces max(u32 - E) and min(u32 + E) over the warp with shuffles, and keeps
-// only the points that can still be an extreme of the 256 (u32_i + E_i >=
+// only the points that can still be an extreme of the 128 (u32_i + E_i >=
 // max_j(u32_j - E_j), and the mirror rule for the minimum): on smooth fields a
 // few points per tile.  The warp collects those candidates in a shared buffer
 // and forms their FP64 values 32 at a time, every lane busy: an FP64
@@ -92,7 +92,8 @@ __device__ __forceinline__ void u_fp32(float2 h, float2 l, float v, float s32, f
     E = __fmaf_rn(2.0f * abs_s, t, __fmaf_rn(ldexpf(1.0f, -18), fabsf(u) + abs_s * rho, (abs_s + 1.0f) * 7.52316385e-37f));
 }
 
-constexpr int kWarpPts = 8;                 // points per lane in one warp tile (256 points)
+constexpr int kWarpPts = 4;                 // points per lane in one warp tile (128 points; 64
+                                            // registers, four blocks per SM)
 constexpr int kCand = 64;                   // a warp's candidate buffer: one batch of 32 and an overflow
 
 // The candidates of one warp waiting for their FP64 value: the point's
