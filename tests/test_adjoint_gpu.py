@@ -262,3 +262,45 @@ def test_adjoint_walk_equals_tile_kernel(prec, shape, lap, stack):
         assert torch.equal(out[rows][1], ref[1]), rows
         assert torch.equal(out[rows][2], ref[2]), rows
 
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_workload_full_size_directional_derivatives(prec):
+    """The gradient workload at its full size (16 states of 512 x 512 sharing V,
+    one stacked context: the launch configuration the benchmark times), 60
+    steps with checkpoints every 20: the adjoint's directional derivatives
+    along a random direction of the 16 initial states and of V equal central
+    differences of the GPU forward loss in FP64 (eps = 1e-4, rel 1e-6); the
+    FP32 gradient equals the FP64 one to 1e-4 of its largest entry."""
+    V, psis, targets, h, a, s = wl.gradient_problem_2d(n=512, batch=16)
+    rdt, cdt = (torch.float32, torch.complex64) if prec == "fp32" else (torch.float64, torch.complex128)
+    probe = nlse.Solver(torch.from_numpy(V).to(DEV), h, 1.0, a, s, prec="fp64", check_stability=False)
+    k = 0.5 * min(probe.invariants(torch.from_numpy(p).to(DEV).contiguous())[2] for p in psis)
+    probe.close()
+    n, ck = 60, 20
+    stack = lambda zs, t: torch.stack([torch.from_numpy(z).to(t) for z in zs]).to(DEV).contiguous()
+    x0, tg = stack(psis, torch.complex128), stack(targets, torch.complex128)
+    V64 = torch.from_numpy(V).to(DEV).contiguous()
+    sv64 = nlse.Solver(V64, h, k, a, s, prec="fp64", check_stability=False, stack=16)
+    L, g, gV = sv64.adjoint(x0, tg, n, ck)
+    if prec == "fp64":
+        def loss_of(p, v):
+            sv = nlse.Solver(v, h, k, a, s, prec="fp64", check_stability=False, stack=16)
+            x = p.clone()
+            sv.run(x, n)
+            sv.close()
+            return float(((x - tg).abs() ** 2).sum())
+
+        eps = 1e-4
+        d = stack([wl.random_field((512, 512), seed=500 + i) for i in range(16)], torch.complex128)
+        fd = (loss_of(x0 + eps * d, V64) - loss_of(x0 - eps * d, V64)) / (2 * eps)
+        assert float(torch.real(torch.sum(torch.conj(g) * d))) == pytest.approx(fd, rel=1e-6)
+        dv = torch.from_numpy(wl.random_potential((512, 512), seed=600) - 0.5).to(DEV)
+        fd = (loss_of(x0, V64 + eps * dv) - loss_of(x0, V64 - eps * dv)) / (2 * eps)
+        assert float((gV * dv).sum()) == pytest.approx(fd, rel=1e-6)
+    else:
+        sv32 = nlse.Solver(V64.float().contiguous(), h, k, a, s, prec="fp32", check_stability=False, stack=16)
+        L32, g32, gV32 = sv32.adjoint(x0.to(cdt), tg.to(cdt), n, ck)
+        assert L32 == pytest.approx(L, rel=1e-5)
+        assert float((g32.to(torch.complex128) - g).abs().max()) <= 1e-4 * float(g.abs().max())
+        assert float((gV32 - gV).abs().max()) <= 1e-4 * float(gV.abs().max())
